@@ -1,0 +1,140 @@
+"""Synthetic workloads and seeded input generators shared by the CUDA path and the oracle.
+
+This module holds only input data: parameter dictionaries in the user units of the
+paper's input tables (bohr, eV, atomic mass units) and seeded random-number helpers.
+It contains none of the method's arithmetic: every conversion, grid, operator and
+sum is computed separately by each side.
+
+The workloads stand in for the H + DH(v=0, j=0) example of Section 6 (its
+BKMP2-like surface, supplementary inputs and ABC reference data are not
+available). The surface is a Sato LEPS for H3 with the constants below; the grids,
+total angular momenta, helicity ranges, iteration counts and energy windows follow
+the five benchmark configurations of this project.
+
+Naming: ``masses_u`` lists (m_A, m_B, m_C) for A + BC with A = H (atom), B = D,
+C = H (the DH diatom), matching the A + BC channel of Section 2.1.
+"""
+from __future__ import annotations
+
+import copy
+
+import numpy as np
+
+# Sato LEPS constants for H3 (every pair shares one Morse curve).
+LEPS_H3 = dict(D_eV=4.7466, beta=1.9426, re=1.4014, delta=0.18)
+
+# Two-state diabatic extension used by the coupled-state workload:
+#   V22 = V11 + bump_eV * exp(-(r - bump_r0)^2 / bump_w2)
+#   V12 = coup_eV * exp(-((R - coup_R0)^2 + (r - coup_r0)^2) / coup_w2)
+TWO_STATE = dict(bump_eV=0.6, bump_r0=1.4, bump_w2=1.0,
+                 coup_eV=0.05, coup_R0=3.0, coup_r0=1.8, coup_w2=1.0)
+
+MASSES_H_DH = (1.00783, 2.01410, 1.00783)   # (A=H, B=D, C=H) in u
+
+CAPS = dict(vcut_eV=2.5, tcut_eV=2.5, erot_eV=5.0)
+
+
+def _absorber(Rmax, RI, rmax, rI, strength=0.04, n=2):
+    """Damping strengths A_x chosen so that phi = strength at the far wall."""
+    return dict(RI=RI, AR=strength / (Rmax - RI) ** n, nR=n,
+                rI=rI, Ar=strength / (rmax - rI) ** n, nr=n)
+
+
+def _cfg(name, grid, J, omega_max, nelec, packet, absorber, analysis, steps,
+         precision, two_state=False):
+    return dict(
+        name=name, grid=dict(grid), J=list(J), omega_max=int(omega_max),
+        nelec=int(nelec), masses_u=MASSES_H_DH,
+        pes=dict(kind="leps", **LEPS_H3, two_state=(dict(TWO_STATE) if two_state else None)),
+        caps=dict(CAPS), packet=dict(packet), absorber=dict(absorber),
+        analysis=dict(analysis), steps=int(steps), precision=precision)
+
+
+_PACKET = dict(R0=10.0, Gamma=0.25, Ecol_eV=0.6, v0=0, j0=0, omega0=0, elec0=0)
+
+# Config 1: H + DH(0,0), J = 0, FP64, 64 x 48 x 24 grid, 1500 iterations.
+C1 = _cfg(
+    "h_dh_j0_64x48x24",
+    grid=dict(NR=64, Rmin=0.5, Rmax=14.0, nr=48, rmin=0.5, rmax=10.0, ngamma=24),
+    J=[0], omega_max=0, nelec=1, packet=_PACKET,
+    absorber=_absorber(14.0, 11.0, 10.0, 7.5),
+    analysis=dict(rstar=6.0, E_lo_eV=0.3, E_hi_eV=1.5, nE=200, Rinf=10.5,
+                  vmax=3, jmax=15, kmin=0),
+    steps=1500, precision="fp64")
+
+# Config 2: J = 10, Omega = 0..10 (11 Coriolis-coupled blocks), 256 x 192 x 96.
+C2 = _cfg(
+    "h_dh_j10_256x192x96",
+    grid=dict(NR=256, Rmin=0.5, Rmax=16.0, nr=192, rmin=0.5, rmax=12.0, ngamma=96),
+    J=[10], omega_max=10, nelec=1, packet=_PACKET,
+    absorber=_absorber(16.0, 12.9, 12.0, 9.7),
+    analysis=dict(rstar=6.0, E_lo_eV=0.3, E_hi_eV=1.5, nE=500, Rinf=11.5,
+                  vmax=3, jmax=15, kmin=0, Rprod_inf=11.0),
+    steps=12000, precision="mixed")
+
+# Config 3: two coupled diabatic states, J = 0, 5, ..., 30 with Omega_max = 15.
+C3 = _cfg(
+    "two_state_j0to30_192x128x64",
+    grid=dict(NR=192, Rmin=0.5, Rmax=16.0, nr=128, rmin=0.5, rmax=12.0, ngamma=64),
+    J=list(range(0, 31, 5)), omega_max=15, nelec=2, packet=_PACKET,
+    absorber=_absorber(16.0, 12.9, 12.0, 9.7),
+    analysis=dict(rstar=6.0, E_lo_eV=0.2, E_hi_eV=1.6, nE=1000, Rinf=11.5,
+                  vmax=3, jmax=15, kmin=0),
+    steps=8000, precision="mixed", two_state=True)
+
+# Config 4: J = 40, Omega = 0..20 (21 blocks), 512 x 384 x 180.
+C4 = _cfg(
+    "h_dh_j40_512x384x180",
+    grid=dict(NR=512, Rmin=0.5, Rmax=18.0, nr=384, rmin=0.5, rmax=14.0, ngamma=180),
+    J=[40], omega_max=20, nelec=1, packet=_PACKET,
+    absorber=_absorber(18.0, 14.5, 14.0, 11.3),
+    analysis=dict(rstar=6.0, E_lo_eV=0.2, E_hi_eV=1.6, nE=1000, Rinf=11.5,
+                  vmax=3, jmax=15, kmin=0),
+    steps=30000, precision="mixed")
+
+# Config 5 (J-interpolation surrogate): the config-3 grid, single surface, trained on
+# J = 0, 4, ..., 48 and judged on J = 2, 6, ..., 46.
+C5 = dict(base=C3, J_train=list(range(0, 49, 4)), J_test=list(range(2, 47, 4)),
+          vmax=3, jmax=15, nE=1000, E_lo_eV=0.2, E_hi_eV=1.6,
+          mlp=dict(n_in=4, width=256, depth=3, n_out=1), fallback_dP=0.01)
+
+CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c4": C4}
+
+
+def shrunk(base: dict, name: str, **over) -> dict:
+    """A copy of ``base`` with grid sizes / J lists / steps replaced (parity sizes)."""
+    cfg = copy.deepcopy(base)
+    cfg["name"] = name
+    for k, v in over.items():
+        if k in cfg["grid"]:
+            cfg["grid"][k] = v
+        elif k in cfg["analysis"]:
+            cfg["analysis"][k] = v
+        else:
+            cfg[k] = v
+    return cfg
+
+
+# Parity-sized copies: the oracle finishes them in seconds, and their sizes span
+# several tiles with ragged tails (radix 2/3/5 line lengths, odd gamma counts).
+C2_SMALL = shrunk(C2, "h_dh_j10_40x36x20", NR=40, nr=36, ngamma=20, steps=240, nE=64)
+C3_SMALL = shrunk(C3, "two_state_j0_5_10_24x20x12", NR=24, nr=20, ngamma=12,
+                  J=[0, 5, 10], omega_max=5, steps=160, nE=48)
+C4_SMALL = shrunk(C4, "h_dh_j40_60x48x30", NR=60, nr=48, ngamma=30, omega_max=4,
+                  steps=80, nE=40)
+SMALL = {"c1": C1, "c2s": C2_SMALL, "c3s": C3_SMALL, "c4s": C4_SMALL}
+
+
+def rng(seed: int) -> np.random.Generator:
+    """The single seeded generator used for every random test input."""
+    return np.random.default_rng(int(seed))
+
+
+def random_state(shape, seed: int = 2412) -> np.ndarray:
+    """Seeded standard-normal FP64 array (Hermiticity and parity probes)."""
+    return rng(seed).standard_normal(shape)
+
+
+def random_unit_state(shape, seed: int = 2412) -> np.ndarray:
+    v = random_state(shape, seed)
+    return v / np.sqrt(np.sum(v * v))
