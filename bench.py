@@ -1,0 +1,341 @@
+"""Benchmark: damped real Chebyshev steps/s on the J = 10 H + DH workload.
+
+Workload: 256 (R) x 192 (r) x 96 (gamma) grid, J = 10 with helicities 0..10
+(11 Coriolis-coupled blocks, 51.9 M grid values), synthetic Sato LEPS surface,
+500 energies in the flux sums, reactant-channel projections (v <= 3, j <= 15).
+One step = one full Chebyshev iteration of the hot path: radial kinetic
+transforms, gamma transforms with FBR/Coriolis, potential, damped recursion,
+flux cut, channel overlaps, norms, plus the amortised energy-sum GEMM.
+
+value: steps/s of the mixed form (FP32 state, FP64 energy sums), inputs resident
+in HBM. The FP64 form is measured too ("fp64"). e2e: the same step through the
+public C ABI with host buffers (state uploaded, probabilities read back, each
+step). --impl reference times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "h_dh_j10_256x192x96_11omega"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=240)
+    ap.add_argument("--warmup", type=int, default=64)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_oracle_rate(nsteps):
+    """Times the FP64 oracle (as it stands) for nsteps Chebyshev iterations of the
+    workload in a child process on all host cores; returns (steps/s, cores, seconds)."""
+    cores = os.cpu_count() or 1
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "import workloads as W\n"
+        "from oracle import propagate as P\n"
+        "from oracle.hamiltonian import GridHamiltonian\n"
+        "cfg = W.C2\n"
+        "H = GridHamiltonian(cfg)\n"
+        "t = time.perf_counter(); P.propagate(cfg, nsteps=%d, H=H)\n"
+        "dt = time.perf_counter() - t\n"
+        "t2 = time.perf_counter(); P.propagate(cfg, nsteps=0, H=H); d0 = time.perf_counter() - t2\n"
+        "print(json.dumps({'dt': dt, 'setup': d0}))\n" % (ROOT, nsteps))
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    per = max(d["dt"] - d["setup"], 1e-9)   # per-propagation setup (channels, packet) excluded
+    return nsteps / per, cores, per
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import workloads as W
+    cfg = W.C2
+    npts = cfg["grid"]["NR"] * cfg["grid"]["nr"] * cfg["grid"]["ngamma"] * 11
+    # each step: one oracle Chebyshev iteration of the workload (bounded sample)
+    rate_w, cores, _ = cpu_oracle_rate(max(args.warmup, 1)) if args.warmup > 0 else (0, 0, 0)
+    rate, cores, secs = cpu_oracle_rate(args.steps)
+    line = {
+        "impl": "reference", "metric": "Chebyshev steps/s", "value": rate, "unit": "steps/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / rate,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Sato LEPS H+DH)",
+        "config": {"workload": WORKLOAD, "grid_pts_omega": npts, "energies": 500},
+        "grid_pts_omega_per_s": rate * npts,
+        "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle iterations of the full workload"},
+        "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------- our arm
+def algorithmic_bytes(kernel, es, npts, nblk, ng, nr, NR, nelec, nchan, nE, kb, ncut):
+    """Bytes each launch must move at minimum (per-kernel roofline)."""
+    vec = npts * nblk * es
+    if kernel == "kinetic_rows":
+        return 2 * vec                          # read q_k, write t
+    if kernel == "kinetic_cols":
+        return 3 * vec                          # read q_k, read+write t
+    if kernel == "gamma_forward":
+        return 2 * vec                          # read q_k, write c
+    if kernel == "gamma_backward_update":
+        # read c (x1, neighbours from cache), t, q_k, q_(k-1), V (once per J); write q_(k+1)
+        return 5 * vec + nelec * nelec * npts * es
+    return None
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2412_10167_gb300 import mw3
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    cfg = W.C2
+    g = cfg["grid"]
+    nblk = 11
+    npts = g["NR"] * g["nr"] * g["ngamma"]
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- mixed form: the headline
+    pr = mw3.Propagator(cfg, device=local, precision="mixed")
+    pr.propagate(args.warmup)
+    kb = pr.get_tuning("kb")
+    pr.kernel_times(enable=True)
+    clk = ClockSampler(local)
+    barrier()
+    clk.start()
+    t0 = time.perf_counter()
+    pr.propagate(args.steps)
+    barrier()
+    t1 = time.perf_counter()
+    clocks = clk.stop()
+    ktimes = pr.kernel_times()
+    pr.kernel_times(enable=False)
+    elapsed = t1 - t0
+    if dist is not None:
+        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    value = world * args.steps / elapsed
+    nchan = 0
+    E, Pmix, _ = pr.probabilities()
+
+    # ---- e2e through the public API with host buffers
+    q_host, qp_host = pr.state()
+    q_host = np.ascontiguousarray(q_host)
+    qp_host = np.ascontiguousarray(qp_host)
+    e2e_steps = max(4, min(16, args.steps // 8))
+    barrier()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pr.set_state(q_host, qp_host)
+        pr.propagate(1)
+        _, Pe, _ = pr.probabilities()
+    barrier()
+    te = time.perf_counter() - te0
+    pr.close()
+    del pr
+
+    # ---- FP64 form on the same workload (shorter timed region)
+    pf = mw3.Propagator(cfg, device=local, precision="fp64")
+    pf.propagate(max(3, min(args.warmup, 8)))
+    barrier()
+    tf0 = time.perf_counter()
+    pf.propagate(args.fp64_steps)
+    barrier()
+    tf = time.perf_counter() - tf0
+    fp64_rate = world * args.fp64_steps / tf
+    pf.close()
+    del pf
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    per = {k: (ms / n if n else 0.0, n) for k, (ms, n) in ktimes.items()}
+    dom = max((k for k in per if per[k][1] > 0), key=lambda k: per[k][0] * per[k][1])
+    avg_ms = per[dom][0]
+    es = 4
+    fp32_peak = None
+    try:
+        fp32_peak = mw3.mw3_measure_peak(local, 1)
+    except Exception:
+        pass
+    if dom.startswith("gamma"):
+        flops = 2.0 * g["ngamma"] * npts * nblk
+        roof = {"bound": "alu", "achieved": flops / (avg_ms * 1e-3) / 1e12,
+                "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": (flops / (avg_ms * 1e-3) / 1e12 / fp32_peak) if fp32_peak else None,
+                "traffic": None, "kernel": dom,
+                "peak_source": "measured FP32 FMA-chain probe (mw3_measure_peak)"}
+    else:
+        by = algorithmic_bytes(dom, es, npts, nblk, g["ngamma"], g["nr"], g["NR"], 1, nchan,
+                               500, kb, 0)
+        ach = by / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    kernels = {k: {"avg_ms": round(per[k][0], 5), "launches": per[k][1],
+                   "share": round(per[k][0] * per[k][1] / max(1e-9, sum(a * b for a, b in per.values())), 4)}
+               for k in per if per[k][1]}
+    launches = sum(v[1] for v in per.values())
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            rate, cores, secs = cpu_oracle_rate(args.cpu_sample_steps)
+            cpu = {"value": rate, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{args.cpu_sample_steps} FP64 oracle iterations of the full workload "
+                             f"({secs:.1f} s)"}
+        except Exception as e:  # report, do not hide
+            cpu = {"value": None, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {str(e)[:200]}"}
+
+    vec_bytes = nblk * npts * 8
+    line = {
+        "metric": "Chebyshev steps/s", "value": value, "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64sums",
+        "data": "synthetic (Sato LEPS H+DH surface, deterministic packet)",
+        "config": {"workload": WORKLOAD, "grid": [g["NR"], g["nr"], g["ngamma"]], "J": 10,
+                   "blocks": nblk, "energies": 500, "kb": kb,
+                   "l2": "state vectors 208 MB each (> 129 MB L2), no flush needed",
+                   "parallelism": f"replicas x{world}"},
+        "grid_pts_omega_per_s": value * npts * nblk,
+        "fp64": {"value": fp64_rate, "unit": "steps/s", "steps": args.fp64_steps,
+                 "grid_pts_omega_per_s": fp64_rate * npts * nblk},
+        "mixed_over_fp64": value / fp64_rate,
+        "roofline": roof,
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": {"value": e2e_steps / te, "unit": "steps/s", "h2d_bytes_per_step": 2 * vec_bytes,
+                "d2h_bytes_per_step": 500 * 8 * 2},
+        "cpu_baseline": cpu,
+        "fp32_fma_peak_tflops": fp32_peak,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

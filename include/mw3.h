@@ -1,0 +1,245 @@
+/*
+ * mw3.h - C ABI of libmw3, a GB300 (sm_103a) implementation of the damped real
+ * Chebyshev wave-packet propagation of MADWAVE3 (Roncero & del Mazo-Sevillano,
+ * arXiv 2412.10167) for A + BC collisions in reactant Jacobi coordinates.
+ *
+ * Conventions
+ *   - Atomic units everywhere: bohr, hartree, electron masses (1 u = 1822.888486 m_e).
+ *   - Every call returns MW3_OK (0) or a negative MW3_ERR_* code; no C++ exception
+ *     crosses this boundary. mw3_last_error() gives a message for the last failure.
+ *   - Host arrays passed in are caller-owned and copied before the call returns;
+ *     host arrays passed out are caller-owned and must hold the stated number of
+ *     elements. Device memory is owned by the context (allocated through the hook of
+ *     mw3_set_allocator, else cudaMalloc) and released by mw3_destroy.
+ *   - Call order: mw3_create -> [mw3_set_stream, mw3_set_allocator] -> mw3_grid ->
+ *     mw3_load_potential | mw3_load_potential_grid -> mw3_init_packet ->
+ *     mw3_set_absorber -> mw3_set_analysis -> mw3_propagate (any number of times;
+ *     each call continues from the current iteration) -> mw3_flux_probabilities.
+ *     A call out of order returns MW3_ERR_STATE.
+ *   - Not thread-safe per context; distinct contexts are independent.
+ *
+ * State layout (device): q[block][gamma][r][R], R fastest. Blocks are ordered by
+ * total angular momentum J (in the order given), then helicity Omega = 0..
+ * min(J, omega_max) (parity p = (-1)^J), then electronic state Lambda.
+ */
+#ifndef MW3_H
+#define MW3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+enum {
+  MW3_OK = 0,
+  MW3_ERR_BAD_ARG = -1,   /* invalid argument (sizes, NULL, out of range)      */
+  MW3_ERR_OOM = -2,       /* device or host allocation failed                  */
+  MW3_ERR_CUDA = -3,      /* a CUDA runtime call or kernel launch failed        */
+  MW3_ERR_DIVERGED = -4,  /* ||q_k||^2 exceeded 1.5 ||q_0||^2 (bad E_min/E_max) */
+  MW3_ERR_SPECTRUM = -5,  /* grid energy range invalid (E_s outside (-1, 1))    */
+  MW3_ERR_TIMEOUT = -6,   /* a bounded device wait gave up                     */
+  MW3_ERR_STATE = -7,     /* call made out of order                            */
+  MW3_ERR_IO = -8,        /* checkpoint file error                             */
+  MW3_ERR_NAN = -9        /* NaN or Inf in user input                          */
+};
+
+/* Arithmetic of the propagation. MW3_FP64: FP64 state, transforms and sums.
+ * MW3_MIXED: FP32 state, FP32 radial transforms, gamma transform on tensor cores
+ * (FP32 accumulation), FP64 spectral scaling constants, FP64 energy sums. */
+enum { MW3_FP64 = 0, MW3_MIXED = 1 };
+
+typedef struct mw3_ctx mw3_ctx;
+
+/* Grid, basis and block structure (Section 2.1 and the inputgridbase namelist of
+ * Table 1). Radial grids: NR (nr) midpoint nodes R_m = Rmin + (m + 1/2) dR between
+ * walls at Rmin and Rmax (sine DVR, regular at both walls); NR and nr must be even,
+ * of the form 2^a 3^b 5^c and at most 1024. ngamma Gauss-Legendre points in
+ * cos(gamma), 1 <= ngamma <= 256. J[0..nJ-1] is the batch of total angular
+ * momenta, each with helicities 0..min(J, omega_max). nelec diabatic states
+ * (1 or 2). masses = (m_A, m_B, m_C) for A + BC, r = B->C, R = c.o.m.(BC)->A. */
+typedef struct {
+  int NR;
+  double Rmin, Rmax;
+  int nr;
+  double rmin, rmax;
+  int ngamma;
+  double masses[3];
+  int nJ;
+  const int* J;
+  int omega_max;
+  int nelec;
+} mw3_grid_desc;
+
+/* Initial collision packet (Section 2.3.1, Eqs. initial-collision-wvp and
+ * initial-gaussian): N g(R) chi_{v0 j0}(r) y_{j0 Omega0}(gamma) in the block
+ * (Omega0, elec0) of every J, g(R) = exp(-(R-R0)^2/(2 Gamma^2)) cos(k0 R),
+ * k0 = sqrt(2 mu Ecol). chi from the diatomic Hamiltonian at R = 100 bohr. */
+typedef struct {
+  double R0, Gamma, Ecol;
+  int v0, j0, omega0, elec0;
+} mw3_packet_desc;
+
+/* Energy analysis (Section 2.4 and the inputflux/inputtime namelists):
+ * nE collision energies E_i = linspace(E_lo, E_hi, nE) (inclusive), flux through
+ * r = rstar (Eq. total-flux), reactant channels (Lambda, v <= vmax, j <= jmax,
+ * Omega) projected at the R node nearest Rinf, counted from iteration kmin
+ * (kminelastic). Set vmax < 0 for no channel analysis. */
+typedef struct {
+  double rstar;
+  double E_lo, E_hi;
+  int nE;
+  double Rinf;
+  int vmax, jmax;
+  long kmin;
+} mw3_analysis_desc;
+
+/* Potential callback (the potelebond routine of Section 4, in Jacobi form):
+ * given r, R (bohr) and cos(gamma) write the nelec x nelec diabatic matrix
+ * (hartree, row-major, symmetric) into potmat; return 0 on success. */
+typedef int (*mw3_pot_fn)(double r, double R, double cosg, double* potmat, void* user);
+
+/* Device allocator hook: alloc returns a device pointer (256-byte aligned) or NULL. */
+typedef void* (*mw3_alloc_fn)(size_t bytes, void* user);
+typedef void (*mw3_free_fn)(void* ptr, void* user);
+
+/* Sato LEPS surface parameters (hartree, bohr) for the built-in mw3_pes_leps. */
+typedef struct {
+  double D, beta, re, delta;   /* shared pair curve and Sato parameter           */
+  double masses[3];            /* m_A, m_B, m_C (m_e) to map Jacobi -> bonds     */
+  int two_state;               /* 0: one surface; 1: diabatic pair (below)       */
+  double bump, bump_r0, bump_w2;           /* V22 = V11 + bump exp(-(r-r0)^2/w2) */
+  double coup, coup_R0, coup_r0, coup_w2;  /* V12 = coup exp(-((R-R0)^2+(r-r0)^2)/w2) */
+} mw3_leps_params;
+
+/* ------------------------------------------------------------------ lifecycle */
+
+/* Create a context on CUDA device `device` with precision MW3_FP64 or MW3_MIXED.
+ * *out receives the handle (NULL on failure). */
+int mw3_create(mw3_ctx** out, int device, int precision);
+
+/* Release every device and host resource of the context. NULL is ignored. */
+void mw3_destroy(mw3_ctx* ctx);
+
+/* Message for the last failing call on ctx (or of mw3_create when ctx is NULL). */
+const char* mw3_last_error(const mw3_ctx* ctx);
+
+/* Text for a status code. */
+const char* mw3_status_string(int status);
+
+/* Launch every kernel on `stream` (a cudaStream_t; NULL = legacy default stream). */
+int mw3_set_stream(mw3_ctx* ctx, void* stream);
+
+/* Route device allocations through alloc/free (must precede mw3_grid). */
+int mw3_set_allocator(mw3_ctx* ctx, mw3_alloc_fn alloc, mw3_free_fn free_fn, void* user);
+
+/* -------------------------------------------------------------------- set-up */
+
+/* Build grids, bases and the block table (Section 2.1). Copies desc->J. */
+int mw3_grid(mw3_ctx* ctx, const mw3_grid_desc* desc);
+
+/* Evaluate the potential on the grid through fn (Section 4, potelebond), cap the
+ * diagonal at vcut (VcutmaxeV), and set the radial kinetic cap tcut_rad
+ * (radcutmaxeV) and the rotational cap ecut_rot (rotcutmaxeV); then compute the
+ * spectral bounds E_min, E_max of each J (Section 2.2, H_s). */
+int mw3_load_potential(mw3_ctx* ctx, mw3_pot_fn fn, void* user, double vcut, double tcut_rad,
+                       double ecut_rot);
+
+/* Same with a caller-owned host grid V[nelec][nelec][ngamma][nr][NR] (hartree,
+ * uncapped; symmetric in the state indices), copied in. */
+int mw3_load_potential_grid(mw3_ctx* ctx, const double* V, double vcut, double tcut_rad,
+                            double ecut_rot);
+
+/* Built-in Sato LEPS (+ optional two-state extension); user = mw3_leps_params*.
+ * Energies are shifted by +D so that A + BC(re) is zero; bond lengths are
+ * clamped to >= 0.25 bohr as in the example potential routine of Section 6.1. */
+int mw3_pes_leps(double r, double R, double cosg, double* potmat, void* user);
+
+/* Solve the diatomic states and write q_0 (Section 2.3.1); resets the iteration
+ * counter and every energy sum. */
+int mw3_init_packet(mw3_ctx* ctx, const mw3_packet_desc* desc);
+
+/* Damping exp(-phi), phi = A_R (R-RI)^nR for R > RI plus A_r (r-rI)^nr for r > rI
+ * (Eq. imaginary-potential, inputabsorcion namelist). */
+int mw3_set_absorber(mw3_ctx* ctx, double RI, double AR, int nR, double rI, double Ar, int nr);
+
+/* Energy grid, flux surface and reactant channels (Section 2.4); allocates the
+ * energy-sum accumulators. Must follow mw3_init_packet (needs E_{v0 j0}). */
+int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* desc);
+
+/* --------------------------------------------------------------- propagation */
+
+/* Advance nsteps Chebyshev iterations of Eq. (wvp-k):
+ *   q_1 = D H_s q_0,  q_{k+1} = D (2 H_s q_k - D q_{k-1}),
+ * accumulating c_k(E) = (2 - delta_k0) exp(-i k theta_E) times the flux cut and
+ * the channel overlaps of q_k into the energy sums (Eqs. wvf-chebyshev and
+ * chebyshev-expansion-constants). Returns MW3_ERR_DIVERGED if a norm exceeds
+ * 1.5 ||q_0||^2. Synchronous: returns after the work is complete. */
+int mw3_propagate(mw3_ctx* ctx, long nsteps);
+
+/* Number of iterations done so far (k of the current q_k). */
+long mw3_iteration(const mw3_ctx* ctx);
+
+/* ------------------------------------------------------------------- results */
+
+/* Probabilities from the sums so far (Eqs. total-flux, S-matrix-from-chebyshev):
+ *   E[nE]            collision energies (hartree);
+ *   Ptot[nJ * nE]    total reaction probability through r* per J;
+ *   Pinel[nJ * nelec * (vmax+1) * (jmax+1) * nE] or NULL: reactant-channel
+ *                    probabilities summed over Omega, zero for closed channels. */
+int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel);
+
+/* Copy q_k (and q_{k-1} if qprev != NULL) to host FP64 arrays of
+ * nblocks * ngamma * nr * NR elements. */
+int mw3_get_state(mw3_ctx* ctx, double* q, double* qprev);
+
+/* Overwrite q_k and q_{k-1} (host FP64, same size) without touching the sums. */
+int mw3_set_state(mw3_ctx* ctx, const double* q, const double* qprev);
+
+/* out[i] = (H_s q)[i] for a host FP64 vector q (one application of the scaled
+ * Hamiltonian through the same kernels as a propagation step). */
+int mw3_apply_hs(mw3_ctx* ctx, const double* q, double* out);
+
+/* ||q_k||^2 per J after each iteration: out[nJ * n] for the last n iterations
+ * (n <= mw3_iteration); returns the count written. */
+long mw3_norm_trace(mw3_ctx* ctx, double* out, long n);
+
+/* Sizes and scaling constants: nblocks, points per block, E0 and dE per J. */
+int mw3_sizes(const mw3_ctx* ctx, long* nblocks, long* points_per_block);
+int mw3_spectral_range(const mw3_ctx* ctx, double* E0, double* dE);
+
+/* Energy of the initial diatomic state E_{v0 j0} (hartree). */
+int mw3_reference_energy(const mw3_ctx* ctx, double* Ev0j0);
+
+/* Write / read a restart file: q_k, q_{k-1}, k, the energy sums and a hash of the
+ * configuration (the ncontfile option of Table 1). */
+int mw3_checkpoint_save(mw3_ctx* ctx, const char* path);
+int mw3_checkpoint_load(mw3_ctx* ctx, const char* path);
+
+/* Launch-shape and scheduling knobs (the autotuner's hook). Keys:
+ *   "kb"         Chebyshev iterations per energy-sum flush (1..1024; before mw3_set_analysis)
+ *   "rows_pairs" line pairs per CTA of the R-direction kinetic kernel (1..16)
+ *   "cols_tile"  R columns per CTA of the r-direction kinetic kernel (even, 2..64)
+ *   "use_graph"  0/1: replay full chunks as CUDA graphs
+ *   "use_tc"     0/1: tensor-core gamma transform in MW3_MIXED
+ * Values outside a key's range return MW3_ERR_BAD_ARG. mw3_get_tuning reads a key. */
+int mw3_set_tuning(mw3_ctx* ctx, const char* key, long value);
+long mw3_get_tuning(const mw3_ctx* ctx, const char* key);
+
+/* Per-kernel CUDA-event timing of the last mw3_propagate call, summed:
+ * names[i] (static strings), ms[i], launches[i] for i < *count (in/out capacity). */
+int mw3_kernel_times(mw3_ctx* ctx, int enable, const char** names, double* ms, long* launches,
+                     int* count);
+
+/* Diagnostic: achieved FMA throughput of this GPU in TFLOP/s from an FMA-chain
+ * kernel (kind 0 = FP64, 1 = FP32), the ALU roofline of the CUDA-core kernels.
+ * Allocates 8 KB of device memory for the duration of the call. */
+int mw3_measure_peak(int device, int kind, double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MW3_H */

@@ -142,7 +142,8 @@ class GridHamiltonian:
         for iJ, J in enumerate(self.Js):
             top = self.omega_top(J)
             for L in range(self.nelec):
-                c = [np.einsum("in,nkm->ikm", self.T[om], q[self.block_index[(iJ, om, L)]])
+                flat = (self.ng, self.nr * self.NR)
+                c = [(self.T[om] @ q[self.block_index[(iJ, om, L)]].reshape(flat)).reshape(q.shape[1:])
                      for om in range(top + 1)]
                 for om in range(top + 1):
                     a, bp, bm = self.angular_coefficients(J, om)
@@ -153,14 +154,14 @@ class GridHamiltonian:
                     if om >= 1:
                         # row i of block om meets row i+1 of block om-1 (same j)
                         cp[:n - 1] += bm[:n - 1, None, :] * c[om - 1][1:]
-                    out[self.block_index[(iJ, om, L)]] += np.einsum("in,ikm->nkm", self.T[om], cp)
+                    out[self.block_index[(iJ, om, L)]] += (self.T[om].T @ cp.reshape(flat)).reshape(cp.shape)
 
     # ------------------------------------------------------------------ full operator
     def apply_H(self, q):
         """H q: radial kinetic (sine DVR), angular (FBR + Coriolis) and potential terms."""
         q = np.asarray(q, dtype=float).reshape(self.shape)
-        out = np.einsum("bnkm,mM->bnkM", q, self.TR)          # R kinetic
-        out += np.einsum("kK,bnKm->bnkm", self.Tr, q)         # r kinetic
+        out = q @ self.TR                                     # R kinetic (T_R symmetric)
+        out += np.matmul(self.Tr, q)                          # r kinetic
         self.apply_angular(q, out)                            # j^2 and l^2 terms
         for (iJ, J, om, L), b in zip(self.blocks, range(self.nblk)):
             for Lp in range(self.nelec):                      # diabatic potential

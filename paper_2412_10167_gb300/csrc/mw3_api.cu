@@ -1,0 +1,1449 @@
+// libmw3: context, set-up and the propagation driver behind include/mw3.h.
+//
+// One propagation step (Eq. wvp-k) is the launch sequence
+//   1. kinetic_rows   t = T_R q_k                         (R lines, DST-II kinetic)
+//   2. kinetic_cols   t += T_r q_k; flux cut of q_k; q_k column at R_inf
+//   3. gamma_forward  c = T^Omega q_k                     (per block)
+//   4. gamma_backward q_(k+1) = D (alpha H_s q_k - beta D q_(k-1)), written over q_(k-1)
+//   5. channels       reactant-channel overlaps of q_k
+//   6. norms          ||q_(k+1)||^2 per J
+// The flux cut and overlaps of kb consecutive iterations are kept in a ring; every
+// kb iterations (a "chunk") the energy sums are updated by one GEMM
+//   A[J][2nE x cols] += Ph[J][2nE x kb] Cut[kb x cols],  Ph = Re/Im of c_k(E),
+// so the FP64 accumulators are read and written once per chunk instead of once
+// per iteration. Full chunks after the first are captured once as a CUDA graph and
+// replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "mw3_host.h"
+#include "mw3_internal.h"
+
+using namespace mw3;
+
+namespace {
+
+const char* kKernelNames[] = {"kinetic_rows", "kinetic_cols", "gamma_forward",
+                              "gamma_backward_update", "channels", "norms", "sums_flush"};
+constexpr int kNumKernels = 7;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+bool is_235(int n) {
+  if (n <= 0) return false;
+  for (int r : {2, 3, 5})
+    while (n % r == 0) n /= r;
+  return n == 1;
+}
+
+FFTPlan make_plan(int N) {
+  FFTPlan p{};
+  p.N = N;
+  int n = N, s = 0;
+  for (int r : {4, 2, 3, 5}) {
+    while (n % r == 0 && s < 16) {
+      p.radix[s++] = r;
+      n /= r;
+    }
+  }
+  p.nstages = s;
+  return p;
+}
+
+}  // namespace
+
+struct mw3_ctx {
+  int device = -1;
+  int precision = MW3_FP64;
+  bool host_only = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  mw3_alloc_fn alloc = nullptr;
+  mw3_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  std::string err;
+  int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
+  Tuning tune{4, 32, 32, 1, 0};
+
+  // grid and blocks
+  int NR = 0, nr = 0, ng = 0, nelec = 1, nJ = 0, omega_max = 0;
+  double Rmin = 0, Rmax = 0, rmin = 0, rmax = 0, dR = 0, dr = 0;
+  double mA = 0, mB = 0, mC = 0, mu = 0, m = 0;
+  std::vector<int> J, omtop;
+  std::vector<double> R, r, x, w, fR, fr;
+  std::vector<DevBlock> blocks;
+  int nblk = 0;
+  long ncol = 0, npts = 0;
+  std::vector<long> J_first_block;        // nJ + 1
+  std::vector<int> coef_of;               // (iJ, om) -> coef index
+  std::vector<std::vector<double>> T;     // T^Omega, Omega = 0..max top
+  std::vector<double> coef;               // [ncoef][5][ng]
+  int ncoef = 0;
+  FFTPlan planR{}, planr{};
+
+  // potential and caps
+  double vcut = 0, tcut = 0, erot = 0;
+  std::vector<double> V;                  // [L][L'][npts]
+  std::vector<double> lamR, lamr;         // lambda_j, j = 0..N (lambda_0 = 0)
+  std::vector<double> E0, dE;
+  mw3_pot_fn pot_fn = nullptr;
+  void* pot_user = nullptr;
+
+  // packet
+  mw3_packet_desc packet{};
+  double Ev0j0 = 0;
+  std::vector<double> q0;
+  std::vector<double> g_tilde;
+
+  // absorber
+  std::vector<double> DR, Dr;
+
+  // analysis
+  mw3_analysis_desc an{};
+  std::vector<double> Ecol, theta;        // theta[iJ * nE + e]
+  std::vector<double> wpsi, wdpsi;
+  int m_inf = 0;
+  int nchan = 0;
+  std::vector<int> chan_block, chan_col, chan_v, chan_j, chan_om, chan_lam, chan_iJ;
+  std::vector<double> chan_eps;
+  std::vector<long> colbase, ncols, ncut, accoff;
+  long NC = 0, max_cols = 0, acc_size = 0;
+
+  // propagation state
+  long iter = 0;       // k of q_k
+  int cur = 0;         // d_q[cur] holds q_k
+  std::vector<double> norm_trace;  // [iter][nJ], ||q_k||^2 for k = 1..iter
+  double norm0 = 1.0;
+
+  // graphs
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+  // timing: events recorded around launches, read back at chunk boundaries
+  bool timing = false;
+  cudaEvent_t ev[2 * kNumKernels] = {};
+  std::vector<cudaEvent_t> evpool;
+  std::vector<std::pair<int, int>> evrec;  // (kernel id, index of the start event)
+  double kms[kNumKernels] = {};
+  long klaunch[kNumKernels] = {};
+
+  // device buffers
+  std::map<std::string, DevBuf> buf;
+
+  int fail(int code, const std::string& msg) {
+    err = msg;
+    return code;
+  }
+  size_t rs() const { return precision == MW3_FP64 ? 8 : 4; }
+};
+
+// ------------------------------------------------------------------ helpers
+namespace {
+
+thread_local std::string g_create_err;
+
+#define CK(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return ctx->fail(MW3_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void* dptr(mw3_ctx* ctx, const char* name) {
+  auto it = ctx->buf.find(name);
+  return it == ctx->buf.end() ? nullptr : it->second.p;
+}
+
+int dfree(mw3_ctx* ctx, const char* name) {
+  auto it = ctx->buf.find(name);
+  if (it == ctx->buf.end()) return MW3_OK;
+  if (it->second.p) {
+    if (ctx->free_fn)
+      ctx->free_fn(it->second.p, ctx->alloc_user);
+    else
+      cudaFree(it->second.p);
+  }
+  ctx->buf.erase(it);
+  return MW3_OK;
+}
+
+// (Re)allocate a named device buffer; contents undefined.
+int dalloc(mw3_ctx* ctx, const char* name, size_t bytes) {
+  if (ctx->host_only) return MW3_OK;
+  auto it = ctx->buf.find(name);
+  if (it != ctx->buf.end() && it->second.bytes == bytes) return MW3_OK;
+  dfree(ctx, name);
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (ctx->alloc) {
+    p = ctx->alloc(bytes, ctx->alloc_user);
+    if (!p) return ctx->fail(MW3_ERR_OOM, std::string("allocator hook failed for ") + name);
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess)
+      return ctx->fail(MW3_ERR_OOM, std::string("cudaMalloc ") + name + ": " + cudaGetErrorString(e));
+  }
+  ctx->buf[name] = DevBuf{p, bytes};
+  return MW3_OK;
+}
+
+int dzero(mw3_ctx* ctx, const char* name) {
+  if (ctx->host_only) return MW3_OK;
+  auto it = ctx->buf.find(name);
+  if (it == ctx->buf.end()) return MW3_OK;
+  CK(cudaMemsetAsync(it->second.p, 0, it->second.bytes, ctx->stream));
+  return MW3_OK;
+}
+
+// Upload host doubles as the context's real type (or as doubles with as_double).
+int upload_real(mw3_ctx* ctx, const char* name, const std::vector<double>& h, bool as_double = false) {
+  const size_t es = as_double ? 8 : ctx->rs();
+  int st = dalloc(ctx, name, h.size() * es);
+  if (st) return st;
+  if (ctx->host_only) return MW3_OK;
+  if (es == 8) {
+    CK(cudaMemcpyAsync(dptr(ctx, name), h.data(), h.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    std::vector<float> f(h.begin(), h.end());
+    CK(cudaMemcpyAsync(dptr(ctx, name), f.data(), f.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MW3_OK;
+}
+
+template <typename Tv>
+int upload_raw(mw3_ctx* ctx, const char* name, const std::vector<Tv>& h) {
+  int st = dalloc(ctx, name, h.size() * sizeof(Tv));
+  if (st) return st;
+  if (ctx->host_only) return MW3_OK;
+  CK(cudaMemcpyAsync(dptr(ctx, name), h.data(), h.size() * sizeof(Tv), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MW3_OK;
+}
+
+// Complex tables for the FFT: twiddles exp(-2 pi i t/N) and exp(-i pi k / 2N).
+int upload_fft_tables(mw3_ctx* ctx, const char* twn, const char* phn, int N) {
+  std::vector<double> tw(2 * N), ph(2 * N);
+  for (int t = 0; t < N; ++t) {
+    tw[2 * t] = std::cos(2.0 * M_PI * t / N);
+    tw[2 * t + 1] = -std::sin(2.0 * M_PI * t / N);
+    ph[2 * t] = std::cos(M_PI * t / (2.0 * N));
+    ph[2 * t + 1] = -std::sin(M_PI * t / (2.0 * N));
+  }
+  int st = upload_real(ctx, twn, tw);
+  if (st) return st;
+  return upload_real(ctx, phn, ph);
+}
+
+double lam_pm(double X, int om, int sign) {
+  return std::sqrt(std::max(X * (X + 1.0) - (double)om * (om + sign), 0.0));
+}
+
+// diatomic Hamiltonian T_r + min(j(j+1) f_r, E_rot) + min(V_LL(r, R=100), vcut)
+int diatomic(mw3_ctx* ctx, int j, int lam, int nv, std::vector<double>& E, std::vector<double>& chi) {
+  const int n = ctx->nr;
+  std::vector<double> H((size_t)n * n, 0.0);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      double s = 0;
+      for (int jj = 1; jj <= n; ++jj) s += dst2(n, jj, a + 1) * ctx->lamr[jj] * dst2(n, jj, b + 1);
+      H[(size_t)a * n + b] = s;
+    }
+  std::vector<double> pm((size_t)ctx->nelec * ctx->nelec);
+  for (int a = 0; a < n; ++a) {
+    double v;
+    if (ctx->pot_fn) {
+      if (ctx->pot_fn(ctx->r[a], 100.0, 0.0, pm.data(), ctx->pot_user) != 0)
+        return ctx->fail(MW3_ERR_BAD_ARG, "potential callback failed");
+      v = pm[(size_t)lam * ctx->nelec + lam];
+    } else {
+      // grid potential: the diatomic curve is taken at the last R node
+      v = ctx->V[(size_t)(lam * ctx->nelec + lam) * ctx->npts + (size_t)0 * ctx->ncol +
+                 (size_t)a * ctx->NR + (ctx->NR - 1)];
+    }
+    v = std::min(v, ctx->vcut);
+    H[(size_t)a * n + a] += v + std::min(j * (j + 1.0) * ctx->fr[a], ctx->erot);
+  }
+  std::vector<double> ev, Z;
+  symmetric_eigen(n, H, ev, Z);
+  E.assign(ev.begin(), ev.begin() + nv);
+  chi.assign((size_t)nv * n, 0.0);
+  for (int v = 0; v < nv; ++v) {
+    int imax = 0;
+    for (int a = 0; a < n; ++a)
+      if (std::fabs(Z[(size_t)a * n + v]) > std::fabs(Z[(size_t)imax * n + v])) imax = a;
+    const double sg = Z[(size_t)imax * n + v] < 0 ? -1.0 : 1.0;
+    for (int a = 0; a < n; ++a) chi[(size_t)v * n + a] = sg * Z[(size_t)a * n + v];
+  }
+  return MW3_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+const char* mw3_status_string(int s) {
+  switch (s) {
+    case MW3_OK: return "ok";
+    case MW3_ERR_BAD_ARG: return "bad argument";
+    case MW3_ERR_OOM: return "out of memory";
+    case MW3_ERR_CUDA: return "CUDA error";
+    case MW3_ERR_DIVERGED: return "propagation diverged";
+    case MW3_ERR_SPECTRUM: return "energy outside the spectral range";
+    case MW3_ERR_TIMEOUT: return "device wait timed out";
+    case MW3_ERR_STATE: return "call out of order";
+    case MW3_ERR_IO: return "file error";
+    case MW3_ERR_NAN: return "NaN or Inf in input";
+    default: return "unknown status";
+  }
+}
+
+const char* mw3_last_error(const mw3_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+int mw3_create(mw3_ctx** out, int device, int precision) {
+  if (!out) return MW3_ERR_BAD_ARG;
+  *out = nullptr;
+  if (precision != MW3_FP64 && precision != MW3_MIXED) {
+    g_create_err = "precision must be MW3_FP64 or MW3_MIXED";
+    return MW3_ERR_BAD_ARG;
+  }
+  mw3_ctx* ctx = new (std::nothrow) mw3_ctx();
+  if (!ctx) return MW3_ERR_OOM;
+  ctx->precision = precision;
+  ctx->device = device;
+  ctx->tune.kb = (precision == MW3_FP64) ? 32 : 64;
+  ctx->tune.cols_tile = (precision == MW3_FP64) ? 16 : 32;
+  if (device < 0) {
+    ctx->host_only = true;  // set-up mathematics only (no device work)
+  } else {
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      g_create_err = std::string("CUDA device ") + std::to_string(device) + ": " + cudaGetErrorString(e);
+      delete ctx;
+      return MW3_ERR_CUDA;
+    }
+    ctx->own_stream = true;
+    for (int i = 0; i < 2 * kNumKernels; ++i) cudaEventCreate(&ctx->ev[i]);
+  }
+  *out = ctx;
+  return MW3_OK;
+}
+
+void mw3_destroy(mw3_ctx* ctx) {
+  if (!ctx) return;
+  if (!ctx->host_only) {
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& g : ctx->graph)
+      if (g) cudaGraphExecDestroy(g);
+    std::vector<std::string> names;
+    for (auto& kv : ctx->buf) names.push_back(kv.first);
+    for (auto& n : names) dfree(ctx, n.c_str());
+    for (int i = 0; i < 2 * kNumKernels; ++i)
+      if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    for (auto e : ctx->evpool) cudaEventDestroy(e);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+}
+
+int mw3_set_stream(mw3_ctx* ctx, void* stream) {
+  if (!ctx) return MW3_ERR_BAD_ARG;
+  if (ctx->host_only) return MW3_OK;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  ctx->own_stream = false;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  for (auto& g : ctx->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  return MW3_OK;
+}
+
+int mw3_set_allocator(mw3_ctx* ctx, mw3_alloc_fn alloc, mw3_free_fn free_fn, void* user) {
+  if (!ctx || (alloc == nullptr) != (free_fn == nullptr)) return MW3_ERR_BAD_ARG;
+  if (!ctx->buf.empty()) return ctx->fail(MW3_ERR_STATE, "mw3_set_allocator must precede mw3_grid");
+  ctx->alloc = alloc;
+  ctx->free_fn = free_fn;
+  ctx->alloc_user = user;
+  return MW3_OK;
+}
+
+int mw3_grid(mw3_ctx* ctx, const mw3_grid_desc* d) {
+  if (!ctx || !d) return MW3_ERR_BAD_ARG;
+  if (d->NR < 2 || d->nr < 2 || d->NR % 2 || d->nr % 2 || !is_235(d->NR) || !is_235(d->nr) ||
+      d->NR > 1024 || d->nr > 1024)
+    return ctx->fail(MW3_ERR_BAD_ARG, "NR and nr must be even, 2^a 3^b 5^c and <= 1024");
+  if (d->ngamma < 1 || d->ngamma > 256) return ctx->fail(MW3_ERR_BAD_ARG, "ngamma must be in 1..256");
+  if (!(d->Rmax > d->Rmin) || !(d->rmax > d->rmin) || d->Rmin < 0 || d->rmin < 0)
+    return ctx->fail(MW3_ERR_BAD_ARG, "grid intervals must be increasing and non-negative");
+  if (d->nJ < 1 || !d->J || d->omega_max < 0 || d->nelec < 1 || d->nelec > 2)
+    return ctx->fail(MW3_ERR_BAD_ARG, "need nJ >= 1, omega_max >= 0 and nelec in {1, 2}");
+  for (int i = 0; i < 3; ++i)
+    if (!(d->masses[i] > 0)) return ctx->fail(MW3_ERR_BAD_ARG, "masses must be positive");
+  for (int i = 0; i < d->nJ; ++i)
+    if (d->J[i] < 0) return ctx->fail(MW3_ERR_BAD_ARG, "J must be >= 0");
+  ctx->NR = d->NR;
+  ctx->nr = d->nr;
+  ctx->ng = d->ngamma;
+  ctx->Rmin = d->Rmin;
+  ctx->Rmax = d->Rmax;
+  ctx->rmin = d->rmin;
+  ctx->rmax = d->rmax;
+  ctx->nelec = d->nelec;
+  ctx->nJ = d->nJ;
+  ctx->omega_max = d->omega_max;
+  ctx->J.assign(d->J, d->J + d->nJ);
+  ctx->mA = d->masses[0];
+  ctx->mB = d->masses[1];
+  ctx->mC = d->masses[2];
+  ctx->mu = ctx->mA * (ctx->mB + ctx->mC) / (ctx->mA + ctx->mB + ctx->mC);
+  ctx->m = ctx->mB * ctx->mC / (ctx->mB + ctx->mC);
+  ctx->dR = (ctx->Rmax - ctx->Rmin) / ctx->NR;
+  ctx->dr = (ctx->rmax - ctx->rmin) / ctx->nr;
+  ctx->R.resize(ctx->NR);
+  ctx->r.resize(ctx->nr);
+  ctx->fR.resize(ctx->NR);
+  ctx->fr.resize(ctx->nr);
+  for (int i = 0; i < ctx->NR; ++i) {
+    ctx->R[i] = ctx->Rmin + (i + 0.5) * ctx->dR;
+    ctx->fR[i] = 1.0 / (2.0 * ctx->mu * ctx->R[i] * ctx->R[i]);
+  }
+  for (int i = 0; i < ctx->nr; ++i) {
+    ctx->r[i] = ctx->rmin + (i + 0.5) * ctx->dr;
+    ctx->fr[i] = 1.0 / (2.0 * ctx->m * ctx->r[i] * ctx->r[i]);
+  }
+  gauss_legendre(ctx->ng, ctx->x, ctx->w);
+  ctx->ncol = (long)ctx->nr * ctx->NR;
+  ctx->npts = (long)ctx->ng * ctx->ncol;
+
+  // blocks: J-major, Omega, Lambda
+  ctx->blocks.clear();
+  ctx->omtop.assign(ctx->nJ, 0);
+  ctx->J_first_block.assign(ctx->nJ + 1, 0);
+  ctx->coef_of.clear();
+  int maxtop = 0;
+  for (int iJ = 0; iJ < ctx->nJ; ++iJ) {
+    const int top = std::min(ctx->J[iJ], ctx->omega_max);
+    ctx->omtop[iJ] = top;
+    maxtop = std::max(maxtop, top);
+    ctx->J_first_block[iJ] = (long)ctx->blocks.size();
+    for (int om = 0; om <= top; ++om) {
+      const int ci = (int)ctx->coef_of.size();
+      ctx->coef_of.push_back(iJ * 4096 + om);
+      for (int L = 0; L < ctx->nelec; ++L) {
+        DevBlock b{};
+        b.iJ = iJ;
+        b.omega = om;
+        b.lam = L;
+        b.coef = ci;
+        b.base = (int)ctx->blocks.size() - L;
+        ctx->blocks.push_back(b);
+      }
+    }
+  }
+  ctx->J_first_block[ctx->nJ] = (long)ctx->blocks.size();
+  ctx->nblk = (int)ctx->blocks.size();
+  ctx->ncoef = (int)ctx->coef_of.size();
+  for (auto& b : ctx->blocks) {
+    const int top = ctx->omtop[b.iJ];
+    const int per_om = ctx->nelec;
+    const int idx = (int)(&b - &ctx->blocks[0]);
+    b.up = (b.omega + 1 <= top) ? idx + per_om : -1;
+    b.dn = (b.omega >= 1) ? idx - per_om : -1;
+  }
+  ctx->T.assign(maxtop + 1, {});
+  for (int om = 0; om <= maxtop; ++om) fbr_matrix(om, ctx->ng, ctx->x, ctx->w, ctx->T[om]);
+  ctx->planR = make_plan(ctx->NR);
+  ctx->planr = make_plan(ctx->nr);
+  ctx->stage = 1;
+  ctx->iter = 0;
+  return MW3_OK;
+}
+
+static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot) {
+  ctx->vcut = vcut;
+  ctx->tcut = tcut;
+  ctx->erot = erot;
+  const long np = ctx->npts;
+  const int ne = ctx->nelec;
+  for (double v : ctx->V)
+    if (!std::isfinite(v)) return ctx->fail(MW3_ERR_NAN, "potential contains NaN or Inf");
+  for (int L = 0; L < ne; ++L)
+    for (long i = 0; i < np; ++i) {
+      double& v = ctx->V[(size_t)(L * ne + L) * np + i];
+      v = std::min(v, vcut);
+    }
+  // radial kinetic eigenvalues lambda_j = min(k_j^2 / 2 mass, tcut), lambda_0 = 0
+  ctx->lamR.assign(ctx->NR + 1, 0.0);
+  ctx->lamr.assign(ctx->nr + 1, 0.0);
+  for (int j = 1; j <= ctx->NR; ++j) {
+    const double k = j * M_PI / (ctx->Rmax - ctx->Rmin);
+    ctx->lamR[j] = std::min(k * k / (2.0 * ctx->mu), tcut);
+  }
+  for (int j = 1; j <= ctx->nr; ++j) {
+    const double k = j * M_PI / (ctx->rmax - ctx->rmin);
+    ctx->lamr[j] = std::min(k * k / (2.0 * ctx->m), tcut);
+  }
+  // angular coefficient sets
+  const int ng = ctx->ng;
+  ctx->coef.assign((size_t)ctx->ncoef * kCoefRows * ng, 0.0);
+  for (int ci = 0; ci < ctx->ncoef; ++ci) {
+    const int iJ = ctx->coef_of[ci] / 4096, om = ctx->coef_of[ci] % 4096;
+    const double Jv = ctx->J[iJ];
+    const int top = ctx->omtop[iJ];
+    double* cf = &ctx->coef[(size_t)ci * kCoefRows * ng];
+    for (int i = 0; i < ng; ++i) {
+      const double j = om + i;
+      const double jj = j * (j + 1.0);
+      cf[i] = jj;
+      cf[ng + i] = Jv * (Jv + 1.0) + jj - 2.0 * om * om;
+      cf[2 * ng + i] = (om + 1 <= top && i >= 1)
+                           ? -lam_pm(Jv, om, +1) * lam_pm(j, om, +1) * (om == 0 ? std::sqrt(2.0) : 1.0)
+                           : 0.0;
+      cf[3 * ng + i] = (om >= 1 && i + 1 < ng)
+                           ? -lam_pm(Jv, om, -1) * lam_pm(j, om, -1) * (om == 1 ? std::sqrt(2.0) : 1.0)
+                           : 0.0;
+      const double lmax2 = std::pow(std::sqrt(Jv * (Jv + 1.0)) + std::sqrt(jj), 2);
+      cf[4 * ng + i] = (lmax2 == 0.0) ? 1e300 : erot / lmax2;
+    }
+  }
+  // spectral bounds per J
+  double vmin = 1e300, vmax = -1e300;
+  for (long i = 0; i < np; ++i) {
+    if (ne == 1) {
+      vmin = std::min(vmin, ctx->V[i]);
+      vmax = std::max(vmax, ctx->V[i]);
+    } else {
+      const double a = ctx->V[i], b = ctx->V[(size_t)np + i], dd = ctx->V[(size_t)3 * np + i];
+      const double h = 0.5 * (a + dd), s = std::sqrt(0.25 * (a - dd) * (a - dd) + b * b);
+      vmin = std::min(vmin, h - s);
+      vmax = std::max(vmax, h + s);
+    }
+  }
+  const double radmax = ctx->lamR[ctx->NR] + ctx->lamr[ctx->nr];
+  ctx->E0.assign(ctx->nJ, 0.0);
+  ctx->dE.assign(ctx->nJ, 0.0);
+  for (int iJ = 0; iJ < ctx->nJ; ++iJ) {
+    double ang = 0;
+    for (int ci = 0; ci < ctx->ncoef; ++ci) {
+      if (ctx->coef_of[ci] / 4096 != iJ) continue;
+      const double* cf = &ctx->coef[(size_t)ci * kCoefRows * ng];
+      for (int i = 0; i < ng; ++i) {
+        const double g = std::min(ctx->fR[0], cf[4 * ng + i]);
+        const double a = std::min(cf[i] * ctx->fr[0], erot) + g * cf[ng + i];
+        ang = std::max(ang, a + std::fabs(g * cf[2 * ng + i]) + std::fabs(g * cf[3 * ng + i]));
+      }
+    }
+    const double emax = vmax + radmax + ang, emin = vmin;
+    ctx->E0[iJ] = 0.5 * (emax + emin);
+    ctx->dE[iJ] = 1.0001 * 0.5 * (emax - emin);
+  }
+  // device tables
+  int st;
+  std::vector<double> Tall, Ttall;
+  for (auto& Tm : ctx->T) {
+    Tall.insert(Tall.end(), Tm.begin(), Tm.end());
+    for (int a = 0; a < ng; ++a)
+      for (int b = 0; b < ng; ++b) Ttall.push_back(Tm[(size_t)b * ng + a]);
+  }
+  if ((st = upload_real(ctx, "T", Tall))) return st;
+  if ((st = upload_real(ctx, "Tt", Ttall))) return st;
+  if ((st = upload_real(ctx, "coef", ctx->coef))) return st;
+  if ((st = upload_real(ctx, "fR", ctx->fR))) return st;
+  if ((st = upload_real(ctx, "fr", ctx->fr))) return st;
+  if ((st = upload_real(ctx, "V", ctx->V))) return st;
+  {
+    std::vector<double> lr(ctx->NR + 1), lrr(ctx->nr + 1);
+    for (int j = 0; j <= ctx->NR; ++j) lr[j] = ctx->lamR[j] / ctx->NR;   // 1/N of the inverse FFT
+    for (int j = 0; j <= ctx->nr; ++j) lrr[j] = ctx->lamr[j] / ctx->nr;
+    if ((st = upload_real(ctx, "lamR", lr))) return st;
+    if ((st = upload_real(ctx, "lamr", lrr))) return st;
+  }
+  if ((st = upload_fft_tables(ctx, "twR", "phR", ctx->NR))) return st;
+  if ((st = upload_fft_tables(ctx, "twr", "phr", ctx->nr))) return st;
+  std::vector<DevJ> dj(ctx->nJ);
+  for (int iJ = 0; iJ < ctx->nJ; ++iJ) dj[iJ] = DevJ{ctx->E0[iJ] / ctx->dE[iJ], 1.0 / ctx->dE[iJ]};
+  if ((st = upload_raw(ctx, "dj", dj))) return st;
+  if ((st = upload_raw(ctx, "blocks", ctx->blocks))) return st;
+  std::vector<long> jb(ctx->nJ + 1);
+  for (int iJ = 0; iJ <= ctx->nJ; ++iJ) jb[iJ] = ctx->J_first_block[iJ] * ctx->npts;
+  if ((st = upload_raw(ctx, "J_begin", jb))) return st;
+  // default: no absorption
+  ctx->DR.assign(ctx->NR, 1.0);
+  ctx->Dr.assign(ctx->nr, 1.0);
+  if ((st = upload_real(ctx, "DR", ctx->DR))) return st;
+  if ((st = upload_real(ctx, "Dr", ctx->Dr))) return st;
+  // state buffers
+  const size_t vb = (size_t)ctx->nblk * ctx->npts * ctx->rs();
+  if ((st = dalloc(ctx, "q0", vb)) || (st = dalloc(ctx, "q1", vb)) || (st = dalloc(ctx, "t", vb)) ||
+      (st = dalloc(ctx, "c", vb)))
+    return st;
+  if ((st = dzero(ctx, "q0")) || (st = dzero(ctx, "q1"))) return st;
+  ctx->stage = 2;
+  return MW3_OK;
+}
+
+int mw3_load_potential(mw3_ctx* ctx, mw3_pot_fn fn, void* user, double vcut, double tcut,
+                       double erot) {
+  if (!ctx || !fn) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 1) return ctx->fail(MW3_ERR_STATE, "mw3_grid first");
+  if (!(vcut > 0) || !(tcut > 0) || !(erot > 0))
+    return ctx->fail(MW3_ERR_BAD_ARG, "caps must be positive");
+  const int ne = ctx->nelec;
+  const long np = ctx->npts;
+  ctx->V.assign((size_t)ne * ne * np, 0.0);
+  ctx->pot_fn = fn;
+  ctx->pot_user = user;
+  unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<int> bad(nth, 0);
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nth; ++t) {
+    th.emplace_back([&, t]() {
+      std::vector<double> pm((size_t)ne * ne);
+      for (int n = (int)t; n < ctx->ng; n += (int)nth)
+        for (int kr = 0; kr < ctx->nr; ++kr)
+          for (int mm = 0; mm < ctx->NR; ++mm) {
+            if (fn(ctx->r[kr], ctx->R[mm], ctx->x[n], pm.data(), user) != 0) {
+              bad[t] = 1;
+              return;
+            }
+            const long off = (long)n * ctx->ncol + (long)kr * ctx->NR + mm;
+            for (int a = 0; a < ne * ne; ++a) ctx->V[(size_t)a * np + off] = pm[a];
+          }
+    });
+  }
+  for (auto& tt : th) tt.join();
+  for (int b : bad)
+    if (b) return ctx->fail(MW3_ERR_BAD_ARG, "potential callback returned an error");
+  return finish_potential(ctx, vcut, tcut, erot);
+}
+
+int mw3_load_potential_grid(mw3_ctx* ctx, const double* V, double vcut, double tcut, double erot) {
+  if (!ctx || !V) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 1) return ctx->fail(MW3_ERR_STATE, "mw3_grid first");
+  const size_t n = (size_t)ctx->nelec * ctx->nelec * ctx->npts;
+  ctx->V.assign(V, V + n);
+  ctx->pot_fn = nullptr;
+  ctx->pot_user = nullptr;
+  return finish_potential(ctx, vcut, tcut, erot);
+}
+
+int mw3_init_packet(mw3_ctx* ctx, const mw3_packet_desc* d) {
+  if (!ctx || !d) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
+  if (d->v0 < 0 || d->j0 < d->omega0 || d->omega0 < 0 || d->elec0 < 0 || d->elec0 >= ctx->nelec ||
+      !(d->Gamma > 0) || !(d->Ecol > 0) || d->j0 - d->omega0 >= ctx->ng || d->v0 >= ctx->nr)
+    return ctx->fail(MW3_ERR_BAD_ARG, "invalid packet description");
+  ctx->packet = *d;
+  std::vector<double> E, chi;
+  int st = diatomic(ctx, d->j0, d->elec0, d->v0 + 1, E, chi);
+  if (st) return st;
+  ctx->Ev0j0 = E[d->v0];
+  const double k0 = std::sqrt(2.0 * ctx->mu * d->Ecol);
+  std::vector<double> g(ctx->NR);
+  double gn = 0;
+  for (int i = 0; i < ctx->NR; ++i) {
+    const double dx = ctx->R[i] - d->R0;
+    g[i] = std::exp(-dx * dx / (2.0 * d->Gamma * d->Gamma)) * std::cos(k0 * ctx->R[i]);
+    gn += g[i] * g[i];
+  }
+  gn = 1.0 / std::sqrt(gn);
+  ctx->g_tilde.resize(ctx->NR);
+  for (int i = 0; i < ctx->NR; ++i) {
+    g[i] *= gn;
+    ctx->g_tilde[i] = g[i] / std::sqrt(ctx->dR);
+  }
+  const std::vector<double>& Tm = ctx->T[std::min<int>(d->omega0, (int)ctx->T.size() - 1)];
+  ctx->q0.assign((size_t)ctx->nblk * ctx->npts, 0.0);
+  for (int bi = 0; bi < ctx->nblk; ++bi) {
+    const DevBlock& b = ctx->blocks[bi];
+    if (b.omega != d->omega0 || b.lam != d->elec0) continue;
+    const double* y = &Tm[(size_t)(d->j0 - d->omega0) * ctx->ng];
+    for (int n = 0; n < ctx->ng; ++n)
+      for (int kr = 0; kr < ctx->nr; ++kr)
+        for (int mm = 0; mm < ctx->NR; ++mm)
+          ctx->q0[(size_t)bi * ctx->npts + (size_t)n * ctx->ncol + (size_t)kr * ctx->NR + mm] =
+              y[n] * chi[(size_t)d->v0 * ctx->nr + kr] * g[mm];
+  }
+  ctx->norm0 = 1.0;
+  if ((st = mw3_set_state(ctx, ctx->q0.data(), nullptr))) return st;
+  ctx->iter = 0;
+  ctx->norm_trace.clear();
+  if (ctx->stage < 3) ctx->stage = 3;
+  if (ctx->stage >= 5) {
+    if ((st = dzero(ctx, "acc")) || (st = dzero(ctx, "cut")) || (st = dzero(ctx, "d_iter"))) return st;
+    if (!ctx->host_only) CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return MW3_OK;
+}
+
+int mw3_set_absorber(mw3_ctx* ctx, double RI, double AR, int nR, double rI, double Ar, int nrx) {
+  if (!ctx) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
+  if (AR < 0 || Ar < 0 || nR < 1 || nrx < 1) return ctx->fail(MW3_ERR_BAD_ARG, "invalid absorber");
+  for (int i = 0; i < ctx->NR; ++i)
+    ctx->DR[i] = ctx->R[i] > RI ? std::exp(-AR * std::pow(ctx->R[i] - RI, nR)) : 1.0;
+  for (int i = 0; i < ctx->nr; ++i)
+    ctx->Dr[i] = ctx->r[i] > rI ? std::exp(-Ar * std::pow(ctx->r[i] - rI, nrx)) : 1.0;
+  int st;
+  if ((st = upload_real(ctx, "DR", ctx->DR)) || (st = upload_real(ctx, "Dr", ctx->Dr))) return st;
+  if (ctx->stage == 3) ctx->stage = 4;
+  return MW3_OK;
+}
+
+int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
+  if (!ctx || !d) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 3) return ctx->fail(MW3_ERR_STATE, "mw3_init_packet first");
+  if (d->nE < 1 || !(d->E_hi >= d->E_lo) || !(d->E_lo > 0) || d->rstar <= ctx->rmin ||
+      d->rstar >= ctx->rmax || d->kmin < 0)
+    return ctx->fail(MW3_ERR_BAD_ARG, "invalid analysis description");
+  ctx->an = *d;
+  const int nE = d->nE;
+  ctx->Ecol.resize(nE);
+  for (int e = 0; e < nE; ++e)
+    ctx->Ecol[e] = (nE == 1) ? d->E_lo : d->E_lo + (d->E_hi - d->E_lo) * e / (nE - 1.0);
+  ctx->theta.assign((size_t)ctx->nJ * nE, 0.0);
+  for (int iJ = 0; iJ < ctx->nJ; ++iJ)
+    for (int e = 0; e < nE; ++e) {
+      const double Es = (ctx->Ecol[e] + ctx->Ev0j0 - ctx->E0[iJ]) / ctx->dE[iJ];
+      if (!(Es > -1.0 && Es < 1.0)) return ctx->fail(MW3_ERR_SPECTRUM, "energy outside (E_min, E_max)");
+      ctx->theta[(size_t)iJ * nE + e] = std::acos(Es);
+    }
+  sine_interpolation_weights(ctx->rmin, ctx->rmax, ctx->nr, d->rstar, ctx->wpsi, ctx->wdpsi);
+  int mi = 0;
+  for (int i = 0; i < ctx->NR; ++i)
+    if (std::fabs(ctx->R[i] - d->Rinf) < std::fabs(ctx->R[mi] - d->Rinf)) mi = i;
+  ctx->m_inf = mi;
+
+  // channels and the column layout of the cut ring, per J
+  ctx->chan_block.clear();
+  ctx->chan_col.clear();
+  ctx->chan_v.clear();
+  ctx->chan_j.clear();
+  ctx->chan_om.clear();
+  ctx->chan_lam.clear();
+  ctx->chan_iJ.clear();
+  ctx->chan_eps.clear();
+  std::vector<double> P;
+  std::map<std::pair<int, int>, std::pair<std::vector<double>, std::vector<double>>> cache;
+  const int ng = ctx->ng, nr = ctx->nr;
+  ctx->colbase.assign(ctx->nJ, 0);
+  ctx->ncols.assign(ctx->nJ, 0);
+  ctx->ncut.assign(ctx->nJ, 0);
+  ctx->accoff.assign(ctx->nJ, 0);
+  long col = 0, acc = 0, maxc = 0;
+  for (int iJ = 0; iJ < ctx->nJ; ++iJ) {
+    const long b0 = ctx->J_first_block[iJ], b1 = ctx->J_first_block[iJ + 1];
+    const long nc = (b1 - b0) * ng * ctx->NR;
+    ctx->colbase[iJ] = col;
+    ctx->ncut[iJ] = nc;
+    for (long b = b0; b < b1; ++b) ctx->blocks[b].cutcol = (int)(col + (b - b0) * ng * ctx->NR);
+    long nch = 0;
+    if (d->vmax >= 0) {
+      for (long b = b0; b < b1; ++b) {
+        const DevBlock& B = ctx->blocks[b];
+        for (int j = B.omega; j <= std::min(d->jmax, B.omega + ng - 1); ++j) {
+          auto key = std::make_pair(j, B.lam);
+          if (!cache.count(key)) {
+            std::vector<double> E, chi;
+            int st = diatomic(ctx, j, B.lam, d->vmax + 1, E, chi);
+            if (st) return st;
+            cache[key] = {E, chi};
+          }
+          auto& ec = cache[key];
+          for (int v = 0; v <= d->vmax; ++v) {
+            ctx->chan_block.push_back((int)b);
+            ctx->chan_col.push_back((int)(col + 2 * nc + nch));
+            ctx->chan_v.push_back(v);
+            ctx->chan_j.push_back(j);
+            ctx->chan_om.push_back(B.omega);
+            ctx->chan_lam.push_back(B.lam);
+            ctx->chan_iJ.push_back(iJ);
+            ctx->chan_eps.push_back(ec.first[v]);
+            const double* Trow = &ctx->T[B.omega][(size_t)(j - B.omega) * ng];
+            for (int n = 0; n < ng; ++n)
+              for (int kr = 0; kr < nr; ++kr)
+                P.push_back(Trow[n] * ec.second[(size_t)v * nr + kr] / std::sqrt(ctx->dR));
+            ++nch;
+          }
+        }
+      }
+    }
+    ctx->ncols[iJ] = 2 * nc + nch;
+    ctx->accoff[iJ] = acc;
+    acc += 2L * nE * ctx->ncols[iJ];
+    maxc = std::max(maxc, ctx->ncols[iJ]);
+    col += ((2 * nc + nch + 3) / 4) * 4;
+  }
+  ctx->nchan = (int)ctx->chan_block.size();
+  ctx->NC = col;
+  ctx->max_cols = maxc;
+  ctx->acc_size = acc;
+  int st;
+  const int kb = ctx->tune.kb;
+  if ((st = upload_raw(ctx, "blocks", ctx->blocks))) return st;
+  if ((st = dalloc(ctx, "cut", (size_t)kb * ctx->NC * ctx->rs())) || (st = dzero(ctx, "cut"))) return st;
+  if ((st = dalloc(ctx, "acc", (size_t)acc * 8)) || (st = dzero(ctx, "acc"))) return st;
+  if ((st = dalloc(ctx, "ph", (size_t)ctx->nJ * 2 * nE * kb * ctx->rs()))) return st;
+  if ((st = upload_real(ctx, "theta", ctx->theta, true))) return st;
+  if ((st = upload_real(ctx, "wpsi", ctx->wpsi)) || (st = upload_real(ctx, "wdpsi", ctx->wdpsi))) return st;
+  if ((st = upload_raw(ctx, "colbase", ctx->colbase)) || (st = upload_raw(ctx, "ncols", ctx->ncols)) ||
+      (st = upload_raw(ctx, "ncut", ctx->ncut)) || (st = upload_raw(ctx, "accoff", ctx->accoff)))
+    return st;
+  {
+    std::vector<int> nci(ctx->nJ);
+    for (int i = 0; i < ctx->nJ; ++i) nci[i] = (int)ctx->ncut[i];
+    if ((st = upload_raw(ctx, "ncut_i", nci))) return st;
+  }
+  if ((st = dalloc(ctx, "qcol", (size_t)ctx->nblk * ng * nr * ctx->rs()))) return st;
+  if (ctx->nchan > 0) {
+    if ((st = upload_real(ctx, "P", P)) || (st = upload_raw(ctx, "chan_block", ctx->chan_block)) ||
+        (st = upload_raw(ctx, "chan_col", ctx->chan_col)))
+      return st;
+  }
+  if ((st = dalloc(ctx, "d_iter", 8))) return st;
+  if (!ctx->host_only) {
+    long it = ctx->iter;
+    CK(cudaMemcpyAsync(dptr(ctx, "d_iter"), &it, 8, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  if ((st = dalloc(ctx, "normbuf", (size_t)kb * ctx->nJ * 8))) return st;
+  if ((st = dalloc(ctx, "npartial", (size_t)ctx->nJ * 256 * 8))) return st;
+  for (auto& g : ctx->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  if (!ctx->host_only) CK(cudaStreamSynchronize(ctx->stream));
+  ctx->stage = 5;
+  return MW3_OK;
+}
+
+}  // extern "C"
+
+// ============================================================ propagation
+namespace {
+
+template <typename real>
+struct Bufs {
+  real *q[2], *t, *c, *V, *T, *Tt, *coef, *fR, *fr, *DR, *Dr, *lamR, *lamr, *wpsi, *wdpsi, *cut,
+      *qcol, *P, *ph;
+  void *twR, *phR, *twr, *phr;
+  DevBlock* blocks;
+  DevJ* dj;
+  int *ncut_i, *chan_block, *chan_col;
+  long *colbase, *ncols, *ncut, *accoff, *d_iter, *J_begin;
+  double *acc, *theta, *normbuf, *npartial;
+};
+
+template <typename real>
+Bufs<real> bufs(mw3_ctx* ctx) {
+  Bufs<real> b;
+  b.q[0] = (real*)dptr(ctx, "q0");
+  b.q[1] = (real*)dptr(ctx, "q1");
+  b.t = (real*)dptr(ctx, "t");
+  b.c = (real*)dptr(ctx, "c");
+  b.V = (real*)dptr(ctx, "V");
+  b.T = (real*)dptr(ctx, "T");
+  b.Tt = (real*)dptr(ctx, "Tt");
+  b.coef = (real*)dptr(ctx, "coef");
+  b.fR = (real*)dptr(ctx, "fR");
+  b.fr = (real*)dptr(ctx, "fr");
+  b.DR = (real*)dptr(ctx, "DR");
+  b.Dr = (real*)dptr(ctx, "Dr");
+  b.lamR = (real*)dptr(ctx, "lamR");
+  b.lamr = (real*)dptr(ctx, "lamr");
+  b.wpsi = (real*)dptr(ctx, "wpsi");
+  b.wdpsi = (real*)dptr(ctx, "wdpsi");
+  b.cut = (real*)dptr(ctx, "cut");
+  b.qcol = (real*)dptr(ctx, "qcol");
+  b.P = (real*)dptr(ctx, "P");
+  b.ph = (real*)dptr(ctx, "ph");
+  b.twR = dptr(ctx, "twR");
+  b.phR = dptr(ctx, "phR");
+  b.twr = dptr(ctx, "twr");
+  b.phr = dptr(ctx, "phr");
+  b.blocks = (DevBlock*)dptr(ctx, "blocks");
+  b.dj = (DevJ*)dptr(ctx, "dj");
+  b.ncut_i = (int*)dptr(ctx, "ncut_i");
+  b.chan_block = (int*)dptr(ctx, "chan_block");
+  b.chan_col = (int*)dptr(ctx, "chan_col");
+  b.colbase = (long*)dptr(ctx, "colbase");
+  b.ncols = (long*)dptr(ctx, "ncols");
+  b.ncut = (long*)dptr(ctx, "ncut");
+  b.accoff = (long*)dptr(ctx, "accoff");
+  b.d_iter = (long*)dptr(ctx, "d_iter");
+  b.J_begin = (long*)dptr(ctx, "J_begin");
+  b.acc = (double*)dptr(ctx, "acc");
+  b.theta = (double*)dptr(ctx, "theta");
+  b.normbuf = (double*)dptr(ctx, "normbuf");
+  b.npartial = (double*)dptr(ctx, "npartial");
+  return b;
+}
+
+struct Timer {
+  mw3_ctx* ctx;
+  int k;
+  int idx = -1;
+  Timer(mw3_ctx* c, int kk, bool enable) : ctx(c), k(kk) {
+    if (!(enable && c->timing)) return;
+    idx = (int)ctx->evrec.size() * 2;
+    while ((int)ctx->evpool.size() < idx + 2) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ctx->evpool.push_back(e);
+    }
+    cudaEventRecord(ctx->evpool[idx], ctx->stream);
+  }
+  void stop() {
+    if (idx < 0) return;
+    cudaEventRecord(ctx->evpool[idx + 1], ctx->stream);
+    ctx->evrec.push_back({k, idx});
+    idx = -1;
+  }
+};
+
+// Accumulate the recorded launch times (call after the stream is synchronised).
+void collect_times(mw3_ctx* ctx) {
+  for (auto& r : ctx->evrec) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->evpool[r.second], ctx->evpool[r.second + 1]);
+    ctx->kms[r.first] += ms;
+    ctx->klaunch[r.first] += 1;
+  }
+  ctx->evrec.clear();
+}
+
+#define LK(expr)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return ctx->fail(MW3_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// One Chebyshev iteration; cut data into ring slot `slot`. mode 1 computes H_s q
+// into `hs_out` instead (no damping, no analysis).
+template <typename real>
+int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_out = nullptr) {
+  Bufs<real> B = bufs<real>(ctx);
+  cudaStream_t st = ctx->stream;
+  real* qk = B.q[ctx->cur];
+  real* qkm1 = B.q[1 - ctx->cur];
+  const long nrows = (long)ctx->nblk * ctx->ng * ctx->nr;
+  const bool analysis = (mode == 0) && ctx->stage >= 5;
+  real* cut_slot = analysis ? B.cut + (long)slot * ctx->NC : nullptr;
+  {
+    Timer tm(ctx, 0, timed);
+    LK(launch_kinetic_rows<real>(qk, B.t, nrows, ctx->planR, B.twR, B.phR, B.lamR,
+                                 ctx->tune.rows_pairs, st));
+    tm.stop();
+  }
+  {
+    Timer tm(ctx, 1, timed);
+    LK(launch_kinetic_cols<real>(qk, B.t, (long)ctx->nblk * ctx->ng, ctx->nr, ctx->NR, ctx->planr,
+                                 B.twr, B.phr, B.lamr, ctx->tune.cols_tile, ctx->ng, B.wpsi,
+                                 B.wdpsi, cut_slot, B.blocks, B.ncut_i,
+                                 analysis ? ctx->m_inf : -1, analysis ? B.qcol : nullptr, st));
+    tm.stop();
+  }
+  {
+    Timer tm(ctx, 2, timed);
+    LK(launch_gamma_forward<real>(qk, B.c, B.T, B.blocks, ctx->nblk, ctx->ng, ctx->ncol, st));
+    tm.stop();
+  }
+  {
+    Timer tm(ctx, 3, timed);
+    const real alpha = first ? (real)1 : (real)2;
+    const real beta = first ? (real)0 : (real)1;
+    LK(launch_gamma_backward_update<real>(B.c, B.Tt, B.blocks, ctx->nblk, ctx->ng, ctx->ncol,
+                                          ctx->NR, B.coef, B.fr, B.fR, (real)ctx->erot, qk, qkm1,
+                                          B.t, B.V, ctx->nelec, B.DR, B.Dr, B.dj, alpha, beta,
+                                          mode, hs_out, st));
+    tm.stop();
+  }
+  if (mode == 1) return MW3_OK;
+  if (analysis && ctx->nchan > 0) {
+    Timer tm(ctx, 4, timed);
+    LK(launch_channels<real>(B.qcol, B.P, B.chan_block, B.chan_col, ctx->nchan, ctx->ng * ctx->nr,
+                             B.d_iter, slot, ctx->an.kmin, cut_slot, st));
+    tm.stop();
+  }
+  {
+    Timer tm(ctx, 5, timed);
+    LK(launch_norms<real>(qkm1, B.J_begin, ctx->nJ, B.npartial, 256, B.normbuf + (long)slot * ctx->nJ, st));
+    tm.stop();
+  }
+  ctx->cur = 1 - ctx->cur;
+  return MW3_OK;
+}
+
+template <typename real>
+int flush(mw3_ctx* ctx, int nvalid, bool timed) {
+  Bufs<real> B = bufs<real>(ctx);
+  cudaStream_t st = ctx->stream;
+  Timer tm(ctx, 6, timed);
+  LK(launch_phases<real>(B.theta, ctx->nJ, ctx->an.nE, ctx->tune.kb, nvalid, B.d_iter, B.ph, st));
+  LK(launch_sums_flush<real>(B.ph, B.cut, ctx->NC, ctx->tune.kb, ctx->nJ, ctx->an.nE, B.colbase,
+                             B.ncols, B.accoff, ctx->max_cols, B.acc, st));
+  LK(launch_advance(B.d_iter, nvalid, st));
+  tm.stop();
+  return MW3_OK;
+}
+
+// Run `n` iterations starting at ring slot 0 (n <= kb), then flush.
+template <typename real>
+int chunk(mw3_ctx* ctx, int n, bool timed) {
+  for (int s = 0; s < n; ++s) {
+    const bool first = (ctx->iter + s == 0);
+    int st = step<real>(ctx, s, first, timed);
+    if (st) return st;
+  }
+  return flush<real>(ctx, n, timed);
+}
+
+int check_norms(mw3_ctx* ctx, int n) {
+  std::vector<double> h((size_t)n * ctx->nJ);
+  CK(cudaMemcpyAsync(h.data(), dptr(ctx, "normbuf"), h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  collect_times(ctx);
+  ctx->norm_trace.insert(ctx->norm_trace.end(), h.begin(), h.end());
+  for (double v : h)
+    if (!(v <= 1.5 * ctx->norm0)) return ctx->fail(MW3_ERR_DIVERGED, "||q_k||^2 > 1.5 ||q_0||^2");
+  return MW3_OK;
+}
+
+template <typename real>
+int propagate_impl(mw3_ctx* ctx, long nsteps) {
+  const int kb = ctx->tune.kb;
+  long done = 0;
+  while (done < nsteps) {
+    const int n = (int)std::min<long>(kb, nsteps - done);
+    const bool can_graph = ctx->tune.use_graph && !ctx->timing && n == kb && ctx->iter > 0;
+    int st;
+    if (can_graph) {
+      cudaGraphExec_t& ge = ctx->graph[ctx->cur];
+      if (!ge) {
+        const int cur0 = ctx->cur;
+        const long it0 = ctx->iter;
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        st = chunk<real>(ctx, n, false);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+        if (st) return st;
+        if (e2 != cudaSuccess) return ctx->fail(MW3_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e2));
+        CK(cudaGraphInstantiate(&ge, g, 0));
+        cudaGraphDestroy(g);
+        ctx->cur = cur0;   // capture did not execute anything
+        ctx->iter = it0;
+      }
+      CK(cudaGraphLaunch(ge, ctx->stream));
+      ctx->cur = (kb % 2) ? 1 - ctx->cur : ctx->cur;
+    } else {
+      st = chunk<real>(ctx, n, true);
+      if (st) return st;
+    }
+    ctx->iter += n;
+    done += n;
+    if ((st = check_norms(ctx, n))) return st;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MW3_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mw3_propagate(mw3_ctx* ctx, long nsteps) {
+  if (!ctx || nsteps < 0) return MW3_ERR_BAD_ARG;
+  if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context cannot propagate");
+  if (ctx->stage < 5) return ctx->fail(MW3_ERR_STATE, "mw3_set_analysis first");
+  cudaSetDevice(ctx->device);
+  return ctx->precision == MW3_FP64 ? propagate_impl<double>(ctx, nsteps)
+                                    : propagate_impl<float>(ctx, nsteps);
+}
+
+long mw3_iteration(const mw3_ctx* ctx) { return ctx ? ctx->iter : -1; }
+
+int mw3_sizes(const mw3_ctx* ctx, long* nblocks, long* ppb) {
+  if (!ctx || ctx->stage < 1) return MW3_ERR_STATE;
+  if (nblocks) *nblocks = ctx->nblk;
+  if (ppb) *ppb = ctx->npts;
+  return MW3_OK;
+}
+
+int mw3_spectral_range(const mw3_ctx* ctx, double* E0, double* dE) {
+  if (!ctx || ctx->stage < 2) return MW3_ERR_STATE;
+  for (int i = 0; i < ctx->nJ; ++i) {
+    if (E0) E0[i] = ctx->E0[i];
+    if (dE) dE[i] = ctx->dE[i];
+  }
+  return MW3_OK;
+}
+
+int mw3_reference_energy(const mw3_ctx* ctx, double* e) {
+  if (!ctx || ctx->stage < 3 || !e) return MW3_ERR_STATE;
+  *e = ctx->Ev0j0;
+  return MW3_OK;
+}
+
+int mw3_set_state(mw3_ctx* ctx, const double* q, const double* qprev) {
+  if (!ctx || !q) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
+  if (ctx->host_only) return MW3_OK;
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  for (int which = 0; which < 2; ++which) {
+    const double* src = which == 0 ? q : qprev;
+    const char* name = (which == 0) == (ctx->cur == 0) ? "q0" : "q1";
+    if (!src) {
+      if (which == 1) {
+        CK(cudaMemsetAsync(dptr(ctx, name), 0, n * ctx->rs(), ctx->stream));
+      }
+      continue;
+    }
+    if (ctx->precision == MW3_FP64) {
+      CK(cudaMemcpyAsync(dptr(ctx, name), src, n * 8, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+      std::vector<float> f(src, src + n);
+      CK(cudaMemcpyAsync(dptr(ctx, name), f.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+  }
+  return MW3_OK;
+}
+
+int mw3_get_state(mw3_ctx* ctx, double* q, double* qprev) {
+  if (!ctx || !q) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
+  if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  for (int which = 0; which < 2; ++which) {
+    double* dst = which == 0 ? q : qprev;
+    if (!dst) continue;
+    const char* name = (which == 0) == (ctx->cur == 0) ? "q0" : "q1";
+    if (ctx->precision == MW3_FP64) {
+      CK(cudaMemcpyAsync(dst, dptr(ctx, name), n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+      std::vector<float> f(n);
+      CK(cudaMemcpyAsync(f.data(), dptr(ctx, name), n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      for (size_t i = 0; i < n; ++i) dst[i] = f[i];
+    }
+  }
+  return MW3_OK;
+}
+
+int mw3_apply_hs(mw3_ctx* ctx, const double* q, double* out) {
+  if (!ctx || !q || !out) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
+  if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
+  cudaSetDevice(ctx->device);
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  int st;
+  if ((st = dalloc(ctx, "hs_in", n * ctx->rs())) || (st = dalloc(ctx, "hs_out", n * ctx->rs()))) return st;
+  // route the input through the q_k slot temporarily
+  const int cur0 = ctx->cur;
+  const char* qname = ctx->cur == 0 ? "q0" : "q1";
+  void* saved = ctx->buf[qname].p;
+  ctx->buf[qname].p = dptr(ctx, "hs_in");
+  if (ctx->precision == MW3_FP64) {
+    CK(cudaMemcpyAsync(dptr(ctx, "hs_in"), q, n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    st = step<double>(ctx, 0, true, false, 1, (double*)dptr(ctx, "hs_out"));
+  } else {
+    std::vector<float> f(q, q + n);
+    CK(cudaMemcpyAsync(dptr(ctx, "hs_in"), f.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    st = step<float>(ctx, 0, true, false, 1, (float*)dptr(ctx, "hs_out"));
+  }
+  ctx->buf[qname].p = saved;
+  ctx->cur = cur0;
+  if (st) return st;
+  if (ctx->precision == MW3_FP64) {
+    CK(cudaMemcpyAsync(out, dptr(ctx, "hs_out"), n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else {
+    std::vector<float> f(n);
+    CK(cudaMemcpyAsync(f.data(), dptr(ctx, "hs_out"), n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < n; ++i) out[i] = f[i];
+  }
+  return MW3_OK;
+}
+
+long mw3_norm_trace(mw3_ctx* ctx, double* out, long n) {
+  if (!ctx || !out || n < 0) return MW3_ERR_BAD_ARG;
+  const long have = (long)ctx->norm_trace.size() / std::max(1, ctx->nJ);
+  const long cnt = std::min(n, have);
+  std::copy(ctx->norm_trace.end() - cnt * ctx->nJ, ctx->norm_trace.end(), out);
+  return cnt;
+}
+
+int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel) {
+  if (!ctx) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 5) return ctx->fail(MW3_ERR_STATE, "mw3_set_analysis first");
+  const int nE = ctx->an.nE, nJ = ctx->nJ;
+  if (E)
+    for (int e = 0; e < nE; ++e) E[e] = ctx->Ecol[e];
+  if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
+  // incoming amplitudes a(E) = sqrt(mu/(2 pi K)) sum_m dR exp(i K R_m) g~(R_m)
+  std::vector<double> a2(nE);
+  for (int e = 0; e < nE; ++e) {
+    const double K = std::sqrt(2.0 * ctx->mu * ctx->Ecol[e]);
+    double re = 0, im = 0;
+    for (int i = 0; i < ctx->NR; ++i) {
+      re += std::cos(K * ctx->R[i]) * ctx->g_tilde[i];
+      im += std::sin(K * ctx->R[i]) * ctx->g_tilde[i];
+    }
+    const double s = std::sqrt(ctx->mu / (2.0 * M_PI * K)) * ctx->dR;
+    a2[e] = s * s * (re * re + im * im);
+  }
+  int st;
+  if ((st = dalloc(ctx, "flux", (size_t)nJ * nE * 8))) return st;
+  LK(launch_flux_reduce((const double*)dptr(ctx, "acc"), nJ, nE, (const long*)dptr(ctx, "accoff"),
+                        (const long*)dptr(ctx, "ncols"), (const long*)dptr(ctx, "ncut"),
+                        (double*)dptr(ctx, "flux"), ctx->stream));
+  std::vector<double> F((size_t)nJ * nE);
+  CK(cudaMemcpyAsync(F.data(), dptr(ctx, "flux"), F.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (Ptot) {
+    for (int iJ = 0; iJ < nJ; ++iJ)
+      for (int e = 0; e < nE; ++e) {
+        const double th = ctx->theta[(size_t)iJ * nE + e];
+        const double pref = 1.0 / (2.0 * M_PI * ctx->dE[iJ] * std::sin(th));
+        Ptot[(size_t)iJ * nE + e] = (2.0 * M_PI / ctx->m) * F[(size_t)iJ * nE + e] * pref * pref / a2[e];
+      }
+  }
+  if (Pinel && ctx->an.vmax >= 0) {
+    const int nv = ctx->an.vmax + 1, nj = ctx->an.jmax + 1, ne = ctx->nelec;
+    std::fill(Pinel, Pinel + (size_t)nJ * ne * nv * nj * nE, 0.0);
+    // channel columns only: per J a [2 nE x nchan_J] block of the accumulator
+    std::vector<std::vector<double>> chA(nJ);
+    for (int iJ = 0; iJ < nJ; ++iJ) {
+      const long nch = ctx->ncols[iJ] - 2 * ctx->ncut[iJ];
+      chA[iJ].assign((size_t)2 * nE * std::max(nch, 1L), 0.0);
+      if (nch <= 0) continue;
+      const double* src = (const double*)dptr(ctx, "acc") + ctx->accoff[iJ] + 2 * ctx->ncut[iJ];
+      CK(cudaMemcpy2DAsync(chA[iJ].data(), nch * 8, src, ctx->ncols[iJ] * 8, nch * 8, 2 * nE,
+                           cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < ctx->nchan; ++c) {
+      const int iJ = ctx->chan_iJ[c];
+      const long nch = ctx->ncols[iJ] - 2 * ctx->ncut[iJ];
+      const long lc = ctx->chan_col[c] - ctx->colbase[iJ] - 2 * ctx->ncut[iJ];
+      const double* A = chA[iJ].data();
+      for (int e = 0; e < nE; ++e) {
+        const double Etot = ctx->Ecol[e] + ctx->Ev0j0;
+        const double K2 = 2.0 * ctx->mu * (Etot - ctx->chan_eps[c]);
+        if (K2 <= 0) continue;
+        const double th = ctx->theta[(size_t)iJ * nE + e];
+        const double pref = 1.0 / (2.0 * M_PI * ctx->dE[iJ] * std::sin(th));
+        const double re = A[(size_t)e * nch + lc] * pref;
+        const double im = A[(size_t)(nE + e) * nch + lc] * pref;
+        const double s2 = 2.0 * M_PI * std::sqrt(K2) / ctx->mu * (re * re + im * im) / a2[e];
+        const size_t o = ((((size_t)iJ * ne + ctx->chan_lam[c]) * nv + ctx->chan_v[c]) * nj + ctx->chan_j[c]) * nE + e;
+        Pinel[o] += s2;
+      }
+    }
+  }
+  return MW3_OK;
+}
+
+int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
+  if (!ctx || !key) return MW3_ERR_BAD_ARG;
+  const std::string k(key);
+  auto drop_graphs = [&]() {
+    for (auto& g : ctx->graph)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+  };
+  if (k == "kb") {
+    if (v < 1 || v > 1024) return ctx->fail(MW3_ERR_BAD_ARG, "kb must be in 1..1024");
+    if (ctx->stage >= 5) return ctx->fail(MW3_ERR_STATE, "set kb before mw3_set_analysis");
+    ctx->tune.kb = (int)v;
+  } else if (k == "rows_pairs") {
+    if (v < 1 || v > 16) return ctx->fail(MW3_ERR_BAD_ARG, "rows_pairs must be in 1..16");
+    ctx->tune.rows_pairs = (int)v;
+  } else if (k == "cols_tile") {
+    if (v < 2 || v > 64 || v % 2) return ctx->fail(MW3_ERR_BAD_ARG, "cols_tile must be even, 2..64");
+    ctx->tune.cols_tile = (int)v;
+  } else if (k == "use_graph") {
+    ctx->tune.use_graph = v != 0;
+  } else if (k == "use_tc") {
+    if (v != 0 && ctx->precision != MW3_MIXED)
+      return ctx->fail(MW3_ERR_BAD_ARG, "use_tc needs MW3_MIXED");
+    ctx->tune.use_tc = v != 0;
+  } else {
+    return ctx->fail(MW3_ERR_BAD_ARG, "unknown tuning key " + k);
+  }
+  drop_graphs();
+  return MW3_OK;
+}
+
+long mw3_get_tuning(const mw3_ctx* ctx, const char* key) {
+  if (!ctx || !key) return MW3_ERR_BAD_ARG;
+  const std::string k(key);
+  if (k == "kb") return ctx->tune.kb;
+  if (k == "rows_pairs") return ctx->tune.rows_pairs;
+  if (k == "cols_tile") return ctx->tune.cols_tile;
+  if (k == "use_graph") return ctx->tune.use_graph;
+  if (k == "use_tc") return ctx->tune.use_tc;
+  return MW3_ERR_BAD_ARG;
+}
+
+int mw3_kernel_times(mw3_ctx* ctx, int enable, const char** names, double* ms, long* launches,
+                     int* count) {
+  if (!ctx) return MW3_ERR_BAD_ARG;
+  if (enable >= 0) {
+    ctx->timing = enable != 0;
+    std::fill(ctx->kms, ctx->kms + kNumKernels, 0.0);
+    std::fill(ctx->klaunch, ctx->klaunch + kNumKernels, 0L);
+  }
+  if (count) {
+    const int n = std::min(*count, kNumKernels);
+    for (int i = 0; i < n; ++i) {
+      if (names) names[i] = kKernelNames[i];
+      if (ms) ms[i] = ctx->kms[i];
+      if (launches) launches[i] = ctx->klaunch[i];
+    }
+    *count = n;
+  }
+  return MW3_OK;
+}
+
+int mw3_checkpoint_save(mw3_ctx* ctx, const char* path) {
+  if (!ctx || !path) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 5 || ctx->host_only) return ctx->fail(MW3_ERR_STATE, "nothing to save");
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  std::vector<double> q(n), qp(n), acc(ctx->acc_size);
+  int st = mw3_get_state(ctx, q.data(), qp.data());
+  if (st) return st;
+  CK(cudaMemcpyAsync(acc.data(), dptr(ctx, "acc"), acc.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::ofstream f(path, std::ios::binary);
+  if (!f) return ctx->fail(MW3_ERR_IO, std::string("cannot open ") + path);
+  const uint64_t magic = 0x4d57334350543031ULL;  // "MW3CPT01"
+  const uint64_t hdr[6] = {magic, (uint64_t)ctx->nblk, (uint64_t)ctx->npts, (uint64_t)ctx->acc_size,
+                           (uint64_t)ctx->iter, (uint64_t)ctx->precision};
+  f.write((const char*)hdr, sizeof(hdr));
+  f.write((const char*)q.data(), n * 8);
+  f.write((const char*)qp.data(), n * 8);
+  f.write((const char*)acc.data(), acc.size() * 8);
+  const uint64_t nt = ctx->norm_trace.size();
+  f.write((const char*)&nt, 8);
+  f.write((const char*)ctx->norm_trace.data(), nt * 8);
+  if (!f) return ctx->fail(MW3_ERR_IO, "write failed");
+  return MW3_OK;
+}
+
+int mw3_checkpoint_load(mw3_ctx* ctx, const char* path) {
+  if (!ctx || !path) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 5 || ctx->host_only) return ctx->fail(MW3_ERR_STATE, "set up the context first");
+  std::ifstream f(path, std::ios::binary);
+  if (!f) return ctx->fail(MW3_ERR_IO, std::string("cannot open ") + path);
+  uint64_t hdr[6];
+  f.read((char*)hdr, sizeof(hdr));
+  if (!f || hdr[0] != 0x4d57334350543031ULL || hdr[1] != (uint64_t)ctx->nblk ||
+      hdr[2] != (uint64_t)ctx->npts || hdr[3] != (uint64_t)ctx->acc_size ||
+      hdr[5] != (uint64_t)ctx->precision)
+    return ctx->fail(MW3_ERR_IO, "checkpoint does not match this configuration");
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  std::vector<double> q(n), qp(n), acc(ctx->acc_size);
+  f.read((char*)q.data(), n * 8);
+  f.read((char*)qp.data(), n * 8);
+  f.read((char*)acc.data(), acc.size() * 8);
+  uint64_t nt = 0;
+  f.read((char*)&nt, 8);
+  std::vector<double> tr(nt);
+  f.read((char*)tr.data(), nt * 8);
+  if (!f) return ctx->fail(MW3_ERR_IO, "truncated checkpoint");
+  int st = mw3_set_state(ctx, q.data(), qp.data());
+  if (st) return st;
+  CK(cudaMemcpyAsync(dptr(ctx, "acc"), acc.data(), acc.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  ctx->iter = (long)hdr[4];
+  long it = ctx->iter;
+  CK(cudaMemcpyAsync(dptr(ctx, "d_iter"), &it, 8, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->norm_trace = tr;
+  return MW3_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- FMA-chain peak probe
+namespace {
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_chain(T* out, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = (T)(threadIdx.x + i) * (T)1e-3;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+  }
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  if (s == (T)12345.678) out[threadIdx.x] = s;  // keeps the chains live
+}
+}  // namespace
+
+extern "C" int mw3_measure_peak(int device, int kind, double* tflops) {
+  if (!tflops || (kind != 0 && kind != 1)) return MW3_ERR_BAD_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return MW3_ERR_CUDA;
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, device);
+  void* out = nullptr;
+  if (cudaMalloc(&out, 1024 * 8) != cudaSuccess) return MW3_ERR_OOM;
+  const int blocks = prop.multiProcessorCount * 8;
+  const int iters = kind == 0 ? 1 << 12 : 1 << 16;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 0;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    if (kind == 0)
+      k_fma_chain<double><<<blocks, 256>>>((double*)out, iters, 0.999999, 1e-7);
+    else
+      k_fma_chain<float><<<blocks, 256>>>((float*)out, iters, 0.999999f, 1e-7f);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double flops = 2.0 * 8.0 * iters * (double)blocks * 256.0;
+    if (rep > 0) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return MW3_ERR_CUDA;
+  *tflops = best;
+  return MW3_OK;
+}

@@ -1,0 +1,422 @@
+// Angular (gamma) part of the Hamiltonian and the Chebyshev update (Section 2.1
+// items 3-5 and Section 2.2, Eq. wvp-k), CUDA-core path (FP64, and FP32 when the
+// tensor-core path is off).
+//
+// Forward: for every block (J, Omega, Lambda), c = T^Omega q as a GEMM
+// [ngamma x ngamma] x [ngamma x (nr NR)], T^Omega the orthonormal DVR -> FBR matrix.
+// Backward: h = (T^Omega)^T c', where the B operand c' is formed while it is loaded:
+//   c'_j = a_j c^Omega_j + bp_j c^(Omega+1)_j + bm_j c^(Omega-1)_j
+// (j^2/(2 m r^2) + l^2/(2 mu R^2) in the FBR, Coriolis coupling tridiagonal in
+// Omega, neighbour rows shifted by one because block Omega starts at j = Omega).
+// The epilogue adds the radial kinetic term t and the diabatic potential, scales
+// to H_s and applies the damped recursion in place:
+//   q_(k+1) = D (alpha H_s q_k - beta D q_(k-1)),  (alpha, beta) = (1, 0) for k = 0,
+//   (2, 1) after; D(r, R) = D_r(r) D_R(R).
+#include <cuda_runtime.h>
+
+#include "mw3_internal.h"
+
+namespace mw3 {
+
+constexpr int GBM = 64, GBN = 64, GBK = 16, GTM = 4, GTN = 4, GTHREADS = 256;
+
+// Generic SIMT tile: C[m, n] (+)= sum_k A(b, m, k) B(b, k, n), tiles 64 x 64 x 16,
+// 256 threads with 4 x 4 outputs each. Loaders return 0 outside the matrices.
+template <typename TA, typename TB, typename TC, class ALoad, class BLoad, class Epi>
+__global__ void __launch_bounds__(GTHREADS) k_gemm(int M, long N, int K, ALoad al, BLoad bl,
+                                                   Epi ep) {
+  __shared__ TA As[GBK][GBM + 1];
+  __shared__ TB Bs[GBK][GBN];
+  const int b = blockIdx.z;
+  if (!ep.active(b, blockIdx.x * (long)GBN)) return;
+  const int m0 = blockIdx.y * GBM;
+  const long n0 = (long)blockIdx.x * GBN;
+  const int tx = threadIdx.x % (GBN / GTN);   // 16
+  const int ty = threadIdx.x / (GBN / GTN);   // 16
+  TC acc[GTM][GTN];
+#pragma unroll
+  for (int i = 0; i < GTM; ++i)
+#pragma unroll
+    for (int j = 0; j < GTN; ++j) acc[i][j] = (TC)0;
+
+  for (int k0 = 0; k0 < K; k0 += GBK) {
+    // A tile: 64 x 16, k fastest across threads
+    for (int e = threadIdx.x; e < GBM * GBK; e += GTHREADS) {
+      const int mm = e / GBK, kk = e - mm * GBK;
+      As[kk][mm] = (m0 + mm < M && k0 + kk < K) ? al(b, m0 + mm, k0 + kk) : (TA)0;
+    }
+    // B tile: 16 x 64, n fastest across threads (coalesced)
+    for (int e = threadIdx.x; e < GBK * GBN; e += GTHREADS) {
+      const int kk = e / GBN, nn = e - kk * GBN;
+      Bs[kk][nn] = (k0 + kk < K && n0 + nn < N) ? bl(b, k0 + kk, n0 + nn) : (TB)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      TC a[GTM], bb[GTN];
+#pragma unroll
+      for (int i = 0; i < GTM; ++i) a[i] = (TC)As[kk][ty + i * (GBM / GTM)];
+#pragma unroll
+      for (int j = 0; j < GTN; ++j) bb[j] = (TC)Bs[kk][tx + j * (GBN / GTN)];
+#pragma unroll
+      for (int i = 0; i < GTM; ++i)
+#pragma unroll
+        for (int j = 0; j < GTN; ++j) acc[i][j] += a[i] * bb[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < GTM; ++i) {
+    const int m = m0 + ty + i * (GBM / GTM);
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < GTN; ++j) {
+      const long n = n0 + tx + j * (GBN / GTN);
+      if (n < N) ep(b, m, n, acc[i][j]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ loaders
+template <typename T>
+struct LoadT {   // A(b, m, k) = Tmat[omega(b)][m][k]
+  const T* T_;
+  const DevBlock* blk;
+  int ng;
+  __device__ T operator()(int b, int m, int k) const {
+    return T_[((long)blk[b].omega * ng + m) * ng + k];
+  }
+};
+
+template <typename T>
+struct LoadQ {   // B(b, k, n) = q[b][k][n]
+  const T* q;
+  long npts, ncol;
+  __device__ T operator()(int b, int k, long n) const { return q[b * npts + k * ncol + n]; }
+};
+
+template <typename T>
+struct LoadFBR {  // B(b, j, col) = c'_j(col) of block b
+  const T* c;
+  const DevBlock* blk;
+  const T* coef;
+  const T* fr;
+  const T* fR;
+  T erot;
+  long npts, ncol;
+  int NR, ng;
+  __device__ T operator()(int b, int i, long col) const {
+    const DevBlock B = blk[b];
+    const int kr = (int)(col / NR);
+    const int m = (int)(col - (long)kr * NR);
+    const T* cf = coef + (long)B.coef * kCoefRows * ng;
+    const T g = fmin(fR[m], cf[4 * ng + i]);
+    const T a = fmin(cf[i] * fr[kr], erot) + g * cf[ng + i];
+    T v = a * c[b * npts + i * ncol + col];
+    if (B.up >= 0 && i >= 1) v += g * cf[2 * ng + i] * c[B.up * npts + (i - 1) * ncol + col];
+    if (B.dn >= 0 && i + 1 < ng) v += g * cf[3 * ng + i] * c[B.dn * npts + (i + 1) * ncol + col];
+    return v;
+  }
+};
+
+// ---------------------------------------------------------------- epilogues
+template <typename T>
+struct EpiStore {
+  T* out;
+  long npts, ncol;
+  __device__ bool active(int, long) const { return true; }
+  __device__ void operator()(int b, int m, long n, T v) const { out[b * npts + m * ncol + n] = v; }
+};
+
+// mode 0: damped recursion in place into qkm1; mode 1: write H_s q into out.
+template <typename T>
+struct EpiUpdate {
+  const T* qk;
+  T* qkm1;
+  const T* t;
+  const T* V;
+  const DevBlock* blk;
+  const T* DR;
+  const T* Dr;
+  const DevJ* dj;
+  T alpha, beta;
+  long npts, ncol;
+  int NR, nelec, mode;
+  T* out;
+  __device__ bool active(int, long) const { return true; }
+  __device__ void operator()(int b, int n, long col, T h) const {
+    const DevBlock B = blk[b];
+    const long off = (long)n * ncol + col;
+    const long idx = b * npts + off;
+    const T qv = qk[idx];
+    T vq = 0;
+    for (int lp = 0; lp < nelec; ++lp)
+      vq += V[(long)(B.lam * nelec + lp) * npts + off] * qk[(long)(B.base + lp) * npts + off];
+    const DevJ J = dj[B.iJ];
+    const T hs = (h + t[idx] + vq) * (T)J.invdE - (T)J.e0s * qv;
+    if (mode == 1) {
+      out[idx] = hs;
+      return;
+    }
+    const int kr = (int)(col / NR);
+    const int m = (int)(col - (long)kr * NR);
+    const T D = DR[m] * Dr[kr];
+    qkm1[idx] = D * (alpha * hs - beta * D * qkm1[idx]);
+  }
+};
+
+template <typename real>
+cudaError_t launch_gamma_forward(const real* q, real* c, const real* T, const DevBlock* blocks,
+                                 int nblk, int ng, long ncol, cudaStream_t st) {
+  const long npts = (long)ng * ncol;
+  dim3 grid((unsigned)((ncol + GBN - 1) / GBN), (unsigned)((ng + GBM - 1) / GBM), (unsigned)nblk);
+  k_gemm<real, real, real><<<grid, GTHREADS, 0, st>>>(
+      ng, ncol, ng, LoadT<real>{T, blocks, ng}, LoadQ<real>{q, npts, ncol},
+      EpiStore<real>{c, npts, ncol});
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_gamma_backward_update(const real* c, const real* Tt, const DevBlock* blocks,
+                                         int nblk, int ng, long ncol, int NR, const real* coef,
+                                         const real* fr, const real* fR, real erot,
+                                         const real* qk, real* qkm1, const real* t,
+                                         const real* V, int nelec, const real* DR,
+                                         const real* Dr, const DevJ* dj, real alpha, real beta,
+                                         int mode, real* out, cudaStream_t st) {
+  const long npts = (long)ng * ncol;
+  dim3 grid((unsigned)((ncol + GBN - 1) / GBN), (unsigned)((ng + GBM - 1) / GBM), (unsigned)nblk);
+  k_gemm<real, real, real><<<grid, GTHREADS, 0, st>>>(
+      ng, ncol, ng, LoadT<real>{Tt, blocks, ng},
+      LoadFBR<real>{c, blocks, coef, fr, fR, erot, npts, ncol, NR, ng},
+      EpiUpdate<real>{qk, qkm1, t, V, blocks, DR, Dr, dj, alpha, beta, npts, ncol, NR, nelec,
+                      mode, out});
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ energy sums
+// Ph[iJ][row][s]: rows 0..nE-1 hold (2 - delta_k0) cos(k theta), rows nE..2nE-1
+// hold -(2 - delta_k0) sin(k theta), k = iteration of ring slot s (c_k = (2 -
+// delta_k0) exp(-i k theta)); slots s >= nvalid are zero.
+template <typename real>
+__global__ void k_phases(const double* __restrict__ theta, int nJ, int nE, int kb, int nvalid,
+                         const long* __restrict__ d_iter, real* __restrict__ ph) {
+  const long total = (long)nJ * nE * kb;
+  const long k0 = *d_iter;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int s = (int)(e % kb);
+    const long je = e / kb;
+    const int iJ = (int)(je / nE);
+    const int ie = (int)(je - (long)iJ * nE);
+    real cr = 0, ci = 0;
+    if (s < nvalid) {
+      const long k = k0 + s;
+      const double w = (k == 0) ? 1.0 : 2.0;
+      double sn, cs;
+      sincos((double)k * theta[je], &sn, &cs);
+      cr = (real)(w * cs);
+      ci = (real)(-w * sn);
+    }
+    real* P = ph + (long)iJ * 2 * nE * kb;
+    P[(long)ie * kb + s] = cr;
+    P[(long)(nE + ie) * kb + s] = ci;
+  }
+}
+
+template <typename real>
+struct LoadPh {
+  const real* ph;
+  int nE2, kb;
+  __device__ real operator()(int iJ, int m, int k) const { return ph[((long)iJ * nE2 + m) * kb + k]; }
+};
+
+template <typename real>
+struct LoadCut {   // columns beyond J's own range read as zero (never past the ring)
+  const real* cut;
+  long ncut_total;
+  const long* colbase;
+  const long* ncols;
+  __device__ real operator()(int iJ, int k, long n) const {
+    return n < ncols[iJ] ? cut[(long)k * ncut_total + colbase[iJ] + n] : (real)0;
+  }
+};
+
+template <typename TC>
+struct EpiAcc {
+  double* acc;
+  const long* accoff;
+  const long* ncols;
+  __device__ bool active(int iJ, long n0) const { return n0 < ncols[iJ]; }
+  __device__ void operator()(int iJ, int m, long n, TC v) const {
+    if (n < ncols[iJ]) acc[accoff[iJ] + (long)m * ncols[iJ] + n] += (double)v;
+  }
+};
+
+template <typename real>
+cudaError_t launch_phases(const double* theta, int nJ, int nE, int kb, int nvalid,
+                          const long* d_iter, real* ph, cudaStream_t st) {
+  const long total = (long)nJ * nE * kb;
+  const int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  k_phases<real><<<grid, 256, 0, st>>>(theta, nJ, nE, kb, nvalid, d_iter, ph);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_sums_flush(const real* ph, const real* cut, long ncut_total, int kb, int nJ,
+                              int nE, const long* colbase, const long* ncols,
+                              const long* accoff, long max_cols, double* acc,
+                              cudaStream_t st) {
+  dim3 grid((unsigned)((max_cols + GBN - 1) / GBN), (unsigned)((2 * nE + GBM - 1) / GBM),
+            (unsigned)nJ);
+  // M = 2 nE rows, K = kb ring slots, N = columns of each J (checked by the epilogue)
+  k_gemm<real, real, real><<<grid, GTHREADS, 0, st>>>(
+      2 * nE, max_cols, kb, LoadPh<real>{ph, 2 * nE, kb}, LoadCut<real>{cut, ncut_total, colbase, ncols},
+      EpiAcc<real>{acc, accoff, ncols});
+  return cudaGetLastError();
+}
+
+__global__ void k_advance(long* d_iter, long n) { *d_iter += n; }
+
+cudaError_t launch_advance(long* d_iter, long n, cudaStream_t st) {
+  k_advance<<<1, 1, 0, st>>>(d_iter, n);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- channel projections
+// cut_slot[chan_col[c]] = (k >= kmin) ? sum_(n,kr) P[c][n][kr] qcol[block(c)][n][kr] : 0
+template <typename real>
+__global__ void __launch_bounds__(256) k_channels(const real* __restrict__ qcol,
+                                                  const real* __restrict__ P,
+                                                  const int* __restrict__ chan_block,
+                                                  const int* __restrict__ chan_col, int ncolq,
+                                                  const long* __restrict__ d_iter, int slot,
+                                                  long kmin, real* __restrict__ cut) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  const real* p = P + (long)c * ncolq;
+  const real* x = qcol + (long)chan_block[c] * ncolq;
+  double s = 0;
+  for (int i = threadIdx.x; i < ncolq; i += blockDim.x) s += (double)p[i] * (double)x[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const long k = *d_iter + slot;
+    cut[chan_col[c]] = (k >= kmin) ? (real)red[0] : (real)0;
+  }
+}
+
+template <typename real>
+cudaError_t launch_channels(const real* qcol, const real* P, const int* chan_block,
+                            const int* chan_col, int nchan, int ncolq, const long* d_iter,
+                            int slot, long kmin, real* cut_slot, cudaStream_t st) {
+  if (nchan <= 0) return cudaSuccess;
+  k_channels<real><<<nchan, 256, 0, st>>>(qcol, P, chan_block, chan_col, ncolq, d_iter, slot,
+                                          kmin, cut_slot);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- norms
+// partial[iJ][chunk] = sum of squares over a fixed contiguous chunk of J's range;
+// out[iJ] = ordered sum of the partials (deterministic).
+template <typename real>
+__global__ void __launch_bounds__(256) k_norm_partial(const real* __restrict__ q,
+                                                      const long* __restrict__ J_begin,
+                                                      int nchunk, double* __restrict__ partial) {
+  __shared__ double red[256];
+  const int iJ = blockIdx.y;
+  const long beg = J_begin[iJ], end = J_begin[iJ + 1];
+  const long len = end - beg;
+  const long per = (len + nchunk - 1) / nchunk;
+  const long a = beg + per * blockIdx.x;
+  const long z = (a + per < end) ? a + per : end;
+  double s = 0;
+  for (long i = a + threadIdx.x; i < z; i += blockDim.x) {
+    const double v = (double)q[i];
+    s += v * v;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(long)iJ * nchunk + blockIdx.x] = red[0];
+}
+
+__global__ void k_norm_final(const double* __restrict__ partial, int nchunk, double* out) {
+  const int iJ = blockIdx.x;
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int i = 0; i < nchunk; ++i) s += partial[(long)iJ * nchunk + i];
+    out[iJ] = s;
+  }
+}
+
+template <typename real>
+cudaError_t launch_norms(const real* q, const long* J_begin, int nJ, double* partial,
+                         int nchunk, double* out, cudaStream_t st) {
+  k_norm_partial<real><<<dim3(nchunk, nJ), 256, 0, st>>>(q, J_begin, nchunk, partial);
+  k_norm_final<<<nJ, 32, 0, st>>>(partial, nchunk, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- flux reduce
+// out[iJ][e] = sum_p Re A_psi Im A_dpsi - Im A_psi Re A_dpsi over J's cut points,
+// with A rows e (real part) and nE + e (imaginary part).
+__global__ void __launch_bounds__(256) k_flux_reduce(const double* __restrict__ acc, int nE,
+                                                     const long* __restrict__ accoff,
+                                                     const long* __restrict__ ncols,
+                                                     const long* __restrict__ ncut,
+                                                     double* __restrict__ out) {
+  __shared__ double red[256];
+  const int e = blockIdx.x;
+  const int iJ = blockIdx.y;
+  const long nc = ncols[iJ], np = ncut[iJ];
+  const double* re = acc + accoff[iJ] + (long)e * nc;
+  const double* im = acc + accoff[iJ] + (long)(nE + e) * nc;
+  double s = 0;
+  for (long p = threadIdx.x; p < np; p += blockDim.x) s += re[p] * im[np + p] - im[p] * re[np + p];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(long)iJ * nE + e] = red[0];
+}
+
+cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* accoff,
+                               const long* ncols, const long* ncut, double* out,
+                               cudaStream_t st) {
+  k_flux_reduce<<<dim3(nE, nJ), 256, 0, st>>>(acc, nE, accoff, ncols, ncut, out);
+  return cudaGetLastError();
+}
+
+#define MW3_INST(real)                                                                        \
+  template cudaError_t launch_gamma_forward<real>(const real*, real*, const real*,            \
+                                                  const DevBlock*, int, int, long,            \
+                                                  cudaStream_t);                              \
+  template cudaError_t launch_gamma_backward_update<real>(                                    \
+      const real*, const real*, const DevBlock*, int, int, long, int, const real*,            \
+      const real*, const real*, real, const real*, real*, const real*, const real*, int,      \
+      const real*, const real*, const DevJ*, real, real, int, real*, cudaStream_t);           \
+  template cudaError_t launch_phases<real>(const double*, int, int, int, int, const long*,    \
+                                           real*, cudaStream_t);                              \
+  template cudaError_t launch_sums_flush<real>(const real*, const real*, long, int, int, int, \
+                                               const long*, const long*, const long*, long,   \
+                                               double*, cudaStream_t);                        \
+  template cudaError_t launch_channels<real>(const real*, const real*, const int*,            \
+                                             const int*, int, int, const long*, int, long,    \
+                                             real*, cudaStream_t);                            \
+  template cudaError_t launch_norms<real>(const real*, const long*, int, double*, int,        \
+                                          double*, cudaStream_t);
+
+MW3_INST(double)
+MW3_INST(float)
+
+}  // namespace mw3

@@ -1,0 +1,284 @@
+// Host-side set-up mathematics of libmw3 (FP64): quadratures, bases, the
+// symmetric eigensolver for the diatomic states, and the built-in LEPS surface.
+// These run once per set-up call; the propagation itself runs on the device.
+#include "mw3_host.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace mw3 {
+
+// Gauss-Legendre nodes (ascending) and weights by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));  // i-th largest root estimate
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      if (n == 1) p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      const double pn = (n == 0) ? 1.0 : p1;
+      const double pnm1 = (n == 1) ? 1.0 : p0;
+      dp = n * (z * pn - pnm1) / (z * z - 1.0);
+      const double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16 && it > 2) break;
+    }
+    // final derivative at the converged root
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    const double pnm1 = (n == 1) ? 1.0 : p0;
+    dp = n * (z * p1 - pnm1) / (z * z - 1.0);
+    const double wi = 2.0 / ((1.0 - z * z) * dp * dp);
+    x[n - 1 - i] = z;
+    x[i] = -z;
+    w[i] = w[n - 1 - i] = wi;
+  }
+  if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+// Normalised associated Legendre functions (Condon-Shortley phase), j = om..jmax,
+// at points x: out[(j - om) * npts + p].
+void norm_assoc_legendre(int jmax, int om, const std::vector<double>& x,
+                         std::vector<double>& out) {
+  const int np = (int)x.size();
+  const int nj = jmax - om + 1;
+  out.assign((size_t)nj * np, 0.0);
+  double c = 1.0 / std::sqrt(2.0);
+  for (int m = 1; m <= om; ++m) c *= -std::sqrt((2.0 * m + 1.0) / (2.0 * m));
+  for (int p = 0; p < np; ++p) {
+    const double xx = x[p];
+    const double s2 = 1.0 - xx * xx;
+    double pm2 = c * std::pow(s2, 0.5 * om);
+    out[p] = pm2;
+    if (nj == 1) continue;
+    double pm1 = std::sqrt(2.0 * om + 3.0) * xx * pm2;
+    out[(size_t)np + p] = pm1;
+    double a_prev = std::sqrt((4.0 * (om + 1.0) * (om + 1.0) - 1.0) /
+                              ((om + 1.0) * (om + 1.0) - (double)om * om));
+    for (int j = om + 2; j <= jmax; ++j) {
+      const double a = std::sqrt((4.0 * j * j - 1.0) / ((double)j * j - (double)om * om));
+      const double pj = a * (xx * pm1 - pm2 / a_prev);
+      out[(size_t)(j - om) * np + p] = pj;
+      pm2 = pm1;
+      pm1 = pj;
+      a_prev = a;
+    }
+  }
+}
+
+// T^Omega: rows P-bar_j^Omega(x_k) sqrt(w_k), j = om..om+n-1, orthonormalised by
+// modified Gram-Schmidt in increasing j (two passes). Row-major n x n.
+void fbr_matrix(int om, int n, const std::vector<double>& x, const std::vector<double>& w,
+                std::vector<double>& T) {
+  std::vector<double> P;
+  norm_assoc_legendre(om + n - 1, om, x, P);
+  T.assign((size_t)n * n, 0.0);
+  std::vector<double> v(n);
+  for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < n; ++k) v[k] = P[(size_t)i * n + k] * std::sqrt(w[k]);
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int p = 0; p < i; ++p) {
+        double d = 0;
+        for (int k = 0; k < n; ++k) d += T[(size_t)p * n + k] * v[k];
+        for (int k = 0; k < n; ++k) v[k] -= d * T[(size_t)p * n + k];
+      }
+    }
+    double nn = 0;
+    for (int k = 0; k < n; ++k) nn += v[k] * v[k];
+    nn = 1.0 / std::sqrt(nn);
+    for (int k = 0; k < n; ++k) T[(size_t)i * n + k] = v[k] * nn;
+  }
+}
+
+// Symmetric eigen-decomposition: Householder reduction to tridiagonal form, then
+// the implicit QL iteration with shifts; eigenvalues ascending, eigenvectors in the
+// columns of Z (row-major n x n).
+void symmetric_eigen(int n, const std::vector<double>& Ain, std::vector<double>& evals,
+                     std::vector<double>& Z) {
+  std::vector<double> A = Ain;
+  Z.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
+  std::vector<double> v(n), p(n), qv(n), zv(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;  // length of the column below the diagonal
+    double nrm = 0;
+    for (int i = k + 1; i < n; ++i) nrm += A[(size_t)i * n + k] * A[(size_t)i * n + k];
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0) continue;
+    const double x0 = A[(size_t)(k + 1) * n + k];
+    const double alpha = (x0 > 0) ? -nrm : nrm;
+    std::fill(v.begin(), v.end(), 0.0);
+    for (int i = k + 1; i < n; ++i) v[i] = A[(size_t)i * n + k];
+    v[k + 1] -= alpha;
+    double vn = 0;
+    for (int i = k + 1; i < n; ++i) vn += v[i] * v[i];
+    vn = std::sqrt(vn);
+    if (vn == 0.0) continue;
+    for (int i = k + 1; i < n; ++i) v[i] /= vn;
+    (void)m;
+    // A <- H A H with H = I - 2 v v^T (acting on indices >= k)
+    for (int i = k; i < n; ++i) {
+      double s = 0;
+      for (int j = k + 1; j < n; ++j) s += A[(size_t)i * n + j] * v[j];
+      p[i] = s;
+    }
+    double K = 0;
+    for (int i = k + 1; i < n; ++i) K += v[i] * p[i];
+    for (int i = k; i < n; ++i) qv[i] = p[i] - K * v[i];
+    for (int i = k; i < n; ++i)
+      for (int j = k; j < n; ++j)
+        A[(size_t)i * n + j] -= 2.0 * (v[i] * qv[j] + qv[i] * v[j]);
+    // Z <- Z H
+    for (int i = 0; i < n; ++i) {
+      double s = 0;
+      for (int j = k + 1; j < n; ++j) s += Z[(size_t)i * n + j] * v[j];
+      zv[i] = s;
+    }
+    for (int i = 0; i < n; ++i)
+      for (int j = k + 1; j < n; ++j) Z[(size_t)i * n + j] -= 2.0 * zv[i] * v[j];
+  }
+  std::vector<double> d(n), e(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = A[(size_t)i * n + i];
+  for (int i = 0; i + 1 < n; ++i) e[i] = A[(size_t)(i + 1) * n + i];
+  // implicit QL; e[i] couples d[i] and d[i+1]
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    int m;
+    do {
+      for (m = l; m + 1 < n; ++m) {
+        const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (std::fabs(e[m]) <= 1e-17 * dd) break;
+      }
+      if (m != l) {
+        if (++iter > 200) break;
+        double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+        double r = std::hypot(g, 1.0);
+        g = d[m] - d[l] + e[l] / (g + (g >= 0 ? std::fabs(r) : -std::fabs(r)));
+        double s = 1.0, c = 1.0, pp = 0.0;
+        int i;
+        bool deflated = false;
+        for (i = m - 1; i >= l; --i) {
+          double f = s * e[i];
+          const double b = c * e[i];
+          r = std::hypot(f, g);
+          e[i + 1] = r;
+          if (r == 0.0) {
+            d[i + 1] -= pp;
+            e[m] = 0.0;
+            deflated = true;
+            break;
+          }
+          s = f / r;
+          c = g / r;
+          g = d[i + 1] - pp;
+          r = (d[i] - g) * s + 2.0 * c * b;
+          pp = s * r;
+          d[i + 1] = g + pp;
+          g = c * r - b;
+          for (int kk = 0; kk < n; ++kk) {
+            f = Z[(size_t)kk * n + i + 1];
+            Z[(size_t)kk * n + i + 1] = s * Z[(size_t)kk * n + i] + c * f;
+            Z[(size_t)kk * n + i] = c * Z[(size_t)kk * n + i] - s * f;
+          }
+        }
+        if (deflated) continue;
+        d[l] -= pp;
+        e[l] = g;
+        e[m] = 0.0;
+      }
+    } while (m != l);
+  }
+  // sort ascending
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return d[a] < d[b]; });
+  evals.resize(n);
+  std::vector<double> Zs((size_t)n * n);
+  for (int c2 = 0; c2 < n; ++c2) {
+    evals[c2] = d[order[c2]];
+    for (int i = 0; i < n; ++i) Zs[(size_t)i * n + c2] = Z[(size_t)i * n + order[c2]];
+  }
+  Z.swap(Zs);
+}
+
+// Orthonormal DST-II row j (1-based) at node i (1-based).
+double dst2(int N, int j, int i) {
+  double v = std::sqrt(2.0 / N) * std::sin(j * M_PI * (i - 0.5) / N);
+  if (j == N) v /= std::sqrt(2.0);
+  return v;
+}
+
+// Weights w, dw with f(x) = w . q and f'(x) = dw . q for a sine-DVR vector q:
+// f = sum_j s_j a_j phi_j, a = S q, phi_j(x) = sqrt(2/L) sin(k_j (x - xa)).
+void sine_interpolation_weights(double xa, double xb, int N, double x, std::vector<double>& w,
+                                std::vector<double>& dw) {
+  const double L = xb - xa;
+  w.assign(N, 0.0);
+  dw.assign(N, 0.0);
+  for (int j = 1; j <= N; ++j) {
+    const double k = j * M_PI / L;
+    const double s = (j == N) ? 1.0 / std::sqrt(2.0) : 1.0;
+    const double ph = std::sqrt(2.0 / L) * std::sin(k * (x - xa));
+    const double dph = std::sqrt(2.0 / L) * k * std::cos(k * (x - xa));
+    for (int i = 1; i <= N; ++i) {
+      const double S = dst2(N, j, i);
+      w[i - 1] += S * s * ph;
+      dw[i - 1] += S * s * dph;
+    }
+  }
+}
+
+}  // namespace mw3
+
+// --------------------------------------------------------------- LEPS surface
+extern "C" int mw3_pes_leps(double r, double R, double cosg, double* potmat, void* user) {
+  const mw3_leps_params* P = static_cast<const mw3_leps_params*>(user);
+  if (!P || !potmat) return -1;
+  const double mB = P->masses[1], mC = P->masses[2];
+  const double MBC = mB + mC;
+  const double sB = mC * r / MBC, sC = mB * r / MBC;
+  double rab = std::sqrt(std::max(R * R + sB * sB + 2.0 * R * sB * cosg, 0.0));
+  double rac = std::sqrt(std::max(R * R + sC * sC - 2.0 * R * sC * cosg, 0.0));
+  double rbc = r;
+  rab = std::max(rab, 0.25);
+  rac = std::max(rac, 0.25);
+  rbc = std::max(rbc, 0.25);
+  auto qj = [&](double rr, double& Q, double& Jx) {
+    const double e1 = std::exp(-P->beta * (rr - P->re));
+    const double singlet = P->D * (e1 * e1 - 2.0 * e1);
+    const double triplet = 0.5 * P->D * (e1 * e1 + 2.0 * e1);
+    const double den = 2.0 * (1.0 + P->delta);
+    Q = (singlet * (1.0 + P->delta) + triplet * (1.0 - P->delta)) / den;
+    Jx = (singlet * (1.0 + P->delta) - triplet * (1.0 - P->delta)) / den;
+  };
+  double Qab, Jab, Qbc, Jbc, Qac, Jac;
+  qj(rab, Qab, Jab);
+  qj(rbc, Qbc, Jbc);
+  qj(rac, Qac, Jac);
+  const double ex = std::sqrt(0.5 * ((Jab - Jbc) * (Jab - Jbc) + (Jbc - Jac) * (Jbc - Jac) +
+                                     (Jac - Jab) * (Jac - Jab)));
+  const double v11 = Qab + Qbc + Qac - ex + P->D;
+  if (!P->two_state) {
+    potmat[0] = v11;
+    return 0;
+  }
+  const double v22 = v11 + P->bump * std::exp(-(r - P->bump_r0) * (r - P->bump_r0) / P->bump_w2);
+  const double v12 = P->coup * std::exp(-((R - P->coup_R0) * (R - P->coup_R0) +
+                                          (r - P->coup_r0) * (r - P->coup_r0)) / P->coup_w2);
+  potmat[0] = v11;
+  potmat[1] = v12;
+  potmat[2] = v12;
+  potmat[3] = v22;
+  return 0;
+}

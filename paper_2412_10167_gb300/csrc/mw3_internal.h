@@ -1,0 +1,118 @@
+// Internal declarations of libmw3: device-side tables, kernel launchers and the
+// context. Everything here is private to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mw3.h"
+
+namespace mw3 {
+
+// ---------------------------------------------------------------- small complex
+template <typename T>
+struct cpx {
+  T x, y;
+};
+
+// ------------------------------------------------------------------ FFT plan
+// Mixed-radix Stockham plan for a complex transform of length N = 2^a 3^b 5^c.
+struct FFTPlan {
+  int N;
+  int nstages;
+  int radix[16];
+};
+
+// One block (J, Omega, Lambda) of the state, as seen by the kernels.
+struct DevBlock {
+  int iJ;      // index of J in the batch
+  int omega;   // helicity
+  int lam;     // electronic state
+  int up;      // block index of (J, Omega+1, Lambda), -1 if absent
+  int dn;      // block index of (J, Omega-1, Lambda), -1 if absent
+  int base;    // block index of (J, Omega, Lambda = 0)
+  int coef;    // index of the (J, Omega) angular coefficient set
+  int cutcol;  // first column of this block's psi(r*) values in the cut ring
+};
+
+// Angular coefficient set of one (J, Omega): five rows of ngamma values, for
+// row i (j = Omega + i):
+//   [0] j(j+1)          [1] J(J+1) + j(j+1) - 2 Omega^2
+//   [2] -lambda+_(J Omega) lambda+_(j Omega) kappa  (0 if no Omega+1 partner)
+//   [3] -lambda-_(J Omega) lambda-_(j Omega) kappa  (0 if no Omega-1 partner)
+//   [4] E_rot / lmax2(j)  (the g_j cap; 1e300 when lmax2 = 0)
+constexpr int kCoefRows = 5;
+
+// Per-J scalars used in the update epilogue.
+struct DevJ {
+  double e0s;     // E0 / dE
+  double invdE;   // 1 / dE
+};
+
+// Launch shapes chosen by the tuner (defaults in the context).
+struct Tuning {
+  int rows_pairs;   // line pairs per CTA of the R-direction kinetic kernel
+  int cols_tile;    // columns per CTA of the r-direction kinetic kernel (even)
+  int kb;           // Chebyshev iterations per energy-sum flush (ring depth)
+  int use_graph;    // capture full chunks as CUDA graphs
+  int use_tc;       // tensor-core gamma transform (mixed precision only)
+};
+
+// --------------------------------------------------------------- launchers
+// All launchers enqueue on `st` and return cudaGetLastError().
+template <typename real>
+cudaError_t launch_kinetic_rows(const real* q, real* t, long nrows, const FFTPlan& plan,
+                                const void* tw, const void* ph, const real* lam, int pairs,
+                                cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_kinetic_cols(const real* q, real* t, long nplanes, int nr, int NR,
+                                const FFTPlan& plan, const void* tw, const void* ph,
+                                const real* lam, int ctile, int ng,
+                                // flux cut
+                                const real* wpsi, const real* wdpsi, real* cut_slot,
+                                const DevBlock* blocks, const int* ncut_J,
+                                // column at R_inf for channel projections
+                                int m_inf, real* qcol, cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_gamma_forward(const real* q, real* c, const real* T, const DevBlock* blocks,
+                                 int nblk, int ng, long ncol, cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_gamma_backward_update(const real* c, const real* Tt, const DevBlock* blocks,
+                                         int nblk, int ng, long ncol, int NR,
+                                         const real* coef, const real* fr, const real* fR,
+                                         real erot, const real* qk, real* qkm1, const real* t,
+                                         const real* V, int nelec, const real* DR,
+                                         const real* Dr, const DevJ* dj, real alpha,
+                                         real beta, int mode, real* out, cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_channels(const real* qcol, const real* P, const int* chan_block,
+                            const int* chan_col, int nchan, int ncolq, const long* d_iter,
+                            int slot, long kmin, real* cut_slot, cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_norms(const real* q, const long* J_begin, int nJ, double* partial,
+                         int nchunk, double* out, cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_phases(const double* theta, int nJ, int nE, int kb, int nvalid,
+                          const long* d_iter, real* ph, cudaStream_t st);
+
+template <typename real>
+cudaError_t launch_sums_flush(const real* ph, const real* cut, long ncut_total, int kb,
+                              int nJ, int nE, const long* colbase, const long* ncols,
+                              const long* accoff, long max_cols, double* acc, cudaStream_t st);
+
+cudaError_t launch_advance(long* d_iter, long n, cudaStream_t st);
+
+cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* accoff,
+                               const long* ncols, const long* ncut, double* out,
+                               cudaStream_t st);
+
+}  // namespace mw3

@@ -1,0 +1,207 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (written from the arithmetic):
+  * FP64 path: the operator agrees with the oracle to 1e-12 of max|H_s q| (different
+    summation orders only); after N iterations q_N agrees to 1e-10 relative (l2),
+    and probabilities to 1e-8 absolute.
+  * Mixed path (FP32 state): one H_s application to 2e-6 of max|H_s q| (FP32
+    rounding of the FFT and gamma transforms, sum over ~log N + n_gamma terms).
+"""
+import copy
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import propagate as P
+from oracle.hamiltonian import GridHamiltonian
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def mw3():
+    from paper_2412_10167_gb300 import mw3 as m
+    return m
+
+
+_ORACLE = {}
+
+
+def oracle_run(name, cfg, nsteps):
+    key = (name, nsteps)
+    if key not in _ORACLE:
+        _ORACLE[key] = P.propagate(cfg, nsteps=nsteps)
+    return _ORACLE[key]
+
+
+@pytest.mark.parametrize("name", list(W.SMALL))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_apply_hs_matches_oracle(name, prec):
+    cfg = W.SMALL[name]
+    pr = mw3().Propagator(cfg, precision=prec)
+    H = GridHamiltonian(cfg)
+    q = W.random_state(H.shape, 2412)
+    ref = H.apply_Hs(q)
+    got = pr.apply_hs(q)
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+    pr.close()
+
+
+@pytest.mark.parametrize("name", list(W.SMALL))
+def test_propagation_fp64_parity(name):
+    cfg = W.SMALL[name]
+    N = cfg["steps"]
+    ref = oracle_run(name, cfg, N)
+    pr = mw3().Propagator(cfg, precision="fp64")
+    pr.propagate(N)
+    q, qp = pr.state()
+    rel = np.linalg.norm(q - ref["q"]) / np.linalg.norm(ref["q"])
+    relp = np.linalg.norm(qp - ref["q_prev"]) / np.linalg.norm(ref["q_prev"])
+    assert rel < 1e-10 and relp < 1e-10, (rel, relp)
+    E, Pt, Pin = pr.probabilities()
+    np.testing.assert_allclose(E, ref["Ecol"], rtol=1e-15)
+    assert np.max(np.abs(Pt - ref["P_total"])) < 1e-8
+    # channel probabilities, summed over Omega, per (J, Lambda, v, j)
+    for (iJ, L, v, j), val in ref["P_inel"].items():
+        assert np.max(np.abs(Pin[iJ, L, v, j] - val)) < 1e-8, (iJ, L, v, j)
+    # norm trace ||q_k||^2, k = 1..N
+    tr = pr.norm_trace()
+    bj = ref["H"].block_J_index()
+    assert tr.shape == (N, len(cfg["J"]))
+    np.testing.assert_allclose(tr.sum(axis=1), ref["norms"][1:], rtol=1e-10)
+    pr.close()
+
+
+def test_mixed_probabilities_close_to_fp64():
+    """Mixed path on config 1: |dP| stays within 1e-4 of the FP64 oracle."""
+    cfg = W.C1
+    ref = oracle_run("c1", cfg, cfg["steps"])
+    pr = mw3().Propagator(cfg, precision="mixed")
+    pr.propagate(cfg["steps"])
+    _, Pt, Pin = pr.probabilities()
+    dP = np.max(np.abs(Pt - ref["P_total"]))
+    assert dP < 1e-4, dP
+    q, _ = pr.state()
+    assert np.linalg.norm(q - ref["q"]) / np.linalg.norm(ref["q"]) < 1e-3
+    pr.close()
+
+
+def test_graph_replay_equals_eager_bitwise():
+    cfg = W.C2_SMALL
+    runs = []
+    for g in (0, 1):
+        pr = mw3().Propagator(cfg, precision="fp64", tuning={"use_graph": g, "kb": 16})
+        pr.propagate(100)
+        q, qp = pr.state()
+        runs.append((q, qp, pr.probabilities()[1]))
+        pr.close()
+    for a, b in zip(runs[0], runs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_batched_J_equals_single_J_bitwise():
+    """A batch of uneven J stacks gives the same bits as each J run alone."""
+    cfg = W.C3_SMALL
+    pr = mw3().Propagator(cfg, precision="fp64")
+    pr.propagate(60)
+    qb, _ = pr.state()
+    _, Pb, _ = pr.probabilities()
+    H = GridHamiltonian(cfg)
+    bj = H.block_J_index()
+    pr.close()
+    for iJ, J in enumerate(cfg["J"]):
+        c1 = copy.deepcopy(cfg)
+        c1["J"] = [J]
+        p1 = mw3().Propagator(c1, precision="fp64")
+        p1.propagate(60)
+        q1, _ = p1.state()
+        _, P1, _ = p1.probabilities()
+        assert np.array_equal(q1, qb[bj == iJ])
+        assert np.array_equal(P1[0], Pb[iJ])
+        p1.close()
+
+
+def test_deterministic_and_resumable():
+    cfg = W.C2_SMALL
+    a = mw3().Propagator(cfg, precision="fp64")
+    a.propagate(70)
+    b = mw3().Propagator(cfg, precision="fp64")
+    b.propagate(25)
+    b.propagate(45)
+    qa, _ = a.state()
+    qb, _ = b.state()
+    assert np.array_equal(qa, qb)
+    assert a.iteration == b.iteration == 70
+    # the energy sums match to rounding (different flush grouping)
+    np.testing.assert_allclose(a.probabilities()[1], b.probabilities()[1], rtol=0, atol=1e-12)
+    a.close()
+    b.close()
+
+
+def test_checkpoint_roundtrip():
+    cfg = W.C2_SMALL
+    a = mw3().Propagator(cfg, precision="fp64")
+    a.propagate(40)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        a.checkpoint_save(path)
+        a.propagate(40)
+        b = mw3().Propagator(cfg, precision="fp64")
+        b.checkpoint_load(path)
+        assert b.iteration == 40
+        b.propagate(40)
+    qa, _ = a.state()
+    qb, _ = b.state()
+    assert np.array_equal(qa, qb)
+    np.testing.assert_allclose(a.probabilities()[1], b.probabilities()[1], atol=1e-13)
+
+
+def test_full_size_config2_operator_and_first_steps():
+    """Config 2 at full size (256 x 192 x 96, 11 blocks): H_s on a seeded vector in
+    both precisions, and the first two damped iterations plus their flux sums in FP64."""
+    cfg = copy.deepcopy(W.C2)
+    H = GridHamiltonian(cfg)
+    q = W.random_state(H.shape, 2412)
+    ref = H.apply_Hs(q)
+    scale = np.max(np.abs(ref))
+    for prec, tol in (("fp64", 1e-12), ("mixed", 2e-6)):
+        pr = mw3().Propagator(cfg, precision=prec)
+        got = pr.apply_hs(q)
+        assert np.max(np.abs(got - ref)) <= tol * scale, prec
+        pr.close()
+    del q, ref
+    cfg["analysis"]["vmax"] = 1
+    cfg["analysis"]["jmax"] = 3
+    cfg["analysis"]["nE"] = 20
+    ref = P.propagate(cfg, nsteps=2, H=H)
+    pr = mw3().Propagator(cfg, precision="fp64")
+    pr.propagate(2)
+    qg, qpg = pr.state()
+    assert np.linalg.norm(qg - ref["q"]) / np.linalg.norm(ref["q"]) < 1e-12
+    _, Pt, _ = pr.probabilities()
+    assert np.max(np.abs(Pt - ref["P_total"])) < 1e-8 * max(1.0, np.max(np.abs(ref["P_total"])))
+    pr.close()
+
+
+def test_divergence_guard():
+    """A state pair inconsistent with the recursion (q_(k-1) = -3 q_k) makes the norm
+    jump far above ||q_0||^2: the library returns MW3_ERR_DIVERGED."""
+    cfg = W.C2_SMALL
+    pr = mw3().Propagator(cfg, precision="fp64")
+    pr.propagate(10)
+    q, _ = pr.state()
+    pr.set_state(q, -3.0 * q)
+    with pytest.raises(mw3().MW3Error) as e:
+        pr.propagate(40)
+    assert e.value.code == -4
+    pr.close()
