@@ -8,8 +8,8 @@ basis (FBR) where their matrix elements are analytic (item 3).
 Reading of the silent points (the paper names only "real sine transform" and the
 FBR): the radial grid is the midpoint sine DVR between walls at the interval ends,
 transformed by the orthonormal DST-II; the FBR of helicity Omega uses normalised
-associated Legendre functions j = Omega .. Omega + n - 1 on the shared
-Gauss-Legendre nodes, orthonormalised by Gram-Schmidt in increasing j.
+associated Legendre functions j = Omega .. n - 1 on the shared n Gauss-Legendre
+nodes, which that quadrature makes exactly orthonormal.
 """
 from __future__ import annotations
 
@@ -80,8 +80,30 @@ def sine_interpolation_weights(xa, xb, N, x):
 # ---------------------------------------------------------------------------- angular
 
 def gauss_legendre(n: int):
-    """Gauss-Legendre nodes x_n = cos(gamma_n) and weights on [-1, 1] (library routine)."""
-    return np.polynomial.legendre.leggauss(n)
+    """Gauss-Legendre nodes x_k = cos(gamma_k) (ascending) and weights on [-1, 1].
+
+    From the definition: the nodes are the roots of P_n, found by Newton's method
+    from cos(pi (k + 3/4) / (n + 1/2)); the weights are w_k = 2 / ((1 - x_k^2) P_n'(x_k)^2).
+    """
+    def pn_dpn(z):
+        p0, p1 = np.ones_like(z), z.copy()
+        for k in range(2, n + 1):
+            p0, p1 = p1, ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k
+        if n == 1:
+            p0 = np.ones_like(z)
+        return p1, n * (z * p1 - p0) / (z * z - 1.0)
+
+    z = np.cos(np.pi * (np.arange(n) + 0.75) / (n + 0.5))
+    for _ in range(100):
+        p, dp = pn_dpn(z)
+        dz = p / dp
+        z = z - dz
+        if np.max(np.abs(dz)) < 1e-16:
+            break
+    _, dp = pn_dpn(z)
+    w = 2.0 / ((1.0 - z * z) * dp * dp)
+    order = np.argsort(z)
+    return z[order], w[order]
 
 
 def norm_assoc_legendre(jmax: int, omega: int, x) -> np.ndarray:
@@ -113,22 +135,16 @@ def norm_assoc_legendre(jmax: int, omega: int, x) -> np.ndarray:
 
 
 def fbr_matrix(omega: int, n: int, x=None, w=None) -> np.ndarray:
-    """Angular transform T^Omega (n x n, orthogonal) from DVR points to the FBR.
+    """Angular transform T^Omega ((n - Omega) x n) from the DVR points to the FBR.
 
-    Rows before orthonormalisation: u_j(k) = P-bar_j^Omega(x_k) sqrt(w_k),
-    j = Omega .. Omega + n - 1. Gauss-Legendre quadrature with n points is exact
-    for polynomial products up to degree 2n - 1, so for Omega = 0 the rows are
-    already orthonormal; for Omega > 0 the high-j rows are not, and the rows are
-    orthonormalised by Gram-Schmidt in increasing j (two passes).
+    Rows T[i, k] = P-bar_j^Omega(x_k) sqrt(w_k) for j = Omega + i = Omega .. n - 1.
+    Every product P-bar_j^Omega P-bar_j'^Omega is (1 - x^2)^Omega times a polynomial
+    of degree j + j' - 2 Omega, so the whole integrand has degree j + j' <= 2n - 2
+    and the n-point Gauss-Legendre rule integrates it exactly: the rows are
+    orthonormal (T T^T = 1). For Omega = 0 the matrix is square and orthogonal.
+    (Completing the Omega > 0 basis to n functions is ill-conditioned on the shared
+    grid and is not done; block Omega carries n - Omega angular functions.)
     """
     if x is None:
         x, w = gauss_legendre(n)
-    U = norm_assoc_legendre(omega + n - 1, omega, x) * np.sqrt(w)[None, :]
-    T = np.zeros_like(U)
-    for i in range(n):
-        v = U[i].copy()
-        for _ in range(2):
-            for p in range(i):
-                v -= np.dot(T[p], v) * T[p]
-        T[i] = v / np.sqrt(np.dot(v, v))
-    return T
+    return norm_assoc_legendre(n - 1, omega, x) * np.sqrt(w)[None, :]

@@ -19,6 +19,11 @@ Readings of silent points (each is restated where it is used):
     lmax2(j) = (sqrt(J(J+1)) + sqrt(j(j+1)))^2, a positive factor per j that keeps
     the operator symmetric and positive semidefinite;
   * the potential cap VcutmaxeV applies to the diagonal of H_e only;
+  * block Omega carries the n - Omega angular functions j = Omega .. n - 1 (exactly
+    orthonormal under the shared n-point Gauss-Legendre rule); the state of a block
+    lies in their span and the potential enters through its quadrature matrix
+    elements in that basis, i.e. as P V P with P = (T^Omega)^T T^Omega (P = 1 for
+    Omega = 0);
   * E_min / E_max are rigorous bounds: the lowest / highest eigenvalue of H_e over
     the grid, plus the largest capped radial eigenvalues, plus the largest
     Gershgorin row sum of the angular FBR matrix.
@@ -59,6 +64,9 @@ class GridHamiltonian:
         self.pes = cfg["pes"]
         self.Js = list(cfg["J"])
         self.omega_max = cfg["omega_max"]
+        if min(max(self.Js), self.omega_max) >= self.ng:
+            raise ValueError("every helicity block needs at least one angular function: "
+                             "min(max J, omega_max) < ngamma")
 
         # radial kinetic operators (item 2): dense sine-DVR matrices
         self.TR = basis.radial_kinetic_matrix(*self.Rlim, self.NR, self.mu, self.tcut)
@@ -111,13 +119,13 @@ class GridHamiltonian:
     def angular_coefficients(self, J, om):
         """a[i,k,m], bp[i,m], bm[i,m] of the FBR operator of block Omega = om.
 
-        For row i (j = Omega + i) at grid point (r_k, R_m):
+        Rows i = 0 .. n - Omega - 1. For row i (j = Omega + i) at grid point (r_k, R_m):
           a  = min(j(j+1)/(2 m r^2), E_rot) + g_j(R) [J(J+1) + j(j+1) - 2 Omega^2]
           bp = -g_j(R) lambda+_(J Omega) lambda+_(j Omega) kappa   (couples to Omega+1, same j)
           bm = -g_j(R) lambda-_(J Omega) lambda-_(j Omega) kappa'  (couples to Omega-1, same j)
         kappa = sqrt(2) when the coupled pair is {0, 1}, otherwise 1.
         """
-        n = self.ng
+        n = self.ng - om
         a = np.zeros((n, self.nr, self.NR))
         bp = np.zeros((n, self.NR))
         bm = np.zeros((n, self.NR))
@@ -131,30 +139,42 @@ class GridHamiltonian:
             if om + 1 <= top and i >= 1:
                 kap = np.sqrt(2.0) if om == 0 else 1.0
                 bp[i] = -gj * _lam(J, om, +1) * _lam(j, om, +1) * kap
-            if om >= 1 and i <= n - 2:
+            if om >= 1:
                 kap = np.sqrt(2.0) if om == 1 else 1.0
                 bm[i] = -gj * _lam(J, om, -1) * _lam(j, om, -1) * kap
         return a, bp, bm
 
     def apply_angular(self, q, out):
-        """out += (T^Omega)^T [a c^Omega + bp c^(Omega+1) + bm c^(Omega-1)], c^Omega = T^Omega q^Omega."""
-        n = self.ng
+        """out += (T^Omega)^T [a c^Omega + bp c^(Omega+1) + bm c^(Omega-1) + T^Omega V P q],
+
+        c^Omega = T^Omega q^Omega, for every block: the j^2 and l^2 terms in the FBR
+        (Coriolis coupling between Omega and Omega +- 1 at equal j) and the diabatic
+        potential through its FBR matrix elements (P V P, P = T^T T per block)."""
+        blk = self.shape[1:]
+        flat = (self.ng, self.nr * self.NR)
         for iJ, J in enumerate(self.Js):
             top = self.omega_top(J)
-            for L in range(self.nelec):
-                flat = (self.ng, self.nr * self.NR)
-                c = [(self.T[om] @ q[self.block_index[(iJ, om, L)]].reshape(flat)).reshape(q.shape[1:])
-                     for om in range(top + 1)]
-                for om in range(top + 1):
-                    a, bp, bm = self.angular_coefficients(J, om)
-                    cp = a * c[om]
+            c, pq = {}, {}
+            for om in range(top + 1):
+                for L in range(self.nelec):
+                    b = self.block_index[(iJ, om, L)]
+                    c[om, L] = (self.T[om] @ q[b].reshape(flat)).reshape((self.ng - om,) + blk[1:])
+                    pq[om, L] = (self.T[om].T @ c[om, L].reshape(self.ng - om, -1)).reshape(blk)
+            for om in range(top + 1):
+                a, bp, bm = self.angular_coefficients(J, om)
+                for L in range(self.nelec):
+                    cp = a * c[om, L]
                     if om + 1 <= top:
                         # row i of block om meets row i-1 of block om+1 (same j)
-                        cp[1:] += bp[1:, None, :] * c[om + 1][:n - 1]
+                        cp[1:] += bp[1:, None, :] * c[om + 1, L]
                     if om >= 1:
                         # row i of block om meets row i+1 of block om-1 (same j)
-                        cp[:n - 1] += bm[:n - 1, None, :] * c[om - 1][1:]
-                    out[self.block_index[(iJ, om, L)]] += (self.T[om].T @ cp.reshape(flat)).reshape(cp.shape)
+                        cp += bm[:, None, :] * c[om - 1, L][1:]
+                    vq = np.zeros(blk)
+                    for Lp in range(self.nelec):
+                        vq += self.V[L, Lp] * pq[om, Lp]
+                    cp = cp.reshape(self.ng - om, -1) + self.T[om] @ vq.reshape(flat)
+                    out[self.block_index[(iJ, om, L)]] += (self.T[om].T @ cp).reshape(blk)
 
     # ------------------------------------------------------------------ full operator
     def apply_H(self, q):
@@ -162,10 +182,16 @@ class GridHamiltonian:
         q = np.asarray(q, dtype=float).reshape(self.shape)
         out = q @ self.TR                                     # R kinetic (T_R symmetric)
         out += np.matmul(self.Tr, q)                          # r kinetic
-        self.apply_angular(q, out)                            # j^2 and l^2 terms
-        for (iJ, J, om, L), b in zip(self.blocks, range(self.nblk)):
-            for Lp in range(self.nelec):                      # diabatic potential
-                out[b] += self.V[L, Lp] * q[self.block_index[(iJ, om, Lp)]]
+        self.apply_angular(q, out)                            # j^2, l^2 and potential
+        return out
+
+    def project(self, q):
+        """P q: each block's component in the span of its angular functions."""
+        q = np.asarray(q, dtype=float).reshape(self.shape)
+        out = np.empty_like(q)
+        flat = (self.ng, self.nr * self.NR)
+        for b, (iJ, J, om, L) in enumerate(self.blocks):
+            out[b] = (self.T[om].T @ (self.T[om] @ q[b].reshape(flat))).reshape(self.shape[1:])
         return out
 
     def block_J_index(self):

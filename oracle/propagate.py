@@ -154,13 +154,13 @@ def reactant_channels(H: GridHamiltonian, analysis: dict):
     """Channels (J index, Omega, Lambda, v, j) with their DVR vectors and energies.
 
     Every block (J, Omega, Lambda) contributes the channels v = 0..vmax,
-    j = max(Omega, 0)..min(jmax, Omega + n_gamma - 1).
+    j = Omega..min(jmax, n_gamma - 1) (the angular functions of the block).
     """
     vmax, jmax = analysis["vmax"], analysis["jmax"]
     chans, chis, eps = [], [], []
     cache = {}
     for (iJ, J, om, L) in H.blocks:
-        for j in range(om, min(jmax, om + H.ng - 1) + 1):
+        for j in range(om, min(jmax, H.ng - 1) + 1):
             if (j, L) not in cache:
                 cache[(j, L)] = diatomic_states(H, j, L, vmax + 1)
             e, U = cache[(j, L)]

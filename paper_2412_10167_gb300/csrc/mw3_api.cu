@@ -1,12 +1,16 @@
 // libmw3: context, set-up and the propagation driver behind include/mw3.h.
 //
-// One propagation step (Eq. wvp-k) is the launch sequence
-//   1. kinetic_rows   t = T_R q_k                         (R lines, DST-II kinetic)
-//   2. kinetic_cols   t += T_r q_k; flux cut of q_k; q_k column at R_inf
-//   3. gamma_forward  c = T^Omega q_k                     (per block)
-//   4. gamma_backward q_(k+1) = D (alpha H_s q_k - beta D q_(k-1)), written over q_(k-1)
-//   5. channels       reactant-channel overlaps of q_k
-//   6. norms          ||q_(k+1)||^2 per J
+// The state of every block is held in its angular FBR (coefficients of the
+// normalised associated Legendre functions j = Omega..ngamma-1 on each (r, R) point;
+// mw3_get_state / mw3_set_state convert to and from values on the Gauss-Legendre
+// grid). One propagation step (Eq. wvp-k) is the launch sequence
+//   1. kinetic_rows   t = T_R c_k                          (R lines, DST-II kinetic)
+//   2. kinetic_cols   t += T_r c_k; flux cut of c_k; c_k column at R_inf
+//   3. gamma_to_dvr   u = (T^Omega)^T c_k                  (per block)
+//   4. gamma_update   w = T^Omega V u; h = w + angular/Coriolis + t;
+//                     c_(k+1) = D (alpha H_s c_k - beta D c_(k-1)), over c_(k-1)
+//   5. channels       reactant-channel overlaps of c_k
+//   6. norms          ||c_(k+1)||^2 per J
 // The flux cut and overlaps of kb consecutive iterations are kept in a ring; every
 // kb iterations (a "chunk") the energy sums are updated by one GEMM
 //   A[J][2nE x cols] += Ph[J][2nE x kb] Cut[kb x cols],  Ph = Re/Im of c_k(E),
@@ -34,8 +38,8 @@ using namespace mw3;
 
 namespace {
 
-const char* kKernelNames[] = {"kinetic_rows", "kinetic_cols", "gamma_forward",
-                              "gamma_backward_update", "channels", "norms", "sums_flush"};
+const char* kKernelNames[] = {"kinetic_rows", "kinetic_cols", "gamma_to_dvr",
+                              "gamma_update", "channels", "norms", "sums_flush"};
 constexpr int kNumKernels = 7;
 
 struct DevBuf {
@@ -118,7 +122,7 @@ struct mw3_ctx {
   std::vector<double> wpsi, wdpsi;
   int m_inf = 0;
   int nchan = 0;
-  std::vector<int> chan_block, chan_col, chan_v, chan_j, chan_om, chan_lam, chan_iJ;
+  std::vector<int> chan_block, chan_row, chan_col, chan_v, chan_j, chan_om, chan_lam, chan_iJ;
   std::vector<double> chan_eps;
   std::vector<long> colbase, ncols, ncut, accoff;
   long NC = 0, max_cols = 0, acc_size = 0;
@@ -293,6 +297,82 @@ int diatomic(mw3_ctx* ctx, int j, int lam, int nv, std::vector<double>& E, std::
   return MW3_OK;
 }
 
+#define LK(expr)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return ctx->fail(MW3_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Transform `n` host FP64 values between the grid (DVR) and the FBR of every block
+// on the device: to_fbr = 1 computes T^Omega x into dst_name, 0 computes (T^Omega)^T x.
+int transform_upload(mw3_ctx* ctx, const double* src, const char* dst_name, bool to_fbr) {
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  int st = dalloc(ctx, "xfer", n * ctx->rs());
+  if (st) return st;
+  if (ctx->precision == MW3_FP64) {
+    CK(cudaMemcpyAsync(dptr(ctx, "xfer"), src, n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    LK(launch_gamma_forward<double>((const double*)dptr(ctx, "xfer"), (double*)dptr(ctx, dst_name),
+                                    (const double*)dptr(ctx, to_fbr ? "T" : "Tt"),
+                                    (const DevBlock*)dptr(ctx, "blocks"), ctx->nblk, ctx->ng,
+                                    ctx->ncol, ctx->stream));
+  } else {
+    std::vector<float> f(src, src + n);
+    CK(cudaMemcpyAsync(dptr(ctx, "xfer"), f.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
+    LK(launch_gamma_forward<float>((const float*)dptr(ctx, "xfer"), (float*)dptr(ctx, dst_name),
+                                   (const float*)dptr(ctx, to_fbr ? "T" : "Tt"),
+                                   (const DevBlock*)dptr(ctx, "blocks"), ctx->nblk, ctx->ng,
+                                   ctx->ncol, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MW3_OK;
+}
+
+int transform_download(mw3_ctx* ctx, const char* src_name, double* dst) {
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  int st = dalloc(ctx, "xfer", n * ctx->rs());
+  if (st) return st;
+  if (ctx->precision == MW3_FP64) {
+    LK(launch_gamma_forward<double>((const double*)dptr(ctx, src_name), (double*)dptr(ctx, "xfer"),
+                                    (const double*)dptr(ctx, "Tt"),
+                                    (const DevBlock*)dptr(ctx, "blocks"), ctx->nblk, ctx->ng,
+                                    ctx->ncol, ctx->stream));
+    CK(cudaMemcpyAsync(dst, dptr(ctx, "xfer"), n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else {
+    LK(launch_gamma_forward<float>((const float*)dptr(ctx, src_name), (float*)dptr(ctx, "xfer"),
+                                   (const float*)dptr(ctx, "Tt"),
+                                   (const DevBlock*)dptr(ctx, "blocks"), ctx->nblk, ctx->ng,
+                                   ctx->ncol, ctx->stream));
+    std::vector<float> f(n);
+    CK(cudaMemcpyAsync(f.data(), dptr(ctx, "xfer"), n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < n; ++i) dst[i] = f[i];
+  }
+  return MW3_OK;
+}
+
+const char* state_name(const mw3_ctx* ctx, bool current) {
+  return (current == (ctx->cur == 0)) ? "q0" : "q1";
+}
+
+// Upload FBR coefficients as q_k (q_(k-1) = 0).
+int upload_state_fbr(mw3_ctx* ctx, const double* c) {
+  if (ctx->host_only) return MW3_OK;
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  if (ctx->precision == MW3_FP64) {
+    CK(cudaMemcpyAsync(dptr(ctx, state_name(ctx, true)), c, n * 8, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    std::vector<float> f(c, c + n);
+    CK(cudaMemcpyAsync(dptr(ctx, state_name(ctx, true)), f.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  CK(cudaMemsetAsync(dptr(ctx, state_name(ctx, false)), 0, n * ctx->rs(), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MW3_OK;
+}
+
 }  // namespace
 
 // ================================================================== C ABI
@@ -402,8 +482,13 @@ int mw3_grid(mw3_ctx* ctx, const mw3_grid_desc* d) {
     return ctx->fail(MW3_ERR_BAD_ARG, "need nJ >= 1, omega_max >= 0 and nelec in {1, 2}");
   for (int i = 0; i < 3; ++i)
     if (!(d->masses[i] > 0)) return ctx->fail(MW3_ERR_BAD_ARG, "masses must be positive");
-  for (int i = 0; i < d->nJ; ++i)
+  int jtop = 0;
+  for (int i = 0; i < d->nJ; ++i) {
     if (d->J[i] < 0) return ctx->fail(MW3_ERR_BAD_ARG, "J must be >= 0");
+    jtop = std::max(jtop, std::min(d->J[i], d->omega_max));
+  }
+  if (jtop >= d->ngamma)
+    return ctx->fail(MW3_ERR_BAD_ARG, "min(J, omega_max) must be < ngamma (angular functions per block)");
   ctx->NR = d->NR;
   ctx->nr = d->nr;
   ctx->ng = d->ngamma;
@@ -459,6 +544,7 @@ int mw3_grid(mw3_ctx* ctx, const mw3_grid_desc* d) {
         b.lam = L;
         b.coef = ci;
         b.base = (int)ctx->blocks.size() - L;
+        b.nrow = ctx->ng - om;
         ctx->blocks.push_back(b);
       }
     }
@@ -515,6 +601,10 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
     const int top = ctx->omtop[iJ];
     double* cf = &ctx->coef[(size_t)ci * kCoefRows * ng];
     for (int i = 0; i < ng; ++i) {
+      if (i >= ng - om) {  // beyond the block's angular functions
+        cf[4 * ng + i] = 1e300;
+        continue;
+      }
       const double j = om + i;
       const double jj = j * (j + 1.0);
       cf[i] = jj;
@@ -522,7 +612,7 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
       cf[2 * ng + i] = (om + 1 <= top && i >= 1)
                            ? -lam_pm(Jv, om, +1) * lam_pm(j, om, +1) * (om == 0 ? std::sqrt(2.0) : 1.0)
                            : 0.0;
-      cf[3 * ng + i] = (om >= 1 && i + 1 < ng)
+      cf[3 * ng + i] = (om >= 1)
                            ? -lam_pm(Jv, om, -1) * lam_pm(j, om, -1) * (om == 1 ? std::sqrt(2.0) : 1.0)
                            : 0.0;
       const double lmax2 = std::pow(std::sqrt(Jv * (Jv + 1.0)) + std::sqrt(jj), 2);
@@ -550,7 +640,8 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
     for (int ci = 0; ci < ctx->ncoef; ++ci) {
       if (ctx->coef_of[ci] / 4096 != iJ) continue;
       const double* cf = &ctx->coef[(size_t)ci * kCoefRows * ng];
-      for (int i = 0; i < ng; ++i) {
+      const int om = ctx->coef_of[ci] % 4096;
+      for (int i = 0; i < ng - om; ++i) {
         const double g = std::min(ctx->fR[0], cf[4 * ng + i]);
         const double a = std::min(cf[i] * ctx->fr[0], erot) + g * cf[ng + i];
         ang = std::max(ang, a + std::fabs(g * cf[2 * ng + i]) + std::fabs(g * cf[3 * ng + i]));
@@ -598,7 +689,7 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
   // state buffers
   const size_t vb = (size_t)ctx->nblk * ctx->npts * ctx->rs();
   if ((st = dalloc(ctx, "q0", vb)) || (st = dalloc(ctx, "q1", vb)) || (st = dalloc(ctx, "t", vb)) ||
-      (st = dalloc(ctx, "c", vb)))
+      (st = dalloc(ctx, "u", vb)))
     return st;
   if ((st = dzero(ctx, "q0")) || (st = dzero(ctx, "q1"))) return st;
   ctx->stage = 2;
@@ -654,7 +745,7 @@ int mw3_init_packet(mw3_ctx* ctx, const mw3_packet_desc* d) {
   if (!ctx || !d) return MW3_ERR_BAD_ARG;
   if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
   if (d->v0 < 0 || d->j0 < d->omega0 || d->omega0 < 0 || d->elec0 < 0 || d->elec0 >= ctx->nelec ||
-      !(d->Gamma > 0) || !(d->Ecol > 0) || d->j0 - d->omega0 >= ctx->ng || d->v0 >= ctx->nr)
+      !(d->Gamma > 0) || !(d->Ecol > 0) || d->j0 >= ctx->ng || d->v0 >= ctx->nr)
     return ctx->fail(MW3_ERR_BAD_ARG, "invalid packet description");
   ctx->packet = *d;
   std::vector<double> E, chi;
@@ -675,20 +766,19 @@ int mw3_init_packet(mw3_ctx* ctx, const mw3_packet_desc* d) {
     g[i] *= gn;
     ctx->g_tilde[i] = g[i] / std::sqrt(ctx->dR);
   }
-  const std::vector<double>& Tm = ctx->T[std::min<int>(d->omega0, (int)ctx->T.size() - 1)];
+  // FBR coefficients of q_0: one angular function (j0, Omega0) times chi g
   ctx->q0.assign((size_t)ctx->nblk * ctx->npts, 0.0);
   for (int bi = 0; bi < ctx->nblk; ++bi) {
     const DevBlock& b = ctx->blocks[bi];
     if (b.omega != d->omega0 || b.lam != d->elec0) continue;
-    const double* y = &Tm[(size_t)(d->j0 - d->omega0) * ctx->ng];
-    for (int n = 0; n < ctx->ng; ++n)
-      for (int kr = 0; kr < ctx->nr; ++kr)
-        for (int mm = 0; mm < ctx->NR; ++mm)
-          ctx->q0[(size_t)bi * ctx->npts + (size_t)n * ctx->ncol + (size_t)kr * ctx->NR + mm] =
-              y[n] * chi[(size_t)d->v0 * ctx->nr + kr] * g[mm];
+    const int i0 = d->j0 - d->omega0;
+    for (int kr = 0; kr < ctx->nr; ++kr)
+      for (int mm = 0; mm < ctx->NR; ++mm)
+        ctx->q0[(size_t)bi * ctx->npts + (size_t)i0 * ctx->ncol + (size_t)kr * ctx->NR + mm] =
+            chi[(size_t)d->v0 * ctx->nr + kr] * g[mm];
   }
   ctx->norm0 = 1.0;
-  if ((st = mw3_set_state(ctx, ctx->q0.data(), nullptr))) return st;
+  if ((st = upload_state_fbr(ctx, ctx->q0.data()))) return st;
   ctx->iter = 0;
   ctx->norm_trace.clear();
   if (ctx->stage < 3) ctx->stage = 3;
@@ -739,6 +829,7 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
 
   // channels and the column layout of the cut ring, per J
   ctx->chan_block.clear();
+  ctx->chan_row.clear();
   ctx->chan_col.clear();
   ctx->chan_v.clear();
   ctx->chan_j.clear();
@@ -764,7 +855,7 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
     if (d->vmax >= 0) {
       for (long b = b0; b < b1; ++b) {
         const DevBlock& B = ctx->blocks[b];
-        for (int j = B.omega; j <= std::min(d->jmax, B.omega + ng - 1); ++j) {
+        for (int j = B.omega; j <= std::min(d->jmax, ng - 1); ++j) {
           auto key = std::make_pair(j, B.lam);
           if (!cache.count(key)) {
             std::vector<double> E, chi;
@@ -782,10 +873,9 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
             ctx->chan_lam.push_back(B.lam);
             ctx->chan_iJ.push_back(iJ);
             ctx->chan_eps.push_back(ec.first[v]);
-            const double* Trow = &ctx->T[B.omega][(size_t)(j - B.omega) * ng];
-            for (int n = 0; n < ng; ++n)
-              for (int kr = 0; kr < nr; ++kr)
-                P.push_back(Trow[n] * ec.second[(size_t)v * nr + kr] / std::sqrt(ctx->dR));
+            ctx->chan_row.push_back(j - B.omega);
+            for (int kr = 0; kr < nr; ++kr)
+              P.push_back(ec.second[(size_t)v * nr + kr] / std::sqrt(ctx->dR));
             ++nch;
           }
         }
@@ -820,6 +910,7 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
   if ((st = dalloc(ctx, "qcol", (size_t)ctx->nblk * ng * nr * ctx->rs()))) return st;
   if (ctx->nchan > 0) {
     if ((st = upload_real(ctx, "P", P)) || (st = upload_raw(ctx, "chan_block", ctx->chan_block)) ||
+        (st = upload_raw(ctx, "chan_row", ctx->chan_row)) ||
         (st = upload_raw(ctx, "chan_col", ctx->chan_col)))
       return st;
   }
@@ -847,12 +938,12 @@ namespace {
 
 template <typename real>
 struct Bufs {
-  real *q[2], *t, *c, *V, *T, *Tt, *coef, *fR, *fr, *DR, *Dr, *lamR, *lamr, *wpsi, *wdpsi, *cut,
+  real *q[2], *t, *u, *V, *T, *Tt, *coef, *fR, *fr, *DR, *Dr, *lamR, *lamr, *wpsi, *wdpsi, *cut,
       *qcol, *P, *ph;
   void *twR, *phR, *twr, *phr;
   DevBlock* blocks;
   DevJ* dj;
-  int *ncut_i, *chan_block, *chan_col;
+  int *ncut_i, *chan_block, *chan_row, *chan_col;
   long *colbase, *ncols, *ncut, *accoff, *d_iter, *J_begin;
   double *acc, *theta, *normbuf, *npartial;
 };
@@ -863,7 +954,7 @@ Bufs<real> bufs(mw3_ctx* ctx) {
   b.q[0] = (real*)dptr(ctx, "q0");
   b.q[1] = (real*)dptr(ctx, "q1");
   b.t = (real*)dptr(ctx, "t");
-  b.c = (real*)dptr(ctx, "c");
+  b.u = (real*)dptr(ctx, "u");
   b.V = (real*)dptr(ctx, "V");
   b.T = (real*)dptr(ctx, "T");
   b.Tt = (real*)dptr(ctx, "Tt");
@@ -888,6 +979,7 @@ Bufs<real> bufs(mw3_ctx* ctx) {
   b.dj = (DevJ*)dptr(ctx, "dj");
   b.ncut_i = (int*)dptr(ctx, "ncut_i");
   b.chan_block = (int*)dptr(ctx, "chan_block");
+  b.chan_row = (int*)dptr(ctx, "chan_row");
   b.chan_col = (int*)dptr(ctx, "chan_col");
   b.colbase = (long*)dptr(ctx, "colbase");
   b.ncols = (long*)dptr(ctx, "ncols");
@@ -935,12 +1027,7 @@ void collect_times(mw3_ctx* ctx) {
   ctx->evrec.clear();
 }
 
-#define LK(expr)                                                                       \
-  do {                                                                                 \
-    cudaError_t e_ = (expr);                                                           \
-    if (e_ != cudaSuccess)                                                             \
-      return ctx->fail(MW3_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
+
 
 // One Chebyshev iteration; cut data into ring slot `slot`. mode 1 computes H_s q
 // into `hs_out` instead (no damping, no analysis).
@@ -956,7 +1043,7 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
   {
     Timer tm(ctx, 0, timed);
     LK(launch_kinetic_rows<real>(qk, B.t, nrows, ctx->planR, B.twR, B.phR, B.lamR,
-                                 ctx->tune.rows_pairs, st));
+                                 ctx->tune.rows_pairs, B.blocks, ctx->ng, ctx->nr, st));
     tm.stop();
   }
   {
@@ -969,24 +1056,23 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
   }
   {
     Timer tm(ctx, 2, timed);
-    LK(launch_gamma_forward<real>(qk, B.c, B.T, B.blocks, ctx->nblk, ctx->ng, ctx->ncol, st));
+    LK(launch_gamma_forward<real>(qk, B.u, B.Tt, B.blocks, ctx->nblk, ctx->ng, ctx->ncol, st));
     tm.stop();
   }
   {
     Timer tm(ctx, 3, timed);
     const real alpha = first ? (real)1 : (real)2;
     const real beta = first ? (real)0 : (real)1;
-    LK(launch_gamma_backward_update<real>(B.c, B.Tt, B.blocks, ctx->nblk, ctx->ng, ctx->ncol,
-                                          ctx->NR, B.coef, B.fr, B.fR, (real)ctx->erot, qk, qkm1,
-                                          B.t, B.V, ctx->nelec, B.DR, B.Dr, B.dj, alpha, beta,
-                                          mode, hs_out, st));
+    LK(launch_gamma_update<real>(B.u, B.T, B.blocks, ctx->nblk, ctx->ng, ctx->ncol, ctx->NR,
+                                 B.coef, B.fr, B.fR, (real)ctx->erot, qk, qkm1, B.t, B.V,
+                                 ctx->nelec, B.DR, B.Dr, B.dj, alpha, beta, mode, hs_out, st));
     tm.stop();
   }
   if (mode == 1) return MW3_OK;
   if (analysis && ctx->nchan > 0) {
     Timer tm(ctx, 4, timed);
-    LK(launch_channels<real>(B.qcol, B.P, B.chan_block, B.chan_col, ctx->nchan, ctx->ng * ctx->nr,
-                             B.d_iter, slot, ctx->an.kmin, cut_slot, st));
+    LK(launch_channels<real>(B.qcol, B.P, B.chan_block, B.chan_row, B.chan_col, ctx->nchan,
+                             ctx->ng, ctx->nr, B.d_iter, slot, ctx->an.kmin, cut_slot, st));
     tm.stop();
   }
   {
@@ -1112,25 +1198,13 @@ int mw3_set_state(mw3_ctx* ctx, const double* q, const double* qprev) {
   if (!ctx || !q) return MW3_ERR_BAD_ARG;
   if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
   if (ctx->host_only) return MW3_OK;
-  const size_t n = (size_t)ctx->nblk * ctx->npts;
-  for (int which = 0; which < 2; ++which) {
-    const double* src = which == 0 ? q : qprev;
-    const char* name = (which == 0) == (ctx->cur == 0) ? "q0" : "q1";
-    if (!src) {
-      if (which == 1) {
-        CK(cudaMemsetAsync(dptr(ctx, name), 0, n * ctx->rs(), ctx->stream));
-      }
-      continue;
-    }
-    if (ctx->precision == MW3_FP64) {
-      CK(cudaMemcpyAsync(dptr(ctx, name), src, n * 8, cudaMemcpyHostToDevice, ctx->stream));
-      CK(cudaStreamSynchronize(ctx->stream));
-    } else {
-      std::vector<float> f(src, src + n);
-      CK(cudaMemcpyAsync(dptr(ctx, name), f.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
-      CK(cudaStreamSynchronize(ctx->stream));
-    }
-  }
+  cudaSetDevice(ctx->device);
+  int st = transform_upload(ctx, q, state_name(ctx, true), true);
+  if (st) return st;
+  if (qprev) return transform_upload(ctx, qprev, state_name(ctx, false), true);
+  CK(cudaMemsetAsync(dptr(ctx, state_name(ctx, false)), 0,
+                     (size_t)ctx->nblk * ctx->npts * ctx->rs(), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return MW3_OK;
 }
 
@@ -1138,21 +1212,10 @@ int mw3_get_state(mw3_ctx* ctx, double* q, double* qprev) {
   if (!ctx || !q) return MW3_ERR_BAD_ARG;
   if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
   if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
-  const size_t n = (size_t)ctx->nblk * ctx->npts;
-  for (int which = 0; which < 2; ++which) {
-    double* dst = which == 0 ? q : qprev;
-    if (!dst) continue;
-    const char* name = (which == 0) == (ctx->cur == 0) ? "q0" : "q1";
-    if (ctx->precision == MW3_FP64) {
-      CK(cudaMemcpyAsync(dst, dptr(ctx, name), n * 8, cudaMemcpyDeviceToHost, ctx->stream));
-      CK(cudaStreamSynchronize(ctx->stream));
-    } else {
-      std::vector<float> f(n);
-      CK(cudaMemcpyAsync(f.data(), dptr(ctx, name), n * 4, cudaMemcpyDeviceToHost, ctx->stream));
-      CK(cudaStreamSynchronize(ctx->stream));
-      for (size_t i = 0; i < n; ++i) dst[i] = f[i];
-    }
-  }
+  cudaSetDevice(ctx->device);
+  int st = transform_download(ctx, state_name(ctx, true), q);
+  if (st) return st;
+  if (qprev) return transform_download(ctx, state_name(ctx, false), qprev);
   return MW3_OK;
 }
 
@@ -1164,33 +1227,20 @@ int mw3_apply_hs(mw3_ctx* ctx, const double* q, double* out) {
   const size_t n = (size_t)ctx->nblk * ctx->npts;
   int st;
   if ((st = dalloc(ctx, "hs_in", n * ctx->rs())) || (st = dalloc(ctx, "hs_out", n * ctx->rs()))) return st;
+  if ((st = transform_upload(ctx, q, "hs_in", true))) return st;
   // route the input through the q_k slot temporarily
   const int cur0 = ctx->cur;
-  const char* qname = ctx->cur == 0 ? "q0" : "q1";
+  const char* qname = state_name(ctx, true);
   void* saved = ctx->buf[qname].p;
   ctx->buf[qname].p = dptr(ctx, "hs_in");
-  if (ctx->precision == MW3_FP64) {
-    CK(cudaMemcpyAsync(dptr(ctx, "hs_in"), q, n * 8, cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->precision == MW3_FP64)
     st = step<double>(ctx, 0, true, false, 1, (double*)dptr(ctx, "hs_out"));
-  } else {
-    std::vector<float> f(q, q + n);
-    CK(cudaMemcpyAsync(dptr(ctx, "hs_in"), f.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+  else
     st = step<float>(ctx, 0, true, false, 1, (float*)dptr(ctx, "hs_out"));
-  }
   ctx->buf[qname].p = saved;
   ctx->cur = cur0;
   if (st) return st;
-  if (ctx->precision == MW3_FP64) {
-    CK(cudaMemcpyAsync(out, dptr(ctx, "hs_out"), n * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-  } else {
-    std::vector<float> f(n);
-    CK(cudaMemcpyAsync(f.data(), dptr(ctx, "hs_out"), n * 4, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    for (size_t i = 0; i < n; ++i) out[i] = f[i];
-  }
-  return MW3_OK;
+  return transform_download(ctx, "hs_out", out);
 }
 
 long mw3_norm_trace(mw3_ctx* ctx, double* out, long n) {

@@ -1,17 +1,18 @@
-// Angular (gamma) part of the Hamiltonian and the Chebyshev update (Section 2.1
-// items 3-5 and Section 2.2, Eq. wvp-k), CUDA-core path (FP64, and FP32 when the
-// tensor-core path is off).
+// Angular (gamma) part of the Hamiltonian, the potential and the Chebyshev update
+// (Section 2.1 items 3-5 and Section 2.2, Eq. wvp-k), CUDA-core path (FP64, and
+// FP32 when the tensor-core path is off).
 //
-// Forward: for every block (J, Omega, Lambda), c = T^Omega q as a GEMM
-// [ngamma x ngamma] x [ngamma x (nr NR)], T^Omega the orthonormal DVR -> FBR matrix.
-// Backward: h = (T^Omega)^T c', where the B operand c' is formed while it is loaded:
-//   c'_j = a_j c^Omega_j + bp_j c^(Omega+1)_j + bm_j c^(Omega-1)_j
-// (j^2/(2 m r^2) + l^2/(2 mu R^2) in the FBR, Coriolis coupling tridiagonal in
-// Omega, neighbour rows shifted by one because block Omega starts at j = Omega).
-// The epilogue adds the radial kinetic term t and the diabatic potential, scales
-// to H_s and applies the damped recursion in place:
-//   q_(k+1) = D (alpha H_s q_k - beta D q_(k-1)),  (alpha, beta) = (1, 0) for k = 0,
-//   (2, 1) after; D(r, R) = D_r(r) D_R(R).
+// The state of block (J, Omega, Lambda) is held in its FBR: rows i = 0..ng-Omega-1
+// are the coefficients of the normalised associated Legendre functions j = Omega + i
+// (rows beyond are zero). Per iteration:
+//   GEMM 1  u = (T^Omega)^T c_k                      FBR -> DVR values on the grid
+//   GEMM 2  w = T^Omega (V u),  (V u)_L = sum_L' V_LL' u_L'  (potential in the DVR)
+//   epilogue, per FBR coefficient:
+//     h = w + a_j c^Omega_j + bp_j c^(Omega+1)_j + bm_j c^(Omega-1)_j + t
+//     (j^2/(2 m r^2) + l^2/(2 mu R^2) with the Coriolis coupling tridiagonal in Omega,
+//     neighbour rows shifted by one because block Omega starts at j = Omega; t is the
+//     radial kinetic term), H_s c = h / dE - (E0 / dE) c, and the damped recursion
+//     c_(k+1) = D (alpha H_s c_k - beta D c_(k-1)) written over c_(k-1).
 #include <cuda_runtime.h>
 
 #include "mw3_internal.h"
@@ -96,25 +97,18 @@ struct LoadQ {   // B(b, k, n) = q[b][k][n]
 };
 
 template <typename T>
-struct LoadFBR {  // B(b, j, col) = c'_j(col) of block b
-  const T* c;
+struct LoadVu {   // B(b, n, col) = sum_L' V_(L L')(n, col) u_(b with L')(n, col)
+  const T* u;
+  const T* V;
   const DevBlock* blk;
-  const T* coef;
-  const T* fr;
-  const T* fR;
-  T erot;
   long npts, ncol;
-  int NR, ng;
-  __device__ T operator()(int b, int i, long col) const {
+  int nelec;
+  __device__ T operator()(int b, int n, long col) const {
     const DevBlock B = blk[b];
-    const int kr = (int)(col / NR);
-    const int m = (int)(col - (long)kr * NR);
-    const T* cf = coef + (long)B.coef * kCoefRows * ng;
-    const T g = fmin(fR[m], cf[4 * ng + i]);
-    const T a = fmin(cf[i] * fr[kr], erot) + g * cf[ng + i];
-    T v = a * c[b * npts + i * ncol + col];
-    if (B.up >= 0 && i >= 1) v += g * cf[2 * ng + i] * c[B.up * npts + (i - 1) * ncol + col];
-    if (B.dn >= 0 && i + 1 < ng) v += g * cf[3 * ng + i] * c[B.dn * npts + (i + 1) * ncol + col];
+    const long off = (long)n * ncol + col;
+    T v = 0;
+    for (int lp = 0; lp < nelec; ++lp)
+      v += V[(long)(B.lam * nelec + lp) * npts + off] * u[(long)(B.base + lp) * npts + off];
     return v;
   }
 };
@@ -128,40 +122,49 @@ struct EpiStore {
   __device__ void operator()(int b, int m, long n, T v) const { out[b * npts + m * ncol + n] = v; }
 };
 
-// mode 0: damped recursion in place into qkm1; mode 1: write H_s q into out.
+// mode 0: damped recursion in place into ckm1; mode 1: write H_s c into out.
 template <typename T>
 struct EpiUpdate {
-  const T* qk;
-  T* qkm1;
+  const T* ck;
+  T* ckm1;
   const T* t;
-  const T* V;
   const DevBlock* blk;
+  const T* coef;
+  const T* fr;
+  const T* fR;
+  T erot;
   const T* DR;
   const T* Dr;
   const DevJ* dj;
   T alpha, beta;
   long npts, ncol;
-  int NR, nelec, mode;
+  int NR, ng, mode;
   T* out;
   __device__ bool active(int, long) const { return true; }
-  __device__ void operator()(int b, int n, long col, T h) const {
+  __device__ void operator()(int b, int i, long col, T w) const {
     const DevBlock B = blk[b];
-    const long off = (long)n * ncol + col;
-    const long idx = b * npts + off;
-    const T qv = qk[idx];
-    T vq = 0;
-    for (int lp = 0; lp < nelec; ++lp)
-      vq += V[(long)(B.lam * nelec + lp) * npts + off] * qk[(long)(B.base + lp) * npts + off];
-    const DevJ J = dj[B.iJ];
-    const T hs = (h + t[idx] + vq) * (T)J.invdE - (T)J.e0s * qv;
-    if (mode == 1) {
-      out[idx] = hs;
+    const long idx = b * npts + (long)i * ncol + col;
+    if (i >= B.nrow) {  // beyond the block's angular functions: stays zero
+      if (mode == 1) out[idx] = 0; else ckm1[idx] = 0;
       return;
     }
     const int kr = (int)(col / NR);
     const int m = (int)(col - (long)kr * NR);
+    const T* cf = coef + (long)B.coef * kCoefRows * ng;
+    const T g = fmin(fR[m], cf[4 * ng + i]);
+    const T a = fmin(cf[i] * fr[kr], erot) + g * cf[ng + i];
+    const T cv = ck[idx];
+    T h = w + a * cv + t[idx];
+    if (B.up >= 0 && i >= 1) h += g * cf[2 * ng + i] * ck[B.up * npts + (long)(i - 1) * ncol + col];
+    if (B.dn >= 0) h += g * cf[3 * ng + i] * ck[B.dn * npts + (long)(i + 1) * ncol + col];
+    const DevJ J = dj[B.iJ];
+    const T hs = h * (T)J.invdE - (T)J.e0s * cv;
+    if (mode == 1) {
+      out[idx] = hs;
+      return;
+    }
     const T D = DR[m] * Dr[kr];
-    qkm1[idx] = D * (alpha * hs - beta * D * qkm1[idx]);
+    ckm1[idx] = D * (alpha * hs - beta * D * ckm1[idx]);
   }
 };
 
@@ -177,20 +180,18 @@ cudaError_t launch_gamma_forward(const real* q, real* c, const real* T, const De
 }
 
 template <typename real>
-cudaError_t launch_gamma_backward_update(const real* c, const real* Tt, const DevBlock* blocks,
-                                         int nblk, int ng, long ncol, int NR, const real* coef,
-                                         const real* fr, const real* fR, real erot,
-                                         const real* qk, real* qkm1, const real* t,
-                                         const real* V, int nelec, const real* DR,
-                                         const real* Dr, const DevJ* dj, real alpha, real beta,
-                                         int mode, real* out, cudaStream_t st) {
+cudaError_t launch_gamma_update(const real* u, const real* T, const DevBlock* blocks, int nblk,
+                                int ng, long ncol, int NR, const real* coef, const real* fr,
+                                const real* fR, real erot, const real* ck, real* ckm1,
+                                const real* t, const real* V, int nelec, const real* DR,
+                                const real* Dr, const DevJ* dj, real alpha, real beta, int mode,
+                                real* out, cudaStream_t st) {
   const long npts = (long)ng * ncol;
   dim3 grid((unsigned)((ncol + GBN - 1) / GBN), (unsigned)((ng + GBM - 1) / GBM), (unsigned)nblk);
   k_gemm<real, real, real><<<grid, GTHREADS, 0, st>>>(
-      ng, ncol, ng, LoadT<real>{Tt, blocks, ng},
-      LoadFBR<real>{c, blocks, coef, fr, fR, erot, npts, ncol, NR, ng},
-      EpiUpdate<real>{qk, qkm1, t, V, blocks, DR, Dr, dj, alpha, beta, npts, ncol, NR, nelec,
-                      mode, out});
+      ng, ncol, ng, LoadT<real>{T, blocks, ng}, LoadVu<real>{u, V, blocks, npts, ncol, nelec},
+      EpiUpdate<real>{ck, ckm1, t, blocks, coef, fr, fR, erot, DR, Dr, dj, alpha, beta, npts,
+                      ncol, NR, ng, mode, out});
   return cudaGetLastError();
 }
 
@@ -284,23 +285,25 @@ cudaError_t launch_advance(long* d_iter, long n, cudaStream_t st) {
 }
 
 // ------------------------------------------------------- channel projections
-// cut_slot[chan_col[c]] = (k >= kmin) ? sum_(n,kr) P[c][n][kr] qcol[block(c)][n][kr] : 0
+// cut_slot[chan_col[c]] = (k >= kmin) ? sum_kr chi[c][kr] qcol[block(c)][row(c)][kr] : 0,
+// chi already divided by sqrt(dR); qcol holds the FBR coefficients at R_inf.
 template <typename real>
-__global__ void __launch_bounds__(256) k_channels(const real* __restrict__ qcol,
-                                                  const real* __restrict__ P,
+__global__ void __launch_bounds__(128) k_channels(const real* __restrict__ qcol,
+                                                  const real* __restrict__ chi,
                                                   const int* __restrict__ chan_block,
-                                                  const int* __restrict__ chan_col, int ncolq,
+                                                  const int* __restrict__ chan_row,
+                                                  const int* __restrict__ chan_col, int ng, int nr,
                                                   const long* __restrict__ d_iter, int slot,
                                                   long kmin, real* __restrict__ cut) {
-  __shared__ double red[256];
+  __shared__ double red[128];
   const int c = blockIdx.x;
-  const real* p = P + (long)c * ncolq;
-  const real* x = qcol + (long)chan_block[c] * ncolq;
+  const real* p = chi + (long)c * nr;
+  const real* x = qcol + ((long)chan_block[c] * ng + chan_row[c]) * nr;
   double s = 0;
-  for (int i = threadIdx.x; i < ncolq; i += blockDim.x) s += (double)p[i] * (double)x[i];
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) s += (double)p[i] * (double)x[i];
   red[threadIdx.x] = s;
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
+  for (int w = 64; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
@@ -311,12 +314,13 @@ __global__ void __launch_bounds__(256) k_channels(const real* __restrict__ qcol,
 }
 
 template <typename real>
-cudaError_t launch_channels(const real* qcol, const real* P, const int* chan_block,
-                            const int* chan_col, int nchan, int ncolq, const long* d_iter,
-                            int slot, long kmin, real* cut_slot, cudaStream_t st) {
+cudaError_t launch_channels(const real* qcol, const real* chi, const int* chan_block,
+                            const int* chan_row, const int* chan_col, int nchan, int ng, int nr,
+                            const long* d_iter, int slot, long kmin, real* cut_slot,
+                            cudaStream_t st) {
   if (nchan <= 0) return cudaSuccess;
-  k_channels<real><<<nchan, 256, 0, st>>>(qcol, P, chan_block, chan_col, ncolq, d_iter, slot,
-                                          kmin, cut_slot);
+  k_channels<real><<<nchan, 128, 0, st>>>(qcol, chi, chan_block, chan_row, chan_col, ng, nr,
+                                          d_iter, slot, kmin, cut_slot);
   return cudaGetLastError();
 }
 
@@ -401,7 +405,7 @@ cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* ac
   template cudaError_t launch_gamma_forward<real>(const real*, real*, const real*,            \
                                                   const DevBlock*, int, int, long,            \
                                                   cudaStream_t);                              \
-  template cudaError_t launch_gamma_backward_update<real>(                                    \
+  template cudaError_t launch_gamma_update<real>(                                             \
       const real*, const real*, const DevBlock*, int, int, long, int, const real*,            \
       const real*, const real*, real, const real*, real*, const real*, const real*, int,      \
       const real*, const real*, const DevJ*, real, real, int, real*, cudaStream_t);           \
@@ -411,8 +415,8 @@ cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* ac
                                                const long*, const long*, const long*, long,   \
                                                double*, cudaStream_t);                        \
   template cudaError_t launch_channels<real>(const real*, const real*, const int*,            \
-                                             const int*, int, int, const long*, int, long,    \
-                                             real*, cudaStream_t);                            \
+                                             const int*, const int*, int, int, int,           \
+                                             const long*, int, long, real*, cudaStream_t);    \
   template cudaError_t launch_norms<real>(const real*, const long*, int, double*, int,        \
                                           double*, cudaStream_t);
 

@@ -77,28 +77,17 @@ void norm_assoc_legendre(int jmax, int om, const std::vector<double>& x,
   }
 }
 
-// T^Omega: rows P-bar_j^Omega(x_k) sqrt(w_k), j = om..om+n-1, orthonormalised by
-// modified Gram-Schmidt in increasing j (two passes). Row-major n x n.
+// T^Omega: rows P-bar_j^Omega(x_k) sqrt(w_k), j = om..n-1 (n - om rows), zero-padded to
+// n x n, row-major. With n Gauss-Legendre points these rows are exactly orthonormal:
+// every product of two of them integrates a polynomial of degree <= 2n - 2.
 void fbr_matrix(int om, int n, const std::vector<double>& x, const std::vector<double>& w,
                 std::vector<double>& T) {
-  std::vector<double> P;
-  norm_assoc_legendre(om + n - 1, om, x, P);
   T.assign((size_t)n * n, 0.0);
-  std::vector<double> v(n);
-  for (int i = 0; i < n; ++i) {
-    for (int k = 0; k < n; ++k) v[k] = P[(size_t)i * n + k] * std::sqrt(w[k]);
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int p = 0; p < i; ++p) {
-        double d = 0;
-        for (int k = 0; k < n; ++k) d += T[(size_t)p * n + k] * v[k];
-        for (int k = 0; k < n; ++k) v[k] -= d * T[(size_t)p * n + k];
-      }
-    }
-    double nn = 0;
-    for (int k = 0; k < n; ++k) nn += v[k] * v[k];
-    nn = 1.0 / std::sqrt(nn);
-    for (int k = 0; k < n; ++k) T[(size_t)i * n + k] = v[k] * nn;
-  }
+  if (om > n - 1) return;
+  std::vector<double> P;
+  norm_assoc_legendre(n - 1, om, x, P);
+  for (int i = 0; i < n - om; ++i)
+    for (int k = 0; k < n; ++k) T[(size_t)i * n + k] = P[(size_t)i * n + k] * std::sqrt(w[k]);
 }
 
 // Symmetric eigen-decomposition: Householder reduction to tridiagonal form, then
@@ -158,7 +147,7 @@ void symmetric_eigen(int n, const std::vector<double>& Ain, std::vector<double>&
     do {
       for (m = l; m + 1 < n; ++m) {
         const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
-        if (std::fabs(e[m]) <= 1e-17 * dd) break;
+        if (std::fabs(e[m]) + dd == dd) break;  // negligible at working precision
       }
       if (m != l) {
         if (++iter > 200) break;

@@ -36,6 +36,8 @@ struct DevBlock {
   int base;    // block index of (J, Omega, Lambda = 0)
   int coef;    // index of the (J, Omega) angular coefficient set
   int cutcol;  // first column of this block's psi(r*) values in the cut ring
+  int nrow;    // angular functions of the block: ngamma - Omega (rows beyond are zero)
+  int pad;
 };
 
 // Angular coefficient set of one (J, Omega): five rows of ngamma values, for
@@ -66,7 +68,7 @@ struct Tuning {
 template <typename real>
 cudaError_t launch_kinetic_rows(const real* q, real* t, long nrows, const FFTPlan& plan,
                                 const void* tw, const void* ph, const real* lam, int pairs,
-                                cudaStream_t st);
+                                const DevBlock* blocks, int ng, int nr, cudaStream_t st);
 
 template <typename real>
 cudaError_t launch_kinetic_cols(const real* q, real* t, long nplanes, int nr, int NR,
@@ -78,23 +80,28 @@ cudaError_t launch_kinetic_cols(const real* q, real* t, long nplanes, int nr, in
                                 // column at R_inf for channel projections
                                 int m_inf, real* qcol, cudaStream_t st);
 
+// out[b] = Tmat[omega(b)] in[b] (per block [ng x ng] x [ng x ncol]); Tmat is T (DVR ->
+// FBR) or its transpose (FBR -> DVR), zero-padded to ng x ng.
 template <typename real>
 cudaError_t launch_gamma_forward(const real* q, real* c, const real* T, const DevBlock* blocks,
                                  int nblk, int ng, long ncol, cudaStream_t st);
 
+// w = T^Omega (V u) per block, then the FBR combination and the damped update:
+// u holds the DVR values of every block (u = (T^Omega)^T c_k), c = c_k.
 template <typename real>
-cudaError_t launch_gamma_backward_update(const real* c, const real* Tt, const DevBlock* blocks,
-                                         int nblk, int ng, long ncol, int NR,
-                                         const real* coef, const real* fr, const real* fR,
-                                         real erot, const real* qk, real* qkm1, const real* t,
-                                         const real* V, int nelec, const real* DR,
-                                         const real* Dr, const DevJ* dj, real alpha,
-                                         real beta, int mode, real* out, cudaStream_t st);
+cudaError_t launch_gamma_update(const real* u, const real* T, const DevBlock* blocks, int nblk,
+                                int ng, long ncol, int NR, const real* coef, const real* fr,
+                                const real* fR, real erot, const real* ck, real* ckm1,
+                                const real* t, const real* V, int nelec, const real* DR,
+                                const real* Dr, const DevJ* dj, real alpha, real beta, int mode,
+                                real* out, cudaStream_t st);
 
+// cut[chan_col[c]] = sum_kr chi[c][kr] qcol[block(c)][row(c)][kr]  (0 before kmin)
 template <typename real>
-cudaError_t launch_channels(const real* qcol, const real* P, const int* chan_block,
-                            const int* chan_col, int nchan, int ncolq, const long* d_iter,
-                            int slot, long kmin, real* cut_slot, cudaStream_t st);
+cudaError_t launch_channels(const real* qcol, const real* chi, const int* chan_block,
+                            const int* chan_row, const int* chan_col, int nchan, int ng, int nr,
+                            const long* d_iter, int slot, long kmin, real* cut_slot,
+                            cudaStream_t st);
 
 template <typename real>
 cudaError_t launch_norms(const real* q, const long* J_begin, int nJ, double* partial,

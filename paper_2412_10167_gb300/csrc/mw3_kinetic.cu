@@ -165,7 +165,9 @@ __global__ void __launch_bounds__(256) k_kinetic_rows(const T* __restrict__ q, T
                                                       long nrows, FFTPlan plan,
                                                       const cpx<T>* __restrict__ twg,
                                                       const cpx<T>* __restrict__ phg,
-                                                      const T* __restrict__ lamg, int P) {
+                                                      const T* __restrict__ lamg, int P,
+                                                      const DevBlock* __restrict__ blocks,
+                                                      int ng, int nr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = plan.N;
   cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -184,8 +186,12 @@ __global__ void __launch_bounds__(256) k_kinetic_rows(const T* __restrict__ q, T
     const int i = idx - p * N;
     const long ra = row0 + 2L * p;
     T xa = 0, xb = 0;
-    if (ra < nrows) xa = q[ra * N + i];
-    if (ra + 1 < nrows) xb = q[(ra + 1) * N + i];
+    // a pair never straddles planes (nr is even); rows beyond a block's angular
+    // functions are zero and are neither read nor written
+    const long plane = ra / nr;
+    const bool live = ra < nrows && (int)(plane % ng) < blocks[plane / ng].nrow;
+    if (live) xa = q[ra * N + i];
+    if (live && ra + 1 < nrows) xb = q[(ra + 1) * N + i];
     const T sg = (i & 1) ? (T)-1 : (T)1;
     za[(long)p * N + perm_pos(i, N)] = {sg * xa, sg * xb};
   }
@@ -202,8 +208,10 @@ __global__ void __launch_bounds__(256) k_kinetic_rows(const T* __restrict__ q, T
     const long ra = row0 + 2L * p;
     const T sg = (i & 1) ? (T)-1 : (T)1;
     const cpx<T> y = Y[(long)p * N + perm_pos(i, N)];
-    if (ra < nrows) t[ra * N + i] = sg * y.x;
-    if (ra + 1 < nrows) t[(ra + 1) * N + i] = sg * y.y;
+    const long plane = ra / nr;
+    const bool live = ra < nrows && (int)(plane % ng) < blocks[plane / ng].nrow;
+    if (live) t[ra * N + i] = sg * y.x;
+    if (live && ra + 1 < nrows) t[(ra + 1) * N + i] = sg * y.y;
   }
 }
 
@@ -231,6 +239,7 @@ __global__ void __launch_bounds__(256) k_kinetic_cols(
   for (int i = threadIdx.x; i <= N; i += blockDim.x) lam[i] = lamg[i];
 
   const long plane = blockIdx.y;                  // = b * ng + n
+  if ((int)(plane % ng) >= blocks[plane / ng].nrow) return;  // beyond the angular functions
   const int c0 = blockIdx.x * C;
   const T* qp = q + plane * (long)nr * NR;
   T* tp = t + plane * (long)nr * NR;
@@ -299,7 +308,7 @@ static size_t kinetic_smem(int N, int P) {
 template <typename real>
 cudaError_t launch_kinetic_rows(const real* q, real* t, long nrows, const FFTPlan& plan,
                                 const void* tw, const void* ph, const real* lam, int pairs,
-                                cudaStream_t st) {
+                                const DevBlock* blocks, int ng, int nr, cudaStream_t st) {
   const size_t sm = kinetic_smem<real>(plan.N, pairs);
   static bool attr_set[2] = {false, false};
   const int slot = sizeof(real) == 8 ? 1 : 0;
@@ -312,7 +321,8 @@ cudaError_t launch_kinetic_rows(const real* q, real* t, long nrows, const FFTPla
   const unsigned grid = (unsigned)((npairs + pairs - 1) / pairs);
   k_kinetic_rows<real><<<grid, 256, sm, st>>>(q, t, nrows, plan,
                                               static_cast<const cpx<real>*>(tw),
-                                              static_cast<const cpx<real>*>(ph), lam, pairs);
+                                              static_cast<const cpx<real>*>(ph), lam, pairs,
+                                              blocks, ng, nr);
   return cudaGetLastError();
 }
 
@@ -341,10 +351,10 @@ cudaError_t launch_kinetic_cols(const real* q, real* t, long nplanes, int nr, in
 
 template cudaError_t launch_kinetic_rows<double>(const double*, double*, long, const FFTPlan&,
                                                  const void*, const void*, const double*, int,
-                                                 cudaStream_t);
+                                                 const DevBlock*, int, int, cudaStream_t);
 template cudaError_t launch_kinetic_rows<float>(const float*, float*, long, const FFTPlan&,
                                                 const void*, const void*, const float*, int,
-                                                cudaStream_t);
+                                                const DevBlock*, int, int, cudaStream_t);
 template cudaError_t launch_kinetic_cols<double>(const double*, double*, long, int, int,
                                                  const FFTPlan&, const void*, const void*,
                                                  const double*, int, int, const double*,

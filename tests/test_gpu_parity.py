@@ -1,5 +1,9 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
 
+States passed to the library are values on the grid; the library holds each block
+in the span of its angular functions (j = Omega..ngamma-1), so random test vectors
+are first projected onto that span.
+
 Tolerances (written from the arithmetic):
   * FP64 path: the operator agrees with the oracle to 1e-12 of max|H_s q| (different
     summation orders only); after N iterations q_N agrees to 1e-10 relative (l2),
@@ -49,7 +53,8 @@ def test_apply_hs_matches_oracle(name, prec):
     cfg = W.SMALL[name]
     pr = mw3().Propagator(cfg, precision=prec)
     H = GridHamiltonian(cfg)
-    q = W.random_state(H.shape, 2412)
+    # the state of a block lies in the span of its angular functions
+    q = H.project(W.random_state(H.shape, 2412))
     ref = H.apply_Hs(q)
     got = pr.apply_hs(q)
     tol = 1e-12 if prec == "fp64" else 2e-6
@@ -171,7 +176,7 @@ def test_full_size_config2_operator_and_first_steps():
     both precisions, and the first two damped iterations plus their flux sums in FP64."""
     cfg = copy.deepcopy(W.C2)
     H = GridHamiltonian(cfg)
-    q = W.random_state(H.shape, 2412)
+    q = H.project(W.random_state(H.shape, 2412))
     ref = H.apply_Hs(q)
     scale = np.max(np.abs(ref))
     for prec, tol in (("fp64", 1e-12), ("mixed", 2e-6)):

@@ -84,6 +84,26 @@ def test_gauss_legendre_exactness(n):
         assert abs(np.sum(w * x ** d) - exact) < 1e-12
 
 
+def test_gauss_legendre_against_library_and_high_precision():
+    """Nodes match numpy's leggauss; weights match 40-digit Newton values to 2e-13
+    (the library routine's weights are only good to ~1e-12 at n = 96)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    for n in (24, 96, 180):
+        x, w = basis.gauss_legendre(n)
+        xl, wl = np.polynomial.legendre.leggauss(n)
+        np.testing.assert_allclose(x, xl, atol=1e-15)
+        np.testing.assert_allclose(w, wl, rtol=1e-11)
+        for i in (0, 1, n // 3, n // 2, n - 1):
+            z = mpmath.mpf(x[i])
+            for _ in range(6):
+                z = z - mpmath.legendre(n, z) / mpmath.diff(lambda t: mpmath.legendre(n, t), z)
+            dp = mpmath.diff(lambda t: mpmath.legendre(n, t), z)
+            wz = 2 / ((1 - z ** 2) * dp ** 2)
+            assert abs(float(z) - x[i]) < 1e-15
+            assert abs(float((wz - w[i]) / wz)) < 2e-13
+
+
 @pytest.mark.parametrize("omega", [0, 1, 2, 5, 10])
 def test_norm_assoc_legendre_matches_scipy(omega):
     x = np.linspace(-0.97, 0.97, 13)
@@ -96,27 +116,23 @@ def test_norm_assoc_legendre_matches_scipy(omega):
         np.testing.assert_allclose(P[j - omega], ref * np.exp(lnorm), rtol=1e-11, atol=1e-12)
 
 
-@pytest.mark.parametrize("omega,n", [(0, 24), (1, 12), (3, 20), (10, 96)])
-def test_fbr_matrix_orthogonal(omega, n):
+@pytest.mark.parametrize("omega,n", [(0, 24), (1, 12), (3, 20), (10, 96), (20, 96), (20, 180)])
+def test_fbr_rows_orthonormal(omega, n):
+    """Quadrature exactness makes the n - Omega rows orthonormal, even at large Omega."""
     T = basis.fbr_matrix(omega, n)
-    np.testing.assert_allclose(T @ T.T, np.eye(n), atol=1e-13)
-    np.testing.assert_allclose(T.T @ T, np.eye(n), atol=1e-13)
+    assert T.shape == (n - omega, n)
+    np.testing.assert_allclose(T @ T.T, np.eye(n - omega), atol=2e-14)
 
 
-def test_fbr_omega0_is_raw_legendre_rows():
-    n = 24
+def test_fbr_rows_are_legendre_functions():
+    n, om = 24, 4
     x, w = basis.gauss_legendre(n)
-    raw = basis.norm_assoc_legendre(n - 1, 0, x) * np.sqrt(w)
-    np.testing.assert_allclose(basis.fbr_matrix(0, n), raw, atol=1e-14)
-
-
-def test_fbr_low_rows_are_raw_legendre_rows():
-    """For Omega > 0 only rows beyond quadrature exactness change under Gram-Schmidt."""
-    om, n = 4, 20
-    x, w = basis.gauss_legendre(n)
-    raw = basis.norm_assoc_legendre(om + n - 1, om, x) * np.sqrt(w)
-    T = basis.fbr_matrix(om, n)
-    # rows i, i' are exactly orthonormal when 2 (om + i) <= 2n - 1 + ... ; the first
-    # n - om rows (degree of P-bar^2 products <= 2n - 1 after removing (1-x^2)^om) stay put
-    k = n - om
-    np.testing.assert_allclose(T[:k], raw[:k], atol=1e-12)
+    T = basis.fbr_matrix(om, n, x, w)
+    for i in (0, 5, n - om - 1):
+        j = om + i
+        ref = scipy.special.lpmv(om, j, x) * np.sqrt((2 * j + 1) / 2.0 * np.exp(
+            scipy.special.gammaln(j - om + 1) - scipy.special.gammaln(j + om + 1)))
+        np.testing.assert_allclose(T[i], ref * np.sqrt(w), atol=1e-13)
+    # Omega = 0 is a square orthogonal matrix
+    T0 = basis.fbr_matrix(0, n, x, w)
+    np.testing.assert_allclose(T0.T @ T0, np.eye(n), atol=1e-14)
