@@ -1389,20 +1389,22 @@ int mw3_kernel_times(mw3_ctx* ctx, int enable, const char** names, double* ms, l
 int mw3_checkpoint_save(mw3_ctx* ctx, const char* path) {
   if (!ctx || !path) return MW3_ERR_BAD_ARG;
   if (ctx->stage < 5 || ctx->host_only) return ctx->fail(MW3_ERR_STATE, "nothing to save");
-  const size_t n = (size_t)ctx->nblk * ctx->npts;
-  std::vector<double> q(n), qp(n), acc(ctx->acc_size);
-  int st = mw3_get_state(ctx, q.data(), qp.data());
-  if (st) return st;
+  // raw device state (FBR coefficients in the context's precision), no conversion
+  const size_t nb = (size_t)ctx->nblk * ctx->npts * ctx->rs();
+  std::vector<char> q(nb), qp(nb);
+  std::vector<double> acc(ctx->acc_size);
+  CK(cudaMemcpyAsync(q.data(), dptr(ctx, state_name(ctx, true)), nb, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(qp.data(), dptr(ctx, state_name(ctx, false)), nb, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(acc.data(), dptr(ctx, "acc"), acc.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   std::ofstream f(path, std::ios::binary);
   if (!f) return ctx->fail(MW3_ERR_IO, std::string("cannot open ") + path);
-  const uint64_t magic = 0x4d57334350543031ULL;  // "MW3CPT01"
+  const uint64_t magic = 0x4d57334350543032ULL;  // "MW3CPT02"
   const uint64_t hdr[6] = {magic, (uint64_t)ctx->nblk, (uint64_t)ctx->npts, (uint64_t)ctx->acc_size,
                            (uint64_t)ctx->iter, (uint64_t)ctx->precision};
   f.write((const char*)hdr, sizeof(hdr));
-  f.write((const char*)q.data(), n * 8);
-  f.write((const char*)qp.data(), n * 8);
+  f.write(q.data(), nb);
+  f.write(qp.data(), nb);
   f.write((const char*)acc.data(), acc.size() * 8);
   const uint64_t nt = ctx->norm_trace.size();
   f.write((const char*)&nt, 8);
@@ -1418,22 +1420,23 @@ int mw3_checkpoint_load(mw3_ctx* ctx, const char* path) {
   if (!f) return ctx->fail(MW3_ERR_IO, std::string("cannot open ") + path);
   uint64_t hdr[6];
   f.read((char*)hdr, sizeof(hdr));
-  if (!f || hdr[0] != 0x4d57334350543031ULL || hdr[1] != (uint64_t)ctx->nblk ||
+  if (!f || hdr[0] != 0x4d57334350543032ULL || hdr[1] != (uint64_t)ctx->nblk ||
       hdr[2] != (uint64_t)ctx->npts || hdr[3] != (uint64_t)ctx->acc_size ||
       hdr[5] != (uint64_t)ctx->precision)
     return ctx->fail(MW3_ERR_IO, "checkpoint does not match this configuration");
-  const size_t n = (size_t)ctx->nblk * ctx->npts;
-  std::vector<double> q(n), qp(n), acc(ctx->acc_size);
-  f.read((char*)q.data(), n * 8);
-  f.read((char*)qp.data(), n * 8);
+  const size_t nb = (size_t)ctx->nblk * ctx->npts * ctx->rs();
+  std::vector<char> q(nb), qp(nb);
+  std::vector<double> acc(ctx->acc_size);
+  f.read(q.data(), nb);
+  f.read(qp.data(), nb);
   f.read((char*)acc.data(), acc.size() * 8);
   uint64_t nt = 0;
   f.read((char*)&nt, 8);
   std::vector<double> tr(nt);
   f.read((char*)tr.data(), nt * 8);
   if (!f) return ctx->fail(MW3_ERR_IO, "truncated checkpoint");
-  int st = mw3_set_state(ctx, q.data(), qp.data());
-  if (st) return st;
+  CK(cudaMemcpyAsync(dptr(ctx, state_name(ctx, true)), q.data(), nb, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(dptr(ctx, state_name(ctx, false)), qp.data(), nb, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(dptr(ctx, "acc"), acc.data(), acc.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
   ctx->iter = (long)hdr[4];
   long it = ctx->iter;
