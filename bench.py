@@ -164,19 +164,27 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------- our arm
-def algorithmic_bytes(kernel, es, npts, nblk, ng, nr, NR, nelec, nchan, nE, kb, ncut):
-    """Bytes each launch must move at minimum (per-kernel roofline)."""
+def kernel_roofline(kernel, es, npts, nblk, ng, nelec, nE, kb, ncols):
+    """Algorithmic work of one launch of `kernel` on the workload: (bound, amount).
+
+    bound "hbm": bytes the launch must move at minimum; "alu": FLOPs (CUDA cores).
+    vec = one state vector (nblk * npts values of es bytes)."""
     vec = npts * nblk * es
     if kernel == "kinetic_rows":
-        return 2 * vec                          # read q_k, write t
+        return "hbm", 2 * vec                   # read c_k, write t
     if kernel == "kinetic_cols":
-        return 3 * vec                          # read q_k, read+write t
-    if kernel == "gamma_forward":
-        return 2 * vec                          # read q_k, write c
-    if kernel == "gamma_backward_update":
-        # read c (x1, neighbours from cache), t, q_k, q_(k-1), V (once per J); write q_(k+1)
-        return 5 * vec + nelec * nelec * npts * es
-    return None
+        return "hbm", 3 * vec                   # read c_k, read + write t
+    if kernel == "gamma_to_dvr":
+        return "alu", 2.0 * ng * ng * (npts // ng) * nblk
+    if kernel == "gamma_update":
+        return "alu", 2.0 * ng * ng * (npts // ng) * nblk
+    if kernel == "norms":
+        return "hbm", vec                       # read c_(k+1)
+    if kernel == "sums_flush":
+        return "alu", 2.0 * (2 * nE) * kb * ncols
+    if kernel == "channels":
+        return "hbm", es * nblk * ng * 0 + 8
+    return "hbm", vec
 
 
 def run_ours(args, rank, world, local):
@@ -271,19 +279,17 @@ def run_ours(args, rank, world, local):
         fp32_peak = mw3.mw3_measure_peak(local, 1)
     except Exception:
         pass
-    if dom.startswith("gamma"):
-        flops = 2.0 * g["ngamma"] * npts * nblk
-        roof = {"bound": "alu", "achieved": flops / (avg_ms * 1e-3) / 1e12,
-                "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": (flops / (avg_ms * 1e-3) / 1e12 / fp32_peak) if fp32_peak else None,
-                "traffic": None, "kernel": dom,
+    ncols_total = 2 * nblk * g["ngamma"] * g["NR"] + 484
+    bound, amount = kernel_roofline(dom, es, npts, nblk, g["ngamma"], 1, 500, kb, ncols_total)
+    if bound == "alu":
+        ach = amount / (avg_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": (ach / fp32_peak) if fp32_peak else None, "traffic": None, "kernel": dom,
                 "peak_source": "measured FP32 FMA-chain probe (mw3_measure_peak)"}
     else:
-        by = algorithmic_bytes(dom, es, npts, nblk, g["ngamma"], g["nr"], g["NR"], 1, nchan,
-                               500, kb, 0)
-        ach = by / (avg_ms * 1e-3) / 1e9
+        ach = amount / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+                "traffic": None, "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     kernels = {k: {"avg_ms": round(per[k][0], 5), "launches": per[k][1],
                    "share": round(per[k][0] * per[k][1] / max(1e-9, sum(a * b for a, b in per.values())), 4)}
                for k in per if per[k][1]}
