@@ -233,6 +233,19 @@ long mw3_get_tuning(const mw3_ctx* ctx, const char* key);
 int mw3_kernel_times(mw3_ctx* ctx, int enable, const char** names, double* ms, long* launches,
                      int* count);
 
+/* Allocation-free sums of squares, for callers that cannot call cudaMalloc (a fixed
+ * memory arena, a region where allocating would stall other streams). The paper has
+ * no counterpart: this is the per-J norm reduction of the propagation (its divergence
+ * check, ||q_k||^2) with the partial-sum scratch in a 128 KB file-scope device array
+ * instead of context memory. out[s] = sum_i x[s * seg_len + i]^2 for s < nseg.
+ *   x    device FP64 [nseg * seg_len], caller-owned;  out  device FP64 [nseg].
+ *   nseg 1..64 (the array's capacity); other values return MW3_ERR_BAD_ARG.
+ * Enqueued on `stream` (a cudaStream_t, NULL = legacy default); returns without
+ * synchronising. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current: make it before any stream
+ * capture. All calls share the array; calls that overlap on the GPU race. */
+int mw3_norms_noalloc(const double* x, long seg_len, int nseg, double* out, void* stream);
+
 /* Diagnostic: achieved FMA throughput of this GPU in TFLOP/s from an FMA-chain
  * kernel (kind 0 = FP64, 1 = FP32), the ALU roofline of the CUDA-core kernels.
  * Allocates 8 KB of device memory for the duration of the call. */

@@ -92,6 +92,7 @@ _SIGS = {
     "mw3_checkpoint_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "mw3_checkpoint_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "mw3_measure_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "mw3_norms_noalloc": (C.c_int, [C.c_void_p, C.c_long, C.c_int, C.c_void_p, C.c_void_p]),
     "mw3_set_tuning": (C.c_int, [C.c_void_p, C.c_char_p, C.c_long]),
     "mw3_get_tuning": (C.c_long, [C.c_void_p, C.c_char_p]),
     "mw3_kernel_times": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p),
@@ -181,6 +182,15 @@ def mw3_propagate(ctx, nsteps):
 
 def mw3_iteration(ctx):
     return lib.mw3_iteration(ctx)
+
+
+def mw3_norms_noalloc(x_ptr: int, seg_len: int, nseg: int, out_ptr: int, stream: int = 0) -> int:
+    """Allocation-free per-segment sums of squares on device pointers (no cudaMalloc)."""
+    code = lib.mw3_norms_noalloc(C.c_void_p(x_ptr), seg_len, nseg, C.c_void_p(out_ptr),
+                                 C.c_void_p(stream))
+    if code != 0:
+        raise MW3Error(code, "mw3_norms_noalloc failed")
+    return code
 
 
 def mw3_measure_peak(device: int, kind: int) -> float:
