@@ -29,6 +29,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "mw3_host.h"
@@ -38,9 +39,9 @@ using namespace mw3;
 
 namespace {
 
-const char* kKernelNames[] = {"kinetic_rows", "kinetic_cols", "gamma_to_dvr",
-                              "gamma_update", "channels", "norms", "sums_flush"};
-constexpr int kNumKernels = 7;
+const char* kKernelNames[] = {"kinetic_rows", "kinetic_cols", "gamma_to_dvr", "gamma_update",
+                              "channels",     "norms",        "sums_flush",   "angular_tc"};
+constexpr int kNumKernels = 8;
 
 struct DevBuf {
   void* p = nullptr;
@@ -82,6 +83,8 @@ struct mw3_ctx {
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
   Tuning tune{4, 32, 32, 1, 0};
+  int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
+  bool tc_ok = false;  // the tensor-core angular step supports this grid
 
   // grid and blocks
   int NR = 0, nr = 0, ng = 0, nelec = 1, nJ = 0, omega_max = 0;
@@ -661,6 +664,41 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
   }
   if ((st = upload_real(ctx, "T", Tall))) return st;
   if ((st = upload_real(ctx, "Tt", Ttall))) return st;
+  // tensor-core operands: T^Omega and its transpose, padded to kp x kp, split into a
+  // TF32-rounded high part and the exact FP32 remainder
+  ctx->kp = ((ng + 15) / 16) * 16;
+  ctx->tc_ok = (ctx->precision == MW3_MIXED) && ctx->kp <= kTcMaxKp;
+  ctx->tune.use_tc = ctx->tc_ok ? 1 : 0;
+  if (ctx->tc_ok) {
+    const int kp = ctx->kp;
+    const size_t nom = ctx->T.size();
+    std::vector<float> th(nom * kp * kp, 0.f), tl(th.size(), 0.f), tth(th.size(), 0.f),
+        ttl(th.size(), 0.f);
+    auto split = [](double v, float& hi, float& lo) {
+      const float x = (float)v;
+      uint32_t u;
+      std::memcpy(&u, &x, 4);
+      u = (u + 0x1000u) & 0xFFFFE000u;  // round to nearest (ties away) at 10 mantissa bits
+      std::memcpy(&hi, &u, 4);
+      lo = x - hi;
+    };
+    for (size_t om = 0; om < nom; ++om)
+      for (int i = 0; i < ng; ++i)
+        for (int n = 0; n < ng; ++n) {
+          const double v = ctx->T[om][(size_t)i * ng + n];
+          split(v, th[(om * kp + i) * kp + n], tl[(om * kp + i) * kp + n]);
+          split(v, tth[(om * kp + n) * kp + i], ttl[(om * kp + n) * kp + i]);
+        }
+    if ((st = upload_raw(ctx, "T_hi", th)) || (st = upload_raw(ctx, "T_lo", tl)) ||
+        (st = upload_raw(ctx, "Tt_hi", tth)) || (st = upload_raw(ctx, "Tt_lo", ttl)))
+      return st;
+    std::vector<int> gb(ctx->nJ + 1);
+    for (int iJ = 0; iJ <= ctx->nJ; ++iJ) gb[iJ] = (int)(ctx->J_first_block[iJ] / ctx->nelec);
+    if ((st = upload_raw(ctx, "g_begin", gb))) return st;
+    const long ntiles = (ctx->ncol + 127) / 128;
+    if ((st = dalloc(ctx, "npart", (size_t)(ctx->nblk / ctx->nelec) * ntiles * 8))) return st;
+    if ((st = dalloc(ctx, "tc_err", 16)) || (st = dzero(ctx, "tc_err"))) return st;
+  }
   if ((st = upload_real(ctx, "coef", ctx->coef))) return st;
   if ((st = upload_real(ctx, "fR", ctx->fR))) return st;
   if ((st = upload_real(ctx, "fr", ctx->fr))) return st;
@@ -1054,12 +1092,51 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
                                  analysis ? ctx->m_inf : -1, analysis ? B.qcol : nullptr, st));
     tm.stop();
   }
-  {
+  const bool tc = std::is_same<real, float>::value && ctx->tc_ok && ctx->tune.use_tc;
+  if (tc) {
+    Timer tm(ctx, 7, timed);
+    TcArgs a{};
+    a.ck = (const float*)qk;
+    a.ckm1 = (float*)qkm1;
+    a.t = (const float*)B.t;
+    a.V = (const float*)B.V;
+    a.T_hi = (const float*)dptr(ctx, "T_hi");
+    a.T_lo = (const float*)dptr(ctx, "T_lo");
+    a.Tt_hi = (const float*)dptr(ctx, "Tt_hi");
+    a.Tt_lo = (const float*)dptr(ctx, "Tt_lo");
+    a.blocks = B.blocks;
+    a.coef = (const float*)B.coef;
+    a.fr = (const float*)B.fr;
+    a.fR = (const float*)B.fR;
+    a.DR = (const float*)B.DR;
+    a.Dr = (const float*)B.Dr;
+    a.dj = B.dj;
+    a.out = (float*)hs_out;
+    a.npart = mode == 0 ? (double*)dptr(ctx, "npart") : nullptr;
+    a.err = (int*)dptr(ctx, "tc_err");
+    a.erot = (float)ctx->erot;
+    a.alpha = first ? 1.0f : 2.0f;
+    a.beta = first ? 0.0f : 1.0f;
+    a.ncol = ctx->ncol;
+    a.npts = ctx->npts;
+    a.ng = ctx->ng;
+    a.kp = ctx->kp;
+    a.NR = ctx->NR;
+    a.nelec = ctx->nelec;
+    a.mode = mode;
+    a.ntiles = (int)((ctx->ncol + 127) / 128);
+    int tc = 32;
+    while (tc < 2 * ctx->nelec * ctx->kp) tc *= 2;
+    a.tmem_cols = tc;
+    LK(launch_angular_tc(a, ctx->nblk / ctx->nelec, (const int*)dptr(ctx, "g_begin"), ctx->nJ,
+                         mode == 0 ? B.normbuf + (long)slot * ctx->nJ : nullptr, st));
+    tm.stop();
+  } else {
     Timer tm(ctx, 2, timed);
     LK(launch_gamma_forward<real>(qk, B.u, B.Tt, B.blocks, ctx->nblk, ctx->ng, ctx->ncol, st));
     tm.stop();
   }
-  {
+  if (!tc) {
     Timer tm(ctx, 3, timed);
     const real alpha = first ? (real)1 : (real)2;
     const real beta = first ? (real)0 : (real)1;
@@ -1075,7 +1152,7 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
                              ctx->ng, ctx->nr, B.d_iter, slot, ctx->an.kmin, cut_slot, st));
     tm.stop();
   }
-  {
+  if (!tc) {
     Timer tm(ctx, 5, timed);
     LK(launch_norms<real>(qkm1, B.J_begin, ctx->nJ, B.npartial, 256, B.normbuf + (long)slot * ctx->nJ, st));
     tm.stop();
@@ -1111,8 +1188,12 @@ int chunk(mw3_ctx* ctx, int n, bool timed) {
 int check_norms(mw3_ctx* ctx, int n) {
   std::vector<double> h((size_t)n * ctx->nJ);
   CK(cudaMemcpyAsync(h.data(), dptr(ctx, "normbuf"), h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  int tc_err = 0;
+  if (dptr(ctx, "tc_err"))
+    CK(cudaMemcpyAsync(&tc_err, dptr(ctx, "tc_err"), 4, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   collect_times(ctx);
+  if (tc_err) return ctx->fail(MW3_ERR_TIMEOUT, "tensor-core step: an mbarrier wait timed out");
   ctx->norm_trace.insert(ctx->norm_trace.end(), h.begin(), h.end());
   for (double v : h)
     if (!(v <= 1.5 * ctx->norm0)) return ctx->fail(MW3_ERR_DIVERGED, "||q_k||^2 > 1.5 ||q_0||^2");

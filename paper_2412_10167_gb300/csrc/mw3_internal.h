@@ -118,6 +118,35 @@ cudaError_t launch_sums_flush(const real* ph, const real* cut, long ncut_total, 
 
 cudaError_t launch_advance(long* d_iter, long n, cudaStream_t st);
 
+// Fused tensor-core angular step (mw3_tc.cu), FP32 state, ngamma padded to kp <= 112.
+struct TcArgs {
+  const float* ck;
+  float* ckm1;
+  const float* t;
+  const float* V;
+  const float* T_hi;    // [omega][kp][kp]  T^Omega[i][n]       (GEMM 2 B: N = i, K = n)
+  const float* T_lo;
+  const float* Tt_hi;   // [omega][kp][kp]  T^Omega[i][n] at [n][i] (GEMM 1 B: N = n, K = i)
+  const float* Tt_lo;
+  const DevBlock* blocks;
+  const float* coef;
+  const float* fr;
+  const float* fR;
+  const float* DR;
+  const float* Dr;
+  const DevJ* dj;
+  float* out;           // mode 1: H_s c
+  double* npart;        // [group][tile] sums of squares of c_(k+1)
+  int* err;             // set on a wait that timed out
+  float erot, alpha, beta;
+  long ncol, npts;
+  int ng, kp, NR, nelec, mode, ntiles, tmem_cols;
+};
+size_t angular_tc_smem(int kp);
+cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
+                              double* norm_out, cudaStream_t st);
+constexpr int kTcMaxKp = 112;
+
 cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* accoff,
                                const long* ncols, const long* ncut, double* out,
                                cudaStream_t st);

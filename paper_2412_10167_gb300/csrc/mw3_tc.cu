@@ -1,0 +1,359 @@
+// Fused angular step on the 5th-generation tensor cores (mixed precision).
+//
+// One CTA handles 128 grid columns (r, R) of one (J, Omega) group (all its
+// electronic states) and performs, per state L (Section 2.1 items 3-5, Eq. wvp-k):
+//   GEMM 1   u_L^T[col][n] = sum_i c_L^T[col][i] T^Omega[i][n]          (FBR -> DVR)
+//   potential (V u)_L[col][n] = sum_L' V_LL'[n][col] u_L'[col][n]
+//   GEMM 2   w_L^T[col][i] = sum_n (V u)_L^T[col][n] T^Omega[i][n]     (DVR -> FBR)
+//   epilogue h = w + a_j c + bp_j c^(Omega+1)_(j) + bm_j c^(Omega-1)_(j) + t,
+//            c_(k+1) = D (alpha (h/dE - (E0/dE) c) - beta D c_(k-1)), norm partials.
+// M = 128 grid columns (TMEM lanes), N = K = ngamma padded to a multiple of 16.
+// FP32 accuracy from TF32 tensor cores by splitting every operand x = hi + lo
+// (hi = x rounded to TF32, lo = x - hi exactly) and accumulating hi*hi + hi*lo + lo*hi
+// in FP32 (the dropped lo*lo term is ~2^-22 relative).
+//
+// Operands are staged in shared memory in the canonical no-swizzle K-major layout:
+// 8-row x 16-byte core matrices, K-adjacent core matrices 128 B apart (leading
+// byte offset), 8-row groups K*4*8/... (stride byte offset = K * 32 B). One elected
+// thread issues tcgen05.mma; completion is signalled through an mbarrier by
+// tcgen05.commit; every wait is bounded and reports through an error word.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mw3_internal.h"
+
+namespace mw3 {
+
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_THREADS = 256;
+constexpr long kWaitLimit = 1L << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// byte offset of element (row, k) of a K-major core-matrix tile whose K extent is kp
+__device__ __forceinline__ uint32_t cm_off(int row, int k, int kp) {
+  return (uint32_t)((row >> 3) * (kp * 32) + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version (tcgen05); base offset 0; no swizzle
+  return d;
+}
+
+// instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major
+__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (long it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Copy a padded kp x kp FP32 matrix pair (hi, lo), row-major, into core-matrix layout.
+__device__ void load_b(const float* __restrict__ hi, const float* __restrict__ lo,
+                       unsigned char* Bhi, unsigned char* Blo, int kp) {
+  const int nq = kp * kp / 4;
+  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+    const int row = e / (kp / 4);
+    const int k4 = (e - row * (kp / 4)) * 4;
+    const float4 h = *reinterpret_cast<const float4*>(hi + (long)row * kp + k4);
+    const float4 l = *reinterpret_cast<const float4*>(lo + (long)row * kp + k4);
+    const uint32_t off = cm_off(row, k4, kp);
+    *reinterpret_cast<float4*>(Bhi + off) = h;
+    *reinterpret_cast<float4*>(Blo + off) = l;
+  }
+}
+
+// 3 x (kp / 8) MMAs: D (+)= Ahi Bhi + Ahi Blo + Alo Bhi over K = kp.
+__device__ void issue_split_gemm(uint32_t dtmem, const unsigned char* Ahi, const unsigned char* Alo,
+                                 const unsigned char* Bhi, const unsigned char* Blo, int kp,
+                                 uint32_t idesc) {
+  const uint32_t sbo = (uint32_t)kp * 32, lbo = 128;
+  const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+  for (int ks = 0; ks < kp / 8; ++ks) {
+    const uint32_t o = (uint32_t)ks * 256;  // two core matrices along K per K-step of 8
+    mma_tf32(dtmem, smem_desc(ah + o, lbo, sbo), smem_desc(bh + o, lbo, sbo), idesc, ks > 0);
+    mma_tf32(dtmem, smem_desc(ah + o, lbo, sbo), smem_desc(bl + o, lbo, sbo), idesc, 1);
+    mma_tf32(dtmem, smem_desc(al + o, lbo, sbo), smem_desc(bh + o, lbo, sbo), idesc, 1);
+  }
+}
+
+}  // namespace
+
+
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int kp = a.kp;
+  const size_t abytes = (size_t)TC_M * kp * 4, bbytes = (size_t)kp * kp * 4;
+  unsigned char* Ahi = sm;
+  unsigned char* Alo = Ahi + abytes;
+  unsigned char* Bhi = Alo + abytes;
+  unsigned char* Blo = Bhi + bbytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + bbytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  double* red = reinterpret_cast<double*>(mbar + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3;          // TMEM lane quarter
+  const int half = warp >> 2;      // which half of the N columns this warp reads
+  const int m = q * 32 + lane;     // tile row = grid column within the tile
+  const long col = (long)blockIdx.x * TC_M + m;
+  const bool live = col < a.ncol;
+  const int g = blockIdx.y;
+  const int b0 = g * a.nelec;
+  const DevBlock B0 = a.blocks[b0];
+  const int om = B0.omega;
+  const int nrow = B0.nrow;
+  const uint32_t mb = smem_u32(mbar);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(a.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  uint32_t phase = 0;
+  bool ok = true;
+  const uint32_t idesc = idesc_tf32(TC_M, kp);
+  const int ncb = kp / 2;           // columns per half
+  const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+
+  // ---------------------------------------------------------- GEMM 1 (per state)
+  load_b(a.Tt_hi + (long)om * kp * kp, a.Tt_lo + (long)om * kp * kp, Bhi, Blo, kp);
+  for (int L = 0; L < a.nelec && ok; ++L) {
+    const float* c = a.ck + (long)(b0 + L) * a.npts;
+    // A[m][i] = c[i][col0 + m], split; rows beyond the block's functions or the grid are 0
+    const int nq = TC_M * (kp / 4);
+    for (int e = tid; e < nq; e += TC_THREADS) {
+      const int i4 = (e / TC_M) * 4;
+      const int mm = e - (e / TC_M) * TC_M;
+      const long cc = (long)blockIdx.x * TC_M + mm;
+      float x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        x[u] = (cc < a.ncol && i4 + u < nrow) ? c[(long)(i4 + u) * a.ncol + cc] : 0.0f;
+      float4 h, l;
+      h.x = tf32_hi(x[0]); l.x = x[0] - h.x;
+      h.y = tf32_hi(x[1]); l.y = x[1] - h.y;
+      h.z = tf32_hi(x[2]); l.z = x[2] - h.z;
+      h.w = tf32_hi(x[3]); l.w = x[3] - h.w;
+      const uint32_t off = cm_off(mm, i4, kp);
+      *reinterpret_cast<float4*>(Ahi + off) = h;
+      *reinterpret_cast<float4*>(Alo + off) = l;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      issue_split_gemm(tmem + (uint32_t)(L * kp), Ahi, Alo, Bhi, Blo, kp, idesc);
+      mma_commit(mb);
+    }
+    ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;  // CTA-uniform
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+
+  // ---------------------------------------------------------- potential + GEMM 2
+  if (ok) {
+    __syncthreads();
+    load_b(a.T_hi + (long)om * kp * kp, a.T_lo + (long)om * kp * kp, Bhi, Blo, kp);
+  }
+  const int kr = live ? (int)(col / a.NR) : 0;
+  const int mR = live ? (int)(col - (long)kr * a.NR) : 0;
+  for (int L = 0; L < a.nelec && ok; ++L) {
+    // (V u)_L[m][n] for this thread's half of n
+    for (int n0 = half * ncb; n0 < (half + 1) * ncb; n0 += 8) {
+      float vu[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int Lp = 0; Lp < a.nelec; ++Lp) {
+        float u[8];
+        tmem_ld8(tmem + lane_base + (uint32_t)(Lp * kp + n0), u);
+        const float* V = a.V + (long)(L * a.nelec + Lp) * a.npts;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int n = n0 + s;
+          if (live && n < a.ng) vu[s] += V[(long)n * a.ncol + col] * u[s];
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 8; s += 4) {
+        float4 h, l;
+        h.x = tf32_hi(vu[s]); l.x = vu[s] - h.x;
+        h.y = tf32_hi(vu[s + 1]); l.y = vu[s + 1] - h.y;
+        h.z = tf32_hi(vu[s + 2]); l.z = vu[s + 2] - h.z;
+        h.w = tf32_hi(vu[s + 3]); l.w = vu[s + 3] - h.w;
+        const uint32_t off = cm_off(m, n0 + s, kp);
+        *reinterpret_cast<float4*>(Ahi + off) = h;
+        *reinterpret_cast<float4*>(Alo + off) = l;
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      issue_split_gemm(tmem + (uint32_t)((a.nelec + L) * kp), Ahi, Alo, Bhi, Blo, kp, idesc);
+      mma_commit(mb);
+    }
+    ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;  // CTA-uniform
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+
+  // ---------------------------------------------------------- epilogue
+  double ss = 0.0;
+  if (ok) {
+    const DevJ J = a.dj[B0.iJ];
+    const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
+    const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
+    const float frk = live ? a.fr[kr] : 0.0f;
+    const float fRm = live ? a.fR[mR] : 0.0f;
+    for (int L = 0; L < a.nelec; ++L) {
+      const int b = b0 + L;
+      const DevBlock Bb = a.blocks[b];
+      const float* c = a.ck + (long)b * a.npts;
+      for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 8) {
+        float w[8];
+        tmem_ld8(tmem + lane_base + (uint32_t)((a.nelec + L) * kp + i0), w);
+        if (!live) continue;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int i = i0 + s;
+          if (i >= a.ng) break;
+          const long idx = (long)b * a.npts + (long)i * a.ncol + col;
+          if (i >= nrow) {
+            if (a.mode == 1) a.out[idx] = 0.0f; else a.ckm1[idx] = 0.0f;
+            continue;
+          }
+          const float g = fminf(fRm, cf[4 * a.ng + i]);
+          const float aa = fminf(cf[i] * frk, a.erot) + g * cf[a.ng + i];
+          const float cv = c[(long)i * a.ncol + col];
+          float h = w[s] + aa * cv + a.t[idx];
+          if (Bb.up >= 0 && i >= 1)
+            h += g * cf[2 * a.ng + i] * a.ck[(long)Bb.up * a.npts + (long)(i - 1) * a.ncol + col];
+          if (Bb.dn >= 0)
+            h += g * cf[3 * a.ng + i] * a.ck[(long)Bb.dn * a.npts + (long)(i + 1) * a.ncol + col];
+          const float hs = h * (float)J.invdE - (float)J.e0s * cv;
+          if (a.mode == 1) {
+            a.out[idx] = hs;
+          } else {
+            const float nv = D * (a.alpha * hs - a.beta * D * a.ckm1[idx]);
+            a.ckm1[idx] = nv;
+            ss += (double)nv * (double)nv;
+          }
+        }
+      }
+    }
+  }
+  // norm partial of this CTA (fixed-order reduction)
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+  if (lane == 0) red[warp] = ss;
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0;
+    for (int w2 = 0; w2 < TC_THREADS / 32; ++w2) s += red[w2];
+    if (a.npart) a.npart[(long)g * a.ntiles + blockIdx.x] = s;
+    if (!ok) atomicExch(a.err, 1);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols));
+  }
+}
+
+// out[iJ] = sum over the (J, Omega) groups of J and their tiles, in order.
+__global__ void k_tc_norm_final(const double* __restrict__ npart, const int* __restrict__ g_begin,
+                                int ntiles, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  const int iJ = blockIdx.x;
+  double s = 0;
+  for (int g = g_begin[iJ]; g < g_begin[iJ + 1]; ++g)
+    for (int t = 0; t < ntiles; ++t) s += npart[(long)g * ntiles + t];
+  out[iJ] = s;
+}
+
+size_t angular_tc_smem(int kp) {
+  return (size_t)2 * TC_M * kp * 4 + (size_t)2 * kp * kp * 4 + 16 + 8 * sizeof(double) + 64;
+}
+
+cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
+                              double* norm_out, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_angular_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  dim3 grid((unsigned)args.ntiles, (unsigned)ngroups);
+  k_angular_tc<<<grid, TC_THREADS, angular_tc_smem(args.kp), st>>>(args);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (norm_out && args.npart) {
+    k_tc_norm_final<<<nJ, 32, 0, st>>>(args.npart, g_begin, args.ntiles, norm_out);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace mw3
