@@ -85,6 +85,7 @@ struct mw3_ctx {
   Tuning tune{4, 32, 32, 1, 0};
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   bool tc_ok = false;  // the tensor-core angular step supports this grid
+  int tc_user = -1;    // explicit "use_tc" setting (-1: default = on when supported)
 
   // grid and blocks
   int NR = 0, nr = 0, ng = 0, nelec = 1, nJ = 0, omega_max = 0;
@@ -668,7 +669,7 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
   // TF32-rounded high part and the exact FP32 remainder
   ctx->kp = ((ng + 15) / 16) * 16;
   ctx->tc_ok = (ctx->precision == MW3_MIXED) && ctx->kp <= kTcMaxKp;
-  ctx->tune.use_tc = ctx->tc_ok ? 1 : 0;
+  ctx->tune.use_tc = (ctx->tc_ok && ctx->tc_user != 0) ? 1 : 0;
   if (ctx->tc_ok) {
     const int kp = ctx->kp;
     const size_t nom = ctx->T.size();
@@ -1428,7 +1429,8 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
   } else if (k == "use_tc") {
     if (v != 0 && ctx->precision != MW3_MIXED)
       return ctx->fail(MW3_ERR_BAD_ARG, "use_tc needs MW3_MIXED");
-    ctx->tune.use_tc = v != 0;
+    ctx->tc_user = v != 0;
+    ctx->tune.use_tc = (v != 0) && (ctx->stage < 2 || ctx->tc_ok);
   } else {
     return ctx->fail(MW3_ERR_BAD_ARG, "unknown tuning key " + k);
   }
@@ -1443,7 +1445,7 @@ long mw3_get_tuning(const mw3_ctx* ctx, const char* key) {
   if (k == "rows_pairs") return ctx->tune.rows_pairs;
   if (k == "cols_tile") return ctx->tune.cols_tile;
   if (k == "use_graph") return ctx->tune.use_graph;
-  if (k == "use_tc") return ctx->tune.use_tc;
+  if (k == "use_tc") return ctx->stage >= 2 ? ctx->tune.use_tc : (ctx->tc_user != 0);
   return MW3_ERR_BAD_ARG;
 }
 
