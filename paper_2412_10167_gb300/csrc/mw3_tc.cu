@@ -28,7 +28,7 @@ namespace mw3 {
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_THREADS = 256;
+constexpr int TC_THREADS = 512;
 constexpr long kWaitLimit = 1L << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -101,6 +101,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Copy a padded kp x kp FP32 matrix pair (hi, lo), row-major, into core-matrix layout.
 __device__ void load_b(const float* __restrict__ hi, const float* __restrict__ lo,
                        unsigned char* Bhi, unsigned char* Blo, int kp) {
@@ -134,9 +144,10 @@ __device__ void issue_split_gemm(uint32_t dtmem, const unsigned char* Ahi, const
 
 
 
+template <int KP, int NE>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  const int kp = a.kp;
+  constexpr int kp = KP;
   const size_t abytes = (size_t)TC_M * kp * 4, bbytes = (size_t)kp * kp * 4;
   unsigned char* Ahi = sm;
   unsigned char* Alo = Ahi + abytes;
@@ -148,12 +159,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q = warp & 3;          // TMEM lane quarter
-  const int half = warp >> 2;      // which half of the N columns this warp reads
+  const int half = warp >> 2;      // which quarter of the N columns this warp reads
   const int m = q * 32 + lane;     // tile row = grid column within the tile
   const long col = (long)blockIdx.x * TC_M + m;
   const bool live = col < a.ncol;
   const int g = blockIdx.y;
-  const int b0 = g * a.nelec;
+  const int b0 = g * NE;
   const DevBlock B0 = a.blocks[b0];
   const int om = B0.omega;
   const int nrow = B0.nrow;
@@ -176,28 +187,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
   uint32_t phase = 0;
   bool ok = true;
   const uint32_t idesc = idesc_tf32(TC_M, kp);
-  const int ncb = kp / 2;           // columns per half
+  constexpr int ncb = kp / 4;       // columns per quarter (a multiple of 4)
   const uint32_t lane_base = (uint32_t)(q * 32) << 16;
 
   // ---------------------------------------------------------- GEMM 1 (per state)
   load_b(a.Tt_hi + (long)om * kp * kp, a.Tt_lo + (long)om * kp * kp, Bhi, Blo, kp);
-  for (int L = 0; L < a.nelec && ok; ++L) {
+  for (int L = 0; L < NE && ok; ++L) {
     const float* c = a.ck + (long)(b0 + L) * a.npts;
-    // A[m][i] = c[i][col0 + m], split; rows beyond the block's functions or the grid are 0
-    const int nq = TC_M * (kp / 4);
-    for (int e = tid; e < nq; e += TC_THREADS) {
+    // A[m][i] = c[i][col0 + m], split; rows beyond the block's functions or the grid are 0.
+    // All of a thread's global loads are issued before any is used.
+    constexpr int nq = TC_M * (kp / 4);
+    constexpr int kMaxItems = (nq + TC_THREADS - 1) / TC_THREADS;
+    float x[kMaxItems][4];
+#pragma unroll
+    for (int it = 0; it < kMaxItems; ++it) {
+      const int e = tid + it * TC_THREADS;
       const int i4 = (e / TC_M) * 4;
       const int mm = e - (e / TC_M) * TC_M;
       const long cc = (long)blockIdx.x * TC_M + mm;
-      float x[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        x[u] = (cc < a.ncol && i4 + u < nrow) ? c[(long)(i4 + u) * a.ncol + cc] : 0.0f;
+        x[it][u] = (e < nq && cc < a.ncol && i4 + u < nrow) ? __ldg(c + (long)(i4 + u) * a.ncol + cc) : 0.0f;
+    }
+#pragma unroll
+    for (int it = 0; it < kMaxItems; ++it) {
+      const int e = tid + it * TC_THREADS;
+      if (e >= nq) break;
+      const int i4 = (e / TC_M) * 4;
+      const int mm = e - (e / TC_M) * TC_M;
       float4 h, l;
-      h.x = tf32_hi(x[0]); l.x = x[0] - h.x;
-      h.y = tf32_hi(x[1]); l.y = x[1] - h.y;
-      h.z = tf32_hi(x[2]); l.z = x[2] - h.z;
-      h.w = tf32_hi(x[3]); l.w = x[3] - h.w;
+      h.x = tf32_hi(x[it][0]); l.x = x[it][0] - h.x;
+      h.y = tf32_hi(x[it][1]); l.y = x[it][1] - h.y;
+      h.z = tf32_hi(x[it][2]); l.z = x[it][2] - h.z;
+      h.w = tf32_hi(x[it][3]); l.w = x[it][3] - h.w;
       const uint32_t off = cm_off(mm, i4, kp);
       *reinterpret_cast<float4*>(Ahi + off) = h;
       *reinterpret_cast<float4*>(Alo + off) = l;
@@ -221,38 +243,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
   }
   const int kr = live ? (int)(col / a.NR) : 0;
   const int mR = live ? (int)(col - (long)kr * a.NR) : 0;
-  for (int L = 0; L < a.nelec && ok; ++L) {
-    // (V u)_L[m][n] for this thread's half of n
-    for (int n0 = half * ncb; n0 < (half + 1) * ncb; n0 += 8) {
-      float vu[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (int Lp = 0; Lp < a.nelec; ++Lp) {
-        float u[8];
-        tmem_ld8(tmem + lane_base + (uint32_t)(Lp * kp + n0), u);
-        const float* V = a.V + (long)(L * a.nelec + Lp) * a.npts;
+  for (int L = 0; L < NE && ok; ++L) {
+    // (V u)_L[m][n] for this thread's quarter of n: V loads first, then TMEM
+    float vv[NE][ncb];
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const int n = n0 + s;
-          if (live && n < a.ng) vu[s] += V[(long)n * a.ncol + col] * u[s];
-        }
-      }
+    for (int Lp = 0; Lp < NE; ++Lp) {
+      const float* V = a.V + (long)(L * NE + Lp) * a.npts;
 #pragma unroll
-      for (int s = 0; s < 8; s += 4) {
-        float4 h, l;
-        h.x = tf32_hi(vu[s]); l.x = vu[s] - h.x;
-        h.y = tf32_hi(vu[s + 1]); l.y = vu[s + 1] - h.y;
-        h.z = tf32_hi(vu[s + 2]); l.z = vu[s + 2] - h.z;
-        h.w = tf32_hi(vu[s + 3]); l.w = vu[s + 3] - h.w;
-        const uint32_t off = cm_off(m, n0 + s, kp);
-        *reinterpret_cast<float4*>(Ahi + off) = h;
-        *reinterpret_cast<float4*>(Alo + off) = l;
+      for (int s2 = 0; s2 < ncb; ++s2) {
+        const int n = half * ncb + s2;
+        vv[Lp][s2] = (live && n < a.ng) ? __ldg(V + (long)n * a.ncol + col) : 0.0f;
       }
+    }
+#pragma unroll
+    for (int s0 = 0; s0 < ncb; s0 += 4) {
+      float vu[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int Lp = 0; Lp < NE; ++Lp) {
+        float u[4];
+        tmem_ld4(tmem + lane_base + (uint32_t)(Lp * kp + half * ncb + s0), u);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) vu[s] += vv[Lp][s0 + s] * u[s];
+      }
+      float4 h, l;
+      h.x = tf32_hi(vu[0]); l.x = vu[0] - h.x;
+      h.y = tf32_hi(vu[1]); l.y = vu[1] - h.y;
+      h.z = tf32_hi(vu[2]); l.z = vu[2] - h.z;
+      h.w = tf32_hi(vu[3]); l.w = vu[3] - h.w;
+      const uint32_t off = cm_off(m, half * ncb + s0, kp);
+      *reinterpret_cast<float4*>(Ahi + off) = h;
+      *reinterpret_cast<float4*>(Alo + off) = l;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      issue_split_gemm(tmem + (uint32_t)((a.nelec + L) * kp), Ahi, Alo, Bhi, Blo, kp, idesc);
+      issue_split_gemm(tmem + (uint32_t)((NE + L) * kp), Ahi, Alo, Bhi, Blo, kp, idesc);
       mma_commit(mb);
     }
     ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;  // CTA-uniform
@@ -268,16 +295,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
     const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
     const float frk = live ? a.fr[kr] : 0.0f;
     const float fRm = live ? a.fR[mR] : 0.0f;
-    for (int L = 0; L < a.nelec; ++L) {
+    for (int L = 0; L < NE; ++L) {
       const int b = b0 + L;
       const DevBlock Bb = a.blocks[b];
       const float* c = a.ck + (long)b * a.npts;
-      for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 8) {
-        float w[8];
-        tmem_ld8(tmem + lane_base + (uint32_t)((a.nelec + L) * kp + i0), w);
+      for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 4) {
+        float w[4];
+        tmem_ld4(tmem + lane_base + (uint32_t)((NE + L) * kp + i0), w);
         if (!live) continue;
+        // issue every global load of the chunk before using any
+        float cv[4], cu[4], cd[4], tv[4], pv[4];
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
+        for (int s = 0; s < 4; ++s) {
+          const int i = i0 + s;
+          const bool in = i < nrow;
+          const long off = (long)i * a.ncol + col;
+          cv[s] = in ? __ldg(c + off) : 0.0f;
+          tv[s] = in ? __ldg(a.t + (long)b * a.npts + off) : 0.0f;
+          pv[s] = (in && a.mode == 0) ? a.ckm1[(long)b * a.npts + off] : 0.0f;
+          cu[s] = (in && Bb.up >= 0 && i >= 1) ? __ldg(a.ck + (long)Bb.up * a.npts + off - a.ncol) : 0.0f;
+          cd[s] = (in && Bb.dn >= 0) ? __ldg(a.ck + (long)Bb.dn * a.npts + off + a.ncol) : 0.0f;
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
           const int i = i0 + s;
           if (i >= a.ng) break;
           const long idx = (long)b * a.npts + (long)i * a.ncol + col;
@@ -287,17 +327,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
           }
           const float g = fminf(fRm, cf[4 * a.ng + i]);
           const float aa = fminf(cf[i] * frk, a.erot) + g * cf[a.ng + i];
-          const float cv = c[(long)i * a.ncol + col];
-          float h = w[s] + aa * cv + a.t[idx];
-          if (Bb.up >= 0 && i >= 1)
-            h += g * cf[2 * a.ng + i] * a.ck[(long)Bb.up * a.npts + (long)(i - 1) * a.ncol + col];
-          if (Bb.dn >= 0)
-            h += g * cf[3 * a.ng + i] * a.ck[(long)Bb.dn * a.npts + (long)(i + 1) * a.ncol + col];
-          const float hs = h * (float)J.invdE - (float)J.e0s * cv;
+          float h = w[s] + aa * cv[s] + tv[s];
+          h += g * cf[2 * a.ng + i] * cu[s];
+          h += g * cf[3 * a.ng + i] * cd[s];
+          const float hs = h * (float)J.invdE - (float)J.e0s * cv[s];
           if (a.mode == 1) {
             a.out[idx] = hs;
           } else {
-            const float nv = D * (a.alpha * hs - a.beta * D * a.ckm1[idx]);
+            const float nv = D * (a.alpha * hs - a.beta * D * pv[s]);
             a.ckm1[idx] = nv;
             ss += (double)nv * (double)nv;
           }
@@ -338,16 +375,37 @@ size_t angular_tc_smem(int kp) {
   return (size_t)2 * TC_M * kp * 4 + (size_t)2 * kp * kp * 4 + 16 + 8 * sizeof(double) + 64;
 }
 
-cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
-                              double* norm_out, cudaStream_t st) {
+template <int KP, int NE>
+static cudaError_t launch_tc_inst(const TcArgs& args, dim3 grid, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_angular_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_angular_tc<KP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
     attr = true;
   }
+  k_angular_tc<KP, NE><<<grid, TC_THREADS, angular_tc_smem(KP), st>>>(args);
+  return cudaGetLastError();
+}
+
+template <int NE>
+static cudaError_t launch_tc_ne(const TcArgs& a, dim3 grid, cudaStream_t st) {
+  switch (a.kp) {
+    case 16: return launch_tc_inst<16, NE>(a, grid, st);
+    case 32: return launch_tc_inst<32, NE>(a, grid, st);
+    case 48: return launch_tc_inst<48, NE>(a, grid, st);
+    case 64: return launch_tc_inst<64, NE>(a, grid, st);
+    case 80: return launch_tc_inst<80, NE>(a, grid, st);
+    case 96: return launch_tc_inst<96, NE>(a, grid, st);
+    case 112: return launch_tc_inst<112, NE>(a, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
+                              double* norm_out, cudaStream_t st) {
   dim3 grid((unsigned)args.ntiles, (unsigned)ngroups);
-  k_angular_tc<<<grid, TC_THREADS, angular_tc_smem(args.kp), st>>>(args);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = (args.nelec == 1) ? launch_tc_ne<1>(args, grid, st)
+                                    : launch_tc_ne<2>(args, grid, st);
   if (e != cudaSuccess) return e;
   if (norm_out && args.npart) {
     k_tc_norm_final<<<nJ, 32, 0, st>>>(args.npart, g_begin, args.ntiles, norm_out);
