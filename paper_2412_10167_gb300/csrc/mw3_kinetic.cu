@@ -305,10 +305,23 @@ static size_t kinetic_smem(int N, int P) {
          sizeof(cpx<T>) * 2 * (size_t)P * N;
 }
 
+template <typename T>
+bool kinetic_rows_fixed(int N, const T* q, T* t, long nrows, const void* tw, const void* ph,
+                        const T* lam, int P, const DevBlock* blocks, int ng, int nr,
+                        cudaStream_t st, cudaError_t* err);
+template <typename T>
+bool kinetic_cols_fixed(int N, const T* q, T* t, long nplanes, int NR, const void* tw,
+                        const void* ph, const T* lam, int C, int ng, const T* wpsi,
+                        const T* wdpsi, T* cut, const DevBlock* blocks, const int* ncut_J,
+                        int m_inf, T* qcol, cudaStream_t st, cudaError_t* err);
+
 template <typename real>
 cudaError_t launch_kinetic_rows(const real* q, real* t, long nrows, const FFTPlan& plan,
                                 const void* tw, const void* ph, const real* lam, int pairs,
                                 const DevBlock* blocks, int ng, int nr, cudaStream_t st) {
+  cudaError_t err = cudaSuccess;
+  if (kinetic_rows_fixed<real>(plan.N, q, t, nrows, tw, ph, lam, pairs, blocks, ng, nr, st, &err))
+    return err;
   const size_t sm = kinetic_smem<real>(plan.N, pairs);
   static bool attr_set[2] = {false, false};
   const int slot = sizeof(real) == 8 ? 1 : 0;
@@ -332,6 +345,10 @@ cudaError_t launch_kinetic_cols(const real* q, real* t, long nplanes, int nr, in
                                 const real* lam, int ctile, int ng, const real* wpsi,
                                 const real* wdpsi, real* cut_slot, const DevBlock* blocks,
                                 const int* ncut_J, int m_inf, real* qcol, cudaStream_t st) {
+  cudaError_t err = cudaSuccess;
+  if (kinetic_cols_fixed<real>(plan.N, q, t, nplanes, NR, tw, ph, lam, ctile, ng, wpsi, wdpsi,
+                               cut_slot, blocks, ncut_J, m_inf, qcol, st, &err))
+    return err;
   const size_t sm = kinetic_smem<real>(plan.N, ctile / 2);
   static bool attr_set[2] = {false, false};
   const int slot = sizeof(real) == 8 ? 1 : 0;

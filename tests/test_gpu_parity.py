@@ -47,10 +47,13 @@ def oracle_run(name, cfg, nsteps):
     return _ORACLE[key]
 
 
-@pytest.mark.parametrize("name", list(W.SMALL))
+APPLY_CASES = dict(W.SMALL, odd=W.C_ODD)
+
+
+@pytest.mark.parametrize("name", list(APPLY_CASES))
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_apply_hs_matches_oracle(name, prec):
-    cfg = W.SMALL[name]
+    cfg = APPLY_CASES[name]
     pr = mw3().Propagator(cfg, precision=prec)
     H = GridHamiltonian(cfg)
     # the state of a block lies in the span of its angular functions

@@ -124,6 +124,10 @@ C4_SMALL = shrunk(C4, "h_dh_j40_60x48x30", NR=60, nr=48, ngamma=30, omega_max=4,
                   steps=80, nE=40)
 SMALL = {"c1": C1, "c2s": C2_SMALL, "c3s": C3_SMALL, "c4s": C4_SMALL}
 
+# Line lengths outside the library's compile-time FFT sizes (runtime-plan kernels).
+C_ODD = shrunk(C2, "h_dh_j3_30x18x10", NR=30, nr=18, ngamma=10, J=[3], omega_max=3, steps=60,
+               nE=16)
+
 
 def rng(seed: int) -> np.random.Generator:
     """The single seeded generator used for every random test input."""
