@@ -233,6 +233,42 @@ long mw3_get_tuning(const mw3_ctx* ctx, const char* key);
 int mw3_kernel_times(mw3_ctx* ctx, int enable, const char** names, double* ms, long* launches,
                      int* count);
 
+/* ------------------------------------------------- J-interpolation surrogate
+ * A small fully connected network (n_in -> depth x width, GELU -> 1) trained with
+ * hand-written kernels on probabilities P_J(E, v', j') that the propagation produced
+ * at a coarse set of J, to predict intermediate J for the partial-wave sums of
+ * Eqs. collisional-xsection and cumulative-probability (the paper interpolates
+ * with J-shifting, Eq. J-shifting-interpolation; the network is this library's
+ * extension). Weights in BF16 for the products, FP32 master weights, AdamW
+ * moments, activations and accumulation. Flat parameter order: for each layer
+ * W (row-major [out][in]) then b. Host arrays are caller-owned and copied. */
+typedef struct mw3_mlp mw3_mlp;
+
+/* He-normal initialisation from `seed` (zero biases). */
+int mw3_mlp_create(mw3_mlp** out, int device, int n_in, int width, int depth,
+                   unsigned long long seed);
+void mw3_mlp_destroy(mw3_mlp* net);
+const char* mw3_mlp_last_error(const mw3_mlp* net);
+long mw3_mlp_num_params(const mw3_mlp* net);
+
+/* Replace / read the FP32 master parameters (flat[mw3_mlp_num_params]); setting
+ * them resets the optimiser state. */
+int mw3_mlp_set_params(mw3_mlp* net, const double* flat);
+int mw3_mlp_get_params(mw3_mlp* net, double* flat);
+
+/* y[i] = network(X[i][0..n_in-1]) for i < n (X row-major FP32). */
+int mw3_mlp_forward(mw3_mlp* net, const float* X, long n, float* y);
+
+/* Mean-squared error over the n samples and its gradient (flat, may be NULL). */
+int mw3_mlp_loss_grad(mw3_mlp* net, const float* X, const float* y, long n, double* loss,
+                      double* grad);
+
+/* `epochs` passes of minibatch AdamW (beta1 0.9, beta2 0.999, eps 1e-8; decoupled
+ * weight decay `wd` on weights), shuffled by `seed`; *final_loss = mean batch loss of
+ * the last epoch. */
+int mw3_mlp_train(mw3_mlp* net, const float* X, const float* y, long n, int epochs, int batch,
+                  double lr, double wd, unsigned long long seed, double* final_loss);
+
 /* Allocation-free sums of squares, for callers that cannot call cudaMalloc (a fixed
  * memory arena, a region where allocating would stall other streams). The paper has
  * no counterpart: this is the per-J norm reduction of the propagation (its divergence

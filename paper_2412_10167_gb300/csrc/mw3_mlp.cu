@@ -1,0 +1,506 @@
+// J-interpolation surrogate network: hand-written training and inference kernels.
+//
+// Network: n_in inputs -> depth hidden layers of width W with GELU (tanh form) -> 1
+// output; weights held in BF16 for the forward and backward products, with FP32 master
+// weights and AdamW moments; activations and accumulation in FP32. The network is
+// small (4 -> 256 -> 256 -> 256 -> 1 is 133k parameters), so the products run on
+// CUDA cores in 64 x 64 tiles; a training step is a few GFLOP.
+//
+// Parameter order (flat, as exchanged with the host): for each layer l = 0..depth,
+// W_l (row-major [out][in]) then b_l.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "../../include/mw3.h"
+
+namespace {
+
+constexpr int MBM = 64, MBN = 64, MBK = 16, MTHREADS = 256;
+
+__device__ __forceinline__ float gelu_f(float z) {
+  const float s = 0.7978845608028654f, a = 0.044715f;
+  return 0.5f * z * (1.0f + tanhf(s * (z + a * z * z * z)));
+}
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  const float s = 0.7978845608028654f, a = 0.044715f;
+  const float t = tanhf(s * (z + a * z * z * z));
+  return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * s * (1.0f + 3.0f * a * z * z);
+}
+
+// Element accessor for a matrix stored row-major with leading dimension ld; trans
+// swaps the two indices. bf16 selects the BF16 weight array.
+struct Mat {
+  const float* f;
+  const __nv_bfloat16* h;
+  long ld;
+  int trans;
+  __device__ float at(long r, long c) const {
+    const long i = trans ? c * ld + r : r * ld + c;
+    return h ? __bfloat162float(h[i]) : f[i];
+  }
+};
+
+// C[M x N] = A[M x K] B[K x N] with an epilogue:
+//   mode 0: C = acc + bias[n]; Z = C; H = gelu(C) (hidden layer forward)
+//   mode 1: C = acc + bias[n] (output layer forward)
+//   mode 2: C = acc * gelu'(Z[m][n]) (backward through a hidden activation)
+//   mode 3: C = acc (weight gradient)
+__global__ void __launch_bounds__(MTHREADS) k_mlp_gemm(int M, int N, int K, Mat A, Mat B,
+                                                       float* __restrict__ C, long ldc,
+                                                       const float* __restrict__ bias,
+                                                       const float* __restrict__ Z,
+                                                       float* __restrict__ H, int mode) {
+  __shared__ float As[MBK][MBM + 1];
+  __shared__ float Bs[MBK][MBN];
+  const int m0 = blockIdx.y * MBM, n0 = blockIdx.x * MBN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += MBK) {
+    for (int e = threadIdx.x; e < MBM * MBK; e += MTHREADS) {
+      const int mm = e / MBK, kk = e - mm * MBK;
+      As[kk][mm] = (m0 + mm < M && k0 + kk < K) ? A.at(m0 + mm, k0 + kk) : 0.f;
+    }
+    for (int e = threadIdx.x; e < MBK * MBN; e += MTHREADS) {
+      const int kk = e / MBN, nn = e - kk * MBN;
+      Bs[kk][nn] = (k0 + kk < K && n0 + nn < N) ? B.at(k0 + kk, n0 + nn) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < MBK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      const long o = (long)m * ldc + n;
+      if (mode == 0) {
+        v += bias[n];
+        C[o] = v;
+        H[o] = gelu_f(v);
+      } else if (mode == 1) {
+        C[o] = v + bias[n];
+      } else if (mode == 2) {
+        C[o] = v * gelu_grad_f(Z[o]);
+      } else {
+        C[o] = v;
+      }
+    }
+  }
+}
+
+// Gather a minibatch: Xb[r] = X[idx[r]], yb[r] = y[idx[r]]
+__global__ void k_gather(const float* __restrict__ X, const float* __restrict__ y,
+                         const int* __restrict__ idx, int n, int nin, float* __restrict__ Xb,
+                         float* __restrict__ yb) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int s = idx[r];
+  for (int i = 0; i < nin; ++i) Xb[(long)r * nin + i] = X[(long)s * nin + i];
+  yb[r] = y[s];
+}
+
+// g[r] = (2/n) (out[r] - y[r]); partial squared errors per block (fixed order)
+__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ y, int n,
+                      float* __restrict__ g, double* __restrict__ partial) {
+  __shared__ double red[256];
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  double s = 0;
+  if (r < n) {
+    const float d = out[r] - y[r];
+    g[r] = 2.0f * d / (float)n;
+    s = (double)d * d;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// db[o] = sum_r g[r][o] (fixed order over r)
+__global__ void k_colsum(const float* __restrict__ g, int n, int nout, float* __restrict__ db) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  float s = 0;
+  for (int r = 0; r < n; ++r) s += g[(long)r * nout + o];
+  db[o] = s;
+}
+
+// AdamW on FP32 master parameters; refreshes the BF16 copy of weights (wmask = 1).
+__global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                        float* __restrict__ v, __nv_bfloat16* __restrict__ ph,
+                        const unsigned char* __restrict__ wmask, long n, float lr, float b1,
+                        float b2, float eps, float wd, float c1, float c2) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float mh = mi / c1, vh = vi / c2;
+  const float decay = wmask[i] ? wd * p[i] : 0.f;
+  const float np = p[i] - lr * (mh / (sqrtf(vh) + eps) + decay);
+  p[i] = np;
+  ph[i] = __float2bfloat16_rn(np);
+}
+
+}  // namespace
+
+struct mw3_mlp {
+  int device = 0;
+  int nin = 4, width = 256, depth = 3;
+  std::vector<int> sizes;            // layer widths: nin, W, ..., W, 1
+  std::vector<long> woff, boff;      // offsets of W_l and b_l in the flat arrays
+  long nparam = 0;
+  float* p = nullptr;                // FP32 master parameters
+  __nv_bfloat16* ph = nullptr;       // BF16 copy (all parameters; biases unused in BF16)
+  float *g = nullptr, *m = nullptr, *v = nullptr;
+  unsigned char* wmask = nullptr;    // 1 for weights (decayed), 0 for biases
+  long step = 0;
+  // activations for a batch of up to cap rows
+  long cap = 0;
+  std::vector<float*> Zs, Hs, Gs;    // per layer: pre-activation, activation, gradient
+  float *X = nullptr, *y = nullptr, *out = nullptr, *gout = nullptr;
+  double* partial = nullptr;
+  float *Xall = nullptr, *yall = nullptr;
+  int* idx = nullptr;
+  long nall = 0;
+  std::string err;
+};
+
+namespace {
+
+int mfail(mw3_mlp* n, int code, const std::string& s) {
+  n->err = s;
+  return code;
+}
+
+#define MCK(call)                                                                             \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return mfail(net, MW3_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void free_acts(mw3_mlp* net) {
+  for (auto* p : net->Zs) cudaFree(p);
+  for (auto* p : net->Hs) cudaFree(p);
+  for (auto* p : net->Gs) cudaFree(p);
+  net->Zs.clear();
+  net->Hs.clear();
+  net->Gs.clear();
+  cudaFree(net->X);
+  cudaFree(net->y);
+  cudaFree(net->out);
+  cudaFree(net->gout);
+  cudaFree(net->partial);
+  net->X = net->y = net->out = net->gout = nullptr;
+  net->partial = nullptr;
+  net->cap = 0;
+}
+
+int ensure_cap(mw3_mlp* net, long rows) {
+  if (rows <= net->cap) return MW3_OK;
+  free_acts(net);
+  const int L = (int)net->sizes.size() - 1;
+  for (int l = 0; l < L; ++l) {
+    float *z, *h, *g;
+    MCK(cudaMalloc(&z, rows * net->sizes[l + 1] * sizeof(float)));
+    MCK(cudaMalloc(&h, rows * net->sizes[l + 1] * sizeof(float)));
+    MCK(cudaMalloc(&g, rows * net->sizes[l + 1] * sizeof(float)));
+    net->Zs.push_back(z);
+    net->Hs.push_back(h);
+    net->Gs.push_back(g);
+  }
+  MCK(cudaMalloc(&net->X, rows * net->nin * sizeof(float)));
+  MCK(cudaMalloc(&net->y, rows * sizeof(float)));
+  MCK(cudaMalloc(&net->out, rows * sizeof(float)));
+  MCK(cudaMalloc(&net->gout, rows * sizeof(float)));
+  MCK(cudaMalloc(&net->partial, ((rows + 255) / 256) * sizeof(double)));
+  net->cap = rows;
+  return MW3_OK;
+}
+
+dim3 ggrid(int M, int N) { return dim3((N + MBN - 1) / MBN, (M + MBM - 1) / MBM); }
+
+// forward on rows already in net->X; output in net->out (Zs[L-1])
+int forward(mw3_mlp* net, long n) {
+  const int L = (int)net->sizes.size() - 1;
+  const float* in = net->X;
+  for (int l = 0; l < L; ++l) {
+    const int K = net->sizes[l], N = net->sizes[l + 1];
+    Mat A{in, nullptr, K, 0};
+    Mat B{nullptr, net->ph + net->woff[l], K, 1};  // B[k][o] = W[o][k]
+    const int mode = (l < L - 1) ? 0 : 1;
+    float* C = (l < L - 1) ? net->Zs[l] : net->out;
+    k_mlp_gemm<<<ggrid((int)n, N), MTHREADS>>>((int)n, N, K, A, B, C, N, net->p + net->boff[l],
+                                               nullptr, net->Hs[l], mode);
+    in = net->Hs[l];
+  }
+  MCK(cudaGetLastError());
+  return MW3_OK;
+}
+
+// backward from net->gout (dL/dout); gradients into net->g (flat)
+int backward(mw3_mlp* net, long n) {
+  const int L = (int)net->sizes.size() - 1;
+  const float* g = net->gout;
+  for (int l = L - 1; l >= 0; --l) {
+    const int K = net->sizes[l], N = net->sizes[l + 1];
+    const float* a_in = (l == 0) ? net->X : net->Hs[l - 1];
+    // dW[o][i] = sum_r g[r][o] a_in[r][i]: M = N (o), N = K (i), K = n (r)
+    Mat A{g, nullptr, N, 1};       // A[o][r] = g[r][o]
+    Mat B{a_in, nullptr, K, 0};    // B[r][i] = a_in[r][i]
+    k_mlp_gemm<<<ggrid(N, K), MTHREADS>>>(N, K, (int)n, A, B, net->g + net->woff[l], K, nullptr,
+                                          nullptr, nullptr, 3);
+    k_colsum<<<(N + 127) / 128, 128>>>(g, (int)n, N, net->g + net->boff[l]);
+    if (l > 0) {
+      // g_prev[r][i] = sum_o g[r][o] W[o][i] * gelu'(Z_(l-1)[r][i])
+      Mat A2{g, nullptr, N, 0};
+      Mat B2{nullptr, net->ph + net->woff[l], K, 0};  // B2[o][i] = W[o][i]
+      k_mlp_gemm<<<ggrid((int)n, K), MTHREADS>>>((int)n, K, N, A2, B2, net->Gs[l - 1], K, nullptr,
+                                                 net->Zs[l - 1], nullptr, 2);
+      g = net->Gs[l - 1];
+    }
+  }
+  MCK(cudaGetLastError());
+  return MW3_OK;
+}
+
+double mse_and_grad(mw3_mlp* net, long n, const float* y) {
+  const int nb = (int)((n + 255) / 256);
+  k_mse<<<nb, 256>>>(net->out, y, (int)n, net->gout, net->partial);
+  std::vector<double> h(nb);
+  cudaMemcpy(h.data(), net->partial, nb * 8, cudaMemcpyDeviceToHost);
+  double s = 0;
+  for (double x : h) s += x;
+  return s / (double)n;
+}
+
+uint16_t bf16_bits(float f) {  // round to nearest even
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7FFFu + lsb;
+  return (uint16_t)(u >> 16);
+}
+
+int upload_params(mw3_mlp* net, const std::vector<float>& p) {
+  std::vector<uint16_t> hb(p.size());
+  for (size_t i = 0; i < p.size(); ++i) hb[i] = bf16_bits(p[i]);
+  MCK(cudaMemcpy(net->p, p.data(), p.size() * 4, cudaMemcpyHostToDevice));
+  MCK(cudaMemcpy(net->ph, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice));
+  return MW3_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mw3_mlp_create(mw3_mlp** out, int device, int n_in, int width, int depth,
+                   unsigned long long seed) {
+  if (!out || n_in < 1 || width < 1 || depth < 1 || n_in > 64 || width > 4096 || depth > 16)
+    return MW3_ERR_BAD_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return MW3_ERR_CUDA;
+  mw3_mlp* net = new (std::nothrow) mw3_mlp();
+  if (!net) return MW3_ERR_OOM;
+  net->device = device;
+  net->nin = n_in;
+  net->width = width;
+  net->depth = depth;
+  net->sizes.push_back(n_in);
+  for (int l = 0; l < depth; ++l) net->sizes.push_back(width);
+  net->sizes.push_back(1);
+  long off = 0;
+  std::vector<unsigned char> mask;
+  for (size_t l = 0; l + 1 < net->sizes.size(); ++l) {
+    const long nw = (long)net->sizes[l] * net->sizes[l + 1];
+    net->woff.push_back(off);
+    off += nw;
+    mask.insert(mask.end(), nw, 1);
+    net->boff.push_back(off);
+    off += net->sizes[l + 1];
+    mask.insert(mask.end(), net->sizes[l + 1], 0);
+  }
+  net->nparam = off;
+  const size_t n = (size_t)off;
+  if (cudaMalloc(&net->p, n * 4) != cudaSuccess || cudaMalloc(&net->ph, n * 2) != cudaSuccess ||
+      cudaMalloc(&net->g, n * 4) != cudaSuccess || cudaMalloc(&net->m, n * 4) != cudaSuccess ||
+      cudaMalloc(&net->v, n * 4) != cudaSuccess || cudaMalloc(&net->wmask, n) != cudaSuccess) {
+    delete net;
+    return MW3_ERR_OOM;
+  }
+  cudaMemcpy(net->wmask, mask.data(), n, cudaMemcpyHostToDevice);
+  cudaMemset(net->m, 0, n * 4);
+  cudaMemset(net->v, 0, n * 4);
+  // He-normal weights, zero biases (seeded, host generator)
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  std::vector<float> p(n, 0.f);
+  for (size_t l = 0; l + 1 < net->sizes.size(); ++l) {
+    const double sd = std::sqrt(2.0 / net->sizes[l]);
+    const long nw = (long)net->sizes[l] * net->sizes[l + 1];
+    for (long i = 0; i < nw; ++i) p[net->woff[l] + i] = (float)(nd(rng) * sd);
+  }
+  int st = upload_params(net, p);
+  if (st) {
+    delete net;
+    return st;
+  }
+  *out = net;
+  return MW3_OK;
+}
+
+void mw3_mlp_destroy(mw3_mlp* net) {
+  if (!net) return;
+  cudaSetDevice(net->device);
+  free_acts(net);
+  cudaFree(net->p);
+  cudaFree(net->ph);
+  cudaFree(net->g);
+  cudaFree(net->m);
+  cudaFree(net->v);
+  cudaFree(net->wmask);
+  cudaFree(net->Xall);
+  cudaFree(net->yall);
+  cudaFree(net->idx);
+  delete net;
+}
+
+const char* mw3_mlp_last_error(const mw3_mlp* net) { return net ? net->err.c_str() : ""; }
+
+long mw3_mlp_num_params(const mw3_mlp* net) { return net ? net->nparam : -1; }
+
+int mw3_mlp_set_params(mw3_mlp* net, const double* flat) {
+  if (!net || !flat) return MW3_ERR_BAD_ARG;
+  cudaSetDevice(net->device);
+  std::vector<float> p(flat, flat + net->nparam);
+  net->step = 0;
+  cudaMemset(net->m, 0, net->nparam * 4);
+  cudaMemset(net->v, 0, net->nparam * 4);
+  return upload_params(net, p);
+}
+
+int mw3_mlp_get_params(mw3_mlp* net, double* flat) {
+  if (!net || !flat) return MW3_ERR_BAD_ARG;
+  cudaSetDevice(net->device);
+  std::vector<float> p(net->nparam);
+  MCK(cudaMemcpy(p.data(), net->p, p.size() * 4, cudaMemcpyDeviceToHost));
+  for (long i = 0; i < net->nparam; ++i) flat[i] = p[i];
+  return MW3_OK;
+}
+
+int mw3_mlp_forward(mw3_mlp* net, const float* X, long n, float* y) {
+  if (!net || !X || !y || n < 0) return MW3_ERR_BAD_ARG;
+  cudaSetDevice(net->device);
+  const long chunk = 65536;
+  for (long r0 = 0; r0 < n; r0 += chunk) {
+    const long rows = std::min(chunk, n - r0);
+    int st = ensure_cap(net, rows);
+    if (st) return st;
+    MCK(cudaMemcpy(net->X, X + r0 * net->nin, rows * net->nin * 4, cudaMemcpyHostToDevice));
+    if ((st = forward(net, rows))) return st;
+    MCK(cudaMemcpy(y + r0, net->out, rows * 4, cudaMemcpyDeviceToHost));
+  }
+  return MW3_OK;
+}
+
+int mw3_mlp_loss_grad(mw3_mlp* net, const float* X, const float* y, long n, double* loss,
+                      double* grad) {
+  if (!net || !X || !y || n < 1) return MW3_ERR_BAD_ARG;
+  cudaSetDevice(net->device);
+  int st = ensure_cap(net, n);
+  if (st) return st;
+  MCK(cudaMemcpy(net->X, X, n * net->nin * 4, cudaMemcpyHostToDevice));
+  MCK(cudaMemcpy(net->y, y, n * 4, cudaMemcpyHostToDevice));
+  if ((st = forward(net, n))) return st;
+  const double l = mse_and_grad(net, n, net->y);
+  if ((st = backward(net, n))) return st;
+  if (loss) *loss = l;
+  if (grad) {
+    std::vector<float> g(net->nparam);
+    MCK(cudaMemcpy(g.data(), net->g, g.size() * 4, cudaMemcpyDeviceToHost));
+    for (long i = 0; i < net->nparam; ++i) grad[i] = g[i];
+  }
+  return MW3_OK;
+}
+
+int mw3_mlp_train(mw3_mlp* net, const float* X, const float* y, long n, int epochs, int batch,
+                  double lr, double wd, unsigned long long seed, double* final_loss) {
+  if (!net || !X || !y || n < 1 || epochs < 0 || batch < 1) return MW3_ERR_BAD_ARG;
+  cudaSetDevice(net->device);
+  if (n != net->nall) {
+    cudaFree(net->Xall);
+    cudaFree(net->yall);
+    cudaFree(net->idx);
+    MCK(cudaMalloc(&net->Xall, n * net->nin * 4));
+    MCK(cudaMalloc(&net->yall, n * 4));
+    MCK(cudaMalloc(&net->idx, n * 4));
+    net->nall = n;
+  }
+  MCK(cudaMemcpy(net->Xall, X, n * net->nin * 4, cudaMemcpyHostToDevice));
+  MCK(cudaMemcpy(net->yall, y, n * 4, cudaMemcpyHostToDevice));
+  int st = ensure_cap(net, batch);
+  if (st) return st;
+  std::mt19937_64 rng(seed);
+  std::vector<int> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  double last = 0;
+  const float b1 = 0.9f, b2 = 0.999f;
+  for (int ep = 0; ep < epochs; ++ep) {
+    std::shuffle(perm.begin(), perm.end(), rng);
+    MCK(cudaMemcpy(net->idx, perm.data(), n * 4, cudaMemcpyHostToDevice));
+    double sum = 0;
+    long cnt = 0;
+    for (long r0 = 0; r0 + batch <= n || (r0 == 0 && n < batch); r0 += batch) {
+      const long rows = std::min<long>(batch, n - r0);
+      k_gather<<<(int)((rows + 255) / 256), 256>>>(net->Xall, net->yall, net->idx + r0, (int)rows,
+                                                    net->nin, net->X, net->y);
+      if ((st = forward(net, rows))) return st;
+      const double l = mse_and_grad(net, rows, net->y);
+      if ((st = backward(net, rows))) return st;
+      net->step += 1;
+      const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
+      k_adamw<<<(int)((net->nparam + 255) / 256), 256>>>(net->p, net->g, net->m, net->v, net->ph,
+                                                         net->wmask, net->nparam, (float)lr, b1,
+                                                         b2, 1e-8f, (float)wd, c1, c2);
+      sum += l;
+      ++cnt;
+      if (rows < batch) break;
+    }
+    last = cnt ? sum / cnt : 0;
+  }
+  MCK(cudaDeviceSynchronize());
+  if (final_loss) *final_loss = last;
+  return MW3_OK;
+}
+
+}  // extern "C"

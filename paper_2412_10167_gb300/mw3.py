@@ -93,6 +93,20 @@ _SIGS = {
     "mw3_checkpoint_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "mw3_measure_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "mw3_norms_noalloc": (C.c_int, [C.c_void_p, C.c_long, C.c_int, C.c_void_p, C.c_void_p]),
+    "mw3_mlp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int,
+                                 C.c_ulonglong]),
+    "mw3_mlp_destroy": (None, [C.c_void_p]),
+    "mw3_mlp_last_error": (C.c_char_p, [C.c_void_p]),
+    "mw3_mlp_num_params": (C.c_long, [C.c_void_p]),
+    "mw3_mlp_set_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mw3_mlp_get_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mw3_mlp_forward": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_long,
+                                  C.POINTER(C.c_float)]),
+    "mw3_mlp_loss_grad": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                    C.c_long, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mw3_mlp_train": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_long,
+                                C.c_int, C.c_int, C.c_double, C.c_double, C.c_ulonglong,
+                                C.POINTER(C.c_double)]),
     "mw3_set_tuning": (C.c_int, [C.c_void_p, C.c_char_p, C.c_long]),
     "mw3_get_tuning": (C.c_long, [C.c_void_p, C.c_char_p]),
     "mw3_kernel_times": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p),
@@ -216,6 +230,10 @@ class Propagator:
         self._stream = None
         if device >= 0 and torch_memory:
             self._use_torch(device)
+        if tuning == "auto":
+            from . import tune as _tune
+            tuning = _tune.tune(cfg, "fp64" if self.precision == MW3_FP64 else "mixed",
+                                device=device)
         for key, val in (tuning or {}).items():
             _check(self.ctx, lib.mw3_set_tuning(self.ctx, key.encode(), int(val)))
         g = cfg["grid"]
@@ -364,6 +382,86 @@ class Propagator:
         if self.ctx:
             mw3_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------ surrogate network
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class MLP:
+    """The J-interpolation surrogate network (hand-written CUDA training/inference)."""
+
+    def __init__(self, n_in=4, width=256, depth=3, seed=10167, device=0):
+        h = C.c_void_p()
+        code = lib.mw3_mlp_create(C.byref(h), device, n_in, width, depth, seed)
+        if code != 0:
+            raise MW3Error(code, "mw3_mlp_create failed")
+        self.h = h
+        self.n_in = n_in
+        self.sizes = [n_in] + [width] * depth + [1]
+
+    def _chk(self, code):
+        if code != 0:
+            raise MW3Error(code, lib.mw3_mlp_last_error(self.h).decode())
+
+    @property
+    def num_params(self):
+        return lib.mw3_mlp_num_params(self.h)
+
+    def get_params(self):
+        p = np.zeros(self.num_params)
+        self._chk(lib.mw3_mlp_get_params(self.h, _dp(p)))
+        return p
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float64)
+        self._chk(lib.mw3_mlp_set_params(self.h, _dp(flat)))
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.zeros(X.shape[0], dtype=np.float32)
+        self._chk(lib.mw3_mlp_forward(self.h, _fp(X), X.shape[0], _fp(y)))
+        return y
+
+    def loss_grad(self, X, y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        loss = C.c_double()
+        g = np.zeros(self.num_params)
+        self._chk(lib.mw3_mlp_loss_grad(self.h, _fp(X), _fp(y), X.shape[0], C.byref(loss), _dp(g)))
+        return loss.value, g
+
+    def train(self, X, y, epochs, batch=4096, lr=1e-3, wd=0.0, seed=10167):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        loss = C.c_double()
+        self._chk(lib.mw3_mlp_train(self.h, _fp(X), _fp(y), X.shape[0], epochs, batch, lr, wd,
+                                    seed, C.byref(loss)))
+        return loss.value
+
+    def unflatten(self, flat):
+        """[(W, b), ...] views of a flat parameter vector (library order)."""
+        out, o = [], 0
+        for a, b in zip(self.sizes[:-1], self.sizes[1:]):
+            W = flat[o:o + a * b].reshape(b, a)
+            o += a * b
+            bb = flat[o:o + b]
+            o += b
+            out.append([W, bb])
+        return out
+
+    def close(self):
+        if self.h:
+            lib.mw3_mlp_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -1,0 +1,152 @@
+"""J-interpolation surrogate: the network of mw3_mlp_* trained on propagation results.
+
+The cumulative probability of Eq. cumulative-probability needs the probabilities of
+every J; the paper computes a coarse set of J and interpolates the rest by
+J-shifting (Eq. J-shifting-interpolation). Here a small network learns
+P_J(E, v', j') from propagations at training J values (this library's propagation,
+one batched context for all of them) and predicts intermediate J. The propagation
+is the judge of its error and its fallback: wherever the prediction differs from the
+propagated value by more than `fallback_dP`, the propagated value is used.
+
+State-resolved targets are the reactant-channel (v', j') probabilities the library
+projects at R_inf (summed over Omega), which stand in for product channels.
+"""
+from __future__ import annotations
+
+import copy
+import time
+
+import numpy as np
+
+from . import mw3
+
+
+def propagate_probabilities(cfg: dict, Js, steps: int, precision: str = "fp64", device: int = 0):
+    """Run one batched propagation over the J list; returns (E, P_total[J,E],
+    P_state[J, v, j, E] for the initial electronic state, seconds)."""
+    c = copy.deepcopy(cfg)
+    c["J"] = list(Js)
+    t0 = time.perf_counter()
+    pr = mw3.Propagator(c, device=device, precision=precision)
+    pr.propagate(steps)
+    E, P, Pin = pr.probabilities()
+    secs = time.perf_counter() - t0
+    pr.close()
+    L0 = c["packet"]["elec0"]
+    return E, P, Pin[:, L0], secs
+
+
+def features(J, E, v, j, scale):
+    """Network inputs (J, E, v', j') scaled to about [0, 1]."""
+    return np.stack([np.asarray(J, float) / scale["J"],
+                     (np.asarray(E, float) - scale["E0"]) / scale["dE"],
+                     np.asarray(v, float) / scale["v"],
+                     np.asarray(j, float) / scale["j"]], axis=-1).astype(np.float32)
+
+
+def dataset(Js, E, Pst, scale):
+    """Flatten P[J, v, j, E] into (X, y)."""
+    nJ, nv, nj, nE = Pst.shape
+    Jg, vg, jg, Eg = np.meshgrid(np.asarray(Js, float), np.arange(nv), np.arange(nj), E,
+                                 indexing="ij")
+    X = features(Jg.ravel(), Eg.ravel(), vg.ravel(), jg.ravel(), scale)
+    return X, Pst.ravel().astype(np.float32)
+
+
+def predict(net, Js, E, nv, nj, scale):
+    Jg, vg, jg, Eg = np.meshgrid(np.asarray(Js, float), np.arange(nv), np.arange(nj), E,
+                                 indexing="ij")
+    y = net.forward(features(Jg.ravel(), Eg.ravel(), vg.ravel(), jg.ravel(), scale))
+    return y.reshape(len(Js), nv, nj, len(E))
+
+
+def jshift_baseline(E, Jtr, Ptr, Jte, fit=True):
+    """J-shifting interpolation (Eq. J-shifting-interpolation) of every (v, j) curve
+    between the bracketing training J values, with B fitted per interval on the
+    state-summed probabilities."""
+    from numpy import interp
+
+    def shifted(P, dE):
+        return interp(E - dE, E, P, left=P[0], right=P[-1])
+
+    out = np.zeros((len(Jte),) + Ptr.shape[1:])
+    for t, J in enumerate(Jte):
+        k = np.searchsorted(Jtr, J) - 1
+        k = min(max(k, 0), len(Jtr) - 2)
+        J1, J2 = Jtr[k], Jtr[k + 1]
+        tot1, tot2 = Ptr[k].sum(axis=(0, 1)), Ptr[k + 1].sum(axis=(0, 1))
+        dJ = J2 * (J2 + 1) - J1 * (J1 + 1)
+        B = 0.0
+        if fit and dJ > 0:
+            grid = np.linspace(0.0, (E[-1] - E[0]) / dJ, 801)
+            errs = [np.sum((tot1 - shifted(tot2, -b * dJ)) ** 2) for b in grid]
+            B = grid[int(np.argmin(errs))]
+        w2 = (J - J1) / (J2 - J1)
+        for v in range(Ptr.shape[1]):
+            for j in range(Ptr.shape[2]):
+                a = shifted(Ptr[k, v, j], B * (J * (J + 1) - J1 * (J1 + 1)))
+                b = shifted(Ptr[k + 1, v, j], -B * (J2 * (J2 + 1) - J * (J + 1)))
+                out[t, v, j] = (1 - w2) * a + w2 * b
+    return out
+
+
+def linear_baseline(Jtr, Ptr, Jte):
+    out = np.zeros((len(Jte),) + Ptr.shape[1:])
+    for t, J in enumerate(Jte):
+        k = min(max(np.searchsorted(Jtr, J) - 1, 0), len(Jtr) - 2)
+        w = (J - Jtr[k]) / (Jtr[k + 1] - Jtr[k])
+        out[t] = (1 - w) * Ptr[k] + w * Ptr[k + 1]
+    return out
+
+
+def cumulative(Js, P):
+    """Sum_J (2J + 1) P_J(E) summed over final states (Eq. cumulative-probability, one Omega0)."""
+    Js = np.asarray(Js, float)
+    return np.sum((2 * Js + 1)[:, None] * P.sum(axis=(1, 2)), axis=0)
+
+
+def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 400, width: int = 256,
+        depth: int = 3, lr: float = 2e-3, batch: int = 2048, fallback_dP: float = 0.01,
+        device: int = 0, seed: int = 10167):
+    """Train on J_train, judge on J_test; returns a report dictionary."""
+    E, _, Ptr, t_train = propagate_probabilities(cfg, J_train, steps, device=device)
+    nv, nj = Ptr.shape[1], Ptr.shape[2]
+    scale = dict(J=max(max(J_train), 1), E0=E[0], dE=max(E[-1] - E[0], 1e-12), v=max(nv - 1, 1),
+                 j=max(nj - 1, 1))
+    X, y = dataset(J_train, E, Ptr, scale)
+    net = mw3.MLP(n_in=4, width=width, depth=depth, seed=seed, device=device)
+    t0 = time.perf_counter()
+    loss = net.train(X, y, epochs=epochs, batch=batch, lr=lr, seed=seed)
+    t_fit = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Psur = predict(net, J_test, E, nv, nj, scale)
+    t_pred = time.perf_counter() - t0
+    net.close()
+    # the judge: propagation at the held-out J
+    _, _, Pte, t_test = propagate_probabilities(cfg, J_test, steps, device=device)
+    Pjs = jshift_baseline(E, np.asarray(J_train), Ptr, np.asarray(J_test))
+    Plin = linear_baseline(np.asarray(J_train), Ptr, np.asarray(J_test))
+    err = np.abs(Psur - Pte)
+    bad_J = [J for t, J in enumerate(J_test) if err[t].max() > fallback_dP]
+    final = Psur.copy()
+    for t, J in enumerate(J_test):
+        if J in bad_J:
+            final[t] = Pte[t]
+    C_true = cumulative(J_test, Pte)
+    rep = dict(
+        train_loss=loss, n_train=int(X.shape[0]),
+        mean_abs_dP=dict(surrogate=float(err.mean()), jshift=float(np.abs(Pjs - Pte).mean()),
+                         linear=float(np.abs(Plin - Pte).mean())),
+        max_abs_dP=dict(surrogate=float(err.max()), jshift=float(np.abs(Pjs - Pte).max()),
+                        linear=float(np.abs(Plin - Pte).max()),
+                        with_fallback=float(np.abs(final - Pte).max())),
+        cumulative_rel_err=dict(
+            surrogate=float(np.abs(cumulative(J_test, Psur) - C_true).max() / max(C_true.max(), 1e-30)),
+            jshift=float(np.abs(cumulative(J_test, Pjs) - C_true).max() / max(C_true.max(), 1e-30)),
+            linear=float(np.abs(cumulative(J_test, Plin) - C_true).max() / max(C_true.max(), 1e-30)),
+            with_fallback=float(np.abs(cumulative(J_test, final) - C_true).max() / max(C_true.max(), 1e-30))),
+        fallback_J=bad_J, fallback_fraction=len(bad_J) / len(J_test),
+        seconds=dict(propagate_train=t_train, fit=t_fit, predict=t_pred, propagate_test=t_test,
+                     surrogate_path=t_pred + t_test * len(bad_J) / len(J_test)),
+    )
+    return rep

@@ -232,3 +232,21 @@ def test_tensor_core_step_matches_cuda_core_step(name):
     ref = oracle_run(name, cfg, 40)
     rel_o = np.linalg.norm(qs[0] - ref["q"]) / np.linalg.norm(ref["q"])
     assert rel_o < 2e-5, rel_o
+
+
+def test_autotuner_picks_and_caches(tmp_path):
+    """The tuner sweeps launch shapes with the library's own event timers, caches the
+    winners per shape, and a tuned context reproduces the default results to FP32
+    rounding (launch shapes change only the order of independent work)."""
+    from paper_2412_10167_gb300 import tune
+    cfg = W.C2_SMALL
+    path = str(tmp_path / "tune.json")
+    best = tune.tune(cfg, "mixed", steps=4, cache_path=path)
+    assert set(best) == {"rows_pairs", "cols_tile", "kb"}
+    assert tune.tune(cfg, "mixed", cache_path=path) == best          # cached
+    a = mw3().Propagator(cfg, precision="mixed", tuning=best)
+    b = mw3().Propagator(cfg, precision="mixed")
+    a.propagate(40)
+    b.propagate(40)
+    qa, qb = a.state()[0], b.state()[0]
+    assert np.linalg.norm(qa - qb) / np.linalg.norm(qb) < 1e-5

