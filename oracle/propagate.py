@@ -9,7 +9,8 @@ Section 2.3.1: initial packet W chi_(v0 j0)(r) Y_(j0 Omega0)(gamma) g(R) with th
 g(R) of Eq. (initial-gaussian) and the incoming amplitude of Eq. (initial-flux-collisions).
 Section 2.4: total reaction probability from the flux through r = r* (Eq. total-flux)
 and state-resolved probabilities from projections at R_inf
-(Eqs. Chebyshev-products-overlaps, S-matrix-from-chebyshev).
+(Eqs. Chebyshev-products-overlaps, S-matrix-from-chebyshev); product channels
+through the projector of oracle/products.py.
 
 Readings (the paper is silent, ambiguous or garbled at these points):
   * "N iterations" means q_0 .. q_(N-1) enter the energy sums;
@@ -35,6 +36,7 @@ import numpy as np
 
 from . import basis, pes
 from .hamiltonian import GridHamiltonian
+from .products import ProductAnalysis
 from .units import AMU, EV
 
 R_DIATOM = 100.0   # bohr: R at which diatomic eigenfunctions are computed (Table 1)
@@ -216,18 +218,20 @@ def chebyshev_iterates(H: GridHamiltonian, q0, D, N):
 
 
 def propagate(cfg: dict, nsteps=None, H: GridHamiltonian = None, flux_axis="r",
-              flux_at=None, keep_states=False, channels=True):
+              flux_at=None, keep_states=False, channels=True, q0=None):
     """Run the modified real Chebyshev recursion and accumulate the energy sums.
 
     Returns a Result with q_N, q_(N-1), the raw sums A (psi) and B (dpsi) per
     energy and cut point, the channel sums, the norm trace ||q_k||^2 (k = 0..N),
-    and the derived probabilities.
+    and the derived probabilities. ``q0`` replaces the initial packet as the first
+    iterate (the packet still defines a(E) and the energy grid).
     """
     if H is None:
         H = GridHamiltonian(cfg)
     N = cfg["steps"] if nsteps is None else int(nsteps)
     an = cfg["analysis"]
-    q0, info = initial_packet(H, cfg["packet"])
+    qp, info = initial_packet(H, cfg["packet"])
+    q0 = qp if q0 is None else np.asarray(q0, dtype=float)
     D = damping_grid(H, cfg["absorber"])[None, None, :, :]
     Ecol, Etot, theta = energy_grid(H, an, info["E_v0j0"])
     bj = H.block_J_index()
@@ -245,6 +249,10 @@ def propagate(cfg: dict, nsteps=None, H: GridHamiltonian = None, flux_axis="r",
         chan_J = np.array([c[0] for c in chans], dtype=int)
         Cc = np.zeros((len(chans), len(Ecol)), dtype=complex)
     kmin = an.get("kmin", 0)
+    prod = an.get("products") if channels else None
+    if prod:
+        pa = ProductAnalysis(H, prod)
+        Cp = [np.zeros((len(pa.channels(iJ)), len(Ecol)), dtype=complex) for iJ in range(len(H.Js))]
 
     norms = [float(np.sum(q0 * q0))]
     states = [q0.copy()] if keep_states else []
@@ -258,6 +266,10 @@ def propagate(cfg: dict, nsteps=None, H: GridHamiltonian = None, flux_axis="r",
             ov = channel_overlaps(H, q, chans, chis, m_inf)
             ckc = (1.0 if k == 0 else 2.0) * np.exp(-1j * k * theta[chan_J])
             Cc += ckc * ov[:, None]
+        if prod:
+            ovp = pa.overlaps(q)
+            for iJ in range(len(H.Js)):
+                Cp[iJ] += ((1.0 if k == 0 else 2.0) * np.exp(-1j * k * theta[iJ]))[None, :] * ovp[iJ][:, None]
         norms.append(float(np.sum(q_next * q_next)))
         if keep_states:
             states.append(q_next.copy())
@@ -289,6 +301,20 @@ def propagate(cfg: dict, nsteps=None, H: GridHamiltonian = None, flux_axis="r",
         for (iJ, om, L, v, j), s2 in zip(chans, S2):
             key = (iJ, L, v, j)
             res["P_inel"][key] = res["P_inel"].get(key, 0.0) + s2
+    if prod:
+        # product channels: |S|^2 = (2 pi K' / mu') |C_E|^2 / |a|^2, summed over Omega'
+        res["P_prod"] = {}
+        res["prod_channels"] = [pa.channels(iJ) for iJ in range(len(H.Js))]
+        res["C_prod_raw"] = Cp
+        for iJ in range(len(H.Js)):
+            pref_p = 1.0 / (2.0 * np.pi * H.dE[iJ] * np.sin(theta[iJ]))
+            for ic, (L, v, j, op, e) in enumerate(pa.channels(iJ)):
+                K2 = 2.0 * pa.mu_p * (Etot - e)
+                Kp = np.sqrt(np.where(K2 > 0, K2, 0.0))
+                s2 = np.where(K2 > 0, 2.0 * np.pi * Kp / pa.mu_p * np.abs(pref_p * Cp[iJ][ic]) ** 2
+                              / np.abs(a) ** 2, 0.0)
+                key = (iJ, L, v, j)
+                res["P_prod"][key] = res["P_prod"].get(key, 0.0) + s2
     return res
 
 
