@@ -96,6 +96,31 @@ typedef struct {
   long kmin;
 } mw3_analysis_desc;
 
+/* Product channels (Section 2.4, Eqs. final-states, Chebyshev-products-overlaps and
+ * S-matrix-from-chebyshev; the inputprod namelist): overlaps of q_k with the
+ * product states chi_(v'j')(r') P-bar_(j')^(Omega')(cos gamma') on the surface
+ * R' = Rinf, for the wave packet held in reactant Jacobi coordinates. The surface
+ * integral uses a product quadrature (the nr midpoint sine-DVR nodes of
+ * [rmin, rmax] times ngamma Gauss-Legendre nodes); at each node the reactant
+ * function is interpolated (4-point Lagrange in R and r, its Legendre series in
+ * gamma) and its helicity components rotated into the product frame with the
+ * Wigner matrix d^J of the angle between R and R' (parity (-1)^J; helicities
+ * above omega_max are zero in both frames), times the Jacobian r'R'/(rR).
+ *   arrangement  1: products AC + B (r' = C - A); 2: products AB + C (r' = B - A)
+ *   vmax, jmax   channels v' <= vmax, j' <= jmax, Omega' <= min(j', J, omega_max),
+ *                for every electronic state (product states from V_LL with the
+ *                departing atom 100 bohr away; needs a potential callback)
+ * Every node's reactant point must lie inside the grid; stencil points beyond the
+ * ends of the grid count as zero. */
+typedef struct {
+  int arrangement;
+  double Rinf;
+  int nr;
+  double rmin, rmax;
+  int ngamma;
+  int vmax, jmax;
+} mw3_products_desc;
+
 /* Potential callback (the potelebond routine of Section 4, in Jacobi form):
  * given r, R (bohr) and cos(gamma) write the nelec x nelec diabatic matrix
  * (hartree, row-major, symmetric) into potmat; return 0 on success. */
@@ -169,6 +194,11 @@ int mw3_set_absorber(mw3_ctx* ctx, double RI, double AR, int nR, double rI, doub
  * energy-sum accumulators. Must follow mw3_init_packet (needs E_{v0 j0}). */
 int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* desc);
 
+/* Enable product channels (call after mw3_init_packet and before mw3_set_analysis;
+ * NULL disables them). MW3_ERR_BAD_ARG for an invalid description, a grid potential
+ * without a callback, or a node outside the grid. */
+int mw3_set_products(mw3_ctx* ctx, const mw3_products_desc* desc);
+
 /* --------------------------------------------------------------- propagation */
 
 /* Advance nsteps Chebyshev iterations of Eq. (wvp-k):
@@ -218,12 +248,21 @@ int mw3_reference_energy(const mw3_ctx* ctx, double* Ev0j0);
 int mw3_checkpoint_save(mw3_ctx* ctx, const char* path);
 int mw3_checkpoint_load(mw3_ctx* ctx, const char* path);
 
+/* State-resolved product probabilities |S|^2 (Eq. S-matrix-from-chebyshev, with the
+ * flux normalisation of the reactant channels: (2 pi K'/mu') |C_E|^2 / |a(E)|^2,
+ * K' = sqrt(2 mu' (E - e_(v'j'))), closed channels 0), summed over Omega':
+ * P[((iJ * nelec + L) * (vmax + 1) + v) * (jmax + 1) + j][e], caller-owned host
+ * array. MW3_ERR_STATE if product channels are not enabled. */
+int mw3_product_probabilities(mw3_ctx* ctx, double* P);
+
 /* Launch-shape and scheduling knobs (the autotuner's hook). Keys:
  *   "kb"         Chebyshev iterations per energy-sum flush (1..1024; before mw3_set_analysis)
  *   "rows_pairs" line pairs per CTA of the R-direction kinetic kernel (1..16)
  *   "cols_tile"  R columns per CTA of the r-direction kinetic kernel (even, 2..64)
  *   "use_graph"  0/1: replay full chunks as CUDA graphs
  *   "use_tc"     0/1: tensor-core gamma transform in MW3_MIXED
+ *   "kin_warp"   0/1: warp-register FFT kinetic kernels for line lengths 32 R
+ *                (R = 1, 2, 3, 4, 6, 8, 12, 16; FP64 up to R = 8); default 1
  * Values outside a key's range return MW3_ERR_BAD_ARG. mw3_get_tuning reads a key. */
 int mw3_set_tuning(mw3_ctx* ctx, const char* key, long value);
 long mw3_get_tuning(const mw3_ctx* ctx, const char* key);

@@ -40,8 +40,9 @@ using namespace mw3;
 namespace {
 
 const char* kKernelNames[] = {"kinetic_rows", "kinetic_cols", "gamma_to_dvr", "gamma_update",
-                              "channels",     "norms",        "sums_flush",   "angular_tc"};
-constexpr int kNumKernels = 8;
+                              "channels",     "norms",        "sums_flush",   "angular_tc",
+                              "products"};
+constexpr int kNumKernels = 9;
 
 struct DevBuf {
   void* p = nullptr;
@@ -82,7 +83,7 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0};
+  Tuning tune{4, 32, 32, 1, 0, 1};
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   bool tc_ok = false;  // the tensor-core angular step supports this grid
   int tc_user = -1;    // explicit "use_tc" setting (-1: default = on when supported)
@@ -130,6 +131,22 @@ struct mw3_ctx {
   std::vector<double> chan_eps;
   std::vector<long> colbase, ncols, ncut, accoff;
   long NC = 0, max_cols = 0, acc_size = 0;
+
+  // product channels (mw3_set_products)
+  bool prod_on = false;
+  mw3_products_desc prod{};
+  double mu_p = 0, m_p = 0;
+  int prod_nn = 0, prod_ltop = 0;
+  std::vector<int> prod_idx;               // [node][8]: R stencil, then r stencil
+  std::vector<double> prod_w;              // [node][8] Lagrange weights (R ones / sqrt(dR dr))
+  std::vector<double> prod_pl;             // [node][ltop][ng] P-bar_(Omega+i)^Omega(cos gamma)
+  std::vector<double> prod_T;              // per J: [node][nom][nom] helicity transforms
+  std::vector<double> prod_jac;            // [node] r'R'/(rR)
+  std::vector<double> prod_W;              // [channel][node] quadrature weights
+  std::vector<ProdGroup> prod_groups;      // col0 set by mw3_set_analysis
+  std::vector<long> prod_first;            // nJ + 1: first channel of each J
+  std::vector<int> pch_L, pch_v, pch_j, pch_op;
+  std::vector<double> pch_eps;
 
   // propagation state
   long iter = 0;       // k of q_k
@@ -413,8 +430,9 @@ int mw3_create(mw3_ctx** out, int device, int precision) {
   if (!ctx) return MW3_ERR_OOM;
   ctx->precision = precision;
   ctx->device = device;
-  ctx->tune.kb = (precision == MW3_FP64) ? 32 : 64;
-  ctx->tune.cols_tile = (precision == MW3_FP64) ? 16 : 32;
+  ctx->tune.kb = (precision == MW3_FP64) ? 32 : 128;
+  ctx->tune.cols_tile = 16;
+  ctx->tune.rows_pairs = (precision == MW3_FP64) ? 4 : 8;
   if (device < 0) {
     ctx->host_only = true;  // set-up mathematics only (no device work)
   } else {
@@ -668,7 +686,8 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
   // tensor-core operands: T^Omega and its transpose, padded to kp x kp, split into a
   // TF32-rounded high part and the exact FP32 remainder
   ctx->kp = ((ng + 15) / 16) * 16;
-  ctx->tc_ok = (ctx->precision == MW3_MIXED) && ctx->kp <= kTcMaxKp;
+  ctx->tc_ok = (ctx->precision == MW3_MIXED) && ctx->kp <= kTcMaxKp &&
+               (ctx->ncol + 127) / 128 <= 65535;
   ctx->tune.use_tc = (ctx->tc_ok && ctx->tc_user != 0) ? 1 : 0;
   if (ctx->tc_ok) {
     const int kp = ctx->kp;
@@ -842,6 +861,172 @@ int mw3_set_absorber(mw3_ctx* ctx, double RI, double AR, int nR, double rI, doub
   return MW3_OK;
 }
 
+int mw3_set_products(mw3_ctx* ctx, const mw3_products_desc* d) {
+  if (!ctx) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 3) return ctx->fail(MW3_ERR_STATE, "mw3_init_packet first");
+  if (ctx->stage >= 5) return ctx->fail(MW3_ERR_STATE, "set products before mw3_set_analysis");
+  ctx->prod_on = false;
+  if (!d) return MW3_OK;
+  if ((d->arrangement != 1 && d->arrangement != 2) || !(d->Rinf > 0) || d->nr < 4 ||
+      !(d->rmin > 0) || !(d->rmax > d->rmin) || d->ngamma < 1 || d->vmax < 0 || d->jmax < 0 ||
+      d->vmax >= d->nr)
+    return ctx->fail(MW3_ERR_BAD_ARG, "invalid products description");
+  if (!ctx->pot_fn)
+    return ctx->fail(MW3_ERR_BAD_ARG, "product channels need a potential callback");
+  const double masses[3] = {ctx->mA, ctx->mB, ctx->mC};
+  product_masses(masses, d->arrangement, &ctx->mu_p, &ctx->m_p);
+  const int nrp = d->nr, ngp = d->ngamma, nn = nrp * ngp, ng = ctx->ng;
+  const double drp = (d->rmax - d->rmin) / nrp;
+  std::vector<double> rp(nrp), xg, wg;
+  for (int a = 0; a < nrp; ++a) rp[a] = d->rmin + (a + 0.5) * drp;
+  gauss_legendre(ngp, xg, wg);
+  // nodes: reactant point, 4-point stencils, Jacobian, frame rotation
+  std::vector<double> cosg(nn), beta(nn);
+  std::vector<int> sa(nn), sc(nn);
+  ctx->prod_idx.assign((size_t)nn * 8, 0);
+  ctx->prod_w.assign((size_t)nn * 8, 0.0);
+  ctx->prod_jac.assign(nn, 0.0);
+  auto stencil = [](double x0, double dx, int n, double x, int* id, double* w, double scale) {
+    const double t = (x - x0) / dx;
+    const int m0 = (int)std::floor(t) - 1;
+    const double u = t - m0;
+    const double L[4] = {-(u - 1) * (u - 2) * (u - 3) / 6.0, u * (u - 2) * (u - 3) / 2.0,
+                         -u * (u - 1) * (u - 3) / 2.0, u * (u - 1) * (u - 2) / 6.0};
+    for (int a = 0; a < 4; ++a) {
+      const int m = m0 + a;
+      const bool in = m >= 0 && m < n;
+      id[a] = in ? m : 0;
+      w[a] = in ? L[a] * scale : 0.0;
+    }
+  };
+  for (int a = 0; a < nrp; ++a)
+    for (int l = 0; l < ngp; ++l) {
+      const int v = a * ngp + l;
+      double R, r;
+      product_point(masses, d->arrangement, d->Rinf, rp[a], xg[l], &R, &r, &cosg[v], &beta[v],
+                    &sa[v], &sc[v]);
+      if (!(R >= ctx->Rmin && R <= ctx->Rmax && r >= ctx->rmin && r <= ctx->rmax))
+        return ctx->fail(MW3_ERR_BAD_ARG, "a product quadrature node lies outside the grid");
+      stencil(ctx->R[0], ctx->dR, ctx->NR, R, &ctx->prod_idx[(size_t)v * 8],
+              &ctx->prod_w[(size_t)v * 8], 1.0 / std::sqrt(ctx->dR * ctx->dr));
+      stencil(ctx->r[0], ctx->dr, ctx->nr, r, &ctx->prod_idx[(size_t)v * 8 + 4],
+              &ctx->prod_w[(size_t)v * 8 + 4], 1.0);
+      ctx->prod_jac[v] = rp[a] * d->Rinf / (r * R);
+    }
+  // Legendre rows of every helicity at the nodes' reactant angles
+  int ltop = 0;
+  for (int iJ = 0; iJ < ctx->nJ; ++iJ) ltop = std::max(ltop, ctx->omtop[iJ] + 1);
+  ctx->prod_ltop = ltop;
+  ctx->prod_pl.assign((size_t)nn * ltop * ng, 0.0);
+  for (int om = 0; om < ltop && om < ng; ++om) {
+    std::vector<double> P;
+    norm_assoc_legendre(ng - 1, om, cosg, P);
+    for (int v = 0; v < nn; ++v)
+      for (int i = 0; i < ng - om; ++i)
+        ctx->prod_pl[((size_t)v * ltop + om) * ng + i] = P[(size_t)i * nn + v];
+  }
+  // helicity transforms per J and node
+  ctx->prod_T.clear();
+  std::vector<long> toff(ctx->nJ);
+  for (int iJ = 0; iJ < ctx->nJ; ++iJ) {
+    toff[iJ] = (long)ctx->prod_T.size();
+    const int nom = ctx->omtop[iJ] + 1;
+    std::vector<double> Tm;
+    for (int v = 0; v < nn; ++v) {
+      helicity_transform(ctx->J[iJ], nom, beta[v], sa[v], sc[v], Tm);
+      ctx->prod_T.insert(ctx->prod_T.end(), Tm.begin(), Tm.end());
+    }
+  }
+  // product diatomic states on the r' sine DVR (departing atom 100 bohr away, collinear)
+  const int nv = d->vmax + 1, ne = ctx->nelec;
+  std::vector<double> lam(nrp + 1, 0.0);
+  for (int jj = 1; jj <= nrp; ++jj) {
+    const double k = jj * M_PI / (d->rmax - d->rmin);
+    lam[jj] = std::min(k * k / (2.0 * ctx->m_p), ctx->tcut);
+  }
+  std::vector<double> Tk((size_t)nrp * nrp, 0.0), Vd((size_t)ne * nrp), pm((size_t)ne * ne);
+  for (int a = 0; a < nrp; ++a)
+    for (int b = 0; b < nrp; ++b) {
+      double s = 0;
+      for (int jj = 1; jj <= nrp; ++jj) s += dst2(nrp, jj, a + 1) * lam[jj] * dst2(nrp, jj, b + 1);
+      Tk[(size_t)a * nrp + b] = s;
+    }
+  for (int a = 0; a < nrp; ++a) {
+    double R, r, cg, bb;
+    int s1, s2;
+    product_point(masses, d->arrangement, 100.0, rp[a], 1.0, &R, &r, &cg, &bb, &s1, &s2);
+    if (ctx->pot_fn(r, R, cg, pm.data(), ctx->pot_user) != 0)
+      return ctx->fail(MW3_ERR_BAD_ARG, "potential callback failed");
+    for (int L = 0; L < ne; ++L) Vd[(size_t)L * nrp + a] = std::min(pm[(size_t)L * ne + L], ctx->vcut);
+  }
+  std::vector<std::vector<double>> chi((size_t)ne * (d->jmax + 1)), eps((size_t)ne * (d->jmax + 1));
+  for (int L = 0; L < ne; ++L)
+    for (int j = 0; j <= d->jmax; ++j) {
+      std::vector<double> H = Tk, ev, Z;
+      for (int a = 0; a < nrp; ++a)
+        H[(size_t)a * nrp + a] += Vd[(size_t)L * nrp + a] +
+                                  std::min(j * (j + 1.0) / (2.0 * ctx->m_p * rp[a] * rp[a]), ctx->erot);
+      symmetric_eigen(nrp, H, ev, Z);
+      auto& c = chi[(size_t)L * (d->jmax + 1) + j];
+      c.assign((size_t)nv * nrp, 0.0);
+      for (int v = 0; v < nv; ++v) {
+        int imax = 0;
+        for (int a = 0; a < nrp; ++a)
+          if (std::fabs(Z[(size_t)a * nrp + v]) > std::fabs(Z[(size_t)imax * nrp + v])) imax = a;
+        const double sg = Z[(size_t)imax * nrp + v] < 0 ? -1.0 : 1.0;
+        for (int a = 0; a < nrp; ++a) c[(size_t)v * nrp + a] = sg * Z[(size_t)a * nrp + v];
+      }
+      eps[(size_t)L * (d->jmax + 1) + j].assign(ev.begin(), ev.begin() + nv);
+    }
+  // channels, grouped by (J, Lambda', Omega'), and their quadrature weights
+  ctx->prod_groups.clear();
+  ctx->prod_W.clear();
+  ctx->pch_L.clear();
+  ctx->pch_v.clear();
+  ctx->pch_j.clear();
+  ctx->pch_op.clear();
+  ctx->pch_eps.clear();
+  ctx->prod_first.assign(ctx->nJ + 1, 0);
+  long nch = 0;
+  for (int iJ = 0; iJ < ctx->nJ; ++iJ) {
+    ctx->prod_first[iJ] = nch;
+    const int nom = ctx->omtop[iJ] + 1;
+    for (int L = 0; L < ne; ++L)
+      for (int op = 0; op < nom && op <= d->jmax; ++op) {
+        std::vector<double> Pp;
+        norm_assoc_legendre(d->jmax, op, xg, Pp);
+        ProdGroup g{};
+        g.b0 = (int)ctx->J_first_block[iJ] + L;
+        g.bstride = ne;
+        g.nom = nom;
+        g.op = op;
+        g.toff = toff[iJ];
+        g.c0 = (int)nch;
+        for (int j = op; j <= d->jmax; ++j)
+          for (int v = 0; v < nv; ++v) {
+            const auto& c = chi[(size_t)L * (d->jmax + 1) + j];
+            for (int a = 0; a < nrp; ++a)
+              for (int l = 0; l < ngp; ++l)
+                ctx->prod_W.push_back(drp * wg[l] * c[(size_t)v * nrp + a] / std::sqrt(drp) *
+                                      Pp[(size_t)(j - op) * ngp + l]);
+            ctx->pch_L.push_back(L);
+            ctx->pch_v.push_back(v);
+            ctx->pch_j.push_back(j);
+            ctx->pch_op.push_back(op);
+            ctx->pch_eps.push_back(eps[(size_t)L * (d->jmax + 1) + j][v]);
+            ++nch;
+          }
+        g.nc = (int)(nch - g.c0);
+        ctx->prod_groups.push_back(g);
+      }
+  }
+  ctx->prod_first[ctx->nJ] = nch;
+  ctx->prod_nn = nn;
+  ctx->prod = *d;
+  ctx->prod_on = true;
+  return MW3_OK;
+}
+
 int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
   if (!ctx || !d) return MW3_ERR_BAD_ARG;
   if (ctx->stage < 3) return ctx->fail(MW3_ERR_STATE, "mw3_init_packet first");
@@ -920,11 +1105,18 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
         }
       }
     }
-    ctx->ncols[iJ] = 2 * nc + nch;
+    long nchp = 0;
+    if (ctx->prod_on) {
+      const long p0 = ctx->prod_first[iJ];
+      nchp = ctx->prod_first[iJ + 1] - p0;
+      for (auto& g : ctx->prod_groups)
+        if (g.c0 >= p0 && g.c0 < p0 + nchp) g.col0 = (int)(col + 2 * nc + nch + (g.c0 - p0));
+    }
+    ctx->ncols[iJ] = 2 * nc + nch + nchp;
     ctx->accoff[iJ] = acc;
     acc += 2L * nE * ctx->ncols[iJ];
     maxc = std::max(maxc, ctx->ncols[iJ]);
-    col += ((2 * nc + nch + 3) / 4) * 4;
+    col += ((ctx->ncols[iJ] + 3) / 4) * 4;
   }
   ctx->nchan = (int)ctx->chan_block.size();
   ctx->NC = col;
@@ -951,6 +1143,14 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
     if ((st = upload_real(ctx, "P", P)) || (st = upload_raw(ctx, "chan_block", ctx->chan_block)) ||
         (st = upload_raw(ctx, "chan_row", ctx->chan_row)) ||
         (st = upload_raw(ctx, "chan_col", ctx->chan_col)))
+      return st;
+  }
+  if (ctx->prod_on) {
+    if ((st = upload_raw(ctx, "p_idx", ctx->prod_idx)) || (st = upload_real(ctx, "p_w", ctx->prod_w)) ||
+        (st = upload_real(ctx, "p_pl", ctx->prod_pl)) || (st = upload_real(ctx, "p_T", ctx->prod_T)) ||
+        (st = upload_real(ctx, "p_jac", ctx->prod_jac)) || (st = upload_real(ctx, "p_W", ctx->prod_W)) ||
+        (st = upload_raw(ctx, "p_groups", ctx->prod_groups)) ||
+        (st = dalloc(ctx, "p_u", (size_t)ctx->nblk * ctx->prod_nn * ctx->rs())))
       return st;
   }
   if ((st = dalloc(ctx, "d_iter", 8))) return st;
@@ -1082,7 +1282,8 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
   {
     Timer tm(ctx, 0, timed);
     LK(launch_kinetic_rows<real>(qk, B.t, nrows, ctx->planR, B.twR, B.phR, B.lamR,
-                                 ctx->tune.rows_pairs, B.blocks, ctx->ng, ctx->nr, st));
+                                 ctx->tune.rows_pairs, B.blocks, ctx->ng, ctx->nr,
+                                 ctx->tune.kin_warp, st));
     tm.stop();
   }
   {
@@ -1090,7 +1291,8 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
     LK(launch_kinetic_cols<real>(qk, B.t, (long)ctx->nblk * ctx->ng, ctx->nr, ctx->NR, ctx->planr,
                                  B.twr, B.phr, B.lamr, ctx->tune.cols_tile, ctx->ng, B.wpsi,
                                  B.wdpsi, cut_slot, B.blocks, B.ncut_i,
-                                 analysis ? ctx->m_inf : -1, analysis ? B.qcol : nullptr, st));
+                                 analysis ? ctx->m_inf : -1, analysis ? B.qcol : nullptr,
+                                 ctx->tune.kin_warp, st));
     tm.stop();
   }
   const bool tc = std::is_same<real, float>::value && ctx->tc_ok && ctx->tune.use_tc;
@@ -1151,6 +1353,18 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
     Timer tm(ctx, 4, timed);
     LK(launch_channels<real>(B.qcol, B.P, B.chan_block, B.chan_row, B.chan_col, ctx->nchan,
                              ctx->ng, ctx->nr, B.d_iter, slot, ctx->an.kmin, cut_slot, st));
+    tm.stop();
+  }
+  if (analysis && ctx->prod_on) {
+    Timer tm(ctx, 8, timed);
+    real* pu = (real*)dptr(ctx, "p_u");
+    LK(launch_prod_eval<real>(qk, B.blocks, ctx->nblk, ctx->ng, ctx->nr, ctx->NR, ctx->prod_nn,
+                              (const int*)dptr(ctx, "p_idx"), (const real*)dptr(ctx, "p_w"),
+                              (const real*)dptr(ctx, "p_pl"), ctx->prod_ltop, pu, st));
+    LK(launch_prod_project<real>(pu, ctx->prod_nn, (const real*)dptr(ctx, "p_T"),
+                                 (const real*)dptr(ctx, "p_jac"), (const real*)dptr(ctx, "p_W"),
+                                 (const ProdGroup*)dptr(ctx, "p_groups"),
+                                 (int)ctx->prod_groups.size(), cut_slot, st));
     tm.stop();
   }
   if (!tc) {
@@ -1237,6 +1451,22 @@ int propagate_impl(mw3_ctx* ctx, long nsteps) {
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return MW3_OK;
+}
+
+// |a(E)|^2 of the incoming packet, a(E) = sqrt(mu/(2 pi K)) sum_m dR exp(i K R_m) g~(R_m).
+void incoming_a2(const mw3_ctx* ctx, std::vector<double>& a2) {
+  const int nE = ctx->an.nE;
+  a2.assign(nE, 0.0);
+  for (int e = 0; e < nE; ++e) {
+    const double K = std::sqrt(2.0 * ctx->mu * ctx->Ecol[e]);
+    double re = 0, im = 0;
+    for (int i = 0; i < ctx->NR; ++i) {
+      re += std::cos(K * ctx->R[i]) * ctx->g_tilde[i];
+      im += std::sin(K * ctx->R[i]) * ctx->g_tilde[i];
+    }
+    const double s = std::sqrt(ctx->mu / (2.0 * M_PI * K)) * ctx->dR;
+    a2[e] = s * s * (re * re + im * im);
+  }
 }
 
 }  // namespace
@@ -1333,6 +1563,41 @@ long mw3_norm_trace(mw3_ctx* ctx, double* out, long n) {
   return cnt;
 }
 
+int mw3_product_probabilities(mw3_ctx* ctx, double* P) {
+  if (!ctx || !P) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 5) return ctx->fail(MW3_ERR_STATE, "mw3_set_analysis first");
+  if (!ctx->prod_on) return ctx->fail(MW3_ERR_STATE, "product channels are not enabled");
+  if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
+  const int nE = ctx->an.nE, nJ = ctx->nJ, ne = ctx->nelec;
+  const int nv = ctx->prod.vmax + 1, nj = ctx->prod.jmax + 1;
+  std::vector<double> a2;
+  incoming_a2(ctx, a2);
+  std::fill(P, P + (size_t)nJ * ne * nv * nj * nE, 0.0);
+  for (int iJ = 0; iJ < nJ; ++iJ) {
+    const long p0 = ctx->prod_first[iJ], np = ctx->prod_first[iJ + 1] - p0;
+    if (np <= 0) continue;
+    const long first = ctx->ncols[iJ] - np;           // local column of the first product channel
+    std::vector<double> A((size_t)2 * nE * np);
+    const double* src = (const double*)dptr(ctx, "acc") + ctx->accoff[iJ] + first;
+    CK(cudaMemcpy2DAsync(A.data(), np * 8, src, ctx->ncols[iJ] * 8, np * 8, 2 * nE,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (long c = 0; c < np; ++c) {
+      const long g = p0 + c;
+      for (int e = 0; e < nE; ++e) {
+        const double K2 = 2.0 * ctx->mu_p * (ctx->Ecol[e] + ctx->Ev0j0 - ctx->pch_eps[g]);
+        if (K2 <= 0) continue;
+        const double th = ctx->theta[(size_t)iJ * nE + e];
+        const double pref = 1.0 / (2.0 * M_PI * ctx->dE[iJ] * std::sin(th));
+        const double re = A[(size_t)e * np + c] * pref, im = A[(size_t)(nE + e) * np + c] * pref;
+        const size_t o = ((((size_t)iJ * ne + ctx->pch_L[g]) * nv + ctx->pch_v[g]) * nj + ctx->pch_j[g]) * nE + e;
+        P[o] += 2.0 * M_PI * std::sqrt(K2) / ctx->mu_p * (re * re + im * im) / a2[e];
+      }
+    }
+  }
+  return MW3_OK;
+}
+
 int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel) {
   if (!ctx) return MW3_ERR_BAD_ARG;
   if (ctx->stage < 5) return ctx->fail(MW3_ERR_STATE, "mw3_set_analysis first");
@@ -1340,18 +1605,8 @@ int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel)
   if (E)
     for (int e = 0; e < nE; ++e) E[e] = ctx->Ecol[e];
   if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
-  // incoming amplitudes a(E) = sqrt(mu/(2 pi K)) sum_m dR exp(i K R_m) g~(R_m)
-  std::vector<double> a2(nE);
-  for (int e = 0; e < nE; ++e) {
-    const double K = std::sqrt(2.0 * ctx->mu * ctx->Ecol[e]);
-    double re = 0, im = 0;
-    for (int i = 0; i < ctx->NR; ++i) {
-      re += std::cos(K * ctx->R[i]) * ctx->g_tilde[i];
-      im += std::sin(K * ctx->R[i]) * ctx->g_tilde[i];
-    }
-    const double s = std::sqrt(ctx->mu / (2.0 * M_PI * K)) * ctx->dR;
-    a2[e] = s * s * (re * re + im * im);
-  }
+  std::vector<double> a2;
+  incoming_a2(ctx, a2);
   int st;
   if ((st = dalloc(ctx, "flux", (size_t)nJ * nE * 8))) return st;
   LK(launch_flux_reduce((const double*)dptr(ctx, "acc"), nJ, nE, (const long*)dptr(ctx, "accoff"),
@@ -1426,6 +1681,8 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
     ctx->tune.cols_tile = (int)v;
   } else if (k == "use_graph") {
     ctx->tune.use_graph = v != 0;
+  } else if (k == "kin_warp") {
+    ctx->tune.kin_warp = v != 0;
   } else if (k == "use_tc") {
     if (v != 0 && ctx->precision != MW3_MIXED)
       return ctx->fail(MW3_ERR_BAD_ARG, "use_tc needs MW3_MIXED");
@@ -1445,6 +1702,7 @@ long mw3_get_tuning(const mw3_ctx* ctx, const char* key) {
   if (k == "rows_pairs") return ctx->tune.rows_pairs;
   if (k == "cols_tile") return ctx->tune.cols_tile;
   if (k == "use_graph") return ctx->tune.use_graph;
+  if (k == "kin_warp") return ctx->tune.kin_warp;
   if (k == "use_tc") return ctx->stage >= 2 ? ctx->tune.use_tc : (ctx->tc_user != 0);
   return MW3_ERR_BAD_ARG;
 }

@@ -228,6 +228,107 @@ void sine_interpolation_weights(double xa, double xb, int N, double x, std::vect
   }
 }
 
+// ------------------------------------------------- product arrangement geometry
+// Atom positions with the BC centre of mass at the origin, as alpha r + beta R:
+// A = R, B = -(m_C / M_BC) r, C = (m_B / M_BC) r.
+void product_jacobi_matrix(const double m[3], int arrangement, double M[2][2]) {
+  const double MBC = m[1] + m[2];
+  const double A[2] = {0.0, 1.0}, B[2] = {-m[2] / MBC, 0.0}, C[2] = {m[1] / MBC, 0.0};
+  for (int c = 0; c < 2; ++c) {
+    if (arrangement == 1) {            // AC + B
+      M[0][c] = C[c] - A[c];
+      M[1][c] = B[c] - (m[0] * A[c] + m[2] * C[c]) / (m[0] + m[2]);
+    } else {                           // AB + C
+      M[0][c] = B[c] - A[c];
+      M[1][c] = C[c] - (m[0] * A[c] + m[1] * B[c]) / (m[0] + m[1]);
+    }
+  }
+}
+
+void product_masses(const double m[3], int arrangement, double* mu_p, double* m_p) {
+  const double Mt = m[0] + m[1] + m[2];
+  if (arrangement == 1) {
+    *mu_p = m[1] * (m[0] + m[2]) / Mt;
+    *m_p = m[0] * m[2] / (m[0] + m[2]);
+  } else {
+    *mu_p = m[2] * (m[0] + m[1]) / Mt;
+    *m_p = m[0] * m[1] / (m[0] + m[1]);
+  }
+}
+
+void product_point(const double masses[3], int arrangement, double Rp, double rp, double cosgp,
+                   double* R, double* r, double* cosg, double* beta, int* sa, int* sc) {
+  double M[2][2];
+  product_jacobi_matrix(masses, arrangement, M);
+  const double det = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+  const double Mi[2][2] = {{M[1][1] / det, -M[0][1] / det}, {-M[1][0] / det, M[0][0] / det}};
+  // plane vectors (x, z) in the product body-fixed frame
+  const double sg = std::sqrt(std::max(1.0 - cosgp * cosgp, 0.0));
+  const double rpv[2] = {rp * sg, rp * cosgp}, Rpv[2] = {0.0, Rp};
+  double rv[2], Rv[2];
+  for (int c = 0; c < 2; ++c) {
+    rv[c] = Mi[0][0] * rpv[c] + Mi[0][1] * Rpv[c];
+    Rv[c] = Mi[1][0] * rpv[c] + Mi[1][1] * Rpv[c];
+  }
+  *R = std::hypot(Rv[0], Rv[1]);
+  *r = std::hypot(rv[0], rv[1]);
+  *cosg = (rv[0] * Rv[0] + rv[1] * Rv[1]) / (*r * *R);
+  // reactant axes in product coordinates: z_r = R / |R|, x_r = unit part of r normal to R
+  const double zr[2] = {Rv[0] / *R, Rv[1] / *R};
+  const double rz = rv[0] * zr[0] + rv[1] * zr[1];
+  double xr[2] = {rv[0] - rz * zr[0], rv[1] - rz * zr[1]};
+  const double nx = std::hypot(xr[0], xr[1]);
+  if (nx > 0) {
+    xr[0] /= nx;
+    xr[1] /= nx;
+  }
+  // y_r = z_r x x_r = sigma y' ; rho = R_z(a) R_y(beta) R_z(c) with a, c in {0, pi}:
+  // rho_zz = z_r . z' = cos beta, rho_xz = x_r . z' = cos(a) sin(beta),
+  // rho_zx = z_r . x' = -sin(beta) cos(c), rho_yy = sigma = cos(a) cos(c)
+  const int sigma = (zr[1] * xr[0] - zr[0] * xr[1]) >= 0 ? 1 : -1;
+  *beta = std::acos(std::max(-1.0, std::min(1.0, zr[1])));
+  if (std::sin(*beta) > 1e-12) {
+    *sa = xr[1] >= 0 ? 1 : -1;
+    *sc = zr[0] <= 0 ? 1 : -1;
+  } else {
+    *sa = 1;
+    *sc = sigma;
+  }
+}
+
+// Wigner's explicit sum, factorials through lgamma.
+double wigner_small_d(int J, int mp, int m, double beta) {
+  const double c = std::cos(0.5 * beta), s = std::sin(0.5 * beta);
+  auto lf = [](int k) { return std::lgamma(k + 1.0); };
+  const double lpre = 0.5 * (lf(J + mp) + lf(J - mp) + lf(J + m) + lf(J - m));
+  double tot = 0.0;
+  for (int k = std::max(0, m - mp); k <= std::min(J + m, J - mp); ++k) {
+    const int pc = 2 * J + m - mp - 2 * k, ps = mp - m + 2 * k;
+    const double mag = std::exp(lpre - lf(J + m - k) - lf(k) - lf(mp - m + k) - lf(J - mp - k));
+    const double sgn = ((mp - m + k) & 1) ? -1.0 : 1.0;
+    tot += sgn * mag * std::pow(c, pc) * std::pow(s, ps);
+  }
+  return tot;
+}
+
+// Unadapted components: Phi'_m' = sum_m D_(m m')(rho) Phi_m with Phi_(-m) = (-1)^m Phi_m
+// and the adapted block m = 0 scaled by sqrt(2).
+void helicity_transform(int J, int nom, double beta, int sa, int sc, std::vector<double>& T) {
+  auto D = [&](int m1, int m2) {   // D^J_(m1 m2)(rho), real
+    double v = wigner_small_d(J, m1, m2, beta);
+    if (sa < 0 && (m1 & 1)) v = -v;
+    if (sc < 0 && (m2 & 1)) v = -v;
+    return v;
+  };
+  T.assign((size_t)nom * nom, 0.0);
+  for (int op = 0; op < nom; ++op)
+    for (int om = 0; om < nom; ++om) {
+      double v = (om == 0 ? std::sqrt(2.0) : 1.0) * D(om, op);
+      if (om > 0) v += ((om & 1) ? -1.0 : 1.0) * D(-om, op);
+      T[(size_t)op * nom + om] = v / (op == 0 ? std::sqrt(2.0) : 1.0);
+    }
+}
+
 }  // namespace mw3
 
 // --------------------------------------------------------------- LEPS surface

@@ -17,4 +17,22 @@ double dst2(int N, int j, int i);
 void sine_interpolation_weights(double xa, double xb, int N, double x, std::vector<double>& w,
                                 std::vector<double>& dw);
 
+// ------------------------------------------------- product arrangement geometry
+// Product Jacobi vectors as (r', R') = M (r, R). arrangement 1: products AC + B
+// (r' = C - A, R' from the AC centre of mass to B); 2: products AB + C.
+void product_jacobi_matrix(const double masses[3], int arrangement, double M[2][2]);
+// Reduced masses (mu' of R', m' of r') of the product arrangement.
+void product_masses(const double masses[3], int arrangement, double* mu_p, double* m_p);
+// Reactant (R, r, cos gamma) of the product point (R', r', cos gamma') and the signs and
+// angle of the rotation between the body-fixed frames: D^J_(m'm)(rho) =
+// sa^m' d^J_(m'm)(beta) sc^m, rho taking the reactant axes (z along R, r in x > 0) to the
+// product axes (z along R', r' in x > 0).
+void product_point(const double masses[3], int arrangement, double Rp, double rp, double cosgp,
+                   double* R, double* r, double* cosg, double* beta, int* sa, int* sc);
+// Wigner d^J_(m'm)(beta).
+double wigner_small_d(int J, int mp, int m, double beta);
+// Helicity transform of the parity-adapted blocks Omega = 0..nom-1 (parity (-1)^J):
+// T[op * nom + om] with Phi'_op = sum_om T[op][om] Phi_om.
+void helicity_transform(int J, int nom, double beta, int sa, int sc, std::vector<double>& T);
+
 }  // namespace mw3

@@ -61,6 +61,7 @@ struct Tuning {
   int kb;           // Chebyshev iterations per energy-sum flush (ring depth)
   int use_graph;    // capture full chunks as CUDA graphs
   int use_tc;       // tensor-core gamma transform (mixed precision only)
+  int kin_warp;     // warp-register FFT kinetic kernels where the line length allows
 };
 
 // --------------------------------------------------------------- launchers
@@ -68,7 +69,8 @@ struct Tuning {
 template <typename real>
 cudaError_t launch_kinetic_rows(const real* q, real* t, long nrows, const FFTPlan& plan,
                                 const void* tw, const void* ph, const real* lam, int pairs,
-                                const DevBlock* blocks, int ng, int nr, cudaStream_t st);
+                                const DevBlock* blocks, int ng, int nr, int warp_fft,
+                                cudaStream_t st);
 
 template <typename real>
 cudaError_t launch_kinetic_cols(const real* q, real* t, long nplanes, int nr, int NR,
@@ -78,7 +80,7 @@ cudaError_t launch_kinetic_cols(const real* q, real* t, long nplanes, int nr, in
                                 const real* wpsi, const real* wdpsi, real* cut_slot,
                                 const DevBlock* blocks, const int* ncut_J,
                                 // column at R_inf for channel projections
-                                int m_inf, real* qcol, cudaStream_t st);
+                                int m_inf, real* qcol, int warp_fft, cudaStream_t st);
 
 // out[b] = Tmat[omega(b)] in[b] (per block [ng x ng] x [ng x ncol]); Tmat is T (DVR ->
 // FBR) or its transpose (FBR -> DVR), zero-padded to ng x ng.
@@ -117,6 +119,27 @@ cudaError_t launch_sums_flush(const real* ph, const real* cut, long ncut_total, 
                               const long* accoff, long max_cols, double* acc, cudaStream_t st);
 
 cudaError_t launch_advance(long* d_iter, long n, cudaStream_t st);
+
+// Product-channel projection (mw3_products.cu): channels of one (J, Lambda', Omega').
+struct ProdGroup {
+  int b0;        // block index of (J, Omega = 0, Lambda')
+  int bstride;   // block index step per Omega (= nelec)
+  int nom;       // helicities of this J
+  int op;        // Omega'
+  long toff;     // offset of this J's helicity matrices [node][nom][nom]
+  int c0, nc;    // rows [c0, c0 + nc) of the channel weight table
+  int col0;      // cut-ring column of channel c0 (the group's channels are consecutive)
+  int pad;
+};
+
+template <typename real>
+cudaError_t launch_prod_eval(const real* q, const DevBlock* blocks, int nblk, int ng, int nr,
+                             int NR, int nn, const int* idx, const real* w, const real* pl,
+                             int ltop, real* u, cudaStream_t st);
+template <typename real>
+cudaError_t launch_prod_project(const real* u, int nn, const real* T, const real* jac,
+                                const real* W, const ProdGroup* groups, int ngroups,
+                                real* cut_slot, cudaStream_t st);
 
 // Fused tensor-core angular step (mw3_tc.cu), FP32 state, ngamma padded to kp <= 112.
 struct TcArgs {

@@ -310,6 +310,15 @@ bool kinetic_rows_fixed(int N, const T* q, T* t, long nrows, const void* tw, con
                         const T* lam, int P, const DevBlock* blocks, int ng, int nr,
                         cudaStream_t st, cudaError_t* err);
 template <typename T>
+bool kinetic_rows_warp(int N, const T* q, T* t, long nrows, const void* tw, const void* ph,
+                       const T* lam, const DevBlock* blocks, int ng, int nr, cudaStream_t st,
+                       cudaError_t* err);
+template <typename T>
+bool kinetic_cols_warp(int N, const T* q, T* t, long nplanes, int NR, const void* tw,
+                       const void* ph, const T* lam, int C, int ng, const T* wpsi,
+                       const T* wdpsi, T* cut, const DevBlock* blocks, const int* ncut_J,
+                       int m_inf, T* qcol, cudaStream_t st, cudaError_t* err);
+template <typename T>
 bool kinetic_cols_fixed(int N, const T* q, T* t, long nplanes, int NR, const void* tw,
                         const void* ph, const T* lam, int C, int ng, const T* wpsi,
                         const T* wdpsi, T* cut, const DevBlock* blocks, const int* ncut_J,
@@ -318,8 +327,12 @@ bool kinetic_cols_fixed(int N, const T* q, T* t, long nplanes, int NR, const voi
 template <typename real>
 cudaError_t launch_kinetic_rows(const real* q, real* t, long nrows, const FFTPlan& plan,
                                 const void* tw, const void* ph, const real* lam, int pairs,
-                                const DevBlock* blocks, int ng, int nr, cudaStream_t st) {
+                                const DevBlock* blocks, int ng, int nr, int warp_fft,
+                                cudaStream_t st) {
   cudaError_t err = cudaSuccess;
+  if (warp_fft &&
+      kinetic_rows_warp<real>(plan.N, q, t, nrows, tw, ph, lam, blocks, ng, nr, st, &err))
+    return err;
   if (kinetic_rows_fixed<real>(plan.N, q, t, nrows, tw, ph, lam, pairs, blocks, ng, nr, st, &err))
     return err;
   const size_t sm = kinetic_smem<real>(plan.N, pairs);
@@ -344,8 +357,12 @@ cudaError_t launch_kinetic_cols(const real* q, real* t, long nplanes, int nr, in
                                 const FFTPlan& plan, const void* tw, const void* ph,
                                 const real* lam, int ctile, int ng, const real* wpsi,
                                 const real* wdpsi, real* cut_slot, const DevBlock* blocks,
-                                const int* ncut_J, int m_inf, real* qcol, cudaStream_t st) {
+                                const int* ncut_J, int m_inf, real* qcol, int warp_fft,
+                                cudaStream_t st) {
   cudaError_t err = cudaSuccess;
+  if (warp_fft && kinetic_cols_warp<real>(plan.N, q, t, nplanes, NR, tw, ph, lam, ctile, ng, wpsi,
+                                          wdpsi, cut_slot, blocks, ncut_J, m_inf, qcol, st, &err))
+    return err;
   if (kinetic_cols_fixed<real>(plan.N, q, t, nplanes, NR, tw, ph, lam, ctile, ng, wpsi, wdpsi,
                                cut_slot, blocks, ncut_J, m_inf, qcol, st, &err))
     return err;
@@ -368,19 +385,19 @@ cudaError_t launch_kinetic_cols(const real* q, real* t, long nplanes, int nr, in
 
 template cudaError_t launch_kinetic_rows<double>(const double*, double*, long, const FFTPlan&,
                                                  const void*, const void*, const double*, int,
-                                                 const DevBlock*, int, int, cudaStream_t);
+                                                 const DevBlock*, int, int, int, cudaStream_t);
 template cudaError_t launch_kinetic_rows<float>(const float*, float*, long, const FFTPlan&,
                                                 const void*, const void*, const float*, int,
-                                                const DevBlock*, int, int, cudaStream_t);
+                                                const DevBlock*, int, int, int, cudaStream_t);
 template cudaError_t launch_kinetic_cols<double>(const double*, double*, long, int, int,
                                                  const FFTPlan&, const void*, const void*,
                                                  const double*, int, int, const double*,
                                                  const double*, double*, const DevBlock*,
-                                                 const int*, int, double*, cudaStream_t);
+                                                 const int*, int, double*, int, cudaStream_t);
 template cudaError_t launch_kinetic_cols<float>(const float*, float*, long, int, int,
                                                 const FFTPlan&, const void*, const void*,
                                                 const float*, int, int, const float*,
                                                 const float*, float*, const DevBlock*,
-                                                const int*, int, float*, cudaStream_t);
+                                                const int*, int, float*, int, cudaStream_t);
 
 }  // namespace mw3

@@ -1,0 +1,527 @@
+// Warp-level radial kinetic kernels for line lengths N = R * 32 (R = 1, 2, 3, 4, 6, 8, 12, 16).
+//
+// Same operator as mw3_kinetic.cu (DST-II kinetic of the sine DVR through a length-N
+// complex FFT carrying two real lines), but each line pair is transformed by one warp
+// entirely in registers: lane t holds elements n = t + 32 s (s < R); a forward FFT is
+//   (1) an R-point DFT over s in registers, (2) twiddles w_N^(t k2), (3) a 32-point DFT
+//   across the lanes by decimation in frequency with __shfl_xor_sync butterflies,
+// leaving X[k2 + R bitrev5(t)] in lane t, slot k2; the inverse runs the three steps
+// backwards (decimation in time across lanes first). No block-wide barrier is taken
+// inside a transform. Tiles are staged through shared memory so that global loads and
+// stores stay coalesced (row tiles for R, [nr x C] column tiles for r).
+#include <cuda_runtime.h>
+
+#include "mw3_internal.h"
+
+namespace mw3 {
+namespace {
+
+__device__ constexpr double kCos48[48] = {1.00000000000000000000,0.99144486137381038215,0.96592582628906831221,0.92387953251128673848,0.86602540378443870761,0.79335334029123516508,0.70710678118654757274,0.60876142900872065589,0.50000000000000011102,0.38268343236508983729,0.25881904510252073948,0.13052619222005171218,0.00000000000000006123,-0.13052619222005160116,-0.25881904510252062845,-0.38268343236508950422,-0.49999999999999977796,-0.60876142900872065589,-0.70710678118654746172,-0.79335334029123505406,-0.86602540378443870761,-0.92387953251128673848,-0.96592582628906820119,-0.99144486137381038215,-1.00000000000000000000,-0.99144486137381038215,-0.96592582628906831221,-0.92387953251128684951,-0.86602540378443881863,-0.79335334029123516508,-0.70710678118654790580,-0.60876142900872087793,-0.50000000000000044409,-0.38268343236508950422,-0.25881904510252062845,-0.13052619222005162891,-0.00000000000000018370,0.13052619222005126809,0.25881904510252029539,0.38268343236508917116,0.50000000000000011102,0.60876142900871987873,0.70710678118654735069,0.79335334029123494304,0.86602540378443837454,0.92387953251128684951,0.96592582628906809017,0.99144486137381038215};
+__device__ constexpr double kSin48[48] = {0.00000000000000000000,0.13052619222005157340,0.25881904510252073948,0.38268343236508978178,0.49999999999999994449,0.60876142900872065589,0.70710678118654746172,0.79335334029123516508,0.86602540378443859659,0.92387953251128673848,0.96592582628906831221,0.99144486137381038215,1.00000000000000000000,0.99144486137381038215,0.96592582628906831221,0.92387953251128684951,0.86602540378443870761,0.79335334029123516508,0.70710678118654757274,0.60876142900872087793,0.49999999999999994449,0.38268343236508989280,0.25881904510252101703,0.13052619222005198973,0.00000000000000012246,-0.13052619222005176769,-0.25881904510252079499,-0.38268343236508967076,-0.49999999999999972244,-0.60876142900872065589,-0.70710678118654712865,-0.79335334029123494304,-0.86602540378443837454,-0.92387953251128684951,-0.96592582628906831221,-0.99144486137381038215,-1.00000000000000000000,-0.99144486137381049318,-0.96592582628906842324,-0.92387953251128696053,-0.86602540378443859659,-0.79335334029123572019,-0.70710678118654768376,-0.60876142900872087793,-0.50000000000000044409,-0.38268343236508955973,-0.25881904510252157214,-0.13052619222005168442};
+
+template <typename T>
+__device__ __forceinline__ cpx<T> cm(cpx<T> a, cpx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> cmc(cpx<T> a, cpx<T> b) {  // a * conj(b)
+  return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> ca(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> cs(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+
+// exp(sign 2 pi i e / R), e in [0, R), R dividing 48
+template <typename T, int R>
+__device__ __forceinline__ cpx<T> wR(int e, T sign) {
+  const int m = (e % R) * (48 / R);
+  return {(T)kCos48[m], sign * (T)kSin48[m]};
+}
+
+template <typename T>
+__device__ __forceinline__ void d2(cpx<T>* v) {
+  cpx<T> a = v[0];
+  v[0] = ca(a, v[1]);
+  v[1] = cs(a, v[1]);
+}
+template <typename T>
+__device__ __forceinline__ void d3(cpx<T>* v, T sign) {
+  const T h = (T)0.86602540378443864676;
+  cpx<T> a = v[0], t1 = ca(v[1], v[2]);
+  cpx<T> t2 = {a.x - (T)0.5 * t1.x, a.y - (T)0.5 * t1.y};
+  cpx<T> d = cs(v[1], v[2]);
+  cpx<T> t3 = {-d.y * h * sign, d.x * h * sign};
+  v[0] = ca(a, t1);
+  v[1] = ca(t2, t3);
+  v[2] = cs(t2, t3);
+}
+template <typename T>
+__device__ __forceinline__ void d4(cpx<T>* v, T sign) {
+  cpx<T> s0 = ca(v[0], v[2]), s1 = cs(v[0], v[2]), s2 = ca(v[1], v[3]), e = cs(v[1], v[3]);
+  cpx<T> s3 = {-e.y * sign, e.x * sign};
+  v[0] = ca(s0, s2);
+  v[1] = ca(s1, s3);
+  v[2] = cs(s0, s2);
+  v[3] = cs(s1, s3);
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void dftR(cpx<T>* v, T sign);
+
+// R = R1 R2: X[k1 + R1 k2] = sum_n2 w_R^(n2 k1) w_R2^(n2 k2) sum_n1 v[R2 n1 + n2] w_R1^(n1 k1)
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void dft_composite(cpx<T>* v, T sign) {
+  constexpr int R = R1 * R2;
+  cpx<T> y[R];
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    cpx<T> u[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) u[n1] = v[R2 * n1 + n2];
+    dftR<T, R1>(u, sign);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1)
+      y[n2 * R1 + k1] = (n2 * k1 == 0) ? u[k1] : cm(u[k1], wR<T, R>(n2 * k1, sign));
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    cpx<T> z[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) z[n2] = y[n2 * R1 + k1];
+    dftR<T, R2>(z, sign);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = z[k2];
+  }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void dftR(cpx<T>* v, T sign) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    d2(v);
+  } else if constexpr (R == 3) {
+    d3(v, sign);
+  } else if constexpr (R == 4) {
+    d4(v, sign);
+  } else if constexpr (R == 6) {
+    dft_composite<T, 2, 3>(v, sign);
+  } else if constexpr (R == 8) {
+    dft_composite<T, 2, 4>(v, sign);
+  } else if constexpr (R == 12) {
+    dft_composite<T, 4, 3>(v, sign);
+  } else {
+    dft_composite<T, 4, 4>(v, sign);  // 16
+  }
+}
+
+__device__ __forceinline__ int bitrev5(int t) { return (int)(__brev((unsigned)t) >> 27); }
+
+template <typename T>
+__device__ __forceinline__ cpx<T> shfl_xor(cpx<T> v, int d) {
+  return {__shfl_xor_sync(0xffffffffu, v.x, d), __shfl_xor_sync(0xffffffffu, v.y, d)};
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> shfl_from(cpx<T> v, int src) {
+  return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
+}
+
+// Per-CTA shared tables laid out so that the 32 lanes of a warp read 32 consecutive
+// entries (no bank conflicts): for slot k2 and lane t, w = exp(-2 pi i / N),
+//   twk[k2][t] = w^(t k2)                           twiddles between the DFT levels
+//   tws[i][t]  = w^((t mod d) N / 2d) on lanes with bit d set, 1 elsewhere (d = 16 >> i)
+//   fk[k2][k1], sk[k2][k1]   spectral scale of index k = k2 + R k1 (see wscale)
+template <typename T, int R>
+struct WTables {
+  cpx<T> twk[R][32];
+  cpx<T> tws[5][32];
+  cpx<T> fk[R][32];
+  T sk[R][32];
+};
+
+template <typename T, int R>
+__device__ __forceinline__ void load_tables(WTables<T, R>& tb, const cpx<T>* __restrict__ twg,
+                                            const cpx<T>* __restrict__ phg,
+                                            const T* __restrict__ lamg) {
+  constexpr int N = 32 * R;
+  for (int e = threadIdx.x; e < R * 32; e += blockDim.x) {
+    const int k2 = e >> 5, t = e & 31;
+    tb.twk[k2][t] = twg[t * k2];
+    // sigma_k = (lambda_(N-k) + lambda_k) / 2, f_k = (lambda_(N-k) - lambda_k) / 2 exp(i pi k / N),
+    // exp(i pi k / N) = conj(ph_k)^2 with ph_k = exp(-i pi k / 2N)
+    const int k = k2 + R * t;
+    const T lr = lamg[N - k], li = lamg[k];
+    const cpx<T> e1 = phg[k];
+    const cpx<T> e2 = {e1.x * e1.x - e1.y * e1.y, -(T)2 * e1.x * e1.y};
+    const T dl = (T)0.5 * (lr - li);
+    tb.sk[k2][t] = (T)0.5 * (lr + li);
+    tb.fk[k2][t] = cpx<T>{dl * e2.x, dl * e2.y};
+  }
+  for (int e = threadIdx.x; e < 5 * 32; e += blockDim.x) {
+    const int i = e >> 5, t = e & 31, d = 16 >> i;
+    tb.tws[i][t] = (t & d) ? twg[(t & (d - 1)) * (N / (2 * d))] : cpx<T>{(T)1, (T)0};
+  }
+}
+
+// Forward FFT of the distributed sequence (lane t, slot s) = z[t + 32 s];
+// out: lane t, slot k2 = Z[k2 + R bitrev5(t)]. Cross-lane decimation in frequency:
+// the lane without bit d keeps v + p, the lane with it (p - v) w; both as (p + s v) w
+// with s = -1 on the lane with bit d and w = 1 on the other.
+template <typename T, int R>
+__device__ __forceinline__ void wfft_fwd(cpx<T>* v, int t, const WTables<T, R>& tb) {
+  dftR<T, R>(v, (T)-1);
+#pragma unroll
+  for (int k2 = 1; k2 < R; ++k2) v[k2] = cm(v[k2], tb.twk[k2][t]);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int d = 16 >> i;
+    const T sg = (t & d) ? (T)-1 : (T)1;
+    const cpx<T> w = tb.tws[i][t];
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) {
+      const cpx<T> p = shfl_xor(v[k2], d);
+      const cpx<T> r = {p.x + sg * v[k2].x, p.y + sg * v[k2].y};
+      v[k2] = (d > 1) ? cm(r, w) : r;   // w = 1 in the last stage
+    }
+  }
+}
+
+// Unnormalised inverse of wfft_fwd: in lane t, slot k2 = W[k2 + R bitrev5(t)];
+// out lane t, slot s = N * IDFT(W)[t + 32 s]. Cross-lane decimation in time: the lane
+// with bit d first multiplies by conj(w); then both take p + s v.
+template <typename T, int R>
+__device__ __forceinline__ void wfft_inv(cpx<T>* v, int t, const WTables<T, R>& tb) {
+#pragma unroll
+  for (int i = 4; i >= 0; --i) {
+    const int d = 16 >> i;
+    const T sg = (t & d) ? (T)-1 : (T)1;
+    const cpx<T> w = tb.tws[i][t];
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) {
+      const cpx<T> u = (d > 1) ? cmc(v[k2], w) : v[k2];
+      const cpx<T> p = shfl_xor(u, d);
+      v[k2] = {p.x + sg * u.x, p.y + sg * u.y};
+    }
+  }
+#pragma unroll
+  for (int k2 = 1; k2 < R; ++k2) v[k2] = cmc(v[k2], tb.twk[k2][t]);
+  dftR<T, R>(v, (T)1);
+}
+
+// Spectral scaling between the transforms. For the pair spectrum Z (two real lines
+// a + i b), the DST-kinetic of mw3_kinetic.cu (split Z into the line spectra, twiddle
+// by exp(-i pi k / 2N), scale real and imaginary parts by lambda_(N-k) and lambda_k,
+// twiddle back, recombine) reduces to
+//   W_k = sigma_k Z_k + f_k Z_(N-k),  sigma_k = (lambda_(N-k) + lambda_k) / 2,
+//   f_k = (lambda_(N-k) - lambda_k) / 2 exp(i pi k / N).
+template <typename T, int R>
+__device__ __forceinline__ void wscale(cpx<T>* v, int t, const WTables<T, R>& tb) {
+  const int k1 = bitrev5(t);
+  cpx<T> o[R];
+#pragma unroll
+  for (int k2 = 0; k2 < R; ++k2) {
+    // partner index N - k: slot (R - k2) % R, k1' = k2 ? 31 - k1 : (32 - k1) % 32
+    const int k1p = k2 ? 31 - k1 : ((32 - k1) & 31);
+    o[k2] = shfl_from(v[(R - k2) % R], bitrev5(k1p));
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < R; ++k2) {
+    const T sgm = tb.sk[k2][k1];
+    const cpx<T> f = tb.fk[k2][k1];
+    const cpx<T> fz = cm(f, o[k2]);
+    v[k2] = {sgm * v[k2].x + fz.x, sgm * v[k2].y + fz.y};
+  }
+}
+
+__device__ __forceinline__ int iperm(int n, int N) { return n < N / 2 ? 2 * n : 2 * (N - 1 - n) + 1; }
+
+// One line pair through forward FFT, spectral scale and inverse FFT. Element i of
+// line a sits at xa[i * stride], of line b at xb[i * stride]; the result
+// overwrites them (sign (-1)^i and the permutation of the DST-via-FFT on both
+// sides).
+template <typename T, int R>
+__device__ __forceinline__ void pair_kinetic(T* xa, T* xb, int stride, int lane,
+                                             const WTables<T, R>& tb) {
+  constexpr int N = 32 * R;
+  cpx<T> v[R];
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int i = iperm(lane + 32 * s, N);
+    const T sg = (i & 1) ? (T)-1 : (T)1;
+    v[s] = {sg * xa[i * stride], sg * xb[i * stride]};
+  }
+  wfft_fwd<T, R>(v, lane, tb);
+  wscale<T, R>(v, lane, tb);
+  wfft_inv<T, R>(v, lane, tb);
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int i = iperm(lane + 32 * s, N);
+    const T sg = (i & 1) ? (T)-1 : (T)1;
+    xa[i * stride] = sg * v[s].x;
+    xb[i * stride] = sg * v[s].y;
+  }
+}
+
+// Resident CTAs per SM asked of the register allocator (8 warps each).
+template <typename T, int R>
+constexpr int kMinBlocks = (sizeof(T) == 4 && R <= 8) ? 4 : (R <= 4 ? 3 : 1);
+
+// 16-byte vector of T (float4 / double2).
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+
+// R direction: CTA of 8 warps = 16 consecutive rows of length N (8 pairs), moved
+// between global and shared memory with 16-byte vector accesses.
+template <typename T, int R>
+__global__ void __launch_bounds__(256, kMinBlocks<T, R>) k_rows_w(const T* __restrict__ q, T* __restrict__ t,
+                                                long nrows, const cpx<T>* __restrict__ twg,
+                                                const cpx<T>* __restrict__ phg,
+                                                const T* __restrict__ lamg,
+                                                const DevBlock* __restrict__ blocks, int ng,
+                                                int nr) {
+  constexpr int N = 32 * R;
+  constexpr int ROWS = 16;
+  using V = typename Vec16<T>::type;
+  constexpr int VE = 16 / sizeof(T);          // elements per vector
+  __shared__ WTables<T, R> tb;
+  __shared__ __align__(16) T tile[ROWS * N];
+  __shared__ int live[ROWS];
+  const long row0 = (long)blockIdx.x * ROWS;
+  if (threadIdx.x < ROWS) {
+    const long row = row0 + threadIdx.x;
+    const long plane = row / nr;
+    live[threadIdx.x] = row < nrows && (int)(plane % ng) < blocks[plane / ng].nrow;
+  }
+  load_tables<T, R>(tb, twg, phg, lamg);
+  const long nvalid = min((long)ROWS, nrows - row0) * N / VE;   // whole rows: N % VE == 0
+  const V* qv = reinterpret_cast<const V*>(q + row0 * N);
+  V* sv = reinterpret_cast<V*>(tile);
+  constexpr int NV = ROWS * N / VE;                             // vectors per CTA
+  constexpr int PER = (NV + 255) / 256;
+  {
+    V z[PER];                                                   // all loads in flight first
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      z[u] = (e < NV && e < nvalid) ? qv[e] : V{};
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      if (e < NV) sv[e] = z[u];
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // a pair never straddles planes (nr is even), so one flag covers both rows
+  if (live[2 * warp]) pair_kinetic<T, R>(tile + 2 * warp * N, tile + (2 * warp + 1) * N, 1, lane, tb);
+  __syncthreads();
+  V* tv = reinterpret_cast<V*>(t + row0 * N);
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int e = threadIdx.x + 256 * u;
+    if (e < NV && e < nvalid && live[(e * VE) / N]) tv[e] = sv[e];
+  }
+}
+
+// r direction: one CTA = one (block, gamma) plane, columns [c0, c0 + C); N = nr.
+template <typename T, int R, int C>
+__global__ void __launch_bounds__(256, kMinBlocks<T, R>) k_cols_w(
+    const T* __restrict__ q, T* __restrict__ t, int NR, const cpx<T>* __restrict__ twg,
+    const cpx<T>* __restrict__ phg, const T* __restrict__ lamg, int ng,
+    const T* __restrict__ wpsi, const T* __restrict__ wdpsi, T* __restrict__ cut,
+    const DevBlock* __restrict__ blocks, const int* __restrict__ ncut_J, int m_inf,
+    T* __restrict__ qcol) {
+  constexpr int N = 32 * R;
+  constexpr int LD = C + 1;
+  constexpr int NOUT = 2 * C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WTables<T, R>& tb = *reinterpret_cast<WTables<T, R>*>(smem_raw);
+  T* tile = reinterpret_cast<T*>(smem_raw + sizeof(WTables<T, R>));   // [N][C + 1]
+  T* part = tile + N * LD;                                            // [4][2C]
+  const long plane = blockIdx.y;
+  const int b = (int)(plane / ng);
+  const int n = (int)(plane - (long)b * ng);
+  if (n >= blocks[b].nrow) return;
+  load_tables<T, R>(tb, twg, phg, lamg);
+  const int c0 = blockIdx.x * C;
+  const T* qp = q + plane * (long)N * NR;
+  T* tp = t + plane * (long)N * NR;
+  constexpr int PER = (N * C + 255) / 256;
+  constexpr int CH = PER < 8 ? PER : 8;                         // loads in flight per thread
+  for (int u0 = 0; u0 < PER; u0 += CH) {
+    T z[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int e = threadIdx.x + 256 * (u0 + u);
+      const int kr = e / C, m = c0 + e % C;
+      z[u] = (e < N * C && m < NR) ? qp[(long)kr * NR + m] : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int e = threadIdx.x + 256 * (u0 + u);
+      if (e < N * C) tile[(e / C) * LD + e % C] = z[u];
+    }
+  }
+  __syncthreads();
+  if (cut != nullptr) {
+    constexpr int SEG = (N + 3) / 4;
+    for (int o = threadIdx.x; o < 4 * NOUT; o += blockDim.x) {
+      const int seg = o / NOUT, oc = o % NOUT, c = oc >> 1;
+      const T* w = (oc & 1) ? wdpsi : wpsi;
+      T s = 0;
+      const int k0 = seg * SEG, k1 = min(N, k0 + SEG);
+      for (int kr = k0; kr < k1; ++kr) s += w[kr] * tile[kr * LD + c];
+      part[seg * NOUT + oc] = s;
+    }
+  }
+  if (qcol != nullptr && m_inf >= c0 && m_inf < c0 + C) {
+    for (int kr = threadIdx.x; kr < N; kr += blockDim.x) qcol[plane * N + kr] = tile[kr * LD + (m_inf - c0)];
+  }
+  __syncthreads();
+  if (cut != nullptr) {
+    const DevBlock B = blocks[b];
+    const long ncut = ncut_J[B.iJ];
+    for (int oc = threadIdx.x; oc < NOUT; oc += blockDim.x) {
+      const int m = c0 + (oc >> 1);
+      if (m >= NR) continue;
+      const T s = ((part[oc] + part[NOUT + oc]) + part[2 * NOUT + oc]) + part[3 * NOUT + oc];
+      cut[B.cutcol + (long)(oc & 1) * ncut + (long)n * NR + m] = s;
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int p = warp; p < C / 2; p += blockDim.x / 32)
+    pair_kinetic<T, R>(tile + 2 * p, tile + 2 * p + 1, LD, lane, tb);
+  __syncthreads();
+  for (int u0 = 0; u0 < PER; u0 += CH) {
+    T z[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int e = threadIdx.x + 256 * (u0 + u);
+      const int kr = e / C, m = c0 + e % C;
+      z[u] = (e < N * C && m < NR) ? tp[(long)kr * NR + m] : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int e = threadIdx.x + 256 * (u0 + u);
+      const int kr = e / C, m = c0 + e % C;
+      if (e < N * C && m < NR) tp[(long)kr * NR + m] = z[u] + tile[kr * LD + e % C];
+    }
+  }
+}
+
+
+// FP64 lines stop at R = 8: beyond that a thread's registers would spill.
+template <typename T, int R>
+constexpr bool kWarpSupported = sizeof(T) == 4 || R <= 8;
+
+template <typename T, int R>
+bool rows_w(const T* q, T* t, long nrows, const void* tw, const void* ph, const T* lam,
+            const DevBlock* blocks, int ng, int nr, cudaStream_t st, cudaError_t* err) {
+  if constexpr (!kWarpSupported<T, R>) {
+    return false;
+  } else {
+    const unsigned grid = (unsigned)((nrows + 15) / 16);
+    k_rows_w<T, R><<<grid, 256, 0, st>>>(q, t, nrows, static_cast<const cpx<T>*>(tw),
+                                         static_cast<const cpx<T>*>(ph), lam, blocks, ng, nr);
+    *err = cudaGetLastError();
+    return true;
+  }
+}
+
+template <typename T, int R, int C>
+bool cols_wc(const T* q, T* t, long nplanes, int NR, const void* tw, const void* ph,
+             const T* lam, int ng, const T* wpsi, const T* wdpsi, T* cut,
+             const DevBlock* blocks, const int* ncut_J, int m_inf, T* qcol, cudaStream_t st,
+             cudaError_t* err) {
+  constexpr int N = 32 * R;
+  const size_t sm = sizeof(WTables<T, R>) + sizeof(T) * ((size_t)N * (C + 1) + 8 * (size_t)C);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cols_w<T, R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr = true;
+  }
+  dim3 grid((unsigned)((NR + C - 1) / C), (unsigned)nplanes);
+  k_cols_w<T, R, C><<<grid, 256, sm, st>>>(q, t, NR, static_cast<const cpx<T>*>(tw),
+                                           static_cast<const cpx<T>*>(ph), lam, ng, wpsi, wdpsi,
+                                           cut, blocks, ncut_J, m_inf, qcol);
+  *err = cudaGetLastError();
+  return true;
+}
+
+template <typename T, int R>
+bool cols_w(const T* q, T* t, long nplanes, int NR, const void* tw, const void* ph,
+            const T* lam, int C, int ng, const T* wpsi, const T* wdpsi, T* cut,
+            const DevBlock* blocks, const int* ncut_J, int m_inf, T* qcol, cudaStream_t st,
+            cudaError_t* err) {
+  if constexpr (!kWarpSupported<T, R>) {
+    return false;
+  } else {
+    switch (C) {
+#define CC(c)                                                                                 \
+  case c:                                                                                     \
+    return cols_wc<T, R, c>(q, t, nplanes, NR, tw, ph, lam, ng, wpsi, wdpsi, cut, blocks,     \
+                            ncut_J, m_inf, qcol, st, err);
+      CC(8) CC(16) CC(32)
+#undef CC
+      default: return false;   // other column tiles: the shared-memory FFT kernels
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+bool kinetic_rows_warp(int N, const T* q, T* t, long nrows, const void* tw, const void* ph,
+                       const T* lam, const DevBlock* blocks, int ng, int nr, cudaStream_t st,
+                       cudaError_t* err) {
+  switch (N) {
+#define CASE(R) \
+  case 32 * R: return rows_w<T, R>(q, t, nrows, tw, ph, lam, blocks, ng, nr, st, err);
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(6) CASE(8) CASE(12) CASE(16)
+#undef CASE
+    default: return false;
+  }
+}
+
+template <typename T>
+bool kinetic_cols_warp(int N, const T* q, T* t, long nplanes, int NR, const void* tw,
+                       const void* ph, const T* lam, int C, int ng, const T* wpsi,
+                       const T* wdpsi, T* cut, const DevBlock* blocks, const int* ncut_J,
+                       int m_inf, T* qcol, cudaStream_t st, cudaError_t* err) {
+  switch (N) {
+#define CASE(R)                                                                              \
+  case 32 * R:                                                                               \
+    return cols_w<T, R>(q, t, nplanes, NR, tw, ph, lam, C, ng, wpsi, wdpsi, cut, blocks,     \
+                        ncut_J, m_inf, qcol, st, err);
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(6) CASE(8) CASE(12) CASE(16)
+#undef CASE
+    default: return false;
+  }
+}
+
+template bool kinetic_rows_warp<float>(int, const float*, float*, long, const void*, const void*,
+                                       const float*, const DevBlock*, int, int, cudaStream_t,
+                                       cudaError_t*);
+template bool kinetic_rows_warp<double>(int, const double*, double*, long, const void*,
+                                        const void*, const double*, const DevBlock*, int, int,
+                                        cudaStream_t, cudaError_t*);
+template bool kinetic_cols_warp<float>(int, const float*, float*, long, int, const void*,
+                                       const void*, const float*, int, int, const float*,
+                                       const float*, float*, const DevBlock*, const int*, int,
+                                       float*, cudaStream_t, cudaError_t*);
+template bool kinetic_cols_warp<double>(int, const double*, double*, long, int, const void*,
+                                        const void*, const double*, int, int, const double*,
+                                        const double*, double*, const DevBlock*, const int*, int,
+                                        double*, cudaStream_t, cudaError_t*);
+
+}  // namespace mw3

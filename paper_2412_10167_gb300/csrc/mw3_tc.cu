@@ -99,6 +99,16 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
   for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Copy a padded kp x kp FP32 matrix pair (hi, lo), row-major, into core-matrix layout.
 __device__ void load_b(const float* __restrict__ hi, const float* __restrict__ lo,
                        unsigned char* Bhi, unsigned char* Blo, int kp) {
@@ -149,9 +159,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
   const int q = warp & 3;          // TMEM lane quarter
   const int half = warp >> 2;      // which quarter of the N columns this warp reads
   const int m = q * 32 + lane;     // tile row = grid column within the tile
-  const long col = (long)blockIdx.x * TC_M + m;
+  // grid (group, tile): the helicity groups of one tile run side by side, so the
+  // Coriolis neighbours' tiles (Omega +- 1) are read from L2
+  const int g = blockIdx.x;
+  const int tile = blockIdx.y;
+  const long col = (long)tile * TC_M + m;
   const bool live = col < a.ncol;
-  const int g = blockIdx.y;
   const int b0 = g * NE;
   const DevBlock B0 = a.blocks[b0];
   const int om = B0.omega;
@@ -192,7 +205,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
       const int e = tid + it * TC_THREADS;
       const int i4 = (e / TC_M) * 4;
       const int mm = e - (e / TC_M) * TC_M;
-      const long cc = (long)blockIdx.x * TC_M + mm;
+      const long cc = (long)tile * TC_M + mm;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         x[it][u] = (e < nq && cc < a.ncol && i4 + u < nrow) ? __ldg(c + (long)(i4 + u) * a.ncol + cc) : 0.0f;
@@ -283,10 +296,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
     const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
     const float frk = live ? a.fr[kr] : 0.0f;
     const float fRm = live ? a.fR[mR] : 0.0f;
+    float* ts = reinterpret_cast<float*>(Ahi);              // [kp][TC_M] t tile
+    float* ps = reinterpret_cast<float*>(Ahi) + kp * TC_M;  // [kp][TC_M] c_(k-1) tile
+    const long col0 = (long)tile * TC_M;
     for (int L = 0; L < NE; ++L) {
       const int b = b0 + L;
       const DevBlock Bb = a.blocks[b];
       const float* c = a.ck + (long)b * a.npts;
+      // one round trip: 16-byte asynchronous copies of this block's t and c_(k-1)
+      // rows [0, nrow) x [col0, col0 + 128) (ncol is a multiple of 4, so a 4-float chunk
+      // is entirely inside or outside the grid)
+      __syncthreads();
+      {
+        const int nch = nrow * (TC_M / 4);
+        for (int e = tid; e < nch; e += TC_THREADS) {
+          const int i = e / (TC_M / 4);
+          const int c4 = (e - i * (TC_M / 4)) * 4;
+          if (col0 + c4 >= a.ncol) continue;
+          const long go = (long)b * a.npts + (long)i * a.ncol + col0 + c4;
+          cp_async16(ts + i * TC_M + c4, a.t + go);
+          if (a.mode == 0) cp_async16(ps + i * TC_M + c4, a.ckm1 + go);
+        }
+        cp_async_wait_all();
+      }
+      __syncthreads();
       for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 4) {
         float w[4];
         tmem_ld4(tmem + lane_base + (uint32_t)((NE + L) * kp + i0), w);
@@ -299,8 +332,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
           const bool in = i < nrow;
           const long off = (long)i * a.ncol + col;
           cv[s] = in ? __ldg(c + off) : 0.0f;
-          tv[s] = in ? __ldg(a.t + (long)b * a.npts + off) : 0.0f;
-          pv[s] = (in && a.mode == 0) ? a.ckm1[(long)b * a.npts + off] : 0.0f;
+          tv[s] = in ? ts[i * TC_M + m] : 0.0f;
+          pv[s] = (in && a.mode == 0) ? ps[i * TC_M + m] : 0.0f;
           cu[s] = (in && Bb.up >= 0 && i >= 1) ? __ldg(a.ck + (long)Bb.up * a.npts + off - a.ncol) : 0.0f;
           cd[s] = (in && Bb.dn >= 0) ? __ldg(a.ck + (long)Bb.dn * a.npts + off + a.ncol) : 0.0f;
         }
@@ -338,7 +371,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
   if (tid == 0) {
     double s = 0;
     for (int w2 = 0; w2 < TC_THREADS / 32; ++w2) s += red[w2];
-    if (a.npart) a.npart[(long)g * a.ntiles + blockIdx.x] = s;
+    if (a.npart) a.npart[(long)g * a.ntiles + tile] = s;
     if (!ok) atomicExch(a.err, 1);
   }
   if (warp == 0) {
@@ -391,7 +424,8 @@ static cudaError_t launch_tc_ne(const TcArgs& a, dim3 grid, cudaStream_t st) {
 
 cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
                               double* norm_out, cudaStream_t st) {
-  dim3 grid((unsigned)args.ntiles, (unsigned)ngroups);
+  if (args.ntiles > 65535) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)ngroups, (unsigned)args.ntiles);
   cudaError_t e = (args.nelec == 1) ? launch_tc_ne<1>(args, grid, st)
                                     : launch_tc_ne<2>(args, grid, st);
   if (e != cudaSuccess) return e;

@@ -46,6 +46,15 @@ class mw3_analysis_desc(C.Structure):
                 ("kmin", C.c_long)]
 
 
+class mw3_products_desc(C.Structure):
+    _fields_ = [("arrangement", C.c_int), ("Rinf", C.c_double), ("nr", C.c_int),
+                ("rmin", C.c_double), ("rmax", C.c_double), ("ngamma", C.c_int),
+                ("vmax", C.c_int), ("jmax", C.c_int)]
+
+
+ARRANGEMENTS = {"AC+B": 1, "AB+C": 2}
+
+
 class mw3_leps_params(C.Structure):
     _fields_ = [("D", C.c_double), ("beta", C.c_double), ("re", C.c_double),
                 ("delta", C.c_double), ("masses", C.c_double * 3), ("two_state", C.c_int),
@@ -78,6 +87,8 @@ _SIGS = {
     "mw3_set_absorber": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_double,
                                    C.c_double, C.c_int]),
     "mw3_set_analysis": (C.c_int, [C.c_void_p, C.POINTER(mw3_analysis_desc)]),
+    "mw3_set_products": (C.c_int, [C.c_void_p, C.POINTER(mw3_products_desc)]),
+    "mw3_product_probabilities": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mw3_propagate": (C.c_int, [C.c_void_p, C.c_long]),
     "mw3_iteration": (C.c_long, [C.c_void_p]),
     "mw3_flux_probabilities": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
@@ -290,6 +301,11 @@ class Propagator:
 
     def set_analysis(self):
         an = self.cfg["analysis"]
+        pd = an.get("products")
+        if pd:
+            d = mw3_products_desc(ARRANGEMENTS[pd["arrangement"]], pd["Rinf"], pd["nr"], pd["rmin"],
+                                  pd["rmax"], pd["ngamma"], pd["vmax"], pd["jmax"])
+            _check(self.ctx, lib.mw3_set_products(self.ctx, C.byref(d)))
         mw3_set_analysis(self.ctx, an["rstar"], an["E_lo_eV"] / HARTREE_EV,
                          an["E_hi_eV"] / HARTREE_EV, an["nE"], an["Rinf"], an.get("vmax", -1),
                          an.get("jmax", 0), an.get("kmin", 0))
@@ -349,6 +365,14 @@ class Propagator:
         _check(self.ctx, lib.mw3_flux_probabilities(self.ctx, _dp(E), _dp(P),
                                                     None if Pin is None else _dp(Pin)))
         return E, P, Pin
+
+    def product_probabilities(self):
+        """|S|^2 of the product channels summed over Omega': [nJ, nelec, v', j', nE]."""
+        pd = self.cfg["analysis"]["products"]
+        P = np.zeros((len(self.cfg["J"]), self.cfg["nelec"], pd["vmax"] + 1, pd["jmax"] + 1,
+                      self.cfg["analysis"]["nE"]))
+        _check(self.ctx, lib.mw3_product_probabilities(self.ctx, _dp(P)))
+        return P
 
     def norm_trace(self, n=None):
         nJ = len(self.cfg["J"])

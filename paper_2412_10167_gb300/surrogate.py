@@ -128,7 +128,7 @@ def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 400, width: int = 
     Plin = linear_baseline(np.asarray(J_train), Ptr, np.asarray(J_test))
     err = np.abs(Psur - Pte)
     bad_J = [J for t, J in enumerate(J_test) if err[t].max() > fallback_dP]
-    final = Psur.copy()
+    final = Psur.astype(np.float64)
     for t, J in enumerate(J_test):
         if J in bad_J:
             final[t] = Pte[t]

@@ -2,6 +2,7 @@
 
 For a workload's grid shape and precision it times short propagations through the
 library's own per-kernel CUDA-event timers (mw3_kernel_times) over a sweep of
+  kin_warp    warp-register FFT kinetic kernels (1) or the shared-memory ones (0),
   rows_pairs  line pairs per CTA of the R-direction kinetic kernel,
   cols_tile   R columns per CTA of the r-direction kinetic kernel,
   kb          iterations per energy-sum flush (ring depth),
@@ -20,8 +21,10 @@ from . import mw3
 DEFAULT_CACHE = os.environ.get("MW3_TUNE_CACHE",
                                os.path.join(os.path.expanduser("~"), ".cache", "mw3_tuning.json"))
 
-SWEEP = dict(rows_pairs=[2, 4, 8, 16], cols_tile=[8, 16, 32, 64], kb=[32, 64, 128])
-CONTROLS = dict(rows_pairs=["kinetic_rows"], cols_tile=["kinetic_cols"], kb=["sums_flush"])
+SWEEP = dict(kin_warp=[1, 0], rows_pairs=[2, 4, 8, 16], cols_tile=[8, 16, 32, 64],
+             kb=[32, 64, 128])
+CONTROLS = dict(kin_warp=["kinetic_rows", "kinetic_cols"], rows_pairs=["kinetic_rows"],
+                cols_tile=["kinetic_cols"], kb=["sums_flush"])
 
 
 def shape_key(cfg: dict, precision: str) -> str:
@@ -71,7 +74,9 @@ def tune(cfg: dict, precision: str = "mixed", steps: int = 0, device: int = 0,
         for v in values:
             setting = dict(best)
             setting[knob] = v
-            n = steps or (2 * v if knob == "kb" else 8)
+            # a flush costs the same however much of the ring is filled, so the
+            # ring-depth sweep always runs whole rings
+            n = max(steps, 2 * v) if knob == "kb" else (steps or 8)
             try:
                 ms = _time_setting(cfg, precision, setting, n, device)
             except mw3.MW3Error:

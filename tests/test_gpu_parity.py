@@ -65,6 +65,32 @@ def test_apply_hs_matches_oracle(name, prec):
     pr.close()
 
 
+# Line lengths 32 R for the warp-register FFT kinetic kernels (R up to 8 in FP64,
+# up to 16 in the mixed path); NR = 72 leaves a ragged column tile in the r kernel.
+WARP_CASES = {
+    "w64x96": W.shrunk(W.C2, "w64x96", NR=64, nr=96, ngamma=8, J=[2], omega_max=2, nE=8),
+    "w128x192": W.shrunk(W.C2, "w128x192", NR=128, nr=192, ngamma=6, J=[1], omega_max=1, nE=8),
+    "w256x32": W.shrunk(W.C2, "w256x32", NR=256, nr=32, ngamma=6, J=[1], omega_max=1, nE=8),
+    "w72x256": W.shrunk(W.C2, "w72x256", NR=72, nr=256, ngamma=5, J=[0], omega_max=0, nE=8),
+    "w384x512": W.shrunk(W.C2, "w384x512", NR=384, nr=512, ngamma=4, J=[1], omega_max=1, nE=8),
+}
+
+
+@pytest.mark.parametrize("name", list(WARP_CASES))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("warp", [1, 0])
+def test_warp_fft_kinetic_matches_oracle(name, prec, warp):
+    cfg = WARP_CASES[name]
+    pr = mw3().Propagator(cfg, precision=prec, tuning={"kin_warp": warp})
+    H = GridHamiltonian(cfg)
+    q = H.project(W.random_state(H.shape, 77))
+    ref = H.apply_Hs(q)
+    got = pr.apply_hs(q)
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+    pr.close()
+
+
 @pytest.mark.parametrize("name", list(W.SMALL))
 def test_propagation_fp64_parity(name):
     cfg = W.SMALL[name]
@@ -87,6 +113,30 @@ def test_propagation_fp64_parity(name):
     bj = ref["H"].block_J_index()
     assert tr.shape == (N, len(cfg["J"]))
     np.testing.assert_allclose(tr.sum(axis=1), ref["norms"][1:], rtol=1e-10)
+    pr.close()
+
+
+@pytest.mark.parametrize("name", ["c2s", "c3s", "c4s"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_product_channels_match_oracle(name, prec):
+    """Product-channel probabilities (Eq. S-matrix-from-chebyshev) from a random first
+    iterate that already overlaps the product surface: FP64 to 1e-9 of the largest
+    value (summation order only), the mixed path to 1e-3 of it (FP32 state and sums
+    within a flush block)."""
+    cfg = W.SMALL[name]
+    H = GridHamiltonian(cfg)
+    q0 = H.project(W.random_unit_state(H.shape, 31))
+    N = 12
+    ref = P.propagate(cfg, nsteps=N, H=H, q0=q0)
+    pr = mw3().Propagator(cfg, precision=prec)
+    pr.set_state(q0)
+    pr.propagate(N)
+    got = pr.product_probabilities()
+    scale = max(np.max(np.abs(v)) for v in ref["P_prod"].values())
+    assert scale > 0
+    tol = 1e-9 if prec == "fp64" else 1e-3
+    for (iJ, L, v, j), val in ref["P_prod"].items():
+        assert np.max(np.abs(got[iJ, L, v, j] - val)) <= tol * scale, (iJ, L, v, j)
     pr.close()
 
 
@@ -242,7 +292,7 @@ def test_autotuner_picks_and_caches(tmp_path):
     cfg = W.C2_SMALL
     path = str(tmp_path / "tune.json")
     best = tune.tune(cfg, "mixed", steps=4, cache_path=path)
-    assert set(best) == {"rows_pairs", "cols_tile", "kb"}
+    assert set(best) == set(tune.SWEEP)
     assert tune.tune(cfg, "mixed", cache_path=path) == best          # cached
     a = mw3().Propagator(cfg, precision="mixed", tuning=best)
     b = mw3().Propagator(cfg, precision="mixed")
