@@ -83,7 +83,8 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0, 1};
+  Tuning tune{4, 32, 32, 1, 0, 1, 1};
+  int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   bool tc_ok = false;  // the tensor-core angular step supports this grid
   int tc_user = -1;    // explicit "use_tc" setting (-1: default = on when supported)
@@ -144,6 +145,9 @@ struct mw3_ctx {
   std::vector<double> prod_jac;            // [node] r'R'/(rR)
   std::vector<double> prod_W;              // [channel][node] quadrature weights
   std::vector<ProdGroup> prod_groups;      // col0 set by mw3_set_analysis
+  std::vector<int> prod_jl;                // [iJ * nelec + L]: its Omega' = 0 group
+  std::vector<int> prod_chan;              // [channel][2]: group, cut column
+  int prod_max_nom = 0;
   std::vector<long> prod_first;            // nJ + 1: first channel of each J
   std::vector<int> pch_L, pch_v, pch_j, pch_op;
   std::vector<double> pch_eps;
@@ -438,6 +442,7 @@ int mw3_create(mw3_ctx** out, int device, int precision) {
   } else {
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
       g_create_err = std::string("CUDA device ") + std::to_string(device) + ": " + cudaGetErrorString(e);
       delete ctx;
@@ -686,8 +691,9 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
   // tensor-core operands: T^Omega and its transpose, padded to kp x kp, split into a
   // TF32-rounded high part and the exact FP32 remainder
   ctx->kp = ((ng + 15) / 16) * 16;
+  // (16-byte asynchronous copies of tile rows need ncol % 4 == 0)
   ctx->tc_ok = (ctx->precision == MW3_MIXED) && ctx->kp <= kTcMaxKp &&
-               (ctx->ncol + 127) / 128 <= 65535;
+               (ctx->ncol + 127) / 128 <= 65535 && ctx->ncol % 4 == 0;
   ctx->tune.use_tc = (ctx->tc_ok && ctx->tc_user != 0) ? 1 : 0;
   if (ctx->tc_ok) {
     const int kp = ctx->kp;
@@ -987,14 +993,19 @@ int mw3_set_products(mw3_ctx* ctx, const mw3_products_desc* d) {
   ctx->pch_op.clear();
   ctx->pch_eps.clear();
   ctx->prod_first.assign(ctx->nJ + 1, 0);
+  ctx->prod_jl.assign((size_t)ctx->nJ * ne, 0);
+  ctx->prod_max_nom = 0;
   long nch = 0;
   for (int iJ = 0; iJ < ctx->nJ; ++iJ) {
     ctx->prod_first[iJ] = nch;
     const int nom = ctx->omtop[iJ] + 1;
-    for (int L = 0; L < ne; ++L)
-      for (int op = 0; op < nom && op <= d->jmax; ++op) {
+    if (nom > 32) return ctx->fail(MW3_ERR_BAD_ARG, "product channels support at most 32 helicities");
+    ctx->prod_max_nom = std::max(ctx->prod_max_nom, nom);
+    for (int L = 0; L < ne; ++L) {
+      ctx->prod_jl[(size_t)iJ * ne + L] = (int)ctx->prod_groups.size();
+      for (int op = 0; op < nom; ++op) {
         std::vector<double> Pp;
-        norm_assoc_legendre(d->jmax, op, xg, Pp);
+        if (op <= d->jmax) norm_assoc_legendre(d->jmax, op, xg, Pp);   // (no channels above jmax)
         ProdGroup g{};
         g.b0 = (int)ctx->J_first_block[iJ] + L;
         g.bstride = ne;
@@ -1019,6 +1030,7 @@ int mw3_set_products(mw3_ctx* ctx, const mw3_products_desc* d) {
         g.nc = (int)(nch - g.c0);
         ctx->prod_groups.push_back(g);
       }
+    }
   }
   ctx->prod_first[ctx->nJ] = nch;
   ctx->prod_nn = nn;
@@ -1146,11 +1158,21 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
       return st;
   }
   if (ctx->prod_on) {
+    ctx->prod_chan.assign(2 * (size_t)ctx->prod_first[ctx->nJ], 0);
+    for (size_t gi = 0; gi < ctx->prod_groups.size(); ++gi) {
+      const ProdGroup& g = ctx->prod_groups[gi];
+      for (int c = 0; c < g.nc; ++c) {
+        ctx->prod_chan[2 * (size_t)(g.c0 + c)] = (int)gi;
+        ctx->prod_chan[2 * (size_t)(g.c0 + c) + 1] = g.col0 + c;
+      }
+    }
+    if ((st = upload_raw(ctx, "p_jl", ctx->prod_jl)) || (st = upload_raw(ctx, "p_chan", ctx->prod_chan)))
+      return st;
     if ((st = upload_raw(ctx, "p_idx", ctx->prod_idx)) || (st = upload_real(ctx, "p_w", ctx->prod_w)) ||
         (st = upload_real(ctx, "p_pl", ctx->prod_pl)) || (st = upload_real(ctx, "p_T", ctx->prod_T)) ||
         (st = upload_real(ctx, "p_jac", ctx->prod_jac)) || (st = upload_real(ctx, "p_W", ctx->prod_W)) ||
         (st = upload_raw(ctx, "p_groups", ctx->prod_groups)) ||
-        (st = dalloc(ctx, "p_u", (size_t)ctx->nblk * ctx->prod_nn * ctx->rs())))
+        (st = dalloc(ctx, "p_v", ctx->prod_groups.size() * (size_t)ctx->prod_nn * ctx->rs())))
       return st;
   }
   if ((st = dalloc(ctx, "d_iter", 8))) return st;
@@ -1328,9 +1350,12 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
     a.nelec = ctx->nelec;
     a.mode = mode;
     a.ntiles = (int)((ctx->ncol + 127) / 128);
+    a.ngroups = ctx->nblk / ctx->nelec;
+    a.persistent = ctx->tune.tc_persist && angular_tc2_supported(ctx->kp, ctx->nelec);
+    a.nsm = ctx->nsm;
     int tc = 32;
     while (tc < 2 * ctx->nelec * ctx->kp) tc *= 2;
-    a.tmem_cols = tc;
+    a.tmem_cols = a.persistent ? 512 : tc;
     LK(launch_angular_tc(a, ctx->nblk / ctx->nelec, (const int*)dptr(ctx, "g_begin"), ctx->nJ,
                          mode == 0 ? B.normbuf + (long)slot * ctx->nJ : nullptr, st));
     tm.stop();
@@ -1357,14 +1382,14 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
   }
   if (analysis && ctx->prod_on) {
     Timer tm(ctx, 8, timed);
-    real* pu = (real*)dptr(ctx, "p_u");
-    LK(launch_prod_eval<real>(qk, B.blocks, ctx->nblk, ctx->ng, ctx->nr, ctx->NR, ctx->prod_nn,
-                              (const int*)dptr(ctx, "p_idx"), (const real*)dptr(ctx, "p_w"),
-                              (const real*)dptr(ctx, "p_pl"), ctx->prod_ltop, pu, st));
-    LK(launch_prod_project<real>(pu, ctx->prod_nn, (const real*)dptr(ctx, "p_T"),
-                                 (const real*)dptr(ctx, "p_jac"), (const real*)dptr(ctx, "p_W"),
-                                 (const ProdGroup*)dptr(ctx, "p_groups"),
-                                 (int)ctx->prod_groups.size(), cut_slot, st));
+    LK(launch_products<real>(qk, ctx->ng, ctx->nr, ctx->NR, ctx->prod_nn,
+                             (const int*)dptr(ctx, "p_idx"), (const real*)dptr(ctx, "p_w"),
+                             (const real*)dptr(ctx, "p_pl"), ctx->prod_ltop,
+                             (const real*)dptr(ctx, "p_T"), (const real*)dptr(ctx, "p_jac"),
+                             (const ProdGroup*)dptr(ctx, "p_groups"), (const int*)dptr(ctx, "p_jl"),
+                             (int)ctx->prod_jl.size(), ctx->prod_max_nom, (real*)dptr(ctx, "p_v"),
+                             (const real*)dptr(ctx, "p_W"), (const int2*)dptr(ctx, "p_chan"),
+                             (int)ctx->prod_first[ctx->nJ], cut_slot, st));
     tm.stop();
   }
   if (!tc) {
@@ -1683,6 +1708,8 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
     ctx->tune.use_graph = v != 0;
   } else if (k == "kin_warp") {
     ctx->tune.kin_warp = v != 0;
+  } else if (k == "tc_persist") {
+    ctx->tune.tc_persist = v != 0;
   } else if (k == "use_tc") {
     if (v != 0 && ctx->precision != MW3_MIXED)
       return ctx->fail(MW3_ERR_BAD_ARG, "use_tc needs MW3_MIXED");
@@ -1703,6 +1730,7 @@ long mw3_get_tuning(const mw3_ctx* ctx, const char* key) {
   if (k == "cols_tile") return ctx->tune.cols_tile;
   if (k == "use_graph") return ctx->tune.use_graph;
   if (k == "kin_warp") return ctx->tune.kin_warp;
+  if (k == "tc_persist") return ctx->tune.tc_persist;
   if (k == "use_tc") return ctx->stage >= 2 ? ctx->tune.use_tc : (ctx->tc_user != 0);
   return MW3_ERR_BAD_ARG;
 }

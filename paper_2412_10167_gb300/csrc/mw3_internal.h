@@ -62,6 +62,7 @@ struct Tuning {
   int use_graph;    // capture full chunks as CUDA graphs
   int use_tc;       // tensor-core gamma transform (mixed precision only)
   int kin_warp;     // warp-register FFT kinetic kernels where the line length allows
+  int tc_persist;   // persistent tensor-core angular step (operands in tensor memory)
 };
 
 // --------------------------------------------------------------- launchers
@@ -132,14 +133,14 @@ struct ProdGroup {
   int pad;
 };
 
+// jl_group[iJ * nelec + L] = index of the Omega' = 0 group of (J, Lambda'); chan[c] =
+// (group, cut column) of product channel c; vbuf holds [groups][nn].
 template <typename real>
-cudaError_t launch_prod_eval(const real* q, const DevBlock* blocks, int nblk, int ng, int nr,
-                             int NR, int nn, const int* idx, const real* w, const real* pl,
-                             int ltop, real* u, cudaStream_t st);
-template <typename real>
-cudaError_t launch_prod_project(const real* u, int nn, const real* T, const real* jac,
-                                const real* W, const ProdGroup* groups, int ngroups,
-                                real* cut_slot, cudaStream_t st);
+cudaError_t launch_products(const real* q, int ng, int nr, int NR, int nn, const int* idx,
+                            const real* w, const real* pl, int ltop, const real* T,
+                            const real* jac, const ProdGroup* groups, const int* jl_group,
+                            int njl, int max_nom, real* vbuf, const real* W, const int2* chan,
+                            int nchan, real* cut_slot, cudaStream_t st);
 
 // Fused tensor-core angular step (mw3_tc.cu), FP32 state, ngamma padded to kp <= 112.
 struct TcArgs {
@@ -164,7 +165,11 @@ struct TcArgs {
   float erot, alpha, beta;
   long ncol, npts;
   int ng, kp, NR, nelec, mode, ntiles, tmem_cols;
+  int ngroups;          // (J, Omega) groups
+  int persistent;       // 1: one CTA per SM over a range of (group, tile) pairs
+  int nsm;              // CTAs of the persistent form
 };
+bool angular_tc2_supported(int kp, int nelec);
 size_t angular_tc_smem(int kp);
 cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
                               double* norm_out, cudaStream_t st);

@@ -2,17 +2,14 @@
 // Eq. Chebyshev-products-overlaps), per Chebyshev iteration, into the cut ring.
 //
 // Two launches per step:
-//   k_prod_eval     u[b][v] = sum_(a,c) wR_a wr_c sum_i P-bar_(Omega_b + i)^(Omega_b)(cos gamma_v)
-//                             c^b_i(r_(k_c), R_(m_a))
-//                   the reactant function of block b at product node v (4-point Lagrange
-//                   stencils in R and r, Legendre series in gamma; 1/sqrt(dR dr) folded
-//                   into wR). One warp per (node, block), lanes over the 16 stencil
-//                   points and two interleaved halves of the FBR rows.
-//   k_prod_project  per (J, Lambda', Omega') group: the rotated, Jacobian-weighted node
-//                   values v'[v] = jac_v sum_Omega T_v[Omega'][Omega] u[b(J, Omega, Lambda')][v]
-//                   in shared memory, then one warp per channel dots them with the
-//                   channel's quadrature weights W[c][v] and writes the overlap into its
-//                   cut-ring column.
+//   k_prod_nodes  u_Omega = sum_(a,c) wR_a wr_c sum_i P-bar_(Omega + i)^Omega(cos gamma_v)
+//                           c^(J,Omega,Lambda')_i(r_(k_c), R_(m_a))
+//                 the reactant function of every helicity block of (J, Lambda') at product
+//                 node v (4-point Lagrange stencils in R and r, Legendre series in gamma;
+//                 1/sqrt(dR dr) folded into wR), then the rotated, Jacobian-weighted node
+//                 values v'[Omega'][v] = jac_v sum_Omega T_v[Omega'][Omega] u_Omega.
+//   k_prod_dots   one warp per channel dots v'[Omega'(c)] with the channel's quadrature
+//                 weights W[c][v] and writes the overlap into its cut-ring column.
 #include <cuda_runtime.h>
 
 #include "mw3_internal.h"
@@ -27,92 +24,105 @@ __device__ __forceinline__ real warp_sum(real s) {
   return s;
 }
 
-// Lane l of the warp of node v takes stencil point (a, c) = (l & 3, (l >> 2) & 3) of the
-// rows i = l >> 4, l >> 4 + 2, ...: one load instruction covers two rows of the 4 x 4
-// stencil (8 short segments of 4 consecutive R values).
+// One CTA per (node v, J, Lambda'): warp w evaluates the reactant function of the block
+// (J, Omega = w, Lambda') at the node. Lane l takes stencil point (a, c) =
+// (l & 3, (l >> 2) & 3) of the rows i = l >> 4, l >> 4 + 2, ...: one load instruction
+// covers two rows of the 4 x 4 stencil (8 short segments of 4 consecutive R values).
+// Then thread Omega' of the CTA rotates the helicities at the node:
+//   v[g(J, Lambda', Omega')][v] = jac_v sum_Omega T_v[Omega'][Omega] u_Omega.
 template <typename real>
-__global__ void __launch_bounds__(256) k_prod_eval(const real* __restrict__ q,
-                                                   const DevBlock* __restrict__ blocks, int ng,
-                                                   int nr, int NR, int nn,
-                                                   const int* __restrict__ idx,
-                                                   const real* __restrict__ w,
-                                                   const real* __restrict__ pl, int ltop,
-                                                   real* __restrict__ u) {
+__global__ void __launch_bounds__(1024) k_prod_nodes(const real* __restrict__ q, int ng, int nr,
+                                                     int NR, int nn,
+                                                     const int* __restrict__ idx,
+                                                     const real* __restrict__ w,
+                                                     const real* __restrict__ pl, int ltop,
+                                                     const real* __restrict__ T,
+                                                     const real* __restrict__ jac,
+                                                     const ProdGroup* __restrict__ groups,
+                                                     const int* __restrict__ jl_group,
+                                                     real* __restrict__ vout) {
+  __shared__ real us[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int v = blockIdx.x * 8 + warp;
-  const int b = blockIdx.y;
-  if (v >= nn) return;   // warp-uniform; the kernel has no block-wide barrier
-  const DevBlock B = blocks[b];
-  const int a = lane & 3, c = (lane >> 2) & 3, sub = lane >> 4;
-  const long plane = (long)nr * NR;
-  const real* src = q + (long)b * ng * plane + (long)idx[v * 8 + 4 + c] * NR + idx[v * 8 + a];
-  const real* P = pl + ((long)v * ltop + B.omega) * ng;
-  real s = 0;
-  for (int i = sub; i < B.nrow; i += 2) s += P[i] * src[(long)i * plane];
-  s *= w[v * 8 + a] * w[v * 8 + 4 + c];
-  s = warp_sum(s);
-  if (lane == 0) u[(long)b * nn + v] = s;
-}
-
-template <typename real>
-__global__ void __launch_bounds__(256) k_prod_project(const real* __restrict__ u, int nn,
-                                                      const real* __restrict__ T,
-                                                      const real* __restrict__ jac,
-                                                      const real* __restrict__ W,
-                                                      const ProdGroup* __restrict__ groups,
-                                                      real* __restrict__ cut) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  real* vp = reinterpret_cast<real*>(smem_raw);
-  const ProdGroup g = groups[blockIdx.x];
-  for (int n = threadIdx.x; n < nn; n += blockDim.x) {
-    const real* Tn = T + g.toff + ((long)n * g.nom + g.op) * g.nom;
-    real s = 0;
-    for (int om = 0; om < g.nom; ++om) s += Tn[om] * u[(long)(g.b0 + om * g.bstride) * nn + n];
-    vp[n] = jac[n] * s;
+  const int v = blockIdx.x;
+  const int g0 = jl_group[blockIdx.y];
+  const ProdGroup G = groups[g0];          // Omega' = 0 group of this (J, Lambda')
+  const int nom = G.nom;
+  if (warp < nom) {
+    const int b = G.b0 + warp * G.bstride;
+    const int a = lane & 3, c = (lane >> 2) & 3, sub = lane >> 4;
+    const long plane = (long)nr * NR;
+    const real* src = q + (long)b * ng * plane + (long)idx[v * 8 + 4 + c] * NR + idx[v * 8 + a];
+    const real* P = pl + ((long)v * ltop + warp) * ng;
+    const int nrow = ng - warp;            // angular functions of helicity Omega = warp
+    real s0 = 0, s1 = 0, s2 = 0, s3 = 0;   // four independent chains: loads in flight
+    int i = sub;
+    for (; i + 6 < nrow; i += 8) {
+      s0 += P[i] * src[(long)i * plane];
+      s1 += P[i + 2] * src[(long)(i + 2) * plane];
+      s2 += P[i + 4] * src[(long)(i + 4) * plane];
+      s3 += P[i + 6] * src[(long)(i + 6) * plane];
+    }
+    for (; i < nrow; i += 2) s0 += P[i] * src[(long)i * plane];
+    real s = (s0 + s1) + (s2 + s3);
+    s *= w[v * 8 + a] * w[v * 8 + 4 + c];
+    s = warp_sum(s);
+    if (lane == 0) us[warp] = s;
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int c = warp; c < g.nc; c += blockDim.x / 32) {
-    const real* Wc = W + (long)(g.c0 + c) * nn;
+  const int op = threadIdx.x;
+  if (op < nom && groups[g0 + op].op == op) {
+    const real* Tv = T + G.toff + ((long)v * nom + op) * nom;
     real s = 0;
-    for (int n = lane; n < nn; n += 32) s += Wc[n] * vp[n];
-    s = warp_sum(s);
-    if (lane == 0) cut[g.col0 + c] = s;
+    for (int om = 0; om < nom; ++om) s += Tv[om] * us[om];
+    vout[(long)(g0 + op) * nn + v] = jac[v] * s;
   }
+}
+
+// One warp per channel: C_c = sum_v W[c][v] v'[group(c)][v], written to its cut column.
+template <typename real>
+__global__ void __launch_bounds__(256) k_prod_dots(const real* __restrict__ vin, int nn,
+                                                   const real* __restrict__ W,
+                                                   const int2* __restrict__ chan, int nchan,
+                                                   real* __restrict__ cut) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + warp;
+  if (c >= nchan) return;
+  const int2 gc = chan[c];   // (group, cut column)
+  const real* Wc = W + (long)c * nn;
+  const real* vg = vin + (long)gc.x * nn;
+  real s = 0;
+  for (int n = lane; n < nn; n += 32) s += Wc[n] * vg[n];
+  s = warp_sum(s);
+  if (lane == 0) cut[gc.y] = s;
 }
 
 }  // namespace
 
 template <typename real>
-cudaError_t launch_prod_eval(const real* q, const DevBlock* blocks, int nblk, int ng, int nr,
-                             int NR, int nn, const int* idx, const real* w, const real* pl,
-                             int ltop, real* u, cudaStream_t st) {
-  dim3 grid((unsigned)((nn + 7) / 8), (unsigned)nblk);
-  k_prod_eval<real><<<grid, 256, 0, st>>>(q, blocks, ng, nr, NR, nn, idx, w, pl, ltop, u);
+cudaError_t launch_products(const real* q, int ng, int nr, int NR, int nn, const int* idx,
+                            const real* w, const real* pl, int ltop, const real* T,
+                            const real* jac, const ProdGroup* groups, const int* jl_group,
+                            int njl, int max_nom, real* vbuf, const real* W, const int2* chan,
+                            int nchan, real* cut_slot, cudaStream_t st) {
+  if (nchan == 0) return cudaSuccess;
+  dim3 g1((unsigned)nn, (unsigned)njl);
+  k_prod_nodes<real><<<g1, 32 * max_nom, 0, st>>>(q, ng, nr, NR, nn, idx, w, pl, ltop, T, jac,
+                                                  groups, jl_group, vbuf);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_prod_dots<real><<<(nchan + 7) / 8, 256, 0, st>>>(vbuf, nn, W, chan, nchan, cut_slot);
   return cudaGetLastError();
 }
 
-template <typename real>
-cudaError_t launch_prod_project(const real* u, int nn, const real* T, const real* jac,
-                                const real* W, const ProdGroup* groups, int ngroups,
-                                real* cut_slot, cudaStream_t st) {
-  if (ngroups == 0) return cudaSuccess;
-  k_prod_project<real><<<ngroups, 256, sizeof(real) * (size_t)nn, st>>>(u, nn, T, jac, W, groups,
-                                                                         cut_slot);
-  return cudaGetLastError();
-}
-
-template cudaError_t launch_prod_eval<float>(const float*, const DevBlock*, int, int, int, int,
-                                             int, const int*, const float*, const float*, int,
-                                             float*, cudaStream_t);
-template cudaError_t launch_prod_eval<double>(const double*, const DevBlock*, int, int, int, int,
-                                              int, const int*, const double*, const double*, int,
-                                              double*, cudaStream_t);
-template cudaError_t launch_prod_project<float>(const float*, int, const float*, const float*,
-                                                const float*, const ProdGroup*, int, float*,
-                                                cudaStream_t);
-template cudaError_t launch_prod_project<double>(const double*, int, const double*,
-                                                 const double*, const double*, const ProdGroup*,
-                                                 int, double*, cudaStream_t);
+template cudaError_t launch_products<float>(const float*, int, int, int, int, const int*,
+                                            const float*, const float*, int, const float*,
+                                            const float*, const ProdGroup*, const int*, int, int,
+                                            float*, const float*, const int2*, int, float*,
+                                            cudaStream_t);
+template cudaError_t launch_products<double>(const double*, int, int, int, int, const int*,
+                                             const double*, const double*, int, const double*,
+                                             const double*, const ProdGroup*, const int*, int,
+                                             int, double*, const double*, const int2*, int,
+                                             double*, cudaStream_t);
 
 }  // namespace mw3

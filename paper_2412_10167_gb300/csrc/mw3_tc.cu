@@ -19,6 +19,7 @@
 // tcgen05.commit; every wait is bounded and reports through an error word.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "mw3_internal.h"
@@ -109,6 +110,25 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+               "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3]))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// D (+)= A B with A (M x K, K-major) read from tensor memory
+__device__ __forceinline__ void mma_tf32_ta(uint32_t dtmem, uint32_t atmem, uint64_t bd,
+                                            uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(dtmem),
+      "r"(atmem), "l"(bd), "r"(idesc), "r"(accum));
+}
+
 // Copy a padded kp x kp FP32 matrix pair (hi, lo), row-major, into core-matrix layout.
 __device__ void load_b(const float* __restrict__ hi, const float* __restrict__ lo,
                        unsigned char* Bhi, unsigned char* Blo, int kp) {
@@ -135,6 +155,21 @@ __device__ void issue_split_gemm(uint32_t dtmem, const unsigned char* Ahi, const
     mma_tf32(dtmem, smem_desc(ah + o, lbo, sbo), smem_desc(bh + o, lbo, sbo), idesc, ks > 0);
     mma_tf32(dtmem, smem_desc(ah + o, lbo, sbo), smem_desc(bl + o, lbo, sbo), idesc, 1);
     mma_tf32(dtmem, smem_desc(al + o, lbo, sbo), smem_desc(bh + o, lbo, sbo), idesc, 1);
+  }
+}
+
+// As issue_split_gemm, with A (hi, lo) in tensor-memory columns [ahi, ahi + kp) and
+// [alo, alo + kp): one K-step of 8 TF32 values is 8 columns.
+__device__ void issue_split_gemm_ta(uint32_t dtmem, uint32_t ahi, uint32_t alo,
+                                    const unsigned char* Bhi, const unsigned char* Blo, int kp,
+                                    uint32_t idesc) {
+  const uint32_t sbo = (uint32_t)kp * 32, lbo = 128;
+  const uint32_t bh = smem_u32(Bhi), bl = smem_u32(Blo);
+  for (int ks = 0; ks < kp / 8; ++ks) {
+    const uint32_t o = (uint32_t)ks * 256, ta = (uint32_t)ks * 8;
+    mma_tf32_ta(dtmem, ahi + ta, smem_desc(bh + o, lbo, sbo), idesc, ks > 0);
+    mma_tf32_ta(dtmem, ahi + ta, smem_desc(bl + o, lbo, sbo), idesc, 1);
+    mma_tf32_ta(dtmem, alo + ta, smem_desc(bh + o, lbo, sbo), idesc, 1);
   }
 }
 
@@ -381,6 +416,267 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
   }
 }
 
+
+// ===================================================================== persistent form
+// One CTA per SM walks a contiguous range of the (group, tile) list, group-major, so
+// it keeps T^Omega and its transpose (hi and lo parts) resident in shared memory
+// until the helicity changes; the data operand of both GEMMs goes to tensor memory
+// with tcgen05.st (no shared-memory staging, no operand reload per tile). Sibling
+// CTAs sit ntiles / (tiles per CTA) apart in the list, so the helicity groups of one
+// tile are processed at about the same time and the Coriolis neighbours come from L2.
+// Tensor-memory columns: A hi [0, kp), A lo [kp, 2kp), u_L at (2 + L) kp; w_0 at
+// (2 + NE) kp when NE = 2 (else it reuses u_0), w_1 reuses u_0.
+template <int KP>
+constexpr size_t tc2_bbytes() { return (size_t)KP * KP * 4; }
+template <int KP>
+constexpr bool tc2_stage_t() { return 4 * tc2_bbytes<KP>() + (size_t)KP * TC_M * 4 + 1024 <= 227 * 1024; }
+template <int KP>
+constexpr size_t tc2_smem() {
+  return 4 * tc2_bbytes<KP>() + (tc2_stage_t<KP>() ? (size_t)KP * TC_M * 4 : 0) + 16 +
+         16 * sizeof(double) + 64;
+}
+
+template <int KP, int NE>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc2(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  constexpr int kp = KP;
+  constexpr size_t bbytes = tc2_bbytes<KP>();
+  constexpr bool stage_t = tc2_stage_t<KP>();
+  unsigned char* B1hi = sm;              // (T^Omega)^T: GEMM 1
+  unsigned char* B1lo = B1hi + bbytes;
+  unsigned char* B2hi = B1lo + bbytes;   // T^Omega: GEMM 2
+  unsigned char* B2lo = B2hi + bbytes;
+  float* ts = reinterpret_cast<float*>(B2lo + bbytes);                 // [kp][TC_M] t tile
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(ts + (stage_t ? kp * TC_M : 0));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  double* red = reinterpret_cast<double*>(mbar + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3;
+  const int half = warp >> 2;
+  const int m = q * 32 + lane;
+  constexpr int ncb = kp / 4;
+  const uint32_t mb = smem_u32(mbar);
+  const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+  const uint32_t idesc = idesc_tf32(TC_M, kp);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(a.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const uint32_t tA_hi = tmem, tA_lo = tmem + kp;
+  auto t_u = [&](int L) { return tmem + (uint32_t)((2 + L) * kp); };
+  auto t_w = [&](int L) {
+    return (NE == 1) ? tmem + (uint32_t)(2 * kp)
+                     : (L == 0 ? tmem + (uint32_t)((2 + NE) * kp) : tmem + (uint32_t)(2 * kp));
+  };
+  uint32_t phase = 0;
+  bool ok = true;
+  int om_cur = -1;
+
+  const long total = (long)a.ngroups * a.ntiles;
+  const long f0 = (long)blockIdx.x * total / gridDim.x;
+  const long f1 = (long)(blockIdx.x + 1) * total / gridDim.x;
+  for (long f = f0; f < f1 && ok; ++f) {
+    const int g = (int)(f / a.ntiles);
+    const int tile = (int)(f - (long)g * a.ntiles);
+    const int b0 = g * NE;
+    const DevBlock B0 = a.blocks[b0];
+    const int om = B0.omega;
+    const int nrow = B0.nrow;
+    const long col0 = (long)tile * TC_M;
+    const long col = col0 + m;
+    const bool live = col < a.ncol;
+    const int kr = live ? (int)(col / a.NR) : 0;
+    const int mR = live ? (int)(col - (long)kr * a.NR) : 0;
+
+    __syncthreads();   // every thread is done with the shared buffers of the last tile
+    if (om != om_cur) {
+      load_b(a.Tt_hi + (long)om * kp * kp, a.Tt_lo + (long)om * kp * kp, B1hi, B1lo, kp);
+      load_b(a.T_hi + (long)om * kp * kp, a.T_lo + (long)om * kp * kp, B2hi, B2lo, kp);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      om_cur = om;
+    }
+    // t rows of state 0 into shared memory while the GEMMs run
+    if (stage_t) {
+      const int nch = nrow * (TC_M / 4);
+      for (int e = tid; e < nch; e += TC_THREADS) {
+        const int i = e / (TC_M / 4);
+        const int c4 = (e - i * (TC_M / 4)) * 4;
+        if (col0 + c4 >= a.ncol) continue;
+        cp_async16(ts + i * TC_M + c4, a.t + (long)b0 * a.npts + (long)i * a.ncol + col0 + c4);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+
+    // ------------------------------------------------------------ GEMM 1 per state
+    for (int L = 0; L < NE && ok; ++L) {
+      const float* c = a.ck + (long)(b0 + L) * a.npts;
+      float x[ncb];
+#pragma unroll
+      for (int s2 = 0; s2 < ncb; ++s2) {
+        const int i = half * ncb + s2;
+        x[s2] = (live && i < nrow) ? __ldg(c + (long)i * a.ncol + col) : 0.0f;
+      }
+#pragma unroll
+      for (int s0 = 0; s0 < ncb; s0 += 4) {
+        float h[4], l[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          h[s] = tf32_hi(x[s0 + s]);
+          l[s] = x[s0 + s] - h[s];
+        }
+        tmem_st4(tA_hi + lane_base + (uint32_t)(half * ncb + s0), h);
+        tmem_st4(tA_lo + lane_base + (uint32_t)(half * ncb + s0), l);
+      }
+      tmem_st_wait();
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        issue_split_gemm_ta(t_u(L), tA_hi, tA_lo, B1hi, B1lo, kp, idesc);
+        mma_commit(mb);
+      }
+      ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
+      phase ^= 1;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+
+    // ------------------------------------------------------------ potential + GEMM 2
+    for (int L = 0; L < NE && ok; ++L) {
+      float vv[NE][ncb];
+#pragma unroll
+      for (int Lp = 0; Lp < NE; ++Lp) {
+        const float* V = a.V + (long)(L * NE + Lp) * a.npts;
+#pragma unroll
+        for (int s2 = 0; s2 < ncb; ++s2) {
+          const int n = half * ncb + s2;
+          vv[Lp][s2] = (live && n < a.ng) ? __ldg(V + (long)n * a.ncol + col) : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int s0 = 0; s0 < ncb; s0 += 4) {
+        float vu[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int Lp = 0; Lp < NE; ++Lp) {
+          float u[4];
+          tmem_ld4(t_u(Lp) + lane_base + (uint32_t)(half * ncb + s0), u);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) vu[s] += vv[Lp][s0 + s] * u[s];
+        }
+        float h[4], l[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          h[s] = tf32_hi(vu[s]);
+          l[s] = vu[s] - h[s];
+        }
+        tmem_st4(tA_hi + lane_base + (uint32_t)(half * ncb + s0), h);
+        tmem_st4(tA_lo + lane_base + (uint32_t)(half * ncb + s0), l);
+      }
+      tmem_st_wait();
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        issue_split_gemm_ta(t_w(L), tA_hi, tA_lo, B2hi, B2lo, kp, idesc);
+        mma_commit(mb);
+      }
+      ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
+      phase ^= 1;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    if (stage_t) {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncthreads();
+    }
+
+    // ------------------------------------------------------------ epilogue
+    double ss = 0.0;
+    if (ok) {
+      const DevJ J = a.dj[B0.iJ];
+      const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
+      const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
+      const float frk = live ? a.fr[kr] : 0.0f;
+      const float fRm = live ? a.fR[mR] : 0.0f;
+      for (int L = 0; L < NE; ++L) {
+        const int b = b0 + L;
+        const DevBlock Bb = a.blocks[b];
+        const float* c = a.ck + (long)b * a.npts;
+        const bool tsm = stage_t && L == 0;
+        for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 4) {
+          float w[4];
+          tmem_ld4(t_w(L) + lane_base + (uint32_t)i0, w);
+          if (!live) continue;
+          float cv[4], cu[4], cd[4], tv[4], pv[4];
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int i = i0 + s;
+            const bool in = i < nrow;
+            const long off = (long)i * a.ncol + col;
+            cv[s] = in ? __ldg(c + off) : 0.0f;
+            tv[s] = in ? (tsm ? ts[i * TC_M + m] : __ldg(a.t + (long)b * a.npts + off)) : 0.0f;
+            pv[s] = (in && a.mode == 0) ? __ldg(a.ckm1 + (long)b * a.npts + off) : 0.0f;
+            cu[s] = (in && Bb.up >= 0 && i >= 1) ? __ldg(a.ck + (long)Bb.up * a.npts + off - a.ncol) : 0.0f;
+            cd[s] = (in && Bb.dn >= 0) ? __ldg(a.ck + (long)Bb.dn * a.npts + off + a.ncol) : 0.0f;
+          }
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int i = i0 + s;
+            if (i >= a.ng) break;
+            const long idx = (long)b * a.npts + (long)i * a.ncol + col;
+            if (i >= nrow) {
+              if (a.mode == 1) a.out[idx] = 0.0f; else a.ckm1[idx] = 0.0f;
+              continue;
+            }
+            const float gg = fminf(fRm, cf[4 * a.ng + i]);
+            const float aa = fminf(cf[i] * frk, a.erot) + gg * cf[a.ng + i];
+            float h = w[s] + aa * cv[s] + tv[s];
+            h += gg * cf[2 * a.ng + i] * cu[s];
+            h += gg * cf[3 * a.ng + i] * cd[s];
+            const float hs = h * (float)J.invdE - (float)J.e0s * cv[s];
+            if (a.mode == 1) {
+              a.out[idx] = hs;
+            } else {
+              const float nv = D * (a.alpha * hs - a.beta * D * pv[s]);
+              a.ckm1[idx] = nv;
+              ss += (double)nv * (double)nv;
+            }
+          }
+        }
+      }
+    }
+    // norm partial of this tile (the same fixed-order reduction as the one-tile form)
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+    if (lane == 0) red[warp] = ss;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      double s2 = 0;
+      for (int w2 = 0; w2 < TC_THREADS / 32; ++w2) s2 += red[w2];
+      if (a.npart) a.npart[(long)g * a.ntiles + tile] = s2;
+    }
+  }
+  if (!ok && tid == 0) atomicExch(a.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols));
+  }
+}
+
 // out[iJ] = sum over the (J, Omega) groups of J and their tiles, in order.
 __global__ void k_tc_norm_final(const double* __restrict__ npart, const int* __restrict__ g_begin,
                                 int ntiles, double* __restrict__ out) {
@@ -408,6 +704,42 @@ static cudaError_t launch_tc_inst(const TcArgs& args, dim3 grid, cudaStream_t st
   return cudaGetLastError();
 }
 
+template <int KP, int NE>
+static cudaError_t launch_tc2_inst(const TcArgs& args, cudaStream_t st) {
+  if constexpr (NE == 2 && (2 + 2 + 1) * KP > 512) {
+    return cudaErrorInvalidValue;   // tensor-memory columns: 5 kp for two states
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_angular_tc2<KP, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           227 * 1024);
+      attr = true;
+    }
+    const long total = (long)args.ngroups * args.ntiles;
+    const unsigned grid = (unsigned)std::min<long>(total, args.nsm);
+    k_angular_tc2<KP, NE><<<grid, TC_THREADS, tc2_smem<KP>(), st>>>(args);
+    return cudaGetLastError();
+  }
+}
+
+template <int NE>
+static cudaError_t launch_tc2_ne(const TcArgs& a, cudaStream_t st) {
+  switch (a.kp) {
+    case 16: return launch_tc2_inst<16, NE>(a, st);
+    case 32: return launch_tc2_inst<32, NE>(a, st);
+    case 48: return launch_tc2_inst<48, NE>(a, st);
+    case 64: return launch_tc2_inst<64, NE>(a, st);
+    case 80: return launch_tc2_inst<80, NE>(a, st);
+    case 96: return launch_tc2_inst<96, NE>(a, st);
+    case 112: return launch_tc2_inst<112, NE>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool angular_tc2_supported(int kp, int nelec) {
+  return kp % 16 == 0 && kp <= kTcMaxKp && (nelec == 1 || 5 * kp <= 512);
+}
+
 template <int NE>
 static cudaError_t launch_tc_ne(const TcArgs& a, dim3 grid, cudaStream_t st) {
   switch (a.kp) {
@@ -424,10 +756,14 @@ static cudaError_t launch_tc_ne(const TcArgs& a, dim3 grid, cudaStream_t st) {
 
 cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
                               double* norm_out, cudaStream_t st) {
-  if (args.ntiles > 65535) return cudaErrorInvalidConfiguration;
-  dim3 grid((unsigned)ngroups, (unsigned)args.ntiles);
-  cudaError_t e = (args.nelec == 1) ? launch_tc_ne<1>(args, grid, st)
-                                    : launch_tc_ne<2>(args, grid, st);
+  cudaError_t e;
+  if (args.persistent) {
+    e = (args.nelec == 1) ? launch_tc2_ne<1>(args, st) : launch_tc2_ne<2>(args, st);
+  } else {
+    if (args.ntiles > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)ngroups, (unsigned)args.ntiles);
+    e = (args.nelec == 1) ? launch_tc_ne<1>(args, grid, st) : launch_tc_ne<2>(args, grid, st);
+  }
   if (e != cudaSuccess) return e;
   if (norm_out && args.npart) {
     k_tc_norm_final<<<nJ, 32, 0, st>>>(args.npart, g_begin, args.ntiles, norm_out);
