@@ -261,8 +261,10 @@ int mw3_product_probabilities(mw3_ctx* ctx, double* P);
  *   "cols_tile"  R columns per CTA of the r-direction kinetic kernel (even, 2..64)
  *   "use_graph"  0/1: replay full chunks as CUDA graphs
  *   "use_tc"     0/1: tensor-core gamma transform in MW3_MIXED
- *   "tc_persist" 0/1: persistent form of the tensor-core angular step (one CTA per SM,
- *                T^Omega resident in shared memory, operands in tensor memory); default 1
+ *   "tc_persist" 0: one tile per CTA; 1: persistent form of the tensor-core angular step
+ *                (one CTA per SM, T^Omega resident in shared memory, operands in tensor
+ *                memory); 2 (default): persistent with the Gauss-Legendre parity split
+ *                (even ngamma <= 96; otherwise 1 is used)
  *   "kin_warp"   0/1: warp-register FFT kinetic kernels for line lengths 32 R
  *                (R = 1, 2, 3, 4, 6, 8, 12, 16; FP64 up to R = 8); default 1
  * Values outside a key's range return MW3_ERR_BAD_ARG. mw3_get_tuning reads a key. */

@@ -83,9 +83,10 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0, 1, 1};
+  Tuning tune{4, 32, 32, 1, 0, 1, 2};
   int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
+  int kh = 0;          // parity-split operand size (0: not applicable)
   bool tc_ok = false;  // the tensor-core angular step supports this grid
   int tc_user = -1;    // explicit "use_tc" setting (-1: default = on when supported)
 
@@ -718,6 +719,26 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
     if ((st = upload_raw(ctx, "T_hi", th)) || (st = upload_raw(ctx, "T_lo", tl)) ||
         (st = upload_raw(ctx, "Tt_hi", tth)) || (st = upload_raw(ctx, "Tt_lo", ttl)))
       return st;
+    // parity-split operands (n_gamma even): with h = n_gamma / 2, n < h, e/o = even/odd row
+    //   G1e[n][e] = T[2e][n], G1o[n][o] = T[2o+1][n], G2e[e][n] = T[2e][n], G2o[o][n] = T[2o+1][n]
+    ctx->kh = angular_tc3_kh(ng, ctx->nelec);
+    if (ctx->kh > 0) {
+      const int kh = ctx->kh, h = ng / 2;
+      std::vector<float> ph(nom * 4 * kh * kh, 0.f), pl(ph.size(), 0.f);
+      for (size_t om = 0; om < nom; ++om)
+        for (int r = 0; r < kh; ++r)
+          for (int n = 0; n < h; ++n)
+            for (int par = 0; par < 2; ++par) {
+              const int i = 2 * r + par;
+              if (i >= ng) continue;
+              const double v = ctx->T[om][(size_t)i * ng + n];
+              const size_t g1 = ((om * 4 + par) * kh + n) * kh + r;       // G1e / G1o
+              const size_t g2 = ((om * 4 + 2 + par) * kh + r) * kh + n;   // G2e / G2o
+              split(v, ph[g1], pl[g1]);
+              split(v, ph[g2], pl[g2]);
+            }
+      if ((st = upload_raw(ctx, "Tp_hi", ph)) || (st = upload_raw(ctx, "Tp_lo", pl))) return st;
+    }
     std::vector<int> gb(ctx->nJ + 1);
     for (int iJ = 0; iJ <= ctx->nJ; ++iJ) gb[iJ] = (int)(ctx->J_first_block[iJ] / ctx->nelec);
     if ((st = upload_raw(ctx, "g_begin", gb))) return st;
@@ -1351,7 +1372,14 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
     a.mode = mode;
     a.ntiles = (int)((ctx->ncol + 127) / 128);
     a.ngroups = ctx->nblk / ctx->nelec;
-    a.persistent = ctx->tune.tc_persist && angular_tc2_supported(ctx->kp, ctx->nelec);
+    a.kh = ctx->kh;
+    a.Tp_hi = (const float*)dptr(ctx, "Tp_hi");
+    a.Tp_lo = (const float*)dptr(ctx, "Tp_lo");
+    a.persistent = 0;
+    if (ctx->tune.tc_persist >= 2 && ctx->kh > 0)
+      a.persistent = 2;
+    else if (ctx->tune.tc_persist >= 1 && angular_tc2_supported(ctx->kp, ctx->nelec))
+      a.persistent = 1;
     a.nsm = ctx->nsm;
     int tc = 32;
     while (tc < 2 * ctx->nelec * ctx->kp) tc *= 2;
@@ -1709,7 +1737,8 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
   } else if (k == "kin_warp") {
     ctx->tune.kin_warp = v != 0;
   } else if (k == "tc_persist") {
-    ctx->tune.tc_persist = v != 0;
+    if (v < 0 || v > 2) return ctx->fail(MW3_ERR_BAD_ARG, "tc_persist must be 0, 1 or 2");
+    ctx->tune.tc_persist = (int)v;
   } else if (k == "use_tc") {
     if (v != 0 && ctx->precision != MW3_MIXED)
       return ctx->fail(MW3_ERR_BAD_ARG, "use_tc needs MW3_MIXED");

@@ -166,10 +166,15 @@ struct TcArgs {
   long ncol, npts;
   int ng, kp, NR, nelec, mode, ntiles, tmem_cols;
   int ngroups;          // (J, Omega) groups
-  int persistent;       // 1: one CTA per SM over a range of (group, tile) pairs
-  int nsm;              // CTAs of the persistent form
+  int persistent;       // 1: one CTA per SM over a range of (group, tile) pairs;
+                        // 2: the same with the parity-split operands (Tp_*)
+  int nsm;              // CTAs of the persistent forms
+  int kh;               // parity-split operand size: n_gamma / 2 rounded up to 16
+  const float* Tp_hi;   // [omega][4][kh][kh]: G1e, G1o, G2e, G2o (see mw3_tc.cu)
+  const float* Tp_lo;
 };
 bool angular_tc2_supported(int kp, int nelec);
+int angular_tc3_kh(int ng, int nelec);   // 0 when the parity-split form does not apply
 size_t angular_tc_smem(int kp);
 cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
                               double* norm_out, cudaStream_t st);

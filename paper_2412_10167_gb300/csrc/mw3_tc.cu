@@ -100,6 +100,16 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
   for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float* v) {
+  uint32_t r[2];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  v[0] = __uint_as_float(r[0]);
+  v[1] = __uint_as_float(r[1]);
+}
+
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)),
                "l"(gsrc)
@@ -677,15 +687,335 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc2(TcArgs a) {
   }
 }
 
-// out[iJ] = sum over the (J, Omega) groups of J and their tiles, in order.
-__global__ void k_tc_norm_final(const double* __restrict__ npart, const int* __restrict__ g_begin,
-                                int ntiles, double* __restrict__ out) {
-  if (threadIdx.x != 0) return;
+
+// ============================================================ parity-split persistent form
+// The Gauss-Legendre nodes are symmetric (x_(n') = -x_n, n' = n_gamma - 1 - n) and
+// P-bar_j^Omega(-x) = (-1)^(j + Omega) P-bar_j^Omega(x), so T^Omega[i][n'] = (-1)^i T^Omega[i][n]
+// (i = j - Omega). With h = n_gamma / 2 (n_gamma even) and n < h:
+//   GEMM 1  u[n] = E[n] + O[n],  u[n'] = E[n] - O[n],
+//           E[n] = sum_(i even) c_i T[i][n],  O[n] = sum_(i odd) c_i T[i][n]
+//   GEMM 2  w_i = sum_(n < h) T[i][n] (y[n] + (-1)^i y[n']),  y = V u
+// Four kh x kh operand matrices (kh = h rounded up to 16) replace two kp x kp ones: half
+// the tensor work and half the shared memory, which then holds the c, t and c_(k-1) tiles
+// copied in asynchronously (c of the next tile while this tile computes).
+// Tensor-memory columns (units of kh): A even hi/lo [0, 2), A odd hi/lo [2, 4); per state
+// E_L, O_L at 4 + 2L, 5 + 2L; w (even, odd) of state 0 at 4 + 2 NE when NE = 2 (else in
+// E_0, O_0); w of state 1 in E_0, O_0.
+template <int KH>
+constexpr size_t tc3_bbytes() { return (size_t)KH * KH * 4; }
+template <int KH>
+constexpr size_t tc3_tile() { return (size_t)2 * KH * TC_M * 4; }   // rows [0, 2 kh) x 128
+template <int KH>
+constexpr size_t tc3_smem() { return 8 * tc3_bbytes<KH>() + 3 * tc3_tile<KH>() + 16 + 16 * sizeof(double) + 64; }
+
+template <int KH, int NE>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  constexpr int kh = KH;
+  constexpr size_t bb = tc3_bbytes<KH>();
+  unsigned char* G = sm;                                   // 8 matrices: G1e, G1o, G2e, G2o (hi, lo)
+  float* cs = reinterpret_cast<float*>(sm + 8 * bb);      // [2 kh][TC_M] c tile (state 0)
+  float* ts = cs + 2 * kh * TC_M;                          // t tile (state 0)
+  float* ps = ts + 2 * kh * TC_M;                          // c_(k-1) tile (state 0)
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(ps + 2 * kh * TC_M);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  double* red = reinterpret_cast<double*>(mbar + 2);
+  auto Gm = [&](int k, int lo) { return G + (size_t)(2 * k + lo) * bb; };
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3;
+  const int half = warp >> 2;
+  const int m = q * 32 + lane;
+  constexpr int nq = kh / 4;         // parity rows / half-nodes per thread
+  constexpr int ncb = kh / 2;        // rows per thread in the epilogue (2 kh / 4)
+  const uint32_t mb = smem_u32(mbar);
+  const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+  const uint32_t idesc = idesc_tf32(TC_M, kh);
+  const int ng = a.ng, h = ng / 2;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(a.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  auto col_of = [&](int unit) { return tmem + (uint32_t)(unit * kh); };
+  const uint32_t tAe_hi = col_of(0), tAe_lo = col_of(1), tAo_hi = col_of(2), tAo_lo = col_of(3);
+  auto tE = [&](int L) { return col_of(4 + 2 * L); };
+  auto tO = [&](int L) { return col_of(5 + 2 * L); };
+  auto tWe = [&](int L) { return (NE == 2 && L == 0) ? col_of(4 + 2 * NE) : col_of(4); };
+  auto tWo = [&](int L) { return (NE == 2 && L == 0) ? col_of(5 + 2 * NE) : col_of(5); };
+
+  const long total = (long)a.ngroups * a.ntiles;
+  const long f0 = (long)blockIdx.x * total / gridDim.x;
+  const long f1 = (long)(blockIdx.x + 1) * total / gridDim.x;
+  // 16-byte asynchronous copy of rows [0, nrow) x [col0, col0 + 128) of plane src into dst
+  auto stage = [&](float* dst, const float* src, int nrow, long col0) {
+    const int nch = nrow * (TC_M / 4);
+    for (int e = tid; e < nch; e += TC_THREADS) {
+      const int i = e / (TC_M / 4);
+      const int c4 = (e - i * (TC_M / 4)) * 4;
+      if (col0 + c4 < a.ncol) cp_async16(dst + i * TC_M + c4, src + (long)i * a.ncol + col0 + c4);
+    }
+  };
+  auto tile_of = [&](long f, int& g, int& tile) {
+    g = (int)(f / a.ntiles);
+    tile = (int)(f - (long)g * a.ntiles);
+  };
+  if (f0 < f1) {
+    int g, tile;
+    tile_of(f0, g, tile);
+    stage(cs, a.ck + (long)(g * NE) * a.npts, a.blocks[g * NE].nrow, (long)tile * TC_M);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+
+  uint32_t phase = 0;
+  bool ok = true;
+  int om_cur = -1;
+  for (long f = f0; f < f1 && ok; ++f) {
+    int g, tile;
+    tile_of(f, g, tile);
+    const int b0 = g * NE;
+    const DevBlock B0 = a.blocks[b0];
+    const int om = B0.omega;
+    const int nrow = B0.nrow;
+    const long col0 = (long)tile * TC_M;
+    const long col = col0 + m;
+    const bool live = col < a.ncol;
+    const int kr = live ? (int)(col / a.NR) : 0;
+    const int mR = live ? (int)(col - (long)kr * a.NR) : 0;
+
+    __syncthreads();   // the previous tile's readers of ts / ps / tensor memory are done
+    if (om != om_cur) {
+      for (int k = 0; k < 4; ++k)
+        load_b(a.Tp_hi + ((long)om * 4 + k) * kh * kh, a.Tp_lo + ((long)om * 4 + k) * kh * kh,
+               Gm(k, 0), Gm(k, 1), kh);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      om_cur = om;
+    }
+    stage(ts, a.t + (long)b0 * a.npts, nrow, col0);
+    if (a.mode == 0) stage(ps, a.ckm1 + (long)b0 * a.npts, nrow, col0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");   // c of this tile has landed
+    __syncthreads();
+
+    // ------------------------------------------------------------ GEMM 1 per state
+    for (int L = 0; L < NE && ok; ++L) {
+      const float* c = a.ck + (long)(b0 + L) * a.npts;
+#pragma unroll
+      for (int s0 = 0; s0 < nq; s0 += 4) {
+        float he[4], le[4], ho[4], lo[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int e = half * nq + s0 + s;
+          const int ie = 2 * e, io = 2 * e + 1;
+          float xe = 0.0f, xo = 0.0f;
+          if (live) {
+            if (L == 0) {
+              xe = ie < nrow ? cs[ie * TC_M + m] : 0.0f;
+              xo = io < nrow ? cs[io * TC_M + m] : 0.0f;
+            } else {
+              xe = ie < nrow ? __ldg(c + (long)ie * a.ncol + col) : 0.0f;
+              xo = io < nrow ? __ldg(c + (long)io * a.ncol + col) : 0.0f;
+            }
+          }
+          he[s] = tf32_hi(xe);
+          le[s] = xe - he[s];
+          ho[s] = tf32_hi(xo);
+          lo[s] = xo - ho[s];
+        }
+        const uint32_t cc = lane_base + (uint32_t)(half * nq + s0);
+        tmem_st4(tAe_hi + cc, he);
+        tmem_st4(tAe_lo + cc, le);
+        tmem_st4(tAo_hi + cc, ho);
+        tmem_st4(tAo_lo + cc, lo);
+      }
+      tmem_st_wait();
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      if (L == 0) {
+        // the c tile is in tensor memory now: bring in the next tile's (its own group)
+        if (f + 1 < f1) {
+          int g2, t2;
+          tile_of(f + 1, g2, t2);
+          stage(cs, a.ck + (long)(g2 * NE) * a.npts, a.blocks[g2 * NE].nrow, (long)t2 * TC_M);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        issue_split_gemm_ta(tE(L), tAe_hi, tAe_lo, Gm(0, 0), Gm(0, 1), kh, idesc);
+        issue_split_gemm_ta(tO(L), tAo_hi, tAo_lo, Gm(1, 0), Gm(1, 1), kh, idesc);
+        mma_commit(mb);
+      }
+      ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
+      phase ^= 1;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+
+    // ------------------------------------------------------------ potential + GEMM 2
+    for (int L = 0; L < NE && ok; ++L) {
+      // V at the node pairs (n, n') of this thread's quarter, loads first
+      float va[NE][nq], vb[NE][nq];
+#pragma unroll
+      for (int Lp = 0; Lp < NE; ++Lp) {
+        const float* V = a.V + (long)(L * NE + Lp) * a.npts;
+#pragma unroll
+        for (int s2 = 0; s2 < nq; ++s2) {
+          const int n = half * nq + s2;
+          const bool in = live && n < h;
+          va[Lp][s2] = in ? __ldg(V + (long)n * a.ncol + col) : 0.0f;
+          vb[Lp][s2] = in ? __ldg(V + (long)(ng - 1 - n) * a.ncol + col) : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int s0 = 0; s0 < nq; s0 += 4) {
+        float ya[4] = {0, 0, 0, 0}, yb[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int Lp = 0; Lp < NE; ++Lp) {
+          float E[4], O[4];
+          tmem_ld4(tE(Lp) + lane_base + (uint32_t)(half * nq + s0), E);
+          tmem_ld4(tO(Lp) + lane_base + (uint32_t)(half * nq + s0), O);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            ya[s] += va[Lp][s0 + s] * (E[s] + O[s]);   // y[n]
+            yb[s] += vb[Lp][s0 + s] * (E[s] - O[s]);   // y[n']
+          }
+        }
+        float hs[4], ls[4], hd[4], ld[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const float S = ya[s] + yb[s], Dd = ya[s] - yb[s];
+          hs[s] = tf32_hi(S);
+          ls[s] = S - hs[s];
+          hd[s] = tf32_hi(Dd);
+          ld[s] = Dd - hd[s];
+        }
+        const uint32_t cc = lane_base + (uint32_t)(half * nq + s0);
+        tmem_st4(tAe_hi + cc, hs);
+        tmem_st4(tAe_lo + cc, ls);
+        tmem_st4(tAo_hi + cc, hd);
+        tmem_st4(tAo_lo + cc, ld);
+      }
+      tmem_st_wait();
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        issue_split_gemm_ta(tWe(L), tAe_hi, tAe_lo, Gm(2, 0), Gm(2, 1), kh, idesc);
+        issue_split_gemm_ta(tWo(L), tAo_hi, tAo_lo, Gm(3, 0), Gm(3, 1), kh, idesc);
+        mma_commit(mb);
+      }
+      ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
+      phase ^= 1;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    asm volatile("cp.async.wait_group 1;" ::: "memory");   // t and c_(k-1) of this tile
+    __syncthreads();
+
+    // ------------------------------------------------------------ epilogue
+    double ss = 0.0;
+    if (ok) {
+      const DevJ J = a.dj[B0.iJ];
+      const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
+      const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
+      const float frk = live ? a.fr[kr] : 0.0f;
+      const float fRm = live ? a.fR[mR] : 0.0f;
+      for (int L = 0; L < NE; ++L) {
+        const int b = b0 + L;
+        const DevBlock Bb = a.blocks[b];
+        const float* c = a.ck + (long)b * a.npts;
+        for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 4) {
+          float we[2], wo[2];
+          tmem_ld2(tWe(L) + lane_base + (uint32_t)(i0 / 2), we);
+          tmem_ld2(tWo(L) + lane_base + (uint32_t)(i0 / 2), wo);
+          if (!live) continue;
+          const float w[4] = {we[0], wo[0], we[1], wo[1]};
+          float cv[4], cu[4], cd[4], tv[4], pv[4];
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int i = i0 + s;
+            const bool in = i < nrow;
+            const long off = (long)i * a.ncol + col;
+            cv[s] = in ? __ldg(c + off) : 0.0f;
+            tv[s] = in ? (L == 0 ? ts[i * TC_M + m] : __ldg(a.t + (long)b * a.npts + off)) : 0.0f;
+            pv[s] = (in && a.mode == 0) ? (L == 0 ? ps[i * TC_M + m] : __ldg(a.ckm1 + (long)b * a.npts + off)) : 0.0f;
+            cu[s] = (in && Bb.up >= 0 && i >= 1) ? __ldg(a.ck + (long)Bb.up * a.npts + off - a.ncol) : 0.0f;
+            cd[s] = (in && Bb.dn >= 0) ? __ldg(a.ck + (long)Bb.dn * a.npts + off + a.ncol) : 0.0f;
+          }
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int i = i0 + s;
+            if (i >= a.ng) break;
+            const long idx = (long)b * a.npts + (long)i * a.ncol + col;
+            if (i >= nrow) {
+              if (a.mode == 1) a.out[idx] = 0.0f; else a.ckm1[idx] = 0.0f;
+              continue;
+            }
+            const float gg = fminf(fRm, cf[4 * a.ng + i]);
+            const float aa = fminf(cf[i] * frk, a.erot) + gg * cf[a.ng + i];
+            float hh = w[s] + aa * cv[s] + tv[s];
+            hh += gg * cf[2 * a.ng + i] * cu[s];
+            hh += gg * cf[3 * a.ng + i] * cd[s];
+            const float hs = hh * (float)J.invdE - (float)J.e0s * cv[s];
+            if (a.mode == 1) {
+              a.out[idx] = hs;
+            } else {
+              const float nv = D * (a.alpha * hs - a.beta * D * pv[s]);
+              a.ckm1[idx] = nv;
+              ss += (double)nv * (double)nv;
+            }
+          }
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+    if (lane == 0) red[warp] = ss;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      double s2 = 0;
+      for (int w2 = 0; w2 < TC_THREADS / 32; ++w2) s2 += red[w2];
+      if (a.npart) a.npart[(long)g * a.ntiles + tile] = s2;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (!ok && tid == 0) atomicExch(a.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols));
+  }
+}
+
+// out[iJ] = sum over the (J, Omega) groups of J and their tiles: 256 threads per J take
+// strided partial sums of the contiguous range, then a fixed-order tree (deterministic).
+__global__ void __launch_bounds__(256) k_tc_norm_final(const double* __restrict__ npart,
+                                                       const int* __restrict__ g_begin,
+                                                       int ntiles, double* __restrict__ out) {
+  __shared__ double red[256];
   const int iJ = blockIdx.x;
+  const long e0 = (long)g_begin[iJ] * ntiles, e1 = (long)g_begin[iJ + 1] * ntiles;
   double s = 0;
-  for (int g = g_begin[iJ]; g < g_begin[iJ + 1]; ++g)
-    for (int t = 0; t < ntiles; ++t) s += npart[(long)g * ntiles + t];
-  out[iJ] = s;
+  for (long e = e0 + threadIdx.x; e < e1; e += 256) s += npart[e];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[iJ] = red[0];
 }
 
 size_t angular_tc_smem(int kp) {
@@ -736,6 +1066,37 @@ static cudaError_t launch_tc2_ne(const TcArgs& a, cudaStream_t st) {
   }
 }
 
+template <int KH, int NE>
+static cudaError_t launch_tc3_inst(const TcArgs& args, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_angular_tc3<KH, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr = true;
+  }
+  const long total = (long)args.ngroups * args.ntiles;
+  const unsigned grid = (unsigned)std::min<long>(total, args.nsm);
+  k_angular_tc3<KH, NE><<<grid, TC_THREADS, tc3_smem<KH>(), st>>>(args);
+  return cudaGetLastError();
+}
+
+template <int NE>
+static cudaError_t launch_tc3_ne(const TcArgs& a, cudaStream_t st) {
+  switch (a.kh) {
+    case 16: return launch_tc3_inst<16, NE>(a, st);
+    case 32: return launch_tc3_inst<32, NE>(a, st);
+    case 48: return launch_tc3_inst<48, NE>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int angular_tc3_kh(int ng, int nelec) {
+  if (ng % 2) return 0;
+  const int kh = ((ng / 2 + 15) / 16) * 16;
+  if (kh > 48 || (nelec == 2 && 10 * kh > 512) || nelec > 2) return 0;
+  return kh;
+}
+
 bool angular_tc2_supported(int kp, int nelec) {
   return kp % 16 == 0 && kp <= kTcMaxKp && (nelec == 1 || 5 * kp <= 512);
 }
@@ -757,7 +1118,9 @@ static cudaError_t launch_tc_ne(const TcArgs& a, dim3 grid, cudaStream_t st) {
 cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
                               double* norm_out, cudaStream_t st) {
   cudaError_t e;
-  if (args.persistent) {
+  if (args.persistent == 2) {
+    e = (args.nelec == 1) ? launch_tc3_ne<1>(args, st) : launch_tc3_ne<2>(args, st);
+  } else if (args.persistent) {
     e = (args.nelec == 1) ? launch_tc2_ne<1>(args, st) : launch_tc2_ne<2>(args, st);
   } else {
     if (args.ntiles > 65535) return cudaErrorInvalidConfiguration;
@@ -766,7 +1129,7 @@ cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begi
   }
   if (e != cudaSuccess) return e;
   if (norm_out && args.npart) {
-    k_tc_norm_final<<<nJ, 32, 0, st>>>(args.npart, g_begin, args.ntiles, norm_out);
+    k_tc_norm_final<<<nJ, 256, 0, st>>>(args.npart, g_begin, args.ntiles, norm_out);
     e = cudaGetLastError();
   }
   return e;

@@ -37,11 +37,32 @@ def propagate_probabilities(cfg: dict, Js, steps: int, precision: str = "fp64", 
 
 
 def features(J, E, v, j, scale):
-    """Network inputs (J, E, v', j') scaled to about [0, 1]."""
-    return np.stack([np.asarray(J, float) / scale["J"],
-                     (np.asarray(E, float) - scale["E0"]) / scale["dE"],
-                     np.asarray(v, float) / scale["v"],
-                     np.asarray(j, float) / scale["j"]], axis=-1).astype(np.float32)
+    """Network inputs scaled to about [0, 1]: J, E, v', j' and the J-shifted energy
+    E - B J(J+1) of the J-shifting model (B fitted on the training propagations), along
+    which the probabilities of different J nearly coincide."""
+    J = np.asarray(J, float)
+    E = np.asarray(E, float)
+    Es = E - scale["B"] * J * (J + 1.0)
+    return np.stack([J / scale["J"], (E - scale["E0"]) / scale["dE"],
+                     np.asarray(v, float) / scale["v"], np.asarray(j, float) / scale["j"],
+                     (Es - scale["E0"]) / scale["dE"]], axis=-1).astype(np.float32)
+
+
+def fit_shift(E, Jtr, Ptr):
+    """Mean rotational constant B over the training intervals: least-squares overlay of
+    the state-summed curve of J2, shifted by B [J2(J2+1) - J1(J1+1)], on that of J1."""
+    from numpy import interp
+    Bs = []
+    for k in range(len(Jtr) - 1):
+        J1, J2 = Jtr[k], Jtr[k + 1]
+        dJ = J2 * (J2 + 1) - J1 * (J1 + 1)
+        if dJ <= 0:
+            continue
+        t1, t2 = Ptr[k].sum(axis=(0, 1)), Ptr[k + 1].sum(axis=(0, 1))
+        grid = np.linspace(0.0, (E[-1] - E[0]) / dJ, 801)
+        err = [np.sum((t1 - interp(E + b * dJ, E, t2, left=t2[0], right=t2[-1])) ** 2) for b in grid]
+        Bs.append(grid[int(np.argmin(err))])
+    return float(np.mean(Bs)) if Bs else 0.0
 
 
 def dataset(Js, E, Pst, scale):
@@ -112,9 +133,9 @@ def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 400, width: int = 
     E, _, Ptr, t_train = propagate_probabilities(cfg, J_train, steps, device=device)
     nv, nj = Ptr.shape[1], Ptr.shape[2]
     scale = dict(J=max(max(J_train), 1), E0=E[0], dE=max(E[-1] - E[0], 1e-12), v=max(nv - 1, 1),
-                 j=max(nj - 1, 1))
+                 j=max(nj - 1, 1), B=fit_shift(E, np.asarray(J_train, float), Ptr))
     X, y = dataset(J_train, E, Ptr, scale)
-    net = mw3.MLP(n_in=4, width=width, depth=depth, seed=seed, device=device)
+    net = mw3.MLP(n_in=X.shape[1], width=width, depth=depth, seed=seed, device=device)
     t0 = time.perf_counter()
     loss = net.train(X, y, epochs=epochs, batch=batch, lr=lr, seed=seed)
     t_fit = time.perf_counter() - t0
@@ -134,7 +155,7 @@ def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 400, width: int = 
             final[t] = Pte[t]
     C_true = cumulative(J_test, Pte)
     rep = dict(
-        train_loss=loss, n_train=int(X.shape[0]),
+        train_loss=loss, n_train=int(X.shape[0]), B_shift=scale["B"],
         mean_abs_dP=dict(surrogate=float(err.mean()), jshift=float(np.abs(Pjs - Pte).mean()),
                          linear=float(np.abs(Plin - Pte).mean())),
         max_abs_dP=dict(surrogate=float(err.max()), jshift=float(np.abs(Pjs - Pte).max()),
