@@ -164,6 +164,29 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------- our arm
+def captured_traffic(kernel_key):
+    """DRAM bytes per launch of `kernel_key` from the committed ncu capture record
+    (profiles/traffic_<kernel_key>_c2_mixed.txt), or None when the kernel's source file has
+    changed since the capture (its SHA-1 is part of the record)."""
+    import hashlib
+    rec = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
+                       f"traffic_{kernel_key}_c2_mixed.txt")
+    try:
+        fields = {}
+        with open(rec) as f:
+            for ln in f:
+                if ln.strip() and not ln.startswith("#"):
+                    k, _, v = ln.strip().partition(" ")
+                    fields[k] = v.strip()
+        src = os.path.join(os.path.dirname(os.path.abspath(__file__)), fields["source"])
+        with open(src, "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != fields["source_sha1"]:
+                return None
+        return float(fields["dram_bytes"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def kernel_roofline(kernel, es, npts, nblk, ng, nelec, nE, kb, ncols):
     """Algorithmic work of one launch of `kernel` on the workload: (bound, amount).
 
@@ -184,6 +207,10 @@ def kernel_roofline(kernel, es, npts, nblk, ng, nelec, nE, kb, ncols):
         return "alu", 2.0 * (2 * nE) * kb * ncols
     if kernel == "channels":
         return "hbm", es * nblk * ng * 0 + 8
+    if kernel == "angular_tc":
+        # the method's own minimum per step (read q_k, read q_(k-1), write q_(k+1)) plus the
+        # potential of the J (shared by its Omega blocks); the unfused design also reads t
+        return "hbm", 3 * vec + (npts * es) * nelec * nelec
     return "hbm", vec
 
 
@@ -274,9 +301,10 @@ def run_ours(args, rank, world, local):
     dom = max((k for k in per if per[k][1] > 0), key=lambda k: per[k][0] * per[k][1])
     avg_ms = per[dom][0]
     es = 4
-    fp32_peak = None
+    fp32_peak = fp64_peak = None
     try:
         fp32_peak = mw3.mw3_measure_peak(local, 1)
+        fp64_peak = mw3.mw3_measure_peak(local, 0)
     except Exception:
         pass
     ncols_total = 2 * nblk * g["ngamma"] * g["NR"] + 484
@@ -289,7 +317,8 @@ def run_ours(args, rank, world, local):
     else:
         ach = amount / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                "traffic": captured_traffic(dom), "kernel": dom,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     kernels = {k: {"avg_ms": round(per[k][0], 5), "launches": per[k][1],
                    "share": round(per[k][0] * per[k][1] / max(1e-9, sum(a * b for a, b in per.values())), 4)}
                for k in per if per[k][1]}
@@ -328,6 +357,7 @@ def run_ours(args, rank, world, local):
                 "d2h_bytes_per_step": 500 * 8 * 2},
         "cpu_baseline": cpu,
         "fp32_fma_peak_tflops": fp32_peak,
+        "fp64_fma_peak_tflops": fp64_peak,
     }
     print(json.dumps(line))
     if dist is not None:

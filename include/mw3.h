@@ -265,6 +265,8 @@ int mw3_product_probabilities(mw3_ctx* ctx, double* P);
  *                (one CTA per SM, T^Omega resident in shared memory, operands in tensor
  *                memory); 2 (default): persistent with the Gauss-Legendre parity split
  *                (even ngamma <= 96; otherwise 1 is used)
+ *   "flush_tc"   0/1: energy-sum flush on the tensor cores in MW3_MIXED (split-TF32 within
+ *                a flush, FP64 accumulators); default 1
  *   "kin_warp"   0/1: warp-register FFT kinetic kernels for line lengths 32 R
  *                (R = 1, 2, 3, 4, 6, 8, 12, 16; FP64 up to R = 8); default 1
  * Values outside a key's range return MW3_ERR_BAD_ARG. mw3_get_tuning reads a key. */

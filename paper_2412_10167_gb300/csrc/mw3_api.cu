@@ -83,7 +83,7 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0, 1, 2};
+  Tuning tune{4, 32, 32, 1, 0, 1, 2, 1};
   int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   int kh = 0;          // parity-split operand size (0: not applicable)
@@ -1435,8 +1435,14 @@ int flush(mw3_ctx* ctx, int nvalid, bool timed) {
   cudaStream_t st = ctx->stream;
   Timer tm(ctx, 6, timed);
   LK(launch_phases<real>(B.theta, ctx->nJ, ctx->an.nE, ctx->tune.kb, nvalid, B.d_iter, B.ph, st));
-  LK(launch_sums_flush<real>(B.ph, B.cut, ctx->NC, ctx->tune.kb, ctx->nJ, ctx->an.nE, B.colbase,
-                             B.ncols, B.accoff, ctx->max_cols, B.acc, st));
+  if (std::is_same<real, float>::value && ctx->tc_ok && ctx->tune.flush_tc) {
+    LK(launch_flush_tc((const float*)B.ph, (const float*)B.cut, ctx->NC, ctx->tune.kb, ctx->nJ,
+                       ctx->an.nE, B.colbase, B.ncols, B.accoff, ctx->max_cols, B.acc,
+                       (int*)dptr(ctx, "tc_err"), st));
+  } else {
+    LK(launch_sums_flush<real>(B.ph, B.cut, ctx->NC, ctx->tune.kb, ctx->nJ, ctx->an.nE,
+                               B.colbase, B.ncols, B.accoff, ctx->max_cols, B.acc, st));
+  }
   LK(launch_advance(B.d_iter, nvalid, st));
   tm.stop();
   return MW3_OK;
@@ -1736,6 +1742,8 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
     ctx->tune.use_graph = v != 0;
   } else if (k == "kin_warp") {
     ctx->tune.kin_warp = v != 0;
+  } else if (k == "flush_tc") {
+    ctx->tune.flush_tc = v != 0;
   } else if (k == "tc_persist") {
     if (v < 0 || v > 2) return ctx->fail(MW3_ERR_BAD_ARG, "tc_persist must be 0, 1 or 2");
     ctx->tune.tc_persist = (int)v;
@@ -1760,6 +1768,7 @@ long mw3_get_tuning(const mw3_ctx* ctx, const char* key) {
   if (k == "use_graph") return ctx->tune.use_graph;
   if (k == "kin_warp") return ctx->tune.kin_warp;
   if (k == "tc_persist") return ctx->tune.tc_persist;
+  if (k == "flush_tc") return ctx->tune.flush_tc;
   if (k == "use_tc") return ctx->stage >= 2 ? ctx->tune.use_tc : (ctx->tc_user != 0);
   return MW3_ERR_BAD_ARG;
 }

@@ -63,6 +63,7 @@ struct Tuning {
   int use_tc;       // tensor-core gamma transform (mixed precision only)
   int kin_warp;     // warp-register FFT kinetic kernels where the line length allows
   int tc_persist;   // persistent tensor-core angular step (operands in tensor memory)
+  int flush_tc;     // energy-sum flush on the tensor cores (mixed precision)
 };
 
 // --------------------------------------------------------------- launchers
@@ -174,6 +175,10 @@ struct TcArgs {
   const float* Tp_lo;
 };
 bool angular_tc2_supported(int kp, int nelec);
+// Energy-sum flush on the tensor cores (FP32 ring, split-TF32, FP64 accumulators).
+cudaError_t launch_flush_tc(const float* ph, const float* cut, long ncut_total, int kb, int nJ,
+                            int nE, const long* colbase, const long* ncols, const long* accoff,
+                            long max_cols, double* acc, int* err, cudaStream_t st);
 int angular_tc3_kh(int ng, int nelec);   // 0 when the parity-split form does not apply
 size_t angular_tc_smem(int kp);
 cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,

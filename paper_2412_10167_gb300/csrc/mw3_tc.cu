@@ -700,7 +700,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc2(TcArgs a) {
 // copied in asynchronously (c of the next tile while this tile computes).
 // Tensor-memory columns (units of kh): A even hi/lo [0, 2), A odd hi/lo [2, 4); per state
 // E_L, O_L at 4 + 2L, 5 + 2L; w (even, odd) of state 0 at 4 + 2 NE when NE = 2 (else in
-// E_0, O_0); w of state 1 in E_0, O_0.
+// E_0, O_0); w of state 1 in E_0, O_0; with one state the c tile itself (even, odd rows)
+// at 6, 7 for the epilogue.
 template <int KH>
 constexpr size_t tc3_bbytes() { return (size_t)KH * KH * 4; }
 template <int KH>
@@ -753,6 +754,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
   auto tO = [&](int L) { return col_of(5 + 2 * L); };
   auto tWe = [&](int L) { return (NE == 2 && L == 0) ? col_of(4 + 2 * NE) : col_of(4); };
   auto tWo = [&](int L) { return (NE == 2 && L == 0) ? col_of(5 + 2 * NE) : col_of(5); };
+  // one state: the raw c tile (even rows, odd rows) stays in tensor memory for the epilogue
+  const uint32_t tCe = col_of(6), tCo = col_of(7);
 
   const long total = (long)a.ngroups * a.ntiles;
   const long f0 = (long)blockIdx.x * total / gridDim.x;
@@ -837,6 +840,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
         tmem_st4(tAe_lo + cc, le);
         tmem_st4(tAo_hi + cc, ho);
         tmem_st4(tAo_lo + cc, lo);
+        if (NE == 1) {
+          float re[4], ro[4];
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            re[s] = he[s] + le[s];   // exact: hi + lo reproduces the FP32 value
+            ro[s] = ho[s] + lo[s];
+          }
+          tmem_st4(tCe + cc, re);
+          tmem_st4(tCo + cc, ro);
+        }
       }
       tmem_st_wait();
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -934,18 +947,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
         const DevBlock Bb = a.blocks[b];
         const float* c = a.ck + (long)b * a.npts;
         for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 4) {
-          float we[2], wo[2];
+          float we[2], wo[2], ce[2] = {0, 0}, co[2] = {0, 0};
           tmem_ld2(tWe(L) + lane_base + (uint32_t)(i0 / 2), we);
           tmem_ld2(tWo(L) + lane_base + (uint32_t)(i0 / 2), wo);
+          if (NE == 1) {
+            tmem_ld2(tCe + lane_base + (uint32_t)(i0 / 2), ce);
+            tmem_ld2(tCo + lane_base + (uint32_t)(i0 / 2), co);
+          }
           if (!live) continue;
           const float w[4] = {we[0], wo[0], we[1], wo[1]};
+          const float cr[4] = {ce[0], co[0], ce[1], co[1]};
           float cv[4], cu[4], cd[4], tv[4], pv[4];
 #pragma unroll
           for (int s = 0; s < 4; ++s) {
             const int i = i0 + s;
             const bool in = i < nrow;
             const long off = (long)i * a.ncol + col;
-            cv[s] = in ? __ldg(c + off) : 0.0f;
+            cv[s] = in ? (NE == 1 ? cr[s] : __ldg(c + off)) : 0.0f;
             tv[s] = in ? (L == 0 ? ts[i * TC_M + m] : __ldg(a.t + (long)b * a.npts + off)) : 0.0f;
             pv[s] = (in && a.mode == 0) ? (L == 0 ? ps[i * TC_M + m] : __ldg(a.ckm1 + (long)b * a.npts + off)) : 0.0f;
             cu[s] = (in && Bb.up >= 0 && i >= 1) ? __ldg(a.ck + (long)Bb.up * a.npts + off - a.ncol) : 0.0f;
@@ -1016,6 +1034,149 @@ __global__ void __launch_bounds__(256) k_tc_norm_final(const double* __restrict_
     __syncthreads();
   }
   if (threadIdx.x == 0) out[iJ] = red[0];
+}
+
+
+// ================================================================== energy-sum flush
+// Mixed precision: for J index iJ (blockIdx.z), a tile of 128 cut-ring columns (blockIdx.y)
+// and 128 phase rows (blockIdx.x, fastest, so the tiles that share columns run together):
+//   D[col][p] = sum_(k < kb) cut[k][colbase + col] ph[iJ][p][k]   (M = columns, N = phases)
+//   acc[accoff + p ncols + col] += D  (FP64)
+// on the tensor cores in split-TF32 (FP32 products within a flush, FP64 across flushes),
+// K in chunks of 32 ring slots. Column j of the tile is tensor-memory lane j, so the FP64
+// read-modify-write of one phase row is 128 consecutive doubles.
+constexpr int FL_M = 128, FL_N = 128, FL_KC = 32, FL_THREADS = 128;
+
+__global__ void __launch_bounds__(FL_THREADS) k_flush_tc(const float* __restrict__ ph,
+                                                         const float* __restrict__ cut,
+                                                         long ncut_total, int kb, int nE2,
+                                                         const long* __restrict__ colbase,
+                                                         const long* __restrict__ ncols,
+                                                         const long* __restrict__ accoff,
+                                                         double* __restrict__ acc,
+                                                         int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  constexpr uint32_t abytes = FL_M * FL_KC * 4, bbytes = FL_N * FL_KC * 4;
+  unsigned char* Ahi = sm;
+  unsigned char* Alo = Ahi + abytes;
+  unsigned char* Bhi = Alo + abytes;
+  unsigned char* Blo = Bhi + bbytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + bbytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int iJ = blockIdx.z;
+  const long nc = ncols[iJ];
+  const long c0 = (long)blockIdx.y * FL_M;
+  const int p0 = blockIdx.x * FL_N;
+  if (c0 >= nc) return;   // CTA-uniform, before any allocation
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const long col = c0 + tid;
+  const bool live = col < nc;
+  const uint32_t mb = smem_u32(mbar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(FL_N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = idesc_tf32(FL_M, FL_N);
+  const float* cutc = cut + colbase[iJ] + col;
+  const float* phr = ph + ((long)iJ * nE2 + p0 + tid) * kb;
+  const bool prow = p0 + tid < nE2;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int kc = 0; kc < kb && ok; kc += FL_KC) {
+    if (kc > 0) __syncthreads();   // the previous chunk's MMAs have completed (waited below)
+    // A: row = column of the tile, K = ring slot; B: row = phase row, K = ring slot
+    float x[FL_KC];
+#pragma unroll
+    for (int k = 0; k < FL_KC; ++k)
+      x[k] = (live && kc + k < kb) ? __ldg(cutc + (long)(kc + k) * ncut_total) : 0.0f;
+    float y[FL_KC];
+#pragma unroll
+    for (int k = 0; k < FL_KC; ++k) y[k] = (prow && kc + k < kb) ? __ldg(phr + kc + k) : 0.0f;
+#pragma unroll
+    for (int k4 = 0; k4 < FL_KC; k4 += 4) {
+      float4 h, l;
+      h.x = tf32_hi(x[k4]); l.x = x[k4] - h.x;
+      h.y = tf32_hi(x[k4 + 1]); l.y = x[k4 + 1] - h.y;
+      h.z = tf32_hi(x[k4 + 2]); l.z = x[k4 + 2] - h.z;
+      h.w = tf32_hi(x[k4 + 3]); l.w = x[k4 + 3] - h.w;
+      const uint32_t off = cm_off(tid, k4, FL_KC);
+      *reinterpret_cast<float4*>(Ahi + off) = h;
+      *reinterpret_cast<float4*>(Alo + off) = l;
+      h.x = tf32_hi(y[k4]); l.x = y[k4] - h.x;
+      h.y = tf32_hi(y[k4 + 1]); l.y = y[k4 + 1] - h.y;
+      h.z = tf32_hi(y[k4 + 2]); l.z = y[k4 + 2] - h.z;
+      h.w = tf32_hi(y[k4 + 3]); l.w = y[k4 + 3] - h.w;
+      *reinterpret_cast<float4*>(Bhi + off) = h;
+      *reinterpret_cast<float4*>(Blo + off) = l;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t sbo = FL_KC * 32, lbo = 128;
+      const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+      for (int ks = 0; ks < FL_KC / 8; ++ks) {
+        const uint32_t o = (uint32_t)ks * 256;
+        mma_tf32(tmem, smem_desc(ah + o, lbo, sbo), smem_desc(bh + o, lbo, sbo), idesc,
+                 (kc > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, smem_desc(ah + o, lbo, sbo), smem_desc(bl + o, lbo, sbo), idesc, 1);
+        mma_tf32(tmem, smem_desc(al + o, lbo, sbo), smem_desc(bh + o, lbo, sbo), idesc, 1);
+      }
+      mma_commit(mb);
+    }
+    ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+  if (ok) {
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    double* accJ = acc + accoff[iJ] + col;
+    for (int j0 = 0; j0 < FL_N; j0 += 4) {
+      float v[4];
+      tmem_ld4(tmem + lane_base + (uint32_t)j0, v);
+      if (!live) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int p = p0 + j0 + j;
+        if (p < nE2) accJ[(long)p * nc] += (double)v[j];
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FL_N));
+  }
+}
+
+cudaError_t launch_flush_tc(const float* ph, const float* cut, long ncut_total, int kb, int nJ,
+                            int nE, const long* colbase, const long* ncols, const long* accoff,
+                            long max_cols, double* acc, int* err, cudaStream_t st) {
+  const long ytiles = (max_cols + FL_M - 1) / FL_M;
+  if (ytiles > 65535) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)((2 * nE + FL_N - 1) / FL_N), (unsigned)ytiles, (unsigned)nJ);
+  const size_t smem = 2 * (size_t)FL_M * FL_KC * 4 + 2 * (size_t)FL_N * FL_KC * 4 + 64;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_flush_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_flush_tc<<<grid, FL_THREADS, smem, st>>>(ph, cut, ncut_total, kb, 2 * nE, colbase, ncols,
+                                             accoff, acc, err);
+  return cudaGetLastError();
 }
 
 size_t angular_tc_smem(int kp) {

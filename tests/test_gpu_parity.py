@@ -287,6 +287,24 @@ def test_tensor_core_step_matches_cuda_core_step(name):
         assert rel_o < 2e-5, rel_o
 
 
+def test_tensor_core_flush_matches_cuda_core_flush():
+    """The energy-sum flush on the tensor cores (split-TF32, FP64 accumulators) gives the
+    probabilities of the FP32 CUDA-core flush to FP32 rounding (and a partial last ring)."""
+    cfg = W.C2_SMALL
+    H = GridHamiltonian(cfg)
+    q0 = H.project(W.random_unit_state(H.shape, 5))   # every sum generic and nonzero
+    out = []
+    for ftc in (1, 0):
+        pr = mw3().Propagator(cfg, precision="mixed", tuning={"flush_tc": ftc, "kb": 32})
+        pr.set_state(q0)
+        pr.propagate(100)
+        E, Pt, Pin = pr.probabilities()
+        out.append((Pt, Pin, pr.product_probabilities()))
+        pr.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.max(np.abs(a - b)) <= 1e-5 * max(np.max(np.abs(b)), 1e-30)
+
+
 def test_autotuner_picks_and_caches(tmp_path):
     """The tuner sweeps launch shapes with the library's own event timers, caches the
     winners per shape, and a tuned context reproduces the default results to FP32
