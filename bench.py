@@ -262,9 +262,12 @@ def run_ours(args, rank, world, local):
     E, Pmix, _ = pr.probabilities()
 
     # ---- e2e through the public API with host buffers
-    q_host, qp_host = pr.state()
-    q_host = np.ascontiguousarray(q_host)
-    qp_host = np.ascontiguousarray(qp_host)
+    q_dev, qp_dev = pr.state()
+    # the step's inputs sit in pinned (page-locked) host memory
+    q_host = torch.empty(q_dev.shape, dtype=torch.float64, pin_memory=True).numpy()
+    qp_host = torch.empty(qp_dev.shape, dtype=torch.float64, pin_memory=True).numpy()
+    q_host[...] = q_dev
+    qp_host[...] = qp_dev
     e2e_steps = max(4, min(16, args.steps // 8))
     barrier()
     te0 = time.perf_counter()

@@ -343,8 +343,11 @@ int transform_upload(mw3_ctx* ctx, const double* src, const char* dst_name, bool
                                     (const DevBlock*)dptr(ctx, "blocks"), ctx->nblk, ctx->ng,
                                     ctx->ncol, ctx->stream));
   } else {
-    std::vector<float> f(src, src + n);
-    CK(cudaMemcpyAsync(dptr(ctx, "xfer"), f.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream));
+    // FP64 host values land in a device FP64 buffer and are narrowed on the device
+    if ((st = dalloc(ctx, "xfer64", n * 8))) return st;
+    CK(cudaMemcpyAsync(dptr(ctx, "xfer64"), src, n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    LK(launch_convert_d2f((const double*)dptr(ctx, "xfer64"), (float*)dptr(ctx, "xfer"), (long)n,
+                          ctx->stream));
     LK(launch_gamma_forward<float>((const float*)dptr(ctx, "xfer"), (float*)dptr(ctx, dst_name),
                                    (const float*)dptr(ctx, to_fbr ? "T" : "Tt"),
                                    (const DevBlock*)dptr(ctx, "blocks"), ctx->nblk, ctx->ng,
@@ -371,10 +374,11 @@ int transform_download(mw3_ctx* ctx, const char* src_name, double* dst) {
                                    (const float*)dptr(ctx, "Tt"),
                                    (const DevBlock*)dptr(ctx, "blocks"), ctx->nblk, ctx->ng,
                                    ctx->ncol, ctx->stream));
-    std::vector<float> f(n);
-    CK(cudaMemcpyAsync(f.data(), dptr(ctx, "xfer"), n * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    if ((st = dalloc(ctx, "xfer64", n * 8))) return st;
+    LK(launch_convert_f2d((const float*)dptr(ctx, "xfer"), (double*)dptr(ctx, "xfer64"), (long)n,
+                          ctx->stream));
+    CK(cudaMemcpyAsync(dst, dptr(ctx, "xfer64"), n * 8, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    for (size_t i = 0; i < n; ++i) dst[i] = f[i];
   }
   return MW3_OK;
 }

@@ -279,6 +279,23 @@ cudaError_t launch_sums_flush(const real* ph, const real* cut, long ncut_total, 
 
 __global__ void k_advance(long* d_iter, long n) { *d_iter += n; }
 
+// Precision conversion of a state vector on the device (host copies stay FP64).
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = (B)in[i];
+}
+
+cudaError_t launch_convert_d2f(const double* in, float* out, long n, cudaStream_t st) {
+  k_convert<double, float><<<1216, 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f2d(const float* in, double* out, long n, cudaStream_t st) {
+  k_convert<float, double><<<1216, 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_advance(long* d_iter, long n, cudaStream_t st) {
   k_advance<<<1, 1, 0, st>>>(d_iter, n);
   return cudaGetLastError();

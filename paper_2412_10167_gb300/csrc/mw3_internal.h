@@ -121,6 +121,8 @@ cudaError_t launch_sums_flush(const real* ph, const real* cut, long ncut_total, 
                               const long* accoff, long max_cols, double* acc, cudaStream_t st);
 
 cudaError_t launch_advance(long* d_iter, long n, cudaStream_t st);
+cudaError_t launch_convert_d2f(const double* in, float* out, long n, cudaStream_t st);
+cudaError_t launch_convert_f2d(const float* in, double* out, long n, cudaStream_t st);
 
 // Product-channel projection (mw3_products.cu): channels of one (J, Lambda', Omega').
 struct ProdGroup {

@@ -1141,14 +1141,21 @@ __global__ void __launch_bounds__(FL_THREADS) k_flush_tc(const float* __restrict
   if (ok) {
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     double* accJ = acc + accoff[iJ] + col;
-    for (int j0 = 0; j0 < FL_N; j0 += 4) {
-      float v[4];
-      tmem_ld4(tmem + lane_base + (uint32_t)j0, v);
-      if (!live) continue;
+    for (int j0 = 0; j0 < FL_N; j0 += 16) {   // 16 read-modify-writes in flight per thread
+      float v[16];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int u = 0; u < 4; ++u) tmem_ld4(tmem + lane_base + (uint32_t)(j0 + 4 * u), v + 4 * u);
+      if (!live) continue;
+      double o[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
         const int p = p0 + j0 + j;
-        if (p < nE2) accJ[(long)p * nc] += (double)v[j];
+        o[j] = p < nE2 ? accJ[(long)p * nc] : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int p = p0 + j0 + j;
+        if (p < nE2) accJ[(long)p * nc] = o[j] + (double)v[j];
       }
     }
   } else if (tid == 0) {
