@@ -357,18 +357,48 @@ __global__ void __launch_bounds__(256, kMinBlocks<T, R>) k_cols_w(
   T* tp = t + plane * (long)N * NR;
   constexpr int PER = (N * C + 255) / 256;
   constexpr int CH = PER < 8 ? PER : 8;                         // loads in flight per thread
-  for (int u0 = 0; u0 < PER; u0 += CH) {
-    T z[CH];
+  using V = typename Vec16<T>::type;
+  constexpr int VE = 16 / sizeof(T);
+  constexpr int NV = N * C / VE;                                // 16-byte vectors per tile
+  constexpr int PERV = (NV + 255) / 256;
+  constexpr int CHV = PERV < 8 ? PERV : 8;
+  // 16-byte vector loads when rows are vector-aligned (C is a multiple of VE; a vector
+  // is then entirely inside or outside the grid)
+  const bool vec = (NR % VE) == 0;
+  if (vec) {
+    for (int u0 = 0; u0 < PERV; u0 += CHV) {
+      V z[CHV];
 #pragma unroll
-    for (int u = 0; u < CH; ++u) {
-      const int e = threadIdx.x + 256 * (u0 + u);
-      const int kr = e / C, m = c0 + e % C;
-      z[u] = (e < N * C && m < NR) ? qp[(long)kr * NR + m] : (T)0;
+      for (int u = 0; u < CHV; ++u) {
+        const int e = threadIdx.x + 256 * (u0 + u);
+        const int kr = e / (C / VE), m = c0 + (e % (C / VE)) * VE;
+        z[u] = (e < NV && m < NR) ? *reinterpret_cast<const V*>(qp + (long)kr * NR + m) : V{};
+      }
+#pragma unroll
+      for (int u = 0; u < CHV; ++u) {
+        const int e = threadIdx.x + 256 * (u0 + u);
+        if (e < NV) {
+          T* dst = tile + (e / (C / VE)) * LD + (e % (C / VE)) * VE;
+          const T* zs = reinterpret_cast<const T*>(&z[u]);
+#pragma unroll
+          for (int v = 0; v < VE; ++v) dst[v] = zs[v];
+        }
+      }
     }
+  } else {
+    for (int u0 = 0; u0 < PER; u0 += CH) {
+      T z[CH];
 #pragma unroll
-    for (int u = 0; u < CH; ++u) {
-      const int e = threadIdx.x + 256 * (u0 + u);
-      if (e < N * C) tile[(e / C) * LD + e % C] = z[u];
+      for (int u = 0; u < CH; ++u) {
+        const int e = threadIdx.x + 256 * (u0 + u);
+        const int kr = e / C, m = c0 + e % C;
+        z[u] = (e < N * C && m < NR) ? qp[(long)kr * NR + m] : (T)0;
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int e = threadIdx.x + 256 * (u0 + u);
+        if (e < N * C) tile[(e / C) * LD + e % C] = z[u];
+      }
     }
   }
   __syncthreads();
@@ -401,19 +431,43 @@ __global__ void __launch_bounds__(256, kMinBlocks<T, R>) k_cols_w(
   for (int p = warp; p < C / 2; p += blockDim.x / 32)
     pair_kinetic<T, R>(tile + 2 * p, tile + 2 * p + 1, LD, lane, tb);
   __syncthreads();
-  for (int u0 = 0; u0 < PER; u0 += CH) {
-    T z[CH];
+  if (vec) {
+    for (int u0 = 0; u0 < PERV; u0 += CHV) {
+      V z[CHV];
 #pragma unroll
-    for (int u = 0; u < CH; ++u) {
-      const int e = threadIdx.x + 256 * (u0 + u);
-      const int kr = e / C, m = c0 + e % C;
-      z[u] = (e < N * C && m < NR) ? tp[(long)kr * NR + m] : (T)0;
+      for (int u = 0; u < CHV; ++u) {
+        const int e = threadIdx.x + 256 * (u0 + u);
+        const int kr = e / (C / VE), m = c0 + (e % (C / VE)) * VE;
+        z[u] = (e < NV && m < NR) ? *reinterpret_cast<const V*>(tp + (long)kr * NR + m) : V{};
+      }
+#pragma unroll
+      for (int u = 0; u < CHV; ++u) {
+        const int e = threadIdx.x + 256 * (u0 + u);
+        const int kr = e / (C / VE), m = c0 + (e % (C / VE)) * VE;
+        if (e < NV && m < NR) {
+          T* zs = reinterpret_cast<T*>(&z[u]);
+          const T* src = tile + kr * LD + (e % (C / VE)) * VE;
+#pragma unroll
+          for (int v = 0; v < VE; ++v) zs[v] += src[v];
+          *reinterpret_cast<V*>(tp + (long)kr * NR + m) = z[u];
+        }
+      }
     }
+  } else {
+    for (int u0 = 0; u0 < PER; u0 += CH) {
+      T z[CH];
 #pragma unroll
-    for (int u = 0; u < CH; ++u) {
-      const int e = threadIdx.x + 256 * (u0 + u);
-      const int kr = e / C, m = c0 + e % C;
-      if (e < N * C && m < NR) tp[(long)kr * NR + m] = z[u] + tile[kr * LD + e % C];
+      for (int u = 0; u < CH; ++u) {
+        const int e = threadIdx.x + 256 * (u0 + u);
+        const int kr = e / C, m = c0 + e % C;
+        z[u] = (e < N * C && m < NR) ? tp[(long)kr * NR + m] : (T)0;
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int e = threadIdx.x + 256 * (u0 + u);
+        const int kr = e / C, m = c0 + e % C;
+        if (e < N * C && m < NR) tp[(long)kr * NR + m] = z[u] + tile[kr * LD + e % C];
+      }
     }
   }
 }

@@ -100,6 +100,26 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
   for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Loads without their wait: several tensor-memory loads share one tcgen05.wait::ld, which
+// takes the destination registers as operands so that no use moves above it.
+__device__ __forceinline__ void tmem_ld4_issue(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld2_issue(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait8(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float* v) {
   uint32_t r[2];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
@@ -894,13 +914,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
         float ya[4] = {0, 0, 0, 0}, yb[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int Lp = 0; Lp < NE; ++Lp) {
-          float E[4], O[4];
-          tmem_ld4(tE(Lp) + lane_base + (uint32_t)(half * nq + s0), E);
-          tmem_ld4(tO(Lp) + lane_base + (uint32_t)(half * nq + s0), O);
+          uint32_t r[8];   // E (4), O (4)
+          tmem_ld4_issue(tE(Lp) + lane_base + (uint32_t)(half * nq + s0), r);
+          tmem_ld4_issue(tO(Lp) + lane_base + (uint32_t)(half * nq + s0), r + 4);
+          tmem_wait8(r);
 #pragma unroll
           for (int s = 0; s < 4; ++s) {
-            ya[s] += va[Lp][s0 + s] * (E[s] + O[s]);   // y[n]
-            yb[s] += vb[Lp][s0 + s] * (E[s] - O[s]);   // y[n']
+            const float E = __uint_as_float(r[s]), O = __uint_as_float(r[4 + s]);
+            ya[s] += va[Lp][s0 + s] * (E + O);   // y[n]
+            yb[s] += vb[Lp][s0 + s] * (E - O);   // y[n']
           }
         }
         float hs[4], ls[4], hd[4], ld[4];
@@ -947,27 +969,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
         const DevBlock Bb = a.blocks[b];
         const float* c = a.ck + (long)b * a.npts;
         for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 4) {
-          float we[2], wo[2], ce[2] = {0, 0}, co[2] = {0, 0};
-          tmem_ld2(tWe(L) + lane_base + (uint32_t)(i0 / 2), we);
-          tmem_ld2(tWo(L) + lane_base + (uint32_t)(i0 / 2), wo);
-          if (NE == 1) {
-            tmem_ld2(tCe + lane_base + (uint32_t)(i0 / 2), ce);
-            tmem_ld2(tCo + lane_base + (uint32_t)(i0 / 2), co);
-          }
-          if (!live) continue;
-          const float w[4] = {we[0], wo[0], we[1], wo[1]};
-          const float cr[4] = {ce[0], co[0], ce[1], co[1]};
+          // global and shared loads first, then the tensor-memory loads under one wait
           float cv[4], cu[4], cd[4], tv[4], pv[4];
 #pragma unroll
           for (int s = 0; s < 4; ++s) {
             const int i = i0 + s;
-            const bool in = i < nrow;
+            const bool in = live && i < nrow;
             const long off = (long)i * a.ncol + col;
-            cv[s] = in ? (NE == 1 ? cr[s] : __ldg(c + off)) : 0.0f;
+            cv[s] = (in && NE != 1) ? __ldg(c + off) : 0.0f;
             tv[s] = in ? (L == 0 ? ts[i * TC_M + m] : __ldg(a.t + (long)b * a.npts + off)) : 0.0f;
             pv[s] = (in && a.mode == 0) ? (L == 0 ? ps[i * TC_M + m] : __ldg(a.ckm1 + (long)b * a.npts + off)) : 0.0f;
             cu[s] = (in && Bb.up >= 0 && i >= 1) ? __ldg(a.ck + (long)Bb.up * a.npts + off - a.ncol) : 0.0f;
             cd[s] = (in && Bb.dn >= 0) ? __ldg(a.ck + (long)Bb.dn * a.npts + off + a.ncol) : 0.0f;
+          }
+          uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // w even, w odd, c even, c odd
+          tmem_ld2_issue(tWe(L) + lane_base + (uint32_t)(i0 / 2), r);
+          tmem_ld2_issue(tWo(L) + lane_base + (uint32_t)(i0 / 2), r + 2);
+          if (NE == 1) {
+            tmem_ld2_issue(tCe + lane_base + (uint32_t)(i0 / 2), r + 4);
+            tmem_ld2_issue(tCo + lane_base + (uint32_t)(i0 / 2), r + 6);
+          }
+          tmem_wait8(r);
+          if (!live) continue;
+          const float w[4] = {__uint_as_float(r[0]), __uint_as_float(r[2]), __uint_as_float(r[1]),
+                              __uint_as_float(r[3])};
+          if (NE == 1) {
+            cv[0] = __uint_as_float(r[4]);
+            cv[1] = __uint_as_float(r[6]);
+            cv[2] = __uint_as_float(r[5]);
+            cv[3] = __uint_as_float(r[7]);
           }
 #pragma unroll
           for (int s = 0; s < 4; ++s) {
