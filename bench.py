@@ -232,9 +232,10 @@ def run_ours(args, rank, world, local):
     nblk = 11
     npts = g["NR"] * g["nr"] * g["ngamma"]
 
+    from paper_2412_10167_gb300 import dist as mdist
+
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        mdist.barrier()
         torch.cuda.synchronize()
 
     # ---- mixed form: the headline
@@ -243,20 +244,19 @@ def run_ours(args, rank, world, local):
     kb = pr.get_tuning("kb")
     pr.kernel_times(enable=True)
     clk = ClockSampler(local)
+    # CUDA events on the library's stream (the stream its kernels are launched on)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
     barrier()
     clk.start()
-    t0 = time.perf_counter()
+    ev0.record(pr.stream)
     pr.propagate(args.steps)
+    ev1.record(pr.stream)
     barrier()
-    t1 = time.perf_counter()
     clocks = clk.stop()
     ktimes = pr.kernel_times()
     pr.kernel_times(enable=False)
-    elapsed = t1 - t0
-    if dist is not None:
-        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = mdist.max_over_ranks(ev0.elapsed_time(ev1) * 1e-3)
     value = world * args.steps / elapsed
     nchan = 0
     E, Pmix, _ = pr.probabilities()
@@ -276,18 +276,21 @@ def run_ours(args, rank, world, local):
         pr.propagate(1)
         _, Pe, _ = pr.probabilities()
     barrier()
-    te = time.perf_counter() - te0
+    te = mdist.max_over_ranks(time.perf_counter() - te0)   # wall clock: host copies included
     pr.close()
     del pr
 
     # ---- FP64 form on the same workload (shorter timed region)
     pf = mw3.Propagator(cfg, device=local, precision="fp64")
     pf.propagate(max(3, min(args.warmup, 8)))
+    fe0 = torch.cuda.Event(enable_timing=True)
+    fe1 = torch.cuda.Event(enable_timing=True)
     barrier()
-    tf0 = time.perf_counter()
+    fe0.record(pf.stream)
     pf.propagate(args.fp64_steps)
+    fe1.record(pf.stream)
     barrier()
-    tf = time.perf_counter() - tf0
+    tf = mdist.max_over_ranks(fe0.elapsed_time(fe1) * 1e-3)
     fp64_rate = world * args.fp64_steps / tf
     pf.close()
     del pf
@@ -356,7 +359,7 @@ def run_ours(args, rank, world, local):
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": clocks,
-        "e2e": {"value": e2e_steps / te, "unit": "steps/s", "h2d_bytes_per_step": 2 * vec_bytes,
+        "e2e": {"value": world * e2e_steps / te, "unit": "steps/s", "h2d_bytes_per_step": 2 * vec_bytes,
                 "d2h_bytes_per_step": 500 * 8 * 2},
         "cpu_baseline": cpu,
         "fp32_fma_peak_tflops": fp32_peak,

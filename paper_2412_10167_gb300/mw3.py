@@ -312,6 +312,11 @@ class Propagator:
 
     # -------------------------------------------------------------- queries
     @property
+    def stream(self):
+        """The torch stream the library's kernels are launched on (None without torch memory)."""
+        return self._stream
+
+    @property
     def shape(self):
         nb, npb = C.c_long(), C.c_long()
         _check(self.ctx, lib.mw3_sizes(self.ctx, C.byref(nb), C.byref(npb)))

@@ -25,6 +25,8 @@ def main(argv=None):
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--tuning", default=None, help="JSON dictionary of mw3_set_tuning keys")
+    ap.add_argument("--compare", action="store_true",
+                    help="also run the FP64 path and report max |dP| of the mixed form")
     args = ap.parse_args(argv)
     table = dict(W.CONFIGS)
     table.update(W.SMALL)
@@ -38,8 +40,27 @@ def main(argv=None):
     out = dict(config=cfg["name"], precision=args.precision, steps=args.steps,
                steps_per_s=args.steps / dt, iteration=pr.iteration,
                P_total_max=float(np.max(P)))
-    if cfg["analysis"].get("products"):
+    has_prod = bool(cfg["analysis"].get("products"))
+    if has_prod:
         out["P_products_max"] = float(np.max(pr.product_probabilities().sum(axis=(1, 2, 3))))
+    if args.compare:
+        Pp = pr.product_probabilities() if has_prod else None
+        _, _, Pin = pr.probabilities()
+        ref = mw3.Propagator(cfg, precision="fp64", tuning=tuning)
+        t0 = time.perf_counter()
+        ref.propagate(args.steps)
+        out["fp64_steps_per_s"] = args.steps / (time.perf_counter() - t0)
+        _, P64, Pin64 = ref.probabilities()
+        out["max_abs_dP"] = {"total": float(np.max(np.abs(P - P64))),
+                             "reactant_channels": float(np.max(np.abs(Pin - Pin64)))
+                             if Pin is not None else None}
+        out["max_P"] = {"total": float(np.max(np.abs(P64))),
+                        "reactant_channels": float(np.max(np.abs(Pin64))) if Pin64 is not None else None}
+        if has_prod:
+            Pp64 = ref.product_probabilities()
+            out["max_abs_dP"]["product_channels"] = float(np.max(np.abs(Pp - Pp64)))
+            out["max_P"]["product_channels"] = float(np.max(np.abs(Pp64)))
+        ref.close()
     pr.close()
     print(json.dumps(out))
 
