@@ -56,6 +56,12 @@ _PRODUCTS = dict(arrangement="AC+B", Rinf=6.5, rmin=0.5, rmax=4.5, nr=48, ngamma
                  vmax=3, jmax=15)
 _PRODUCTS_SMALL = dict(_PRODUCTS, nr=24, ngamma=12, vmax=2, jmax=6)
 
+# kminelastic: the real initial packet is half outgoing, and that half passes R_inf before
+# any scattered flux; reactant-channel sums start after it (iteration counts estimated from
+# the packet speed and the spectral half-width of each Hamiltonian).
+KMIN_C1 = 200
+KMIN = 300
+
 _PACKET = dict(R0=10.0, Gamma=0.25, Ecol_eV=0.6, v0=0, j0=0, omega0=0, elec0=0)
 
 # Config 1: H + DH(0,0), J = 0, FP64, 64 x 48 x 24 grid, 1500 iterations.
@@ -65,7 +71,7 @@ C1 = _cfg(
     J=[0], omega_max=0, nelec=1, packet=_PACKET,
     absorber=_absorber(14.0, 11.0, 10.0, 7.5),
     analysis=dict(rstar=6.0, E_lo_eV=0.3, E_hi_eV=1.5, nE=200, Rinf=10.5,
-                  vmax=3, jmax=15, kmin=0),
+                  vmax=3, jmax=15, kmin=KMIN_C1),
     steps=1500, precision="fp64")
 
 # Config 2: J = 10, Omega = 0..10 (11 Coriolis-coupled blocks), 256 x 192 x 96.
@@ -75,7 +81,7 @@ C2 = _cfg(
     J=[10], omega_max=10, nelec=1, packet=_PACKET,
     absorber=_absorber(16.0, 12.9, 12.0, 9.7),
     analysis=dict(rstar=6.0, E_lo_eV=0.3, E_hi_eV=1.5, nE=500, Rinf=11.5,
-                  vmax=3, jmax=15, kmin=0, products=dict(_PRODUCTS, Rinf=6.5)),
+                  vmax=3, jmax=15, kmin=KMIN, products=dict(_PRODUCTS, Rinf=6.5)),
     steps=12000, precision="mixed")
 
 # Config 3: two coupled diabatic states, J = 0, 5, ..., 30 with Omega_max = 15.
@@ -85,7 +91,7 @@ C3 = _cfg(
     J=list(range(0, 31, 5)), omega_max=15, nelec=2, packet=_PACKET,
     absorber=_absorber(16.0, 12.9, 12.0, 9.7),
     analysis=dict(rstar=6.0, E_lo_eV=0.2, E_hi_eV=1.6, nE=1000, Rinf=11.5,
-                  vmax=3, jmax=15, kmin=0, products=dict(_PRODUCTS, Rinf=6.5)),
+                  vmax=3, jmax=15, kmin=KMIN, products=dict(_PRODUCTS, Rinf=6.5)),
     steps=8000, precision="mixed", two_state=True)
 
 # Config 4: J = 40, Omega = 0..20 (21 blocks), 512 x 384 x 180.
@@ -95,7 +101,7 @@ C4 = _cfg(
     J=[40], omega_max=20, nelec=1, packet=_PACKET,
     absorber=_absorber(18.0, 14.5, 14.0, 11.3),
     analysis=dict(rstar=6.0, E_lo_eV=0.2, E_hi_eV=1.6, nE=1000, Rinf=11.5,
-                  vmax=3, jmax=15, kmin=0, products=dict(_PRODUCTS, Rinf=8.0)),
+                  vmax=3, jmax=15, kmin=KMIN, products=dict(_PRODUCTS, Rinf=8.0)),
     steps=30000, precision="mixed")
 
 # Config 5 (J-interpolation surrogate): the config-3 grid, single surface, trained on
@@ -124,17 +130,17 @@ def shrunk(base: dict, name: str, **over) -> dict:
 # Parity-sized copies: the oracle finishes them in seconds, and their sizes span
 # several tiles with ragged tails (radix 2/3/5 line lengths, odd gamma counts).
 C2_SMALL = shrunk(C2, "h_dh_j10_40x36x20", NR=40, nr=36, ngamma=20, steps=240, nE=64,
-                  products=dict(_PRODUCTS_SMALL, Rinf=6.5))
+                  kmin=60, products=dict(_PRODUCTS_SMALL, Rinf=6.5))
 C3_SMALL = shrunk(C3, "two_state_j0_5_10_24x20x12", NR=24, nr=20, ngamma=12,
-                  J=[0, 5, 10], omega_max=5, steps=160, nE=48,
+                  J=[0, 5, 10], omega_max=5, steps=160, nE=48, kmin=40,
                   products=dict(_PRODUCTS_SMALL, Rinf=6.5))
 C4_SMALL = shrunk(C4, "h_dh_j40_60x48x30", NR=60, nr=48, ngamma=30, omega_max=4,
-                  steps=80, nE=40, products=dict(_PRODUCTS_SMALL, Rinf=8.0))
+                  steps=80, nE=40, kmin=20, products=dict(_PRODUCTS_SMALL, Rinf=8.0))
 SMALL = {"c1": C1, "c2s": C2_SMALL, "c3s": C3_SMALL, "c4s": C4_SMALL}
 
 # Line lengths outside the library's compile-time FFT sizes (runtime-plan kernels).
 C_ODD = shrunk(C2, "h_dh_j3_30x18x10", NR=30, nr=18, ngamma=10, J=[3], omega_max=3, steps=60,
-               nE=16)
+               nE=16, kmin=10)
 
 
 def rng(seed: int) -> np.random.Generator:
