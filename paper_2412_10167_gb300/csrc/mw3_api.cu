@@ -86,7 +86,8 @@ struct mw3_ctx {
   Tuning tune{4, 32, 32, 1, 0, 1, 2, 1};
   int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
-  int kh = 0;          // parity-split operand size (0: not applicable)
+  int kh = 0;          // parity-split operand size, resident form (0: not applicable)
+  int kh4 = 0;         // parity-split operand size, streamed form (0: not applicable)
   bool tc_ok = false;  // the tensor-core angular step supports this grid
   int tc_user = -1;    // explicit "use_tc" setting (-1: default = on when supported)
 
@@ -696,8 +697,10 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
   // tensor-core operands: T^Omega and its transpose, padded to kp x kp, split into a
   // TF32-rounded high part and the exact FP32 remainder
   ctx->kp = ((ng + 15) / 16) * 16;
+  ctx->kh = angular_tc3_kh(ng, ctx->nelec);
+  ctx->kh4 = angular_tc4_kh(ng, ctx->nelec);
   // (16-byte asynchronous copies of tile rows need ncol % 4 == 0)
-  ctx->tc_ok = (ctx->precision == MW3_MIXED) && ctx->kp <= kTcMaxKp &&
+  ctx->tc_ok = (ctx->precision == MW3_MIXED) && (ctx->kp <= kTcMaxKp || ctx->kh4 > 0) &&
                (ctx->ncol + 127) / 128 <= 65535 && ctx->ncol % 4 == 0;
   ctx->tune.use_tc = (ctx->tc_ok && ctx->tc_user != 0) ? 1 : 0;
   if (ctx->tc_ok) {
@@ -725,9 +728,9 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
       return st;
     // parity-split operands (n_gamma even): with h = n_gamma / 2, n < h, e/o = even/odd row
     //   G1e[n][e] = T[2e][n], G1o[n][o] = T[2o+1][n], G2e[e][n] = T[2e][n], G2o[o][n] = T[2o+1][n]
-    ctx->kh = angular_tc3_kh(ng, ctx->nelec);
-    if (ctx->kh > 0) {
-      const int kh = ctx->kh, h = ng / 2;
+    const int khp = ctx->kh > 0 ? ctx->kh : ctx->kh4;
+    if (khp > 0) {
+      const int kh = khp, h = ng / 2;
       std::vector<float> ph(nom * 4 * kh * kh, 0.f), pl(ph.size(), 0.f);
       for (size_t om = 0; om < nom; ++om)
         for (int r = 0; r < kh; ++r)
@@ -1380,10 +1383,14 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
     a.Tp_hi = (const float*)dptr(ctx, "Tp_hi");
     a.Tp_lo = (const float*)dptr(ctx, "Tp_lo");
     a.persistent = 0;
-    if (ctx->tune.tc_persist >= 2 && ctx->kh > 0)
+    if (ctx->tune.tc_persist >= 2 && ctx->kh > 0) {
       a.persistent = 2;
-    else if (ctx->tune.tc_persist >= 1 && angular_tc2_supported(ctx->kp, ctx->nelec))
+    } else if (ctx->kh4 > 0 && (ctx->kp > kTcMaxKp || ctx->tune.tc_persist >= 2)) {
+      a.persistent = 3;   // the only tensor-core form beyond kTcMaxKp
+      a.kh = ctx->kh4;
+    } else if (ctx->tune.tc_persist >= 1 && angular_tc2_supported(ctx->kp, ctx->nelec)) {
       a.persistent = 1;
+    }
     a.nsm = ctx->nsm;
     int tc = 32;
     while (tc < 2 * ctx->nelec * ctx->kp) tc *= 2;

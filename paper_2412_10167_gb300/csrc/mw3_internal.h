@@ -170,7 +170,8 @@ struct TcArgs {
   int ng, kp, NR, nelec, mode, ntiles, tmem_cols;
   int ngroups;          // (J, Omega) groups
   int persistent;       // 1: one CTA per SM over a range of (group, tile) pairs;
-                        // 2: the same with the parity-split operands (Tp_*)
+                        // 2: the same with the parity-split operands (Tp_*);
+                        // 3: parity-split with the operand matrices streamed (kh 64..96)
   int nsm;              // CTAs of the persistent forms
   int kh;               // parity-split operand size: n_gamma / 2 rounded up to 16
   const float* Tp_hi;   // [omega][4][kh][kh]: G1e, G1o, G2e, G2o (see mw3_tc.cu)
@@ -182,6 +183,7 @@ cudaError_t launch_flush_tc(const float* ph, const float* cut, long ncut_total, 
                             int nE, const long* colbase, const long* ncols, const long* accoff,
                             long max_cols, double* acc, int* err, cudaStream_t st);
 int angular_tc3_kh(int ng, int nelec);   // 0 when the parity-split form does not apply
+int angular_tc4_kh(int ng, int nelec);   // 0 when the streamed parity-split form does not apply
 size_t angular_tc_smem(int kp);
 cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
                               double* norm_out, cudaStream_t st);

@@ -1047,6 +1047,264 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
   }
 }
 
+
+// ============================================================ streamed parity-split form
+// For n_gamma from 98 to 192 (kh = 64..96) the four half matrices do not fit in shared
+// memory together: they stream through two buffers in the order G1e, G1o, G2e, G2o, each
+// copied with cp.async while the MMAs of the previous one run, and the even and odd
+// operand halves pass through tensor memory one after the other. One electronic state.
+// Tensor-memory columns (units of kh): A hi/lo [0, 2), E 2, O 3, w_even 4; the potential
+// step leaves S in A and D in O's columns; w_odd goes to E's columns.
+template <int KH>
+constexpr size_t tc4_smem() { return 4 * (size_t)KH * KH * 4 + 16 + 16 * sizeof(double) + 64; }
+
+// 16-byte asynchronous copy of a kh x kh (hi, lo) pair, row-major, into core-matrix layout
+__device__ __forceinline__ void load_b_async(const float* __restrict__ hi,
+                                             const float* __restrict__ lo, unsigned char* Bhi,
+                                             unsigned char* Blo, int kh) {
+  const int nq = kh * kh / 4;
+  for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+    const int row = e / (kh / 4);
+    const int k4 = (e - row * (kh / 4)) * 4;
+    const uint32_t off = cm_off(row, k4, kh);
+    cp_async16(Bhi + off, hi + (long)row * kh + k4);
+    cp_async16(Blo + off, lo + (long)row * kh + k4);
+  }
+}
+
+template <int KH>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc4(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  constexpr int kh = KH;
+  constexpr size_t bb = (size_t)KH * KH * 4;
+  auto Bbuf = [&](int buf, int lo) { return sm + (size_t)(2 * buf + lo) * bb; };
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 4 * bb);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  double* red = reinterpret_cast<double*>(mbar + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3;
+  const int half = warp >> 2;
+  const int m = q * 32 + lane;
+  constexpr int nq = kh / 4;
+  constexpr int ncb = kh / 2;
+  const uint32_t mb = smem_u32(mbar);
+  const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+  const uint32_t idesc = idesc_tf32(TC_M, kh);
+  const int ng = a.ng, h = ng / 2;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(a.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const uint32_t tA_hi = tmem, tA_lo = tmem + kh, tE = tmem + 2 * kh, tO = tmem + 3 * kh,
+                 tWe = tmem + 4 * kh, tWo = tE;
+
+  const long total = (long)a.ngroups * a.ntiles;
+  const long f0 = (long)blockIdx.x * total / gridDim.x;
+  const long f1 = (long)(blockIdx.x + 1) * total / gridDim.x;
+  auto omega_of = [&](long f) { return a.blocks[(int)(f / a.ntiles)].omega; };
+  auto issue_b = [&](long f, int k) {   // matrix k (G1e, G1o, G2e, G2o) of tile f -> buffer k & 1
+    if (f < f1) {
+      const long base = ((long)omega_of(f) * 4 + k) * kh * kh;
+      load_b_async(a.Tp_hi + base, a.Tp_lo + base, Bbuf(k & 1, 0), Bbuf(k & 1, 1), kh);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // MMA of matrix k of the current tile: its copy landed in every thread, visible to the
+  // tensor core, and every operand store to tensor memory is complete
+  uint32_t phase = 0;
+  bool ok = true;
+  auto run_mma = [&](uint32_t dtmem, int k) {
+    tmem_st_wait();
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      issue_split_gemm_ta(dtmem, tA_hi, tA_lo, Bbuf(k & 1, 0), Bbuf(k & 1, 1), kh, idesc);
+      mma_commit(mb);
+    }
+    ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  };
+  issue_b(f0, 0);
+  issue_b(f0, 1);
+
+  for (long f = f0; f < f1 && ok; ++f) {
+    const int g = (int)(f / a.ntiles);
+    const int tile = (int)(f - (long)g * a.ntiles);
+    const DevBlock B0 = a.blocks[g];
+    const int nrow = B0.nrow;
+    const long col = (long)tile * TC_M + m;
+    const bool live = col < a.ncol;
+    const int kr = live ? (int)(col / a.NR) : 0;
+    const int mR = live ? (int)(col - (long)kr * a.NR) : 0;
+    const float* c = a.ck + (long)g * a.npts;
+
+    // ---- GEMM 1: E = c_even G1e, O = c_odd G1o (the operand halves in turn)
+    for (int par = 0; par < 2 && ok; ++par) {
+#pragma unroll 2
+      for (int s0 = 0; s0 < nq; s0 += 4) {
+        float hh[4], ll[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int i = 2 * (half * nq + s0 + s) + par;
+          const float x = (live && i < nrow) ? __ldg(c + (long)i * a.ncol + col) : 0.0f;
+          hh[s] = tf32_hi(x);
+          ll[s] = x - hh[s];
+        }
+        const uint32_t cc = lane_base + (uint32_t)(half * nq + s0);
+        tmem_st4(tA_hi + cc, hh);
+        tmem_st4(tA_lo + cc, ll);
+      }
+      run_mma(par == 0 ? tE : tO, par);
+      issue_b(f, 2 + par);                       // the buffer just used takes G2e / G2o
+    }
+    if (!ok) break;
+
+    // ---- potential: y = V u at the node pairs; S = y(n) + y(n') into A, D = y(n) - y(n')
+    // into O's columns
+#pragma unroll 2
+    for (int s0 = 0; s0 < nq; s0 += 4) {
+      float va[4], vb[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int n = half * nq + s0 + s;
+        const bool in = live && n < h;
+        va[s] = in ? __ldg(a.V + (long)n * a.ncol + col) : 0.0f;
+        vb[s] = in ? __ldg(a.V + (long)(ng - 1 - n) * a.ncol + col) : 0.0f;
+      }
+      uint32_t r[8];
+      tmem_ld4_issue(tE + lane_base + (uint32_t)(half * nq + s0), r);
+      tmem_ld4_issue(tO + lane_base + (uint32_t)(half * nq + s0), r + 4);
+      tmem_wait8(r);
+      float hs[4], ls[4], dd[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const float E = __uint_as_float(r[s]), O = __uint_as_float(r[4 + s]);
+        const float ya = va[s] * (E + O), yb = vb[s] * (E - O);
+        const float S = ya + yb;
+        dd[s] = ya - yb;
+        hs[s] = tf32_hi(S);
+        ls[s] = S - hs[s];
+      }
+      const uint32_t cc = lane_base + (uint32_t)(half * nq + s0);
+      tmem_st4(tA_hi + cc, hs);
+      tmem_st4(tA_lo + cc, ls);
+      tmem_st4(tO + cc, dd);
+    }
+    run_mma(tWe, 2);
+    issue_b(f + 1, 0);                           // next tile's G1e
+    if (!ok) break;
+#pragma unroll 2
+    for (int s0 = 0; s0 < nq; s0 += 4) {
+      uint32_t r[4];
+      tmem_ld4_issue(tO + lane_base + (uint32_t)(half * nq + s0), r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
+      float hd[4], ld[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const float Dd = __uint_as_float(r[s]);
+        hd[s] = tf32_hi(Dd);
+        ld[s] = Dd - hd[s];
+      }
+      const uint32_t cc = lane_base + (uint32_t)(half * nq + s0);
+      tmem_st4(tA_hi + cc, hd);
+      tmem_st4(tA_lo + cc, ld);
+    }
+    run_mma(tWo, 3);
+    issue_b(f + 1, 1);                           // next tile's G1o
+    if (!ok) break;
+
+    // ---- epilogue
+    double ss = 0.0;
+    {
+      const DevJ J = a.dj[B0.iJ];
+      const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
+      const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
+      const float frk = live ? a.fr[kr] : 0.0f;
+      const float fRm = live ? a.fR[mR] : 0.0f;
+      const int b = g;
+      for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 4) {
+        float cv[4], cu[4], cd[4], tv[4], pv[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int i = i0 + s;
+          const bool in = live && i < nrow;
+          const long off = (long)i * a.ncol + col;
+          cv[s] = in ? __ldg(c + off) : 0.0f;
+          tv[s] = in ? __ldg(a.t + (long)b * a.npts + off) : 0.0f;
+          pv[s] = (in && a.mode == 0) ? __ldg(a.ckm1 + (long)b * a.npts + off) : 0.0f;
+          cu[s] = (in && B0.up >= 0 && i >= 1) ? __ldg(a.ck + (long)B0.up * a.npts + off - a.ncol) : 0.0f;
+          cd[s] = (in && B0.dn >= 0) ? __ldg(a.ck + (long)B0.dn * a.npts + off + a.ncol) : 0.0f;
+        }
+        uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        tmem_ld2_issue(tWe + lane_base + (uint32_t)(i0 / 2), r);
+        tmem_ld2_issue(tWo + lane_base + (uint32_t)(i0 / 2), r + 2);
+        tmem_wait8(r);
+        if (!live) continue;
+        const float w[4] = {__uint_as_float(r[0]), __uint_as_float(r[2]), __uint_as_float(r[1]),
+                            __uint_as_float(r[3])};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int i = i0 + s;
+          if (i >= a.ng) break;
+          const long idx = (long)b * a.npts + (long)i * a.ncol + col;
+          if (i >= nrow) {
+            if (a.mode == 1) a.out[idx] = 0.0f; else a.ckm1[idx] = 0.0f;
+            continue;
+          }
+          const float gg = fminf(fRm, cf[4 * a.ng + i]);
+          const float aa = fminf(cf[i] * frk, a.erot) + gg * cf[a.ng + i];
+          float hh = w[s] + aa * cv[s] + tv[s];
+          hh += gg * cf[2 * a.ng + i] * cu[s];
+          hh += gg * cf[3 * a.ng + i] * cd[s];
+          const float hs = hh * (float)J.invdE - (float)J.e0s * cv[s];
+          if (a.mode == 1) {
+            a.out[idx] = hs;
+          } else {
+            const float nv = D * (a.alpha * hs - a.beta * D * pv[s]);
+            a.ckm1[idx] = nv;
+            ss += (double)nv * (double)nv;
+          }
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+    if (lane == 0) red[warp] = ss;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      double s2 = 0;
+      for (int w2 = 0; w2 < TC_THREADS / 32; ++w2) s2 += red[w2];
+      if (a.npart) a.npart[(long)g * a.ntiles + tile] = s2;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (!ok && tid == 0) atomicExch(a.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols));
+  }
+}
+
 // out[iJ] = sum over the (J, Omega) groups of J and their tiles: 256 threads per J take
 // strided partial sums of the contiguous range, then a fixed-order tree (deterministic).
 __global__ void __launch_bounds__(256) k_tc_norm_final(const double* __restrict__ npart,
@@ -1288,6 +1546,35 @@ static cudaError_t launch_tc3_ne(const TcArgs& a, cudaStream_t st) {
   }
 }
 
+template <int KH>
+static cudaError_t launch_tc4_inst(const TcArgs& args, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_angular_tc4<KH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr = true;
+  }
+  const long total = (long)args.ngroups * args.ntiles;
+  const unsigned grid = (unsigned)std::min<long>(total, args.nsm);
+  k_angular_tc4<KH><<<grid, TC_THREADS, tc4_smem<KH>(), st>>>(args);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_tc4(const TcArgs& a, cudaStream_t st) {
+  switch (a.kh) {
+    case 64: return launch_tc4_inst<64>(a, st);
+    case 80: return launch_tc4_inst<80>(a, st);
+    case 96: return launch_tc4_inst<96>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int angular_tc4_kh(int ng, int nelec) {
+  if (ng % 2 || nelec != 1) return 0;
+  const int kh = ((ng / 2 + 15) / 16) * 16;
+  return (kh > 48 && kh <= 96) ? kh : 0;
+}
+
 int angular_tc3_kh(int ng, int nelec) {
   if (ng % 2) return 0;
   const int kh = ((ng / 2 + 15) / 16) * 16;
@@ -1316,7 +1603,9 @@ static cudaError_t launch_tc_ne(const TcArgs& a, dim3 grid, cudaStream_t st) {
 cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
                               double* norm_out, cudaStream_t st) {
   cudaError_t e;
-  if (args.persistent == 2) {
+  if (args.persistent == 3) {
+    e = launch_tc4(args, st);
+  } else if (args.persistent == 2) {
     e = (args.nelec == 1) ? launch_tc3_ne<1>(args, st) : launch_tc3_ne<2>(args, st);
   } else if (args.persistent) {
     e = (args.nelec == 1) ? launch_tc2_ne<1>(args, st) : launch_tc2_ne<2>(args, st);

@@ -265,13 +265,21 @@ def test_divergence_guard():
     pr.close()
 
 
-@pytest.mark.parametrize("name", ["c1", "c2s", "c3s", "c4s"])
+# n_gamma beyond the resident parity-split form (streamed operand matrices, kh = 64 and 96)
+TC_CASES = dict(W.SMALL,
+                ng100=W.shrunk(W.C2, "ng100", NR=40, nr=36, ngamma=100, J=[2], omega_max=2,
+                               steps=40, nE=16, kmin=10),
+                ng180=W.shrunk(W.C4, "ng180", NR=24, nr=20, ngamma=180, J=[1], omega_max=1,
+                               steps=40, nE=16, kmin=10))
+
+
+@pytest.mark.parametrize("name", list(TC_CASES))
 def test_tensor_core_step_matches_cuda_core_step(name):
     """Mixed precision: the fused tcgen05 angular step (split-TF32), in its persistent
     parity-split form, its persistent tensor-memory-operand form and its one-tile-per-CTA
     form, agrees with the CUDA-core FP32 step to FP32 rounding after 40 iterations, and
     with the oracle."""
-    cfg = W.SMALL[name]
+    cfg = TC_CASES[name]
     qs = []
     for tc, persist in ((1, 2), (1, 1), (1, 0), (0, 0)):
         pr = mw3().Propagator(cfg, precision="mixed", tuning={"use_tc": tc, "tc_persist": persist})
