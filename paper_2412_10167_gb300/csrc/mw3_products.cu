@@ -54,20 +54,16 @@ __global__ void __launch_bounds__(1024) k_prod_nodes(const real* __restrict__ q,
     const real* src = q + (long)b * ng * plane + (long)idx[v * 8 + 4 + c] * NR + idx[v * 8 + a];
     const real* P = pl + ((long)v * ltop + warp) * ng;
     const int nrow = ng - warp;            // angular functions of helicity Omega = warp
-    real acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // eight independent chains: loads in flight
+    real s0 = 0, s1 = 0, s2 = 0, s3 = 0;   // four independent chains: loads in flight
     int i = sub;
-    for (; i + 14 < nrow; i += 16) {
-      real x[8], p[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        x[u] = src[(long)(i + 2 * u) * plane];
-        p[u] = P[i + 2 * u];
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u] += p[u] * x[u];
+    for (; i + 6 < nrow; i += 8) {
+      s0 += P[i] * src[(long)i * plane];
+      s1 += P[i + 2] * src[(long)(i + 2) * plane];
+      s2 += P[i + 4] * src[(long)(i + 4) * plane];
+      s3 += P[i + 6] * src[(long)(i + 6) * plane];
     }
-    for (; i < nrow; i += 2) acc[0] += P[i] * src[(long)i * plane];
-    real s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    for (; i < nrow; i += 2) s0 += P[i] * src[(long)i * plane];
+    real s = (s0 + s1) + (s2 + s3);
     s *= w[v * 8 + a] * w[v * 8 + 4 + c];
     s = warp_sum(s);
     if (lane == 0) us[warp] = s;

@@ -831,6 +831,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
     __syncthreads();
 
     // ------------------------------------------------------------ GEMM 1 per state
+    float v1a[nq], v1b[nq];   // one state: V(n), V(n') prefetched during GEMM 1
     for (int L = 0; L < NE && ok; ++L) {
       const float* c = a.ck + (long)(b0 + L) * a.npts;
 #pragma unroll
@@ -889,6 +890,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
         issue_split_gemm_ta(tO(L), tAo_hi, tAo_lo, Gm(1, 0), Gm(1, 1), kh, idesc);
         mma_commit(mb);
       }
+      if (NE == 1) {
+        // the potential at this thread's node pairs, loaded while the MMAs run
+#pragma unroll
+        for (int s2 = 0; s2 < nq; ++s2) {
+          const int n = half * nq + s2;
+          const bool in = live && n < h;
+          v1a[s2] = in ? __ldg(a.V + (long)n * a.ncol + col) : 0.0f;
+          v1b[s2] = in ? __ldg(a.V + (long)(ng - 1 - n) * a.ncol + col) : 0.0f;
+        }
+      }
       ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
       phase ^= 1;
       asm volatile("tcgen05.fence::after_thread_sync;");
@@ -905,8 +916,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
         for (int s2 = 0; s2 < nq; ++s2) {
           const int n = half * nq + s2;
           const bool in = live && n < h;
-          va[Lp][s2] = in ? __ldg(V + (long)n * a.ncol + col) : 0.0f;
-          vb[Lp][s2] = in ? __ldg(V + (long)(ng - 1 - n) * a.ncol + col) : 0.0f;
+          if (NE == 1) {
+            va[Lp][s2] = v1a[s2];
+            vb[Lp][s2] = v1b[s2];
+          } else {
+            va[Lp][s2] = in ? __ldg(V + (long)n * a.ncol + col) : 0.0f;
+            vb[Lp][s2] = in ? __ldg(V + (long)(ng - 1 - n) * a.ncol + col) : 0.0f;
+          }
         }
       }
 #pragma unroll
