@@ -261,10 +261,13 @@ int mw3_product_probabilities(mw3_ctx* ctx, double* P);
  *   "cols_tile"  R columns per CTA of the r-direction kinetic kernel (even, 2..64)
  *   "use_graph"  0/1: replay full chunks as CUDA graphs
  *   "use_tc"     0/1: tensor-core gamma transform in MW3_MIXED
- *   "tc_persist" 0: one tile per CTA; 1: persistent form of the tensor-core angular step
+ *   "tc_persist" form of the tensor-core angular step: 0 one tile per CTA; 1 persistent
  *                (one CTA per SM, T^Omega resident in shared memory, operands in tensor
- *                memory); 2 (default): persistent with the Gauss-Legendre parity split
- *                (even ngamma <= 96; otherwise 1 is used)
+ *                memory); 2 persistent with the Gauss-Legendre parity split (even
+ *                ngamma <= 96); 4 (default) the parity split walked tile-major with the
+ *                Coriolis neighbours kept on chip (one electronic state); each falls back
+ *                to the next lower form that applies. Even ngamma 98..192 always use the
+ *                streamed parity split.
  *   "flush_tc"   0/1: energy-sum flush on the tensor cores in MW3_MIXED (split-TF32 within
  *                a flush, FP64 accumulators); default 1
  *   "kin_warp"   0/1: warp-register FFT kinetic kernels for line lengths 32 R

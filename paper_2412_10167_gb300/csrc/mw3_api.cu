@@ -83,7 +83,7 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0, 1, 2, 1};
+  Tuning tune{4, 32, 32, 1, 0, 1, 4, 1};
   int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   int kh = 0;          // parity-split operand size, resident form (0: not applicable)
@@ -1383,7 +1383,9 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
     a.Tp_hi = (const float*)dptr(ctx, "Tp_hi");
     a.Tp_lo = (const float*)dptr(ctx, "Tp_lo");
     a.persistent = 0;
-    if (ctx->tune.tc_persist >= 2 && ctx->kh > 0) {
+    if (ctx->tune.tc_persist >= 4 && ctx->kh > 0 && ctx->nelec == 1) {
+      a.persistent = 4;
+    } else if (ctx->tune.tc_persist >= 2 && ctx->kh > 0) {
       a.persistent = 2;
     } else if (ctx->kh4 > 0 && (ctx->kp > kTcMaxKp || ctx->tune.tc_persist >= 2)) {
       a.persistent = 3;   // the only tensor-core form beyond kTcMaxKp
@@ -1756,7 +1758,7 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
   } else if (k == "flush_tc") {
     ctx->tune.flush_tc = v != 0;
   } else if (k == "tc_persist") {
-    if (v < 0 || v > 2) return ctx->fail(MW3_ERR_BAD_ARG, "tc_persist must be 0, 1 or 2");
+    if (v < 0 || v > 4) return ctx->fail(MW3_ERR_BAD_ARG, "tc_persist must be in 0..4");
     ctx->tune.tc_persist = (int)v;
   } else if (k == "use_tc") {
     if (v != 0 && ctx->precision != MW3_MIXED)

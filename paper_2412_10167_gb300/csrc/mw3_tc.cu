@@ -1321,6 +1321,316 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc4(TcArgs a) {
   }
 }
 
+
+// ================================================================ tile-major form
+// One electronic state, kh <= 48. Each CTA walks a contiguous range of (tile, block) units
+// in tile-major order, so consecutive units are the helicities Omega, Omega + 1, ... of one
+// (r, R) tile. The Coriolis neighbours then come from on-chip copies: c^(Omega-1) is the
+// raw c tile the previous unit left in tensor memory, c^(Omega+1) is the next unit's c tile,
+// already copied into shared memory for its GEMM 1. The potential of the tile stays in
+// registers across its units. The four half matrices change with Omega and stream through
+// two shared-memory buffers (G1e, G1o, G2e, G2o), each copy overlapping earlier MMAs.
+// Tensor-memory columns (units of kh): A even hi/lo 0, 1, A odd hi/lo 2, 3, E 4, O 5 (w even,
+// w odd after GEMM 2), raw c tiles (even rows, odd rows) in two slots at 6, 7 and 8, 9.
+template <int KH>
+constexpr size_t tc5_smem() {
+  return 4 * (size_t)KH * KH * 4 + 3 * (size_t)2 * KH * TC_M * 4 + 16 + 16 * sizeof(double) + 64;
+}
+
+template <int KH>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  constexpr int kh = KH;
+  constexpr size_t bb = (size_t)KH * KH * 4;
+  auto Bbuf = [&](int buf, int lo) { return sm + (size_t)(2 * buf + lo) * bb; };
+  float* cs = reinterpret_cast<float*>(sm + 4 * bb);   // [2 kh][TC_M] c of the next unit
+  float* ts = cs + 2 * kh * TC_M;                       // t of this unit
+  float* ps = ts + 2 * kh * TC_M;                       // c_(k-1) of this unit
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(ps + 2 * kh * TC_M);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  double* red = reinterpret_cast<double*>(mbar + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3;
+  const int half = warp >> 2;
+  const int m = q * 32 + lane;
+  constexpr int nq = kh / 4;
+  constexpr int ncb = kh / 2;
+  const uint32_t mb = smem_u32(mbar);
+  const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+  const uint32_t idesc = idesc_tf32(TC_M, kh);
+  const int ng = a.ng, h = ng / 2;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(a.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  auto col_of = [&](int unit) { return tmem + (uint32_t)(unit * kh); };
+  const uint32_t tAe_hi = col_of(0), tAe_lo = col_of(1), tAo_hi = col_of(2), tAo_lo = col_of(3);
+  const uint32_t tE = col_of(4), tO = col_of(5);
+
+  const int ngr = a.ngroups;
+  const long total = (long)ngr * a.ntiles;
+  const long u0 = (long)blockIdx.x * total / gridDim.x;
+  const long u1 = (long)(blockIdx.x + 1) * total / gridDim.x;
+  auto unit_tile = [&](long u) { return (int)(u / ngr); };
+  auto unit_block = [&](long u) { return (int)(u - (long)(u / ngr) * ngr); };
+  auto stage = [&](float* dst, const float* src, int nrow, long col0) {
+    const int nch = nrow * (TC_M / 4);
+    for (int e = tid; e < nch; e += TC_THREADS) {
+      const int i = e / (TC_M / 4);
+      const int c4 = (e - i * (TC_M / 4)) * 4;
+      if (col0 + c4 < a.ncol) cp_async16(dst + i * TC_M + c4, src + (long)i * a.ncol + col0 + c4);
+    }
+  };
+  auto issue_b = [&](long u, int k) {   // matrix k of unit u -> buffer k & 1
+    if (u < u1) {
+      const long base = ((long)a.blocks[unit_block(u)].omega * 4 + k) * kh * kh;
+      load_b_async(a.Tp_hi + base, a.Tp_lo + base, Bbuf(k & 1, 0), Bbuf(k & 1, 1), kh);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  uint32_t phase = 0;
+  bool ok = true;
+  // the MMAs of matrix k: its copy complete (all but the `pending` newest groups), visible to
+  // the tensor core, operand stores to tensor memory complete
+  auto run_mma = [&](uint32_t dt, uint32_t ahi, uint32_t alo, int k, int pending) {
+    tmem_st_wait();
+    if (pending >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else asm volatile("cp.async.wait_group 1;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      issue_split_gemm_ta(dt, ahi, alo, Bbuf(k & 1, 0), Bbuf(k & 1, 1), kh, idesc);
+      mma_commit(mb);
+    }
+    ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  };
+
+  if (u0 < u1) {
+    const int b = unit_block(u0);
+    stage(cs, a.ck + (long)b * a.npts, a.blocks[b].nrow, (long)unit_tile(u0) * TC_M);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  issue_b(u0, 0);
+  issue_b(u0, 1);
+
+  float va[nq], vb[nq];
+  int vtile = -1;
+  int slot = 0;             // tensor-memory slot of this unit's raw c
+  long prev_u = -2;         // last unit processed by this CTA
+  for (long u = u0; u < u1 && ok; ++u) {
+    const int tile = unit_tile(u);
+    const int b = unit_block(u);
+    const DevBlock B0 = a.blocks[b];
+    const int nrow = B0.nrow;
+    const long col0 = (long)tile * TC_M;
+    const long col = col0 + m;
+    const bool live = col < a.ncol;
+    const int kr = live ? (int)(col / a.NR) : 0;
+    const int mR = live ? (int)(col - (long)kr * a.NR) : 0;
+    const uint32_t tC = col_of(6 + 2 * slot), tCp = col_of(6 + 2 * (slot ^ 1));
+    // c^(Omega-1) in tensor memory when the previous unit was that block of this tile
+    const bool dn_chip = B0.dn >= 0 && prev_u == u - 1 && B0.dn == b - 1 && tile == unit_tile(u - 1);
+    // c^(Omega+1) in shared memory when the next unit is that block of this tile
+    const bool up_chip = B0.up >= 0 && B0.up == b + 1 && u + 1 < u1 && unit_tile(u + 1) == tile;
+
+    __syncthreads();   // previous unit's readers of ts, ps, cs and tensor memory are done
+    asm volatile("cp.async.wait_group 2;" ::: "memory");   // this unit's c tile
+    __syncthreads();
+    // ---- GEMM 1 operands (both parities) and the raw c tile, from shared memory
+#pragma unroll
+    for (int s0 = 0; s0 < nq; s0 += 4) {
+      float he[4], le[4], ho[4], lo[4], re[4], ro[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int e = half * nq + s0 + s;
+        const int ie = 2 * e, io = 2 * e + 1;
+        const float xe = (live && ie < nrow) ? cs[ie * TC_M + m] : 0.0f;
+        const float xo = (live && io < nrow) ? cs[io * TC_M + m] : 0.0f;
+        re[s] = xe;
+        ro[s] = xo;
+        he[s] = tf32_hi(xe);
+        le[s] = xe - he[s];
+        ho[s] = tf32_hi(xo);
+        lo[s] = xo - ho[s];
+      }
+      const uint32_t cc = lane_base + (uint32_t)(half * nq + s0);
+      tmem_st4(tAe_hi + cc, he);
+      tmem_st4(tAe_lo + cc, le);
+      tmem_st4(tAo_hi + cc, ho);
+      tmem_st4(tAo_lo + cc, lo);
+      tmem_st4(tC + cc, re);
+      tmem_st4(tC + kh + cc, ro);
+    }
+    __syncthreads();   // cs is free: the next unit's c (this unit's upper neighbour), t, c_(k-1)
+    if (u + 1 < u1) {
+      const int bn = unit_block(u + 1);
+      stage(cs, a.ck + (long)bn * a.npts, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
+    }
+    stage(ts, a.t + (long)b * a.npts, nrow, col0);
+    if (a.mode == 0) stage(ps, a.ckm1 + (long)b * a.npts, nrow, col0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // pending now: G1e(u), G1o(u), [c(u+1), t, p]
+    if (tile != vtile) {
+#pragma unroll
+      for (int s2 = 0; s2 < nq; ++s2) {
+        const int n = half * nq + s2;
+        const bool in = live && n < h;
+        va[s2] = in ? __ldg(a.V + (long)n * a.ncol + col) : 0.0f;
+        vb[s2] = in ? __ldg(a.V + (long)(ng - 1 - n) * a.ncol + col) : 0.0f;
+      }
+      vtile = tile;
+    }
+    run_mma(tE, tAe_hi, tAe_lo, 0, 2);           // E = c_even G1e
+    issue_b(u, 2);                                // pending: G1o, [c t p], G2e
+    run_mma(tO, tAo_hi, tAo_lo, 1, 2);           // O = c_odd G1o
+    issue_b(u, 3);                                // pending: [c t p], G2e, G2o
+    if (!ok) break;
+
+    // ---- potential: S = y(n) + y(n') into A even, D = y(n) - y(n') into A odd
+#pragma unroll
+    for (int s0 = 0; s0 < nq; s0 += 4) {
+      uint32_t r[8];
+      tmem_ld4_issue(tE + lane_base + (uint32_t)(half * nq + s0), r);
+      tmem_ld4_issue(tO + lane_base + (uint32_t)(half * nq + s0), r + 4);
+      tmem_wait8(r);
+      float hs[4], ls[4], hd[4], ld[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const float E = __uint_as_float(r[s]), O = __uint_as_float(r[4 + s]);
+        const float ya = va[s0 + s] * (E + O), yb = vb[s0 + s] * (E - O);
+        const float S = ya + yb, Dd = ya - yb;
+        hs[s] = tf32_hi(S);
+        ls[s] = S - hs[s];
+        hd[s] = tf32_hi(Dd);
+        ld[s] = Dd - hd[s];
+      }
+      const uint32_t cc = lane_base + (uint32_t)(half * nq + s0);
+      tmem_st4(tAe_hi + cc, hs);
+      tmem_st4(tAe_lo + cc, ls);
+      tmem_st4(tAo_hi + cc, hd);
+      tmem_st4(tAo_lo + cc, ld);
+    }
+    run_mma(tE, tAe_hi, tAe_lo, 2, 1);           // w_even = S G2e (also completes [c t p])
+    issue_b(u + 1, 0);                            // pending: G2o, G1e(u+1)
+    run_mma(tO, tAo_hi, tAo_lo, 3, 1);           // w_odd = D G2o
+    issue_b(u + 1, 1);                            // pending: G1e(u+1), G1o(u+1)
+    if (!ok) break;
+
+    // ---- epilogue: w, c, c^(Omega-1) from tensor memory; c^(Omega+1), t, c_(k-1) from shared
+    double ss = 0.0;
+    {
+      const DevJ J = a.dj[B0.iJ];
+      const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
+      const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
+      const float frk = live ? a.fr[kr] : 0.0f;
+      const float fRm = live ? a.fR[mR] : 0.0f;
+      for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 4) {
+        float cu[4], cd[4], tv[4], pv[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int i = i0 + s;
+          const bool in = live && i < nrow;
+          const long off = (long)i * a.ncol + col;
+          tv[s] = in ? ts[i * TC_M + m] : 0.0f;
+          pv[s] = (in && a.mode == 0) ? ps[i * TC_M + m] : 0.0f;
+          // row i of block Omega+1 is its row i - 1 (j = Omega + i)
+          cu[s] = (in && B0.up >= 0 && i >= 1)
+                      ? (up_chip ? cs[(i - 1) * TC_M + m] : __ldg(a.ck + (long)B0.up * a.npts + off - a.ncol))
+                      : 0.0f;
+          cd[s] = (in && B0.dn >= 0 && !dn_chip) ? __ldg(a.ck + (long)B0.dn * a.npts + off + a.ncol) : 0.0f;
+        }
+        uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // w even, w odd, c even, c odd
+        tmem_ld2_issue(tE + lane_base + (uint32_t)(i0 / 2), r);
+        tmem_ld2_issue(tO + lane_base + (uint32_t)(i0 / 2), r + 2);
+        tmem_ld2_issue(tC + lane_base + (uint32_t)(i0 / 2), r + 4);
+        tmem_ld2_issue(tC + kh + lane_base + (uint32_t)(i0 / 2), r + 6);
+        tmem_wait8(r);
+        if (dn_chip) {
+          // row i of block Omega-1 is its row i + 1: rows i0+1..i0+4 = (odd, even, odd, even)
+          // of the previous unit's raw tile, columns i0/2 (odd), i0/2 + 1 (even), i0/2 + 1 (odd),
+          // i0/2 + 2 (even)
+          uint32_t p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+          tmem_ld2_issue(tCp + kh + lane_base + (uint32_t)(i0 / 2), p);         // odd  i0/2, i0/2+1
+          tmem_ld2_issue(tCp + lane_base + (uint32_t)(i0 / 2 + 1), p + 2);      // even i0/2+1, i0/2+2
+          tmem_wait8(p);
+          const float pr4[4] = {__uint_as_float(p[0]), __uint_as_float(p[2]), __uint_as_float(p[1]),
+                                __uint_as_float(p[3])};
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int i = i0 + s;
+            cd[s] = (live && i < nrow && i + 1 < ng) ? pr4[s] : 0.0f;
+          }
+        }
+        if (!live) continue;
+        const float w[4] = {__uint_as_float(r[0]), __uint_as_float(r[2]), __uint_as_float(r[1]),
+                            __uint_as_float(r[3])};
+        const float cv[4] = {__uint_as_float(r[4]), __uint_as_float(r[6]), __uint_as_float(r[5]),
+                             __uint_as_float(r[7])};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int i = i0 + s;
+          if (i >= a.ng) break;
+          const long idx = (long)b * a.npts + (long)i * a.ncol + col;
+          if (i >= nrow) {
+            if (a.mode == 1) a.out[idx] = 0.0f; else a.ckm1[idx] = 0.0f;
+            continue;
+          }
+          const float gg = fminf(fRm, cf[4 * a.ng + i]);
+          const float aa = fminf(cf[i] * frk, a.erot) + gg * cf[a.ng + i];
+          float hh = w[s] + aa * cv[s] + tv[s];
+          hh += gg * cf[2 * a.ng + i] * cu[s];
+          hh += gg * cf[3 * a.ng + i] * cd[s];
+          const float hs = hh * (float)J.invdE - (float)J.e0s * cv[s];
+          if (a.mode == 1) {
+            a.out[idx] = hs;
+          } else {
+            const float nv = D * (a.alpha * hs - a.beta * D * pv[s]);
+            a.ckm1[idx] = nv;
+            ss += (double)nv * (double)nv;
+          }
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+    if (lane == 0) red[warp] = ss;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      double s2 = 0;
+      for (int w2 = 0; w2 < TC_THREADS / 32; ++w2) s2 += red[w2];
+      if (a.npart) a.npart[(long)b * a.ntiles + tile] = s2;
+    }
+    prev_u = u;
+    slot ^= 1;
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (!ok && tid == 0) atomicExch(a.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols));
+  }
+}
+
 // out[iJ] = sum over the (J, Omega) groups of J and their tiles: 256 threads per J take
 // strided partial sums of the contiguous range, then a fixed-order tree (deterministic).
 __global__ void __launch_bounds__(256) k_tc_norm_final(const double* __restrict__ npart,
@@ -1585,6 +1895,29 @@ static cudaError_t launch_tc4(const TcArgs& a, cudaStream_t st) {
   }
 }
 
+template <int KH>
+static cudaError_t launch_tc5_inst(const TcArgs& args, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_angular_tc5<KH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr = true;
+  }
+  const long total = (long)args.ngroups * args.ntiles;
+  const unsigned grid = (unsigned)std::min<long>(total, args.nsm);
+  k_angular_tc5<KH><<<grid, TC_THREADS, tc5_smem<KH>(), st>>>(args);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_tc5(const TcArgs& a, cudaStream_t st) {
+  switch (a.kh) {
+    case 16: return launch_tc5_inst<16>(a, st);
+    case 32: return launch_tc5_inst<32>(a, st);
+    case 48: return launch_tc5_inst<48>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 int angular_tc4_kh(int ng, int nelec) {
   if (ng % 2 || nelec != 1) return 0;
   const int kh = ((ng / 2 + 15) / 16) * 16;
@@ -1619,7 +1952,9 @@ static cudaError_t launch_tc_ne(const TcArgs& a, dim3 grid, cudaStream_t st) {
 cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
                               double* norm_out, cudaStream_t st) {
   cudaError_t e;
-  if (args.persistent == 3) {
+  if (args.persistent == 4) {
+    e = launch_tc5(args, st);
+  } else if (args.persistent == 3) {
     e = launch_tc4(args, st);
   } else if (args.persistent == 2) {
     e = (args.nelec == 1) ? launch_tc3_ne<1>(args, st) : launch_tc3_ne<2>(args, st);

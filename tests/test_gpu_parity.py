@@ -275,21 +275,21 @@ TC_CASES = dict(W.SMALL,
 
 @pytest.mark.parametrize("name", list(TC_CASES))
 def test_tensor_core_step_matches_cuda_core_step(name):
-    """Mixed precision: the fused tcgen05 angular step (split-TF32), in its persistent
-    parity-split form, its persistent tensor-memory-operand form and its one-tile-per-CTA
-    form, agrees with the CUDA-core FP32 step to FP32 rounding after 40 iterations, and
-    with the oracle."""
+    """Mixed precision: the fused tcgen05 angular step (split-TF32) in each of its forms —
+    tile-major with on-chip Coriolis neighbours, persistent parity-split (resident or
+    streamed operands), persistent tensor-memory-operand, one tile per CTA — agrees with
+    the CUDA-core FP32 step to FP32 rounding after 40 iterations, and with the oracle."""
     cfg = TC_CASES[name]
     qs = []
-    for tc, persist in ((1, 2), (1, 1), (1, 0), (0, 0)):
+    for tc, persist in ((1, 4), (1, 2), (1, 1), (1, 0), (0, 0)):
         pr = mw3().Propagator(cfg, precision="mixed", tuning={"use_tc": tc, "tc_persist": persist})
         assert pr.get_tuning("use_tc") == tc
         pr.propagate(40)
         qs.append(pr.state()[0])
         pr.close()
     ref = oracle_run(name, cfg, 40)
-    for q in qs[:3]:
-        rel = np.linalg.norm(q - qs[3]) / np.linalg.norm(qs[3])
+    for q in qs[:4]:
+        rel = np.linalg.norm(q - qs[4]) / np.linalg.norm(qs[4])
         assert rel < 2e-5, rel
         rel_o = np.linalg.norm(q - ref["q"]) / np.linalg.norm(ref["q"])
         assert rel_o < 2e-5, rel_o
