@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
   }
 
   // ---------------------------------------------------------- epilogue
-  double ss = 0.0;
+  float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
   if (ok) {
     const DevJ J = a.dj[B0.iJ];
     const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
@@ -422,13 +422,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
           } else {
             const float nv = D * (a.alpha * hs - a.beta * D * pv[s]);
             a.ckm1[idx] = nv;
-            ss += (double)nv * (double)nv;
+            ssf = fmaf(nv, nv, ssf);
           }
         }
       }
     }
   }
   // norm partial of this CTA (fixed-order reduction)
+  double ss = (double)ssf;
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
   if (lane == 0) red[warp] = ss;
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -631,7 +632,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc2(TcArgs a) {
     }
 
     // ------------------------------------------------------------ epilogue
-    double ss = 0.0;
+    float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
     if (ok) {
       const DevJ J = a.dj[B0.iJ];
       const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
@@ -679,13 +680,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc2(TcArgs a) {
             } else {
               const float nv = D * (a.alpha * hs - a.beta * D * pv[s]);
               a.ckm1[idx] = nv;
-              ss += (double)nv * (double)nv;
+              ssf = fmaf(nv, nv, ssf);
             }
           }
         }
       }
     }
     // norm partial of this tile (the same fixed-order reduction as the one-tile form)
+    double ss = (double)ssf;
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
     if (lane == 0) red[warp] = ss;
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -973,7 +975,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
     __syncthreads();
 
     // ------------------------------------------------------------ epilogue
-    double ss = 0.0;
+    float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
     if (ok) {
       const DevJ J = a.dj[B0.iJ];
       const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
@@ -1035,12 +1037,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
             } else {
               const float nv = D * (a.alpha * hs - a.beta * D * pv[s]);
               a.ckm1[idx] = nv;
-              ss += (double)nv * (double)nv;
+              ssf = fmaf(nv, nv, ssf);
             }
           }
         }
       }
     }
+    double ss = (double)ssf;
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
     if (lane == 0) red[warp] = ss;
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1246,7 +1249,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc4(TcArgs a) {
     if (!ok) break;
 
     // ---- epilogue
-    double ss = 0.0;
+    float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
     {
       const DevJ J = a.dj[B0.iJ];
       const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
@@ -1294,11 +1297,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc4(TcArgs a) {
           } else {
             const float nv = D * (a.alpha * hs - a.beta * D * pv[s]);
             a.ckm1[idx] = nv;
-            ss += (double)nv * (double)nv;
+            ssf = fmaf(nv, nv, ssf);
           }
         }
       }
     }
+    double ss = (double)ssf;
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
     if (lane == 0) red[warp] = ss;
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1533,7 +1537,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     if (!ok) break;
 
     // ---- epilogue: w, c, c^(Omega-1) from tensor memory; c^(Omega+1), t, c_(k-1) from shared
-    double ss = 0.0;
+    float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
     {
       const DevJ J = a.dj[B0.iJ];
       const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
@@ -1602,11 +1606,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
           } else {
             const float nv = D * (a.alpha * hs - a.beta * D * pv[s]);
             a.ckm1[idx] = nv;
-            ss += (double)nv * (double)nv;
+            ssf = fmaf(nv, nv, ssf);
           }
         }
       }
     }
+    double ss = (double)ssf;
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
     if (lane == 0) red[warp] = ss;
     asm volatile("tcgen05.fence::before_thread_sync;");
