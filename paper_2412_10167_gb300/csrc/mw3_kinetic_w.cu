@@ -11,6 +11,8 @@
 // stores stay coalesced (row tiles for R, [nr x C] column tiles for r).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "mw3_internal.h"
 
 namespace mw3 {
@@ -278,8 +280,18 @@ struct Vec16<double> {
   using type = double2;
 };
 
-// R direction: CTA of 8 warps = 16 consecutive rows of length N (8 pairs), moved
-// between global and shared memory with 16-byte vector accesses.
+// R direction, persistent: each CTA loads the FFT tables once and walks blocks of 16
+// consecutive rows of length N (8 warps, one line pair each) with stride gridDim.x. The next
+// block's rows are copied into the second shared buffer with cp.async while this block's
+// transforms run; results leave with 16-byte vector stores (live rows only).
+template <typename T>
+__device__ __forceinline__ void cp_async16_ca(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+
 template <typename T, int R>
 __global__ void __launch_bounds__(256, kMinBlocks<T, R>) k_rows_w(const T* __restrict__ q, T* __restrict__ t,
                                                 long nrows, const cpx<T>* __restrict__ twg,
@@ -291,45 +303,49 @@ __global__ void __launch_bounds__(256, kMinBlocks<T, R>) k_rows_w(const T* __res
   constexpr int ROWS = 16;
   using V = typename Vec16<T>::type;
   constexpr int VE = 16 / sizeof(T);          // elements per vector
-  __shared__ WTables<T, R> tb;
-  __shared__ __align__(16) T tile[ROWS * N];
+  constexpr int NV = ROWS * N / VE;           // vectors per block of rows
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WTables<T, R>& tb = *reinterpret_cast<WTables<T, R>*>(smem_raw);
+  T* tiles = reinterpret_cast<T*>(smem_raw + ((sizeof(WTables<T, R>) + 15) / 16) * 16);  // [2][ROWS * N]
   __shared__ int live[ROWS];
-  const long row0 = (long)blockIdx.x * ROWS;
-  if (threadIdx.x < ROWS) {
-    const long row = row0 + threadIdx.x;
-    const long plane = row / nr;
-    live[threadIdx.x] = row < nrows && (int)(plane % ng) < blocks[plane / ng].nrow;
-  }
   load_tables<T, R>(tb, twg, phg, lamg);
-  const long nvalid = min((long)ROWS, nrows - row0) * N / VE;   // whole rows: N % VE == 0
-  const V* qv = reinterpret_cast<const V*>(q + row0 * N);
-  V* sv = reinterpret_cast<V*>(tile);
-  constexpr int NV = ROWS * N / VE;                             // vectors per CTA
-  constexpr int PER = (NV + 255) / 256;
-  {
-    V z[PER];                                                   // all loads in flight first
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int e = threadIdx.x + 256 * u;
-      z[u] = (e < NV && e < nvalid) ? qv[e] : V{};
+  const long nrb = (nrows + ROWS - 1) / ROWS;
+  auto prefetch = [&](long rb, int buf) {
+    if (rb < nrb) {
+      const long row0 = rb * ROWS;
+      const long nvalid = min((long)ROWS, nrows - row0) * N / VE;
+      const T* src = q + row0 * N;
+      T* dst = tiles + buf * ROWS * N;
+      for (int e = threadIdx.x; e < nvalid; e += blockDim.x)
+        cp_async16_ca<T>(dst + (long)e * VE, src + (long)e * VE);
     }
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int e = threadIdx.x + 256 * u;
-      if (e < NV) sv[e] = z[u];
-    }
-  }
-  __syncthreads();
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // a pair never straddles planes (nr is even), so one flag covers both rows
-  if (live[2 * warp]) pair_kinetic<T, R>(tile + 2 * warp * N, tile + (2 * warp + 1) * N, 1, lane, tb);
-  __syncthreads();
-  V* tv = reinterpret_cast<V*>(t + row0 * N);
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const int e = threadIdx.x + 256 * u;
-    if (e < NV && e < nvalid && live[(e * VE) / N]) tv[e] = sv[e];
+  int buf = 0;
+  prefetch(blockIdx.x, 0);
+  for (long rb = blockIdx.x; rb < nrb; rb += gridDim.x, buf ^= 1) {
+    __syncthreads();                              // the other buffer's last readers are done
+    prefetch(rb + gridDim.x, buf ^ 1);
+    const long row0 = rb * ROWS;
+    if (threadIdx.x < ROWS) {
+      const long row = row0 + threadIdx.x;
+      const long plane = row / nr;
+      live[threadIdx.x] = row < nrows && (int)(plane % ng) < blocks[plane / ng].nrow;
+    }
+    asm volatile("cp.async.wait_group 1;" ::: "memory");   // this block's rows
+    __syncthreads();
+    T* tile = tiles + buf * ROWS * N;
+    // a pair never straddles planes (nr is even), so one flag covers both rows
+    if (live[2 * warp]) pair_kinetic<T, R>(tile + 2 * warp * N, tile + (2 * warp + 1) * N, 1, lane, tb);
+    __syncthreads();
+    const long nvalid = min((long)ROWS, nrows - row0) * N / VE;
+    const V* sv = reinterpret_cast<const V*>(tile);
+    V* tv = reinterpret_cast<V*>(t + row0 * N);
+    for (int e = threadIdx.x; e < NV; e += blockDim.x)
+      if (e < nvalid && live[(e * VE) / N]) tv[e] = sv[e];
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // r direction: one CTA = one (block, gamma) plane, columns [c0, c0 + C); N = nr.
@@ -483,9 +499,21 @@ bool rows_w(const T* q, T* t, long nrows, const void* tw, const void* ph, const 
   if constexpr (!kWarpSupported<T, R>) {
     return false;
   } else {
-    const unsigned grid = (unsigned)((nrows + 15) / 16);
-    k_rows_w<T, R><<<grid, 256, 0, st>>>(q, t, nrows, static_cast<const cpx<T>*>(tw),
-                                         static_cast<const cpx<T>*>(ph), lam, blocks, ng, nr);
+    constexpr int N = 32 * R;
+    const size_t sm = ((sizeof(WTables<T, R>) + 15) / 16) * 16 + 2 * 16 * (size_t)N * sizeof(T);
+    static bool attr = false;
+    static int nsm = 0;
+    if (!attr) {
+      cudaFuncSetAttribute(k_rows_w<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      attr = true;
+    }
+    const long nrb = (nrows + 15) / 16;
+    const unsigned grid = (unsigned)std::min<long>(nrb, (long)std::max(nsm, 1) * kMinBlocks<T, R>);
+    k_rows_w<T, R><<<grid, 256, sm, st>>>(q, t, nrows, static_cast<const cpx<T>*>(tw),
+                                          static_cast<const cpx<T>*>(ph), lam, blocks, ng, nr);
     *err = cudaGetLastError();
     return true;
   }

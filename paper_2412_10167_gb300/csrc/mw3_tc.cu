@@ -357,6 +357,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
   float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
   if (ok) {
     const DevJ J = a.dj[B0.iJ];
+    const float invdE = (float)J.invdE, e0s = (float)J.e0s;   // once, not per row
     const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
     const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
     const float frk = live ? a.fr[kr] : 0.0f;
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
           float h = w[s] + aa * cv[s] + tv[s];
           h += g * cf[2 * a.ng + i] * cu[s];
           h += g * cf[3 * a.ng + i] * cd[s];
-          const float hs = h * (float)J.invdE - (float)J.e0s * cv[s];
+          const float hs = h * invdE - e0s * cv[s];
           if (a.mode == 1) {
             a.out[idx] = hs;
           } else {
@@ -635,6 +636,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc2(TcArgs a) {
     float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
     if (ok) {
       const DevJ J = a.dj[B0.iJ];
+      const float invdE = (float)J.invdE, e0s = (float)J.e0s;   // once, not per row
       const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
       const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
       const float frk = live ? a.fr[kr] : 0.0f;
@@ -674,7 +676,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc2(TcArgs a) {
             float h = w[s] + aa * cv[s] + tv[s];
             h += gg * cf[2 * a.ng + i] * cu[s];
             h += gg * cf[3 * a.ng + i] * cd[s];
-            const float hs = h * (float)J.invdE - (float)J.e0s * cv[s];
+            const float hs = h * invdE - e0s * cv[s];
             if (a.mode == 1) {
               a.out[idx] = hs;
             } else {
@@ -978,6 +980,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
     float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
     if (ok) {
       const DevJ J = a.dj[B0.iJ];
+      const float invdE = (float)J.invdE, e0s = (float)J.e0s;   // once, not per row
       const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
       const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
       const float frk = live ? a.fr[kr] : 0.0f;
@@ -1031,7 +1034,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
             float hh = w[s] + aa * cv[s] + tv[s];
             hh += gg * cf[2 * a.ng + i] * cu[s];
             hh += gg * cf[3 * a.ng + i] * cd[s];
-            const float hs = hh * (float)J.invdE - (float)J.e0s * cv[s];
+            const float hs = hh * invdE - e0s * cv[s];
             if (a.mode == 1) {
               a.out[idx] = hs;
             } else {
@@ -1252,6 +1255,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc4(TcArgs a) {
     float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
     {
       const DevJ J = a.dj[B0.iJ];
+      const float invdE = (float)J.invdE, e0s = (float)J.e0s;   // once, not per row
       const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
       const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
       const float frk = live ? a.fr[kr] : 0.0f;
@@ -1291,7 +1295,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc4(TcArgs a) {
           float hh = w[s] + aa * cv[s] + tv[s];
           hh += gg * cf[2 * a.ng + i] * cu[s];
           hh += gg * cf[3 * a.ng + i] * cd[s];
-          const float hs = hh * (float)J.invdE - (float)J.e0s * cv[s];
+          const float hs = hh * invdE - e0s * cv[s];
           if (a.mode == 1) {
             a.out[idx] = hs;
           } else {
@@ -1540,6 +1544,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
     {
       const DevJ J = a.dj[B0.iJ];
+      const float invdE = (float)J.invdE, e0s = (float)J.e0s;   // once, not per row
       const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
       const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
       const float frk = live ? a.fr[kr] : 0.0f;
@@ -1600,7 +1605,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
           float hh = w[s] + aa * cv[s] + tv[s];
           hh += gg * cf[2 * a.ng + i] * cu[s];
           hh += gg * cf[3 * a.ng + i] * cd[s];
-          const float hs = hh * (float)J.invdE - (float)J.e0s * cv[s];
+          const float hs = hh * invdE - e0s * cv[s];
           if (a.mode == 1) {
             a.out[idx] = hs;
           } else {
