@@ -495,11 +495,20 @@ __global__ void __launch_bounds__(256, kMinBlocks<T, R>) k_cols_w(
 // unit's q tile into the second buffer, both overlapping this unit's cut, transforms and
 // update. q tiles are [N][C + 1] (padded for the column access of the transforms), the t
 // tile [N][C].
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(smem_dst)),
-               "l"(gsrc)
-               : "memory");
+// asynchronous copy of one element (4 or 8 bytes)
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
+  if constexpr (sizeof(T) == 4) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gsrc)
+                 : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gsrc)
+                 : "memory");
+  }
 }
 
 template <typename T, int R, int C>
@@ -531,7 +540,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<T, R>) k_cols_wp(
       T* dst = qtiles + buf * N * LD;
       for (int e = threadIdx.x; e < N * C; e += blockDim.x) {
         const int kr = e / C, c = e % C;
-        if (c0 + c < NR) cp_async4(dst + kr * LD + c, qp + (long)kr * NR + c0 + c);
+        if (c0 + c < NR) cp_async_elem<T>(dst + kr * LD + c, qp + (long)kr * NR + c0 + c);
       }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");

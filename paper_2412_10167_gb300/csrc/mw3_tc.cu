@@ -1401,27 +1401,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
       if (col0 + c4 < a.ncol) cp_async16(dst + i * TC_M + c4, src + (long)i * a.ncol + col0 + c4);
     }
   };
-  auto issue_b = [&](long u, int k) {   // matrix k of unit u -> buffer k & 1
+  // matrices k0 (buffer 0) and k0 + 1 (buffer 1) of unit u, as one copy group
+  auto issue_b2 = [&](long u, int k0) {
     if (u < u1) {
-      const long base = ((long)a.blocks[unit_block(u)].omega * 4 + k) * kh * kh;
-      load_b_async(a.Tp_hi + base, a.Tp_lo + base, Bbuf(k & 1, 0), Bbuf(k & 1, 1), kh);
+      const long om = a.blocks[unit_block(u)].omega;
+      for (int k = k0; k < k0 + 2; ++k) {
+        const long base = (om * 4 + k) * kh * kh;
+        load_b_async(a.Tp_hi + base, a.Tp_lo + base, Bbuf(k & 1, 0), Bbuf(k & 1, 1), kh);
+      }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   uint32_t phase = 0;
   bool ok = true;
-  // the MMAs of matrix k: its copy complete (all but the `pending` newest groups), visible to
-  // the tensor core, operand stores to tensor memory complete
-  auto run_mma = [&](uint32_t dt, uint32_t ahi, uint32_t alo, int k, int pending) {
+  // both parities' MMAs of one GEMM (even: A even x buffer 0, odd: A odd x buffer 1) under
+  // one commit: the copies complete (all but the `pending` newest groups), visible to the
+  // tensor core, operand stores to tensor memory complete
+  auto run_mma2 = [&](uint32_t de, uint32_t dodd, int pending) {
     tmem_st_wait();
-    if (pending >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
-    else asm volatile("cp.async.wait_group 1;" ::: "memory");
+    if (pending >= 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      issue_split_gemm_ta(dt, ahi, alo, Bbuf(k & 1, 0), Bbuf(k & 1, 1), kh, idesc);
+      issue_split_gemm_ta(de, tAe_hi, tAe_lo, Bbuf(0, 0), Bbuf(0, 1), kh, idesc);
+      issue_split_gemm_ta(dodd, tAo_hi, tAo_lo, Bbuf(1, 0), Bbuf(1, 1), kh, idesc);
       mma_commit(mb);
     }
     ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
@@ -1434,8 +1440,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     stage(cs, a.ck + (long)b * a.npts, a.blocks[b].nrow, (long)unit_tile(u0) * TC_M);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
-  issue_b(u0, 0);
-  issue_b(u0, 1);
+  issue_b2(u0, 0);
 
   float va[nq], vb[nq];
   int vtile = -1;
@@ -1458,7 +1463,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     const bool up_chip = B0.up >= 0 && B0.up == b + 1 && u + 1 < u1 && unit_tile(u + 1) == tile;
 
     __syncthreads();   // previous unit's readers of ts, ps, cs and tensor memory are done
-    asm volatile("cp.async.wait_group 2;" ::: "memory");   // this unit's c tile
+    asm volatile("cp.async.wait_group 1;" ::: "memory");   // this unit's c tile
     __syncthreads();
     // ---- GEMM 1 operands (both parities) and the raw c tile, from shared memory
 #pragma unroll
@@ -1493,7 +1498,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     stage(ts, a.t + (long)b * a.npts, nrow, col0);
     if (a.mode == 0) stage(ps, a.ckm1 + (long)b * a.npts, nrow, col0);
     asm volatile("cp.async.commit_group;" ::: "memory");
-    // pending now: G1e(u), G1o(u), [c(u+1), t, p]
+    // pending now: [G1e G1o](u), [c(u+1) t p]
     if (tile != vtile) {
 #pragma unroll
       for (int s2 = 0; s2 < nq; ++s2) {
@@ -1504,10 +1509,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
       }
       vtile = tile;
     }
-    run_mma(tE, tAe_hi, tAe_lo, 0, 2);           // E = c_even G1e
-    issue_b(u, 2);                                // pending: G1o, [c t p], G2e
-    run_mma(tO, tAo_hi, tAo_lo, 1, 2);           // O = c_odd G1o
-    issue_b(u, 3);                                // pending: [c t p], G2e, G2o
+    run_mma2(tE, tO, 1);                          // E = c_even G1e, O = c_odd G1o
+    issue_b2(u, 2);                               // pending: [c t p], [G2e G2o]
     if (!ok) break;
 
     // ---- potential: S = y(n) + y(n') into A even, D = y(n) - y(n') into A odd
@@ -1534,10 +1537,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
       tmem_st4(tAo_hi + cc, hd);
       tmem_st4(tAo_lo + cc, ld);
     }
-    run_mma(tE, tAe_hi, tAe_lo, 2, 1);           // w_even = S G2e (also completes [c t p])
-    issue_b(u + 1, 0);                            // pending: G2o, G1e(u+1)
-    run_mma(tO, tAo_hi, tAo_lo, 3, 1);           // w_odd = D G2o
-    issue_b(u + 1, 1);                            // pending: G1e(u+1), G1o(u+1)
+    run_mma2(tE, tO, 0);                          // w_even = S G2e, w_odd = D G2o; [c t p] done
+    issue_b2(u + 1, 0);                           // pending: [G1e G1o](u+1)
     if (!ok) break;
 
     // ---- epilogue: w, c, c^(Omega-1) from tensor memory; c^(Omega+1), t, c_(k-1) from shared
