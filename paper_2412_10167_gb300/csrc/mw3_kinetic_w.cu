@@ -489,133 +489,6 @@ __global__ void __launch_bounds__(256, kMinBlocks<T, R>) k_cols_w(
 }
 
 
-// r direction, persistent (rows of 16-byte vectors, NR % (16 / sizeof(T)) == 0): each CTA
-// loads the tables once and walks the live (plane, column tile) units with stride
-// gridDim.x. For each unit the t tile is copied in asynchronously at its start and the next
-// unit's q tile into the second buffer, both overlapping this unit's cut, transforms and
-// update. q tiles are [N][C + 1] (padded for the column access of the transforms), the t
-// tile [N][C].
-// asynchronous copy of one element (4 or 8 bytes)
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
-  if constexpr (sizeof(T) == 4) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                     (uint32_t)__cvta_generic_to_shared(smem_dst)),
-                 "l"(gsrc)
-                 : "memory");
-  } else {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
-                     (uint32_t)__cvta_generic_to_shared(smem_dst)),
-                 "l"(gsrc)
-                 : "memory");
-  }
-}
-
-template <typename T, int R, int C>
-__global__ void __launch_bounds__(256, kMinBlocks<T, R>) k_cols_wp(
-    const T* __restrict__ q, T* __restrict__ t, int NR, const cpx<T>* __restrict__ twg,
-    const cpx<T>* __restrict__ phg, const T* __restrict__ lamg, int ng, long nunits, int ntc,
-    const T* __restrict__ wpsi, const T* __restrict__ wdpsi, T* __restrict__ cut,
-    const DevBlock* __restrict__ blocks, const int* __restrict__ ncut_J, int m_inf,
-    T* __restrict__ qcol) {
-  constexpr int N = 32 * R;
-  constexpr int LD = C + 1;
-  constexpr int NOUT = 2 * C;
-  constexpr int VE = 16 / sizeof(T);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  WTables<T, R>& tb = *reinterpret_cast<WTables<T, R>*>(smem_raw);
-  T* ttile = reinterpret_cast<T*>(smem_raw + ((sizeof(WTables<T, R>) + 15) / 16) * 16);  // [N][C]
-  T* qtiles = ttile + N * C;                                                            // [2][N][LD]
-  T* part = qtiles + 2 * N * LD;                                                        // [4][2C]
-  load_tables<T, R>(tb, twg, phg, lamg);
-  auto unit_live = [&](long u) {
-    const long plane = u / ntc;
-    return (int)(plane % ng) < blocks[plane / ng].nrow;
-  };
-  auto prefetch_q = [&](long u, int buf) {
-    if (u < nunits && unit_live(u)) {
-      const long plane = u / ntc;
-      const int c0 = (int)(u - plane * ntc) * C;
-      const T* qp = q + plane * (long)N * NR;
-      T* dst = qtiles + buf * N * LD;
-      for (int e = threadIdx.x; e < N * C; e += blockDim.x) {
-        const int kr = e / C, c = e % C;
-        if (c0 + c < NR) cp_async_elem<T>(dst + kr * LD + c, qp + (long)kr * NR + c0 + c);
-      }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int buf = 0;
-  prefetch_q(blockIdx.x, 0);
-  for (long u = blockIdx.x; u < nunits; u += gridDim.x, buf ^= 1) {
-    __syncthreads();                              // last unit's readers of both buffers are done
-    const bool live = unit_live(u);
-    const long plane = u / ntc;
-    const int c0 = (int)(u - plane * ntc) * C;
-    T* tp = t + plane * (long)N * NR;
-    if (live) {                                   // t tile of this unit
-      for (int e = threadIdx.x; e < N * C / VE; e += blockDim.x) {
-        const int kr = e / (C / VE), c = (e % (C / VE)) * VE;
-        if (c0 + c < NR) cp_async16_ca<T>(ttile + kr * C + c, tp + (long)kr * NR + c0 + c);
-      }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    prefetch_q(u + gridDim.x, buf ^ 1);
-    if (!live) continue;                          // (uniform) nothing copied for this unit
-    asm volatile("cp.async.wait_group 2;" ::: "memory");   // this unit's q tile
-    __syncthreads();
-    T* tile = qtiles + buf * N * LD;
-    for (int e = threadIdx.x; e < N * C; e += blockDim.x) {   // columns beyond the grid
-      const int c = e % C;
-      if (c0 + c >= NR) tile[(e / C) * LD + c] = (T)0;
-    }
-    const int b = (int)(plane / ng);
-    const int n = (int)(plane - (long)b * ng);
-    __syncthreads();
-    if (cut != nullptr) {
-      constexpr int SEG = (N + 3) / 4;
-      for (int o = threadIdx.x; o < 4 * NOUT; o += blockDim.x) {
-        const int seg = o / NOUT, oc = o % NOUT, c = oc >> 1;
-        const T* w = (oc & 1) ? wdpsi : wpsi;
-        T sum = 0;
-        const int k0 = seg * SEG, k1 = min(N, k0 + SEG);
-        for (int kr = k0; kr < k1; ++kr) sum += w[kr] * tile[kr * LD + c];
-        part[seg * NOUT + oc] = sum;
-      }
-    }
-    if (qcol != nullptr && m_inf >= c0 && m_inf < c0 + C) {
-      for (int kr = threadIdx.x; kr < N; kr += blockDim.x) qcol[plane * N + kr] = tile[kr * LD + (m_inf - c0)];
-    }
-    __syncthreads();
-    if (cut != nullptr) {
-      const DevBlock Bk = blocks[b];
-      const long ncut = ncut_J[Bk.iJ];
-      for (int oc = threadIdx.x; oc < NOUT; oc += blockDim.x) {
-        const int m = c0 + (oc >> 1);
-        if (m >= NR) continue;
-        const T sum = ((part[oc] + part[NOUT + oc]) + part[2 * NOUT + oc]) + part[3 * NOUT + oc];
-        cut[Bk.cutcol + (long)(oc & 1) * ncut + (long)n * NR + m] = sum;
-      }
-    }
-    for (int p = warp; p < C / 2; p += blockDim.x / 32)
-      pair_kinetic<T, R>(tile + 2 * p, tile + 2 * p + 1, LD, lane, tb);
-    asm volatile("cp.async.wait_group 1;" ::: "memory");   // the t tile
-    __syncthreads();
-    using V = typename Vec16<T>::type;
-    for (int e = threadIdx.x; e < N * C / VE; e += blockDim.x) {
-      const int kr = e / (C / VE), c = (e % (C / VE)) * VE;
-      if (c0 + c >= NR) continue;
-      V z = *reinterpret_cast<const V*>(ttile + kr * C + c);
-      T* zs = reinterpret_cast<T*>(&z);
-#pragma unroll
-      for (int v = 0; v < VE; ++v) zs[v] += tile[kr * LD + c + v];
-      *reinterpret_cast<V*>(tp + (long)kr * NR + c0 + c) = z;
-    }
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-
 // FP64 lines stop at R = 8: beyond that a thread's registers would spill.
 template <typename T, int R>
 constexpr bool kWarpSupported = sizeof(T) == 4 || R <= 8;
@@ -652,29 +525,6 @@ bool cols_wc(const T* q, T* t, long nplanes, int NR, const void* tw, const void*
              const DevBlock* blocks, const int* ncut_J, int m_inf, T* qcol, cudaStream_t st,
              cudaError_t* err) {
   constexpr int N = 32 * R;
-  constexpr int VE = 16 / sizeof(T);
-  if (NR % VE == 0) {
-    const size_t sm = ((sizeof(WTables<T, R>) + 15) / 16) * 16 +
-                      sizeof(T) * ((size_t)N * C + 2 * (size_t)N * (C + 1) + 8 * (size_t)C);
-    static bool attr = false;
-    static int nsm = 0;
-    if (!attr) {
-      cudaFuncSetAttribute(k_cols_wp<T, R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           227 * 1024);
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      attr = true;
-    }
-    const int ntc = (NR + C - 1) / C;
-    const long nunits = nplanes * ntc;
-    const unsigned grid = (unsigned)std::min<long>(nunits, (long)std::max(nsm, 1) * kMinBlocks<T, R>);
-    k_cols_wp<T, R, C><<<grid, 256, sm, st>>>(q, t, NR, static_cast<const cpx<T>*>(tw),
-                                              static_cast<const cpx<T>*>(ph), lam, ng, nunits, ntc,
-                                              wpsi, wdpsi, cut, blocks, ncut_J, m_inf, qcol);
-    *err = cudaGetLastError();
-    return true;
-  }
   const size_t sm = sizeof(WTables<T, R>) + sizeof(T) * ((size_t)N * (C + 1) + 8 * (size_t)C);
   static bool attr = false;
   if (!attr) {
