@@ -120,14 +120,13 @@ __device__ __forceinline__ void tmem_wait8(uint32_t* r) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float* v) {
-  uint32_t r[2];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
-               : "=r"(r[0]), "=r"(r[1])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-  v[0] = __uint_as_float(r[0]);
-  v[1] = __uint_as_float(r[1]);
+__device__ __forceinline__ void tmem_wait16(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
 }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
@@ -200,6 +199,23 @@ __device__ void issue_split_gemm_ta(uint32_t dtmem, uint32_t ahi, uint32_t alo,
     mma_tf32_ta(dtmem, ahi + ta, smem_desc(bh + o, lbo, sbo), idesc, ks > 0);
     mma_tf32_ta(dtmem, ahi + ta, smem_desc(bl + o, lbo, sbo), idesc, 1);
     mma_tf32_ta(dtmem, alo + ta, smem_desc(bh + o, lbo, sbo), idesc, 1);
+  }
+}
+
+// issue_split_gemm_ta for a compile-time K (= KP): the loop unrolls and the B descriptors are
+// formed once; a K-step of 8 values advances the start-address field (16-byte units) by 16.
+template <int KP>
+__device__ __forceinline__ void issue_split_gemm_tk(uint32_t dtmem, uint32_t ahi, uint32_t alo,
+                                                    const unsigned char* Bhi,
+                                                    const unsigned char* Blo, uint32_t idesc) {
+  constexpr uint32_t sbo = (uint32_t)KP * 32, lbo = 128;
+  const uint64_t dh = smem_desc(smem_u32(Bhi), lbo, sbo), dl = smem_desc(smem_u32(Blo), lbo, sbo);
+#pragma unroll
+  for (int ks = 0; ks < KP / 8; ++ks) {
+    const uint64_t o = (uint64_t)ks * 16;
+    mma_tf32_ta(dtmem, ahi + ks * 8, dh + o, idesc, ks > 0);
+    mma_tf32_ta(dtmem, ahi + ks * 8, dl + o, idesc, 1);
+    mma_tf32_ta(dtmem, alo + ks * 8, dh + o, idesc, 1);
   }
 }
 
@@ -1342,7 +1358,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc4(TcArgs a) {
 // w odd after GEMM 2), raw c tiles (even rows, odd rows) in two slots at 6, 7 and 8, 9.
 template <int KH>
 constexpr size_t tc5_smem() {
-  return 4 * (size_t)KH * KH * 4 + 3 * (size_t)2 * KH * TC_M * 4 + 16 + 16 * sizeof(double) + 64;
+  return 4 * (size_t)KH * KH * 4 + 3 * (size_t)2 * KH * TC_M * 4 + 16 + 16 * sizeof(double) +
+         (size_t)2 * KH * 8 * 4 + 64;
 }
 
 template <int KH>
@@ -1357,6 +1374,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
   uint64_t* mbar = reinterpret_cast<uint64_t*>(ps + 2 * kh * TC_M);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   double* red = reinterpret_cast<double*>(mbar + 2);
+  float* cfs = reinterpret_cast<float*>(red + 16);           // [2 kh][8] coefficients
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q = warp & 3;
@@ -1376,7 +1394,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(mb));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1414,22 +1432,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
   };
   uint32_t phase = 0;
   bool ok = true;
-  // both parities' MMAs of one GEMM (even: A even x buffer 0, odd: A odd x buffer 1) under
-  // one commit: the copies complete (all but the `pending` newest groups), visible to the
-  // tensor core, operand stores to tensor memory complete
-  auto run_mma2 = [&](uint32_t de, uint32_t dodd, int pending) {
+  // both parities' MMAs of one GEMM (even: A even x buffer 0, odd: A odd x buffer 1), issued
+  // once every copy group has landed (visible to the tensor core) and the operand stores to
+  // tensor memory are complete; the wait comes later, so that CUDA-core work overlaps the MMAs
+  auto issue_mma2 = [&](uint32_t de, uint32_t dodd) {
     tmem_st_wait();
-    if (pending >= 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // two issuing threads in different warps (one parity each); each commit arrives once on
+    // the barrier, which completes on the second
     if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      issue_split_gemm_ta(de, tAe_hi, tAe_lo, Bbuf(0, 0), Bbuf(0, 1), kh, idesc);
-      issue_split_gemm_ta(dodd, tAo_hi, tAo_lo, Bbuf(1, 0), Bbuf(1, 1), kh, idesc);
+      issue_split_gemm_tk<KH>(de, tAe_hi, tAe_lo, Bbuf(0, 0), Bbuf(0, 1), idesc);
+      mma_commit(mb);
+    } else if (tid == 32) {
+      issue_split_gemm_tk<KH>(dodd, tAo_hi, tAo_lo, Bbuf(1, 0), Bbuf(1, 1), idesc);
       mma_commit(mb);
     }
+  };
+  auto wait_mma = [&]() {
     ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
     phase ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -1490,7 +1513,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
       tmem_st4(tC + cc, re);
       tmem_st4(tC + kh + cc, ro);
     }
-    __syncthreads();   // cs is free: the next unit's c (this unit's upper neighbour), t, c_(k-1)
+    // ---- GEMM 1: E = c_even G1e, O = c_odd G1o. While it runs: stage this unit's t and
+    // c_(k-1) and the next unit's c tile (its upper neighbour), and on a new tile the potential
+    issue_mma2(tE, tO);                           // pending before: [G1e G1o](u) only
     if (u + 1 < u1) {
       const int bn = unit_block(u + 1);
       stage(cs, a.ck + (long)bn * a.npts, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
@@ -1498,7 +1523,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     stage(ts, a.t + (long)b * a.npts, nrow, col0);
     if (a.mode == 0) stage(ps, a.ckm1 + (long)b * a.npts, nrow, col0);
     asm volatile("cp.async.commit_group;" ::: "memory");
-    // pending now: [G1e G1o](u), [c(u+1) t p]
+    if (tid < ng) {   // the block's five coefficient rows, interleaved per row i
+      const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
+      *reinterpret_cast<float4*>(cfs + tid * 8) =
+          make_float4(cf[tid], cf[ng + tid], cf[2 * ng + tid], cf[3 * ng + tid]);
+      cfs[tid * 8 + 4] = cf[4 * ng + tid];
+    }
     if (tile != vtile) {
 #pragma unroll
       for (int s2 = 0; s2 < nq; ++s2) {
@@ -1509,9 +1539,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
       }
       vtile = tile;
     }
-    run_mma2(tE, tO, 1);                          // E = c_even G1e, O = c_odd G1o
-    issue_b2(u, 2);                               // pending: [c t p], [G2e G2o]
+    wait_mma();
     if (!ok) break;
+    issue_b2(u, 2);                               // pending: [c t p], [G2e G2o]
 
     // ---- potential: S = y(n) + y(n') into A even, D = y(n) - y(n') into A odd
 #pragma unroll
@@ -1537,83 +1567,96 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
       tmem_st4(tAo_hi + cc, hd);
       tmem_st4(tAo_lo + cc, ld);
     }
-    run_mma2(tE, tO, 0);                          // w_even = S G2e, w_odd = D G2o; [c t p] done
-    issue_b2(u + 1, 0);                           // pending: [G1e G1o](u+1)
-    if (!ok) break;
 
-    // ---- epilogue: w, c, c^(Omega-1) from tensor memory; c^(Omega+1), t, c_(k-1) from shared
-    float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
+    // ---- GEMM 2: w_even = S G2e, w_odd = D G2o. While it runs, every term of the result
+    // but w: with r = a c + b+ c^(Omega+1) + b- c^(Omega-1) + t,
+    //   H_s c = invdE (w + r) - e0s c,  c_(k+1) = D (alpha H_s c - beta D c_(k-1)),
+    // so the result is k1 w + r2 with r2 written over t in shared memory.
+    issue_mma2(tE, tO);                           // [c t p] and [G2e G2o] have landed
+    const DevJ J = a.dj[B0.iJ];
+    const float invdE = (float)J.invdE, e0s = (float)J.e0s;   // once, not per row
+    const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
+    const float k1 = a.mode == 1 ? invdE : D * a.alpha * invdE;
     {
-      const DevJ J = a.dj[B0.iJ];
-      const float invdE = (float)J.invdE, e0s = (float)J.e0s;   // once, not per row
-      const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
-      const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
+      const float kc = a.mode == 1 ? 1.0f : D * a.alpha;
+      const float kq = a.mode == 1 ? 0.0f : a.beta * D * D;
       const float frk = live ? a.fr[kr] : 0.0f;
       const float fRm = live ? a.fR[mR] : 0.0f;
-      for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 4) {
-        float cu[4], cd[4], tv[4], pv[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const int i = i0 + s;
-          const bool in = live && i < nrow;
-          const long off = (long)i * a.ncol + col;
-          tv[s] = in ? ts[i * TC_M + m] : 0.0f;
-          pv[s] = (in && a.mode == 0) ? ps[i * TC_M + m] : 0.0f;
-          // row i of block Omega+1 is its row i - 1 (j = Omega + i)
-          cu[s] = (in && B0.up >= 0 && i >= 1)
-                      ? (up_chip ? cs[(i - 1) * TC_M + m] : __ldg(a.ck + (long)B0.up * a.npts + off - a.ncol))
-                      : 0.0f;
-          cd[s] = (in && B0.dn >= 0 && !dn_chip) ? __ldg(a.ck + (long)B0.dn * a.npts + off + a.ncol) : 0.0f;
-        }
-        uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // w even, w odd, c even, c odd
-        tmem_ld2_issue(tE + lane_base + (uint32_t)(i0 / 2), r);
-        tmem_ld2_issue(tO + lane_base + (uint32_t)(i0 / 2), r + 2);
-        tmem_ld2_issue(tC + lane_base + (uint32_t)(i0 / 2), r + 4);
-        tmem_ld2_issue(tC + kh + lane_base + (uint32_t)(i0 / 2), r + 6);
-        tmem_wait8(r);
+      const float erot = a.erot;
+      for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 8) {
+        // c of this unit: even columns i0/2.. = rows i0, i0+2, i0+4, i0+6, odd columns = rows
+        // i0+1, ...; with c^(Omega-1) on chip, its rows i0+1.. = odd columns i0/2.. (rows
+        // i0+1, i0+3, ...) and even columns i0/2+1.. (rows i0+2, i0+4, ...) of the previous
+        // unit's raw tile (row i of block Omega-1 is its row i + 1)
+        uint32_t r[16];
+        tmem_ld4_issue(tC + lane_base + (uint32_t)(i0 / 2), r);
+        tmem_ld4_issue(tC + kh + lane_base + (uint32_t)(i0 / 2), r + 4);
         if (dn_chip) {
-          // row i of block Omega-1 is its row i + 1: rows i0+1..i0+4 = (odd, even, odd, even)
-          // of the previous unit's raw tile, columns i0/2 (odd), i0/2 + 1 (even), i0/2 + 1 (odd),
-          // i0/2 + 2 (even)
-          uint32_t p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          tmem_ld2_issue(tCp + kh + lane_base + (uint32_t)(i0 / 2), p);         // odd  i0/2, i0/2+1
-          tmem_ld2_issue(tCp + lane_base + (uint32_t)(i0 / 2 + 1), p + 2);      // even i0/2+1, i0/2+2
-          tmem_wait8(p);
-          const float pr4[4] = {__uint_as_float(p[0]), __uint_as_float(p[2]), __uint_as_float(p[1]),
-                                __uint_as_float(p[3])};
+          tmem_ld4_issue(tCp + kh + lane_base + (uint32_t)(i0 / 2), r + 8);
+          tmem_ld4_issue(tCp + lane_base + (uint32_t)(i0 / 2 + 1), r + 12);
+        } else {
 #pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            const int i = i0 + s;
-            cd[s] = (live && i < nrow && i + 1 < ng) ? pr4[s] : 0.0f;
-          }
+          for (int s = 8; s < 16; ++s) r[s] = 0u;
         }
+        tmem_wait16(r);
         if (!live) continue;
-        const float w[4] = {__uint_as_float(r[0]), __uint_as_float(r[2]), __uint_as_float(r[1]),
-                            __uint_as_float(r[3])};
-        const float cv[4] = {__uint_as_float(r[4]), __uint_as_float(r[6]), __uint_as_float(r[5]),
-                             __uint_as_float(r[7])};
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < 8; ++s) {
           const int i = i0 + s;
-          if (i >= a.ng) break;
-          const long idx = (long)b * a.npts + (long)i * a.ncol + col;
-          if (i >= nrow) {
-            if (a.mode == 1) a.out[idx] = 0.0f; else a.ckm1[idx] = 0.0f;
-            continue;
+          if (i >= nrow) break;
+          const long off = (long)i * a.ncol + col;
+          const float cv = __uint_as_float(r[(s & 1) * 4 + (s >> 1)]);
+          float cd = 0.0f;
+          if (dn_chip) {
+            if (i + 1 < ng) cd = __uint_as_float(r[8 + (s & 1) * 4 + (s >> 1)]);
+          } else if (B0.dn >= 0) {
+            cd = __ldg(a.ck + (long)B0.dn * a.npts + off + a.ncol);
           }
-          const float gg = fminf(fRm, cf[4 * a.ng + i]);
-          const float aa = fminf(cf[i] * frk, a.erot) + gg * cf[a.ng + i];
-          float hh = w[s] + aa * cv[s] + tv[s];
-          hh += gg * cf[2 * a.ng + i] * cu[s];
-          hh += gg * cf[3 * a.ng + i] * cd[s];
-          const float hs = hh * invdE - e0s * cv[s];
-          if (a.mode == 1) {
-            a.out[idx] = hs;
-          } else {
-            const float nv = D * (a.alpha * hs - a.beta * D * pv[s]);
-            a.ckm1[idx] = nv;
-            ssf = fmaf(nv, nv, ssf);
-          }
+          // row i of block Omega+1 is its row i - 1 (j = Omega + i)
+          float cu = 0.0f;
+          if (B0.up >= 0 && i >= 1)
+            cu = up_chip ? cs[(i - 1) * TC_M + m] : __ldg(a.ck + (long)B0.up * a.npts + off - a.ncol);
+          const float tv = ts[i * TC_M + m];
+          const float pv = a.mode == 0 ? ps[i * TC_M + m] : 0.0f;
+          const float4 c4 = *reinterpret_cast<const float4*>(cfs + i * 8);
+          const float gg = fminf(fRm, cfs[i * 8 + 4]);
+          const float aa = fminf(c4.x * frk, erot) + gg * c4.y;
+          float rr = aa * cv + tv;
+          rr += gg * c4.z * cu;
+          rr += gg * c4.w * cd;
+          ts[i * TC_M + m] = kc * (rr * invdE - e0s * cv) - kq * pv;
+        }
+      }
+    }
+    wait_mma();
+    if (!ok) break;
+    issue_b2(u + 1, 0);                           // pending: [G1e G1o](u+1)
+
+    // ---- result = k1 w + r2, eight rows per tensor-memory wait (w even: rows i0, i0 + 2, ...;
+    // w odd: rows i0 + 1, i0 + 3, ...); rows nrow..ng-1 of the block are zero
+    float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
+    for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 8) {
+      uint32_t r[8];
+      tmem_ld4_issue(tE + lane_base + (uint32_t)(i0 / 2), r);
+      tmem_ld4_issue(tO + lane_base + (uint32_t)(i0 / 2), r + 4);
+      tmem_wait8(r);
+      if (!live) continue;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int i = i0 + s;
+        if (i >= ng) break;
+        const float w = __uint_as_float(r[(s & 1) * 4 + (s >> 1)]);
+        const long idx = (long)b * a.npts + (long)i * a.ncol + col;
+        if (i >= nrow) {
+          if (a.mode == 1) a.out[idx] = 0.0f; else a.ckm1[idx] = 0.0f;
+          continue;
+        }
+        const float v = fmaf(k1, w, ts[i * TC_M + m]);
+        if (a.mode == 1) {
+          a.out[idx] = v;
+        } else {
+          a.ckm1[idx] = v;
+          ssf = fmaf(v, v, ssf);
         }
       }
     }
