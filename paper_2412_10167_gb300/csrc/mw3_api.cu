@@ -767,7 +767,10 @@ static int finish_potential(mw3_ctx* ctx, double vcut, double tcut, double erot)
   if ((st = upload_fft_tables(ctx, "twR", "phR", ctx->NR))) return st;
   if ((st = upload_fft_tables(ctx, "twr", "phr", ctx->nr))) return st;
   std::vector<DevJ> dj(ctx->nJ);
-  for (int iJ = 0; iJ < ctx->nJ; ++iJ) dj[iJ] = DevJ{ctx->E0[iJ] / ctx->dE[iJ], 1.0 / ctx->dE[iJ]};
+  for (int iJ = 0; iJ < ctx->nJ; ++iJ) {
+    const double e0s = ctx->E0[iJ] / ctx->dE[iJ], invdE = 1.0 / ctx->dE[iJ];
+    dj[iJ] = DevJ{e0s, invdE, (float)e0s, (float)invdE};
+  }
   if ((st = upload_raw(ctx, "dj", dj))) return st;
   if ((st = upload_raw(ctx, "blocks", ctx->blocks))) return st;
   std::vector<long> jb(ctx->nJ + 1);

@@ -52,6 +52,8 @@ constexpr int kCoefRows = 5;
 struct DevJ {
   double e0s;     // E0 / dE
   double invdE;   // 1 / dE
+  float e0s_f;    // the same rounded to FP32 (FP64 arithmetic is slow on this part)
+  float invdE_f;
 };
 
 // Launch shapes chosen by the tuner (defaults in the context).

@@ -30,6 +30,7 @@ namespace {
 
 constexpr int TC_M = 128;
 constexpr int TC_THREADS = 512;
+static_assert(TC_THREADS / 32 <= 16, "warp sums reduced by one warp in 4 shuffle levels");
 constexpr long kWaitLimit = 1L << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -1375,6 +1376,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   double* red = reinterpret_cast<double*>(mbar + 2);
   float* cfs = reinterpret_cast<float*>(red + 16);           // [2 kh][8] coefficients
+  float* redf = reinterpret_cast<float*>(red);                // per-warp sums of squares
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q = warp & 3;
@@ -1573,8 +1575,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     //   H_s c = invdE (w + r) - e0s c,  c_(k+1) = D (alpha H_s c - beta D c_(k-1)),
     // so the result is k1 w + r2 with r2 written over t in shared memory.
     issue_mma2(tE, tO);                           // [c t p] and [G2e G2o] have landed
-    const DevJ J = a.dj[B0.iJ];
-    const float invdE = (float)J.invdE, e0s = (float)J.e0s;   // once, not per row
+    const float invdE = a.dj[B0.iJ].invdE_f, e0s = a.dj[B0.iJ].e0s_f;
     const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
     const float k1 = a.mode == 1 ? invdE : D * a.alpha * invdE;
     {
@@ -1660,16 +1661,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
         }
       }
     }
-    double ss = (double)ssf;
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
-    if (lane == 0) red[warp] = ss;
+    // the sum of squares reduced in FP32 (across the warp, then across the 16 warps by warp 0):
+    // one FP64 value per (block, tile)
+    float ws = ssf;
+    for (int o = 16; o > 0; o >>= 1) ws += __shfl_down_sync(0xffffffffu, ws, o);
+    if (lane == 0) redf[warp] = ws;
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
-      double s2 = 0;
-      for (int w2 = 0; w2 < TC_THREADS / 32; ++w2) s2 += red[w2];
-      if (a.npart) a.npart[(long)b * a.ntiles + tile] = s2;
+    if (warp == 0) {
+      float v = lane < TC_THREADS / 32 ? redf[lane] : 0.0f;
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0 && a.npart) a.npart[(long)b * a.ntiles + tile] = (double)v;
     }
     prev_u = u;
     slot ^= 1;
