@@ -1437,9 +1437,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
   // both parities' MMAs of one GEMM (even: A even x buffer 0, odd: A odd x buffer 1), issued
   // once every copy group has landed (visible to the tensor core) and the operand stores to
   // tensor memory are complete; the wait comes later, so that CUDA-core work overlaps the MMAs
-  auto issue_mma2 = [&](uint32_t de, uint32_t dodd) {
+  auto issue_mma2 = [&](uint32_t de, uint32_t dodd, bool one_pending) {
     tmem_st_wait();
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (one_pending) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -1460,12 +1461,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;");
   };
 
-  if (u0 < u1) {
-    const int b = unit_block(u0);
-    stage(cs, a.ck + (long)b * a.npts, a.blocks[b].nrow, (long)unit_tile(u0) * TC_M);
-  }
+  // Copy groups, in commit order: [c(u)] during GEMM 1 of unit u-1, [t(u), G1e G1o(u)] after
+  // GEMM 2 of unit u-1, [c_(k-1)(u)] after the result of unit u-1 is written, [G2e G2o(u)]
+  // after GEMM 1 of unit u; the first unit's three come from here.
+  const int b00 = u0 < u1 ? unit_block(u0) : 0;
+  const long c00 = u0 < u1 ? (long)unit_tile(u0) * TC_M : 0;
+  if (u0 < u1) stage(cs, a.ck + (long)b00 * a.npts, a.blocks[b00].nrow, c00);
   asm volatile("cp.async.commit_group;" ::: "memory");
+  if (u0 < u1) stage(ts, a.t + (long)b00 * a.npts, a.blocks[b00].nrow, c00);
   issue_b2(u0, 0);
+  if (u0 < u1 && a.mode == 0) stage(ps, a.ckm1 + (long)b00 * a.npts, a.blocks[b00].nrow, c00);
+  asm volatile("cp.async.commit_group;" ::: "memory");
 
   float va[nq], vb[nq];
   int vtile = -1;
@@ -1488,7 +1494,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     const bool up_chip = B0.up >= 0 && B0.up == b + 1 && u + 1 < u1 && unit_tile(u + 1) == tile;
 
     __syncthreads();   // previous unit's readers of ts, ps, cs and tensor memory are done
-    asm volatile("cp.async.wait_group 1;" ::: "memory");   // this unit's c tile
+    asm volatile("cp.async.wait_group 2;" ::: "memory");   // this unit's c tile
     __syncthreads();
     // ---- GEMM 1 operands (both parities) and the raw c tile, from shared memory
 #pragma unroll
@@ -1515,15 +1521,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
       tmem_st4(tC + cc, re);
       tmem_st4(tC + kh + cc, ro);
     }
-    // ---- GEMM 1: E = c_even G1e, O = c_odd G1o. While it runs: stage this unit's t and
-    // c_(k-1) and the next unit's c tile (its upper neighbour), and on a new tile the potential
-    issue_mma2(tE, tO);                           // pending before: [G1e G1o](u) only
+    // ---- GEMM 1: E = c_even G1e, O = c_odd G1o. While it runs: stage the next unit's c tile
+    // (this unit's upper neighbour), and on a new tile load the potential
+    issue_mma2(tE, tO, true);                     // [t G1e G1o](u) landed; [c_(k-1)](u) may not
     if (u + 1 < u1) {
       const int bn = unit_block(u + 1);
       stage(cs, a.ck + (long)bn * a.npts, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
     }
-    stage(ts, a.t + (long)b * a.npts, nrow, col0);
-    if (a.mode == 0) stage(ps, a.ckm1 + (long)b * a.npts, nrow, col0);
     asm volatile("cp.async.commit_group;" ::: "memory");
     if (tid < ng) {   // the block's five coefficient rows, interleaved per row i
       const float* cf = a.coef + (long)B0.coef * kCoefRows * a.ng;
@@ -1573,8 +1577,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     // ---- GEMM 2: w_even = S G2e, w_odd = D G2o. While it runs, every term of the result
     // but w: with r = a c + b+ c^(Omega+1) + b- c^(Omega-1) + t,
     //   H_s c = invdE (w + r) - e0s c,  c_(k+1) = D (alpha H_s c - beta D c_(k-1)),
-    // so the result is k1 w + r2 with r2 written over t in shared memory.
-    issue_mma2(tE, tO);                           // [c t p] and [G2e G2o] have landed
+    // so the result is k1 w + r2 with r2 written over c_(k-1) in shared memory.
+    issue_mma2(tE, tO, false);                    // c(u+1), c_(k-1)(u), G2e G2o(u) landed
     const float invdE = a.dj[B0.iJ].invdE_f, e0s = a.dj[B0.iJ].e0s_f;
     const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
     const float k1 = a.mode == 1 ? invdE : D * a.alpha * invdE;
@@ -1625,13 +1629,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
           float rr = aa * cv + tv;
           rr += gg * c4.z * cu;
           rr += gg * c4.w * cd;
-          ts[i * TC_M + m] = kc * (rr * invdE - e0s * cv) - kq * pv;
+          ps[i * TC_M + m] = kc * (rr * invdE - e0s * cv) - kq * pv;
         }
       }
     }
     wait_mma();
     if (!ok) break;
-    issue_b2(u + 1, 0);                           // pending: [G1e G1o](u+1)
+    // t is free: the next unit's t with its G1e G1o, one group
+    if (u + 1 < u1) {
+      const int bn = unit_block(u + 1);
+      stage(ts, a.t + (long)bn * a.npts, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
+    }
+    issue_b2(u + 1, 0);
 
     // ---- result = k1 w + r2, eight rows per tensor-memory wait (w even: rows i0, i0 + 2, ...;
     // w odd: rows i0 + 1, i0 + 3, ...); rows nrow..ng-1 of the block are zero
@@ -1652,7 +1661,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
           if (a.mode == 1) a.out[idx] = 0.0f; else a.ckm1[idx] = 0.0f;
           continue;
         }
-        const float v = fmaf(k1, w, ts[i * TC_M + m]);
+        const float v = fmaf(k1, w, ps[i * TC_M + m]);
         if (a.mode == 1) {
           a.out[idx] = v;
         } else {
@@ -1669,6 +1678,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
+    // c_(k-1) is free: the next unit's
+    if (u + 1 < u1 && a.mode == 0) {
+      const int bn = unit_block(u + 1);
+      stage(ps, a.ckm1 + (long)bn * a.npts, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
     if (warp == 0) {
       float v = lane < TC_THREADS / 32 ? redf[lane] : 0.0f;
       for (int o = 8; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
