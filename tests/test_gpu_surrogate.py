@@ -81,7 +81,7 @@ def test_surrogate_pipeline_against_propagation():
     from paper_2412_10167_gb300 import surrogate
     cfg = surrogate_cfg()
     rep = surrogate.run(cfg, J_train=list(range(0, 25, 4)), J_test=list(range(2, 23, 4)),
-                        steps=600, epochs=300, width=256, depth=3, batch=512)
+                        steps=600, epochs=1500, width=256, depth=3, batch=512, ensemble=3)
     print(json.dumps(rep, indent=1))
     # the propagation fallback bounds every final probability error
     assert rep["max_abs_dP"]["with_fallback"] <= 0.01 + 1e-12
