@@ -89,6 +89,8 @@ struct mw3_ctx {
   int kh = 0;          // parity-split operand size, resident form (0: not applicable)
   int kh4 = 0;         // parity-split operand size, streamed form (0: not applicable)
   bool tc_ok = false;  // the tensor-core angular step supports this grid
+  // |a(E)|^2 of the incoming packet on the energy grid, kept until the packet or the grid changes
+  std::vector<double> a2_cache;
   int tc_user = -1;    // explicit "use_tc" setting (-1: default = on when supported)
 
   // grid and blocks
@@ -837,6 +839,7 @@ int mw3_load_potential_grid(mw3_ctx* ctx, const double* V, double vcut, double t
 }
 
 int mw3_init_packet(mw3_ctx* ctx, const mw3_packet_desc* d) {
+  if (ctx) ctx->a2_cache.clear();
   if (!ctx || !d) return MW3_ERR_BAD_ARG;
   if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
   if (d->v0 < 0 || d->j0 < d->omega0 || d->omega0 < 0 || d->elec0 < 0 || d->elec0 >= ctx->nelec ||
@@ -1071,6 +1074,7 @@ int mw3_set_products(mw3_ctx* ctx, const mw3_products_desc* d) {
 }
 
 int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
+  if (ctx) ctx->a2_cache.clear();
   if (!ctx || !d) return MW3_ERR_BAD_ARG;
   if (ctx->stage < 3) return ctx->fail(MW3_ERR_STATE, "mw3_init_packet first");
   if (d->nE < 1 || !(d->E_hi >= d->E_lo) || !(d->E_lo > 0) || d->rstar <= ctx->rmin ||
@@ -1452,7 +1456,7 @@ int flush(mw3_ctx* ctx, int nvalid, bool timed) {
   Timer tm(ctx, 6, timed);
   LK(launch_phases<real>(B.theta, ctx->nJ, ctx->an.nE, ctx->tune.kb, nvalid, B.d_iter, B.ph, st));
   if (std::is_same<real, float>::value && ctx->tc_ok && ctx->tune.flush_tc) {
-    LK(launch_flush_tc((const float*)B.ph, (const float*)B.cut, ctx->NC, ctx->tune.kb, ctx->nJ,
+    LK(launch_flush_tc((const float*)B.ph, (const float*)B.cut, ctx->NC, ctx->tune.kb, nvalid, ctx->nJ,
                        ctx->an.nE, B.colbase, B.ncols, B.accoff, ctx->max_cols, B.acc,
                        (int*)dptr(ctx, "tc_err"), st));
   } else {
@@ -1529,8 +1533,12 @@ int propagate_impl(mw3_ctx* ctx, long nsteps) {
 }
 
 // |a(E)|^2 of the incoming packet, a(E) = sqrt(mu/(2 pi K)) sum_m dR exp(i K R_m) g~(R_m).
-void incoming_a2(const mw3_ctx* ctx, std::vector<double>& a2) {
+void incoming_a2(mw3_ctx* ctx, std::vector<double>& a2) {
   const int nE = ctx->an.nE;
+  if ((int)ctx->a2_cache.size() == nE) {
+    a2 = ctx->a2_cache;
+    return;
+  }
   a2.assign(nE, 0.0);
   for (int e = 0; e < nE; ++e) {
     const double K = std::sqrt(2.0 * ctx->mu * ctx->Ecol[e]);
@@ -1542,6 +1550,7 @@ void incoming_a2(const mw3_ctx* ctx, std::vector<double>& a2) {
     const double s = std::sqrt(ctx->mu / (2.0 * M_PI * K)) * ctx->dR;
     a2[e] = s * s * (re * re + im * im);
   }
+  ctx->a2_cache = a2;
 }
 
 }  // namespace

@@ -181,7 +181,7 @@ struct TcArgs {
 };
 bool angular_tc2_supported(int kp, int nelec);
 // Energy-sum flush on the tensor cores (FP32 ring, split-TF32, FP64 accumulators).
-cudaError_t launch_flush_tc(const float* ph, const float* cut, long ncut_total, int kb, int nJ,
+cudaError_t launch_flush_tc(const float* ph, const float* cut, long ncut_total, int kb, int nvalid, int nJ,
                             int nE, const long* colbase, const long* ncols, const long* accoff,
                             long max_cols, double* acc, int* err, cudaStream_t st);
 int angular_tc3_kh(int ng, int nelec);   // 0 when the parity-split form does not apply

@@ -1735,7 +1735,7 @@ constexpr int FL_M = 128, FL_N = 128, FL_KC = 32, FL_THREADS = 128;
 
 __global__ void __launch_bounds__(FL_THREADS) k_flush_tc(const float* __restrict__ ph,
                                                          const float* __restrict__ cut,
-                                                         long ncut_total, int kb, int nE2,
+                                                         long ncut_total, int kb, int kn, int nE2,
                                                          const long* __restrict__ colbase,
                                                          const long* __restrict__ ncols,
                                                          const long* __restrict__ accoff,
@@ -1778,16 +1778,16 @@ __global__ void __launch_bounds__(FL_THREADS) k_flush_tc(const float* __restrict
   const bool prow = p0 + tid < nE2;
   uint32_t phase = 0;
   bool ok = true;
-  for (int kc = 0; kc < kb && ok; kc += FL_KC) {
+  for (int kc = 0; kc < kn && ok; kc += FL_KC) {
     if (kc > 0) __syncthreads();   // the previous chunk's MMAs have completed (waited below)
     // A: row = column of the tile, K = ring slot; B: row = phase row, K = ring slot
     float x[FL_KC];
 #pragma unroll
     for (int k = 0; k < FL_KC; ++k)
-      x[k] = (live && kc + k < kb) ? __ldg(cutc + (long)(kc + k) * ncut_total) : 0.0f;
+      x[k] = (live && kc + k < kn) ? __ldg(cutc + (long)(kc + k) * ncut_total) : 0.0f;
     float y[FL_KC];
 #pragma unroll
-    for (int k = 0; k < FL_KC; ++k) y[k] = (prow && kc + k < kb) ? __ldg(phr + kc + k) : 0.0f;
+    for (int k = 0; k < FL_KC; ++k) y[k] = (prow && kc + k < kn) ? __ldg(phr + kc + k) : 0.0f;
 #pragma unroll
     for (int k4 = 0; k4 < FL_KC; k4 += 4) {
       float4 h, l;
@@ -1855,7 +1855,7 @@ __global__ void __launch_bounds__(FL_THREADS) k_flush_tc(const float* __restrict
   }
 }
 
-cudaError_t launch_flush_tc(const float* ph, const float* cut, long ncut_total, int kb, int nJ,
+cudaError_t launch_flush_tc(const float* ph, const float* cut, long ncut_total, int kb, int nvalid, int nJ,
                             int nE, const long* colbase, const long* ncols, const long* accoff,
                             long max_cols, double* acc, int* err, cudaStream_t st) {
   const long ytiles = (max_cols + FL_M - 1) / FL_M;
@@ -1867,7 +1867,11 @@ cudaError_t launch_flush_tc(const float* ph, const float* cut, long ncut_total, 
     cudaFuncSetAttribute(k_flush_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_flush_tc<<<grid, FL_THREADS, smem, st>>>(ph, cut, ncut_total, kb, 2 * nE, colbase, ncols,
+  // ring slots past the valid ones carry zero phases: multiply the valid ones only (K rounded up
+  // to the chunk of 32); ph rows keep the stride kb
+  const int kn = std::min(kb, ((nvalid + FL_KC - 1) / FL_KC) * FL_KC);
+  if (kn <= 0) return cudaSuccess;
+  k_flush_tc<<<grid, FL_THREADS, smem, st>>>(ph, cut, ncut_total, kb, kn, 2 * nE, colbase, ncols,
                                              accoff, acc, err);
   return cudaGetLastError();
 }
