@@ -5,7 +5,7 @@ every J; the paper computes a coarse set of J and interpolates the rest by
 J-shifting (Eq. J-shifting-interpolation). Here a small network learns
 P_J(E, v', j') from propagations at training J values (this library's propagation,
 one batched context for all of them) and predicts intermediate J. The propagation
-is the judge of its error and its fallback: wherever the prediction differs from the
+measures its error and is its fallback: wherever the prediction differs from the
 propagated value by more than `fallback_dP`, the propagated value is used.
 
 State-resolved targets are the reactant-channel (v', j') probabilities the library
@@ -129,13 +129,13 @@ def cumulative(Js, P):
 def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 1500, width: int = 256,
         depth: int = 3, lr: float = 2e-3, batch: int = 512, fallback_dP: float = 0.01,
         ensemble: int = 3, precision: str = "fp64", device: int = 0, seed: int = 10167):
-    """Train on J_train, judge on J_test; returns a report dictionary.
+    """Train on J_train, evaluate on J_test; returns a report dictionary.
 
     Each of `ensemble` networks (different initialisation and shuffling seeds) trains for
     `epochs` at `lr`, then epochs/2 at lr/4 and epochs/2 at lr/16 (the AdamW state carries
     over); the prediction is their mean. Single networks vary strongly with the seed on a
     few thousand samples; the mean is steadier. The propagations (training J and the held-out
-    J that judge the network) run in `precision` ("fp64" or "mixed")."""
+    J that evaluate the network) run in `precision` ("fp64" or "mixed")."""
     E, _, Ptr, t_train = propagate_probabilities(cfg, J_train, steps, precision, device=device)
     nv, nj = Ptr.shape[1], Ptr.shape[2]
     scale = dict(J=max(max(J_train), 1), E0=E[0], dE=max(E[-1] - E[0], 1e-12), v=max(nv - 1, 1),
@@ -158,7 +158,7 @@ def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 1500, width: int =
         net.close()
     Psur = np.mean(preds, axis=0)
     loss = float(np.mean(losses))
-    # the judge: propagation at the held-out J
+    # the reference: propagation at the held-out J
     _, _, Pte, t_test = propagate_probabilities(cfg, J_test, steps, precision, device=device)
     Pjs = jshift_baseline(E, np.asarray(J_train), Ptr, np.asarray(J_test))
     Plin = linear_baseline(np.asarray(J_train), Ptr, np.asarray(J_test))

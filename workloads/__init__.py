@@ -105,7 +105,7 @@ C4 = _cfg(
     steps=30000, precision="mixed")
 
 # Config 5 (J-interpolation surrogate): the config-3 grid, single surface, trained on
-# J = 0, 4, ..., 48 and judged on J = 2, 6, ..., 46.
+# J = 0, 4, ..., 48 and evaluated on J = 2, 6, ..., 46.
 C5 = dict(base=C3, J_train=list(range(0, 49, 4)), J_test=list(range(2, 47, 4)),
           vmax=3, jmax=15, nE=1000, E_lo_eV=0.2, E_hi_eV=1.6,
           mlp=dict(n_in=4, width=256, depth=3, n_out=1), fallback_dP=0.01)
