@@ -284,6 +284,11 @@ def run_ours(args, rank, world, local):
     q_host[...] = q_dev
     qp_host[...] = qp_dev
     e2e_steps = max(4, min(16, args.steps // 8))
+    # one untimed iteration: upload buffers, the copy stream and the cached packet amplitudes
+    # are set up on first use
+    pr.set_state(q_host, qp_host)
+    pr.propagate(1)
+    pr.probabilities()
     barrier()
     te0 = time.perf_counter()
     for _ in range(e2e_steps):

@@ -77,6 +77,10 @@ struct mw3_ctx {
   int precision = MW3_FP64;
   bool host_only = false;
   cudaStream_t stream = nullptr;
+  // host-to-device state uploads: a copy stream and one event per block group, so that a
+  // group's conversion and gamma transform overlap the next group's copy
+  cudaStream_t up_stream = nullptr;
+  cudaEvent_t up_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool own_stream = false;
   mw3_alloc_fn alloc = nullptr;
   mw3_free_fn free_fn = nullptr;
@@ -339,23 +343,46 @@ int transform_upload(mw3_ctx* ctx, const double* src, const char* dst_name, bool
   const size_t n = (size_t)ctx->nblk * ctx->npts;
   int st = dalloc(ctx, "xfer", n * ctx->rs());
   if (st) return st;
-  if (ctx->precision == MW3_FP64) {
-    CK(cudaMemcpyAsync(dptr(ctx, "xfer"), src, n * 8, cudaMemcpyHostToDevice, ctx->stream));
-    LK(launch_gamma_forward<double>((const double*)dptr(ctx, "xfer"), (double*)dptr(ctx, dst_name),
-                                    (const double*)dptr(ctx, to_fbr ? "T" : "Tt"),
-                                    (const DevBlock*)dptr(ctx, "blocks"), ctx->nblk, ctx->ng,
-                                    ctx->ncol, ctx->stream));
-  } else {
-    // FP64 host values land in a device FP64 buffer and are narrowed on the device
-    if ((st = dalloc(ctx, "xfer64", n * 8))) return st;
-    CK(cudaMemcpyAsync(dptr(ctx, "xfer64"), src, n * 8, cudaMemcpyHostToDevice, ctx->stream));
-    LK(launch_convert_d2f((const double*)dptr(ctx, "xfer64"), (float*)dptr(ctx, "xfer"), (long)n,
-                          ctx->stream));
-    LK(launch_gamma_forward<float>((const float*)dptr(ctx, "xfer"), (float*)dptr(ctx, dst_name),
-                                   (const float*)dptr(ctx, to_fbr ? "T" : "Tt"),
-                                   (const DevBlock*)dptr(ctx, "blocks"), ctx->nblk, ctx->ng,
-                                   ctx->ncol, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+  const bool mixed = ctx->precision != MW3_FP64;
+  // FP64 host values land in a device FP64 buffer (narrowed on the device in the mixed form)
+  if (mixed && (st = dalloc(ctx, "xfer64", n * 8))) return st;
+  double* d64 = (double*)dptr(ctx, mixed ? "xfer64" : "xfer");
+  if (!ctx->up_stream) {
+    CK(cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking));
+    for (auto& e : ctx->up_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  // the copies start after earlier work on the library's stream (which may still read xfer)
+  CK(cudaEventRecord(ctx->up_ev[4], ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->up_stream, ctx->up_ev[4], 0));
+  const int G = std::min(ctx->nblk, 4);
+  auto group = [&](int g, long& b0, long& nb) {
+    b0 = (long)g * ctx->nblk / G;
+    nb = (long)(g + 1) * ctx->nblk / G - b0;
+  };
+  for (int g = 0; g < G; ++g) {
+    long b0, nb;
+    group(g, b0, nb);
+    CK(cudaMemcpyAsync(d64 + b0 * ctx->npts, src + b0 * ctx->npts, (size_t)nb * ctx->npts * 8,
+                       cudaMemcpyHostToDevice, ctx->up_stream));
+    CK(cudaEventRecord(ctx->up_ev[g], ctx->up_stream));
+  }
+  const DevBlock* blk = (const DevBlock*)dptr(ctx, "blocks");
+  for (int g = 0; g < G; ++g) {
+    long b0, nb;
+    group(g, b0, nb);
+    const long off = b0 * ctx->npts;
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->up_ev[g], 0));
+    if (mixed) {
+      float* x = (float*)dptr(ctx, "xfer");
+      LK(launch_convert_d2f(d64 + off, x + off, nb * ctx->npts, ctx->stream));
+      LK(launch_gamma_forward<float>(x + off, (float*)dptr(ctx, dst_name) + off,
+                                     (const float*)dptr(ctx, to_fbr ? "T" : "Tt"), blk + b0,
+                                     (int)nb, ctx->ng, ctx->ncol, ctx->stream));
+    } else {
+      LK(launch_gamma_forward<double>(d64 + off, (double*)dptr(ctx, dst_name) + off,
+                                      (const double*)dptr(ctx, to_fbr ? "T" : "Tt"), blk + b0,
+                                      (int)nb, ctx->ng, ctx->ncol, ctx->stream));
+    }
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return MW3_OK;
@@ -476,6 +503,9 @@ void mw3_destroy(mw3_ctx* ctx) {
     for (int i = 0; i < 2 * kNumKernels; ++i)
       if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     for (auto e : ctx->evpool) cudaEventDestroy(e);
+    for (auto e : ctx->up_ev)
+      if (e) cudaEventDestroy(e);
+    if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   }
   delete ctx;
