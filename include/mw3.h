@@ -225,7 +225,10 @@ int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel)
  * nblocks * ngamma * nr * NR elements. */
 int mw3_get_state(mw3_ctx* ctx, double* q, double* qprev);
 
-/* Overwrite q_k and q_{k-1} (host FP64, same size) without touching the sums. */
+/* Overwrite q_k and q_{k-1} (host FP64, same size; qprev == NULL sets q_{k-1} = 0) without
+ * touching the sums. Synchronous. The values cross to the device in four block groups on a
+ * library-owned copy stream, each group's conversion and DVR -> FBR transform overlapping the
+ * next group's copy; page-locked host memory gives the full link bandwidth. */
 int mw3_set_state(mw3_ctx* ctx, const double* q, const double* qprev);
 
 /* out[i] = (H_s q)[i] for a host FP64 vector q (one application of the scaled
