@@ -1751,22 +1751,34 @@ int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel)
                            cudaMemcpyDeviceToHost, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
+    // |S|^2 = 2 pi k_c / mu |pref A_c(E)|^2 / |a(E)|^2 with pref = 1 / (2 pi dE sin theta_E):
+    // energies outer so that a J's channel columns are read contiguously, the factors that
+    // depend on (J, E) only formed once
+    std::vector<double> fJE((size_t)nJ * nE);
+    for (int iJ = 0; iJ < nJ; ++iJ)
+      for (int e = 0; e < nE; ++e) {
+        const double pref = 1.0 / (2.0 * M_PI * ctx->dE[iJ] * std::sin(ctx->theta[(size_t)iJ * nE + e]));
+        fJE[(size_t)iJ * nE + e] = 2.0 * M_PI / ctx->mu * pref * pref / a2[e];
+      }
+    std::vector<long> nchJ(nJ);
+    for (int iJ = 0; iJ < nJ; ++iJ) nchJ[iJ] = ctx->ncols[iJ] - 2 * ctx->ncut[iJ];
+    std::vector<long> lcol(ctx->nchan);
+    std::vector<size_t> obase(ctx->nchan);
     for (int c = 0; c < ctx->nchan; ++c) {
       const int iJ = ctx->chan_iJ[c];
-      const long nch = ctx->ncols[iJ] - 2 * ctx->ncut[iJ];
-      const long lc = ctx->chan_col[c] - ctx->colbase[iJ] - 2 * ctx->ncut[iJ];
-      const double* A = chA[iJ].data();
-      for (int e = 0; e < nE; ++e) {
-        const double Etot = ctx->Ecol[e] + ctx->Ev0j0;
+      lcol[c] = ctx->chan_col[c] - ctx->colbase[iJ] - 2 * ctx->ncut[iJ];
+      obase[c] = ((((size_t)iJ * ne + ctx->chan_lam[c]) * nv + ctx->chan_v[c]) * nj + ctx->chan_j[c]) * nE;
+    }
+    for (int e = 0; e < nE; ++e) {
+      const double Etot = ctx->Ecol[e] + ctx->Ev0j0;
+      for (int c = 0; c < ctx->nchan; ++c) {
         const double K2 = 2.0 * ctx->mu * (Etot - ctx->chan_eps[c]);
         if (K2 <= 0) continue;
-        const double th = ctx->theta[(size_t)iJ * nE + e];
-        const double pref = 1.0 / (2.0 * M_PI * ctx->dE[iJ] * std::sin(th));
-        const double re = A[(size_t)e * nch + lc] * pref;
-        const double im = A[(size_t)(nE + e) * nch + lc] * pref;
-        const double s2 = 2.0 * M_PI * std::sqrt(K2) / ctx->mu * (re * re + im * im) / a2[e];
-        const size_t o = ((((size_t)iJ * ne + ctx->chan_lam[c]) * nv + ctx->chan_v[c]) * nj + ctx->chan_j[c]) * nE + e;
-        Pinel[o] += s2;
+        const int iJ = ctx->chan_iJ[c];
+        const double* A = chA[iJ].data();
+        const double re = A[(size_t)e * nchJ[iJ] + lcol[c]];
+        const double im = A[(size_t)(nE + e) * nchJ[iJ] + lcol[c]];
+        Pinel[obase[c] + e] += std::sqrt(K2) * fJE[(size_t)iJ * nE + e] * (re * re + im * im);
       }
     }
   }
