@@ -1435,8 +1435,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
   uint32_t phase = 0;
   bool ok = true;
   // both parities' MMAs of one GEMM (even: A even x buffer 0, odd: A odd x buffer 1), issued
-  // once every copy group has landed (visible to the tensor core) and the operand stores to
-  // tensor memory are complete; the wait comes later, so that CUDA-core work overlaps the MMAs
+  // once the copy groups it needs have landed (all, or all but the newest: visible to the tensor
+  // core) and the operand stores to tensor memory are complete; the wait comes later, so that
+  // CUDA-core work overlaps the MMAs
   auto issue_mma2 = [&](uint32_t de, uint32_t dodd, bool one_pending) {
     tmem_st_wait();
     if (one_pending) asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -1547,7 +1548,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     }
     wait_mma();
     if (!ok) break;
-    issue_b2(u, 2);                               // pending: [c t p], [G2e G2o]
+    issue_b2(u, 2);                               // pending: [c_(k-1)(u)], [c(u+1)], [G2e G2o(u)]
 
     // ---- potential: S = y(n) + y(n') into A even, D = y(n) - y(n') into A odd
 #pragma unroll
