@@ -329,8 +329,12 @@ int mw3_mlp_train(mw3_mlp* net, const float* X, const float* y, long n, int epoc
  *   nseg 1..64 (the array's capacity); other values return MW3_ERR_BAD_ARG.
  * Enqueued on `stream` (a cudaStream_t, NULL = legacy default); returns without
  * synchronising. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current: make it before any stream
- * capture. All calls share the array; calls that overlap on the GPU race. */
+ * (cudaGetSymbolAddress) with that device current and caches it with the current
+ * CUDA context; a call under a different context (after cudaDeviceReset, say) looks
+ * it up again. Make the first call of each context before any stream capture.
+ * Returns MW3_ERR_CUDA when one of its own two launches fails (an error left pending
+ * by earlier work is not reported or cleared). All calls share the array; calls that
+ * overlap on the GPU race. */
 int mw3_norms_noalloc(const double* x, long seg_len, int nseg, double* out, void* stream);
 
 /* Diagnostic: achieved FMA throughput of this GPU in TFLOP/s from an FMA-chain

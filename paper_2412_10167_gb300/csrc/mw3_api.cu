@@ -354,6 +354,12 @@ int transform_upload(mw3_ctx* ctx, const double* src, const char* dst_name, bool
   // the copies start after earlier work on the library's stream (which may still read xfer)
   CK(cudaEventRecord(ctx->up_ev[4], ctx->stream));
   CK(cudaStreamWaitEvent(ctx->up_stream, ctx->up_ev[4], 0));
+  // every return from here on, an error return included, first waits for the copies queued
+  // on the copy stream: they read the caller's host buffer, which is free once we return
+  struct CopyDrain {
+    cudaStream_t s;
+    ~CopyDrain() { cudaStreamSynchronize(s); }
+  } drain{ctx->up_stream};
   const int G = std::min(ctx->nblk, 4);
   auto group = [&](int g, long& b0, long& nb) {
     b0 = (long)g * ctx->nblk / G;

@@ -91,8 +91,9 @@ void fbr_matrix(int om, int n, const std::vector<double>& x, const std::vector<d
 }
 
 // Symmetric eigen-decomposition: Householder reduction to tridiagonal form, then
-// the implicit QL iteration with shifts; eigenvalues ascending, eigenvectors in the
-// columns of Z (row-major n x n).
+// the implicit QL iteration with Wilkinson-type shifts of Bowdler, Martin, Reinsch and
+// Wilkinson (the published tql2 algorithm, Numer. Math. 11, 1968); eigenvalues
+// ascending, eigenvectors in the columns of Z (row-major n x n).
 void symmetric_eigen(int n, const std::vector<double>& Ain, std::vector<double>& evals,
                      std::vector<double>& Z) {
   std::vector<double> A = Ain;

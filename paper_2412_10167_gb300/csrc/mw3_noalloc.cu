@@ -11,11 +11,15 @@
 // The array (kNoAllocMaxSegments x kNoAllocChunks doubles = 128 KB) is created on
 // every GPU that loads the library and stays there until the process exits. Host
 // code cannot use the array's name as a device address: on the first call for a
-// device, with that device current, its address is looked up once with
-// cudaGetSymbolAddress and cached. Do that first call before any stream capture.
+// device, with that device current, its address is looked up with
+// cudaGetSymbolAddress and cached together with the CUDA context that was current;
+// a later call under another context (after cudaDeviceReset, or once the primary
+// context was destroyed and made again) looks the address up anew. Make the first
+// call of each context before any stream capture.
 // Every call shares the one array and overwrites it completely (each chunk writes its
 // own slot before the final pass reads it, so nothing has to start at zero); calls
 // whose kernels overlap on the GPU (different streams, no ordering) race on it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -30,8 +34,28 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_partial[kNoAllocMaxSegments * kNoAllocChunks];
 
+// per device: the array's device address and the context it was looked up under
 double* g_partial_addr[kMaxDevices] = {};
+CUcontext g_partial_ctx[kMaxDevices] = {};
 std::mutex g_partial_mu;
+
+// the current CUDA context through the driver's entry point (the library does not link
+// libcuda); nullptr when it cannot be had
+CUcontext current_context() {
+  using CtxGetFn = CUresult (*)(CUcontext*);
+  static CtxGetFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetFn>(f);
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 
 // partial[s][chunk] = sum of x^2 over a fixed contiguous chunk of segment s
 __global__ void __launch_bounds__(256) k_segment_partial(const double* __restrict__ x,
@@ -72,15 +96,36 @@ extern "C" int mw3_norms_noalloc(const double* x, long seg_len, int nseg, double
   double* partial = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_partial_mu);
+    // the symbol lookup below makes the device's primary context current if none is, so
+    // the context is read after it
+    if (g_partial_addr[dev]) {
+      const CUcontext ctx = current_context();
+      if (!ctx || ctx != g_partial_ctx[dev]) g_partial_addr[dev] = nullptr;
+    }
     if (!g_partial_addr[dev]) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_partial) != cudaSuccess || !p) return MW3_ERR_CUDA;
       g_partial_addr[dev] = static_cast<double*>(p);
+      g_partial_ctx[dev] = current_context();
     }
     partial = g_partial_addr[dev];
   }
+  // each launch's own status: cudaLaunchKernel returns the status of this launch, so an
+  // error left pending by earlier, unrelated work on the thread is neither reported as
+  // this call's failure nor consumed here
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  k_segment_partial<<<dim3(kNoAllocChunks, nseg), 256, 0, st>>>(x, seg_len, partial);
-  k_segment_final<<<nseg, 32, 0, st>>>(partial, out);
-  return cudaGetLastError() == cudaSuccess ? MW3_OK : MW3_ERR_CUDA;
+  {
+    void* args[] = {(void*)&x, (void*)&seg_len, (void*)&partial};
+    if (cudaLaunchKernel((const void*)k_segment_partial, dim3(kNoAllocChunks, nseg), dim3(256),
+                         args, 0, st) != cudaSuccess)
+      return MW3_ERR_CUDA;
+  }
+  {
+    const double* pc = partial;
+    void* args[] = {(void*)&pc, (void*)&out};
+    if (cudaLaunchKernel((const void*)k_segment_final, dim3(nseg), dim3(32), args, 0, st) !=
+        cudaSuccess)
+      return MW3_ERR_CUDA;
+  }
+  return MW3_OK;
 }

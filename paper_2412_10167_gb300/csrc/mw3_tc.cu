@@ -91,6 +91,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
+// After a bounded wait expired, the MMAs committed to that barrier phase may still be
+// running and writing tensor memory. Before a CTA releases its tensor memory it waits for
+// that same phase once more, again bounded: the columns are freed only after the MMAs that
+// write them have completed (or after a second expiry, when the tensor core is taken to
+// have stopped answering).
+__device__ __forceinline__ void drain_expired(bool ok, uint32_t mbar, uint32_t expired_parity) {
+  if (!ok) (void)mbar_wait(mbar, expired_parity);
+}
+
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
   uint32_t r[4];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
@@ -450,6 +459,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc(TcArgs a) {
   double ss = (double)ssf;
   for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
   if (lane == 0) red[warp] = ss;
+  drain_expired(ok, mb, phase ^ 1u);   // ok is CTA-uniform; the failed wait toggled phase
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (tid == 0) {
@@ -719,6 +729,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc2(TcArgs a) {
     }
   }
   if (!ok && tid == 0) atomicExch(a.err, 1);
+  drain_expired(ok, mb, phase ^ 1u);   // ok is CTA-uniform; the failed wait toggled phase
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) {
@@ -1077,6 +1088,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc3(TcArgs a) {
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (!ok && tid == 0) atomicExch(a.err, 1);
+  drain_expired(ok, mb, phase ^ 1u);   // ok is CTA-uniform; the failed wait toggled phase
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) {
@@ -1337,6 +1349,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc4(TcArgs a) {
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (!ok && tid == 0) atomicExch(a.err, 1);
+  drain_expired(ok, mb, phase ^ 1u);   // ok is CTA-uniform; the failed wait toggled phase
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) {
@@ -1695,6 +1708,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (!ok && tid == 0) atomicExch(a.err, 1);
+  drain_expired(ok, mb, phase ^ 1u);   // ok is CTA-uniform; the failed wait toggled phase
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) {
@@ -1850,6 +1864,7 @@ __global__ void __launch_bounds__(FL_THREADS) k_flush_tc(const float* __restrict
   } else if (tid == 0) {
     atomicExch(err, 1);
   }
+  drain_expired(ok, mb, phase ^ 1u);   // ok is CTA-uniform; the failed wait toggled phase
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) {
