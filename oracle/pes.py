@@ -85,6 +85,8 @@ def potential_matrix(r, R, cosg, masses, pes):
                                      np.asarray(cosg, float))
     if pes.get("kind") == "separable_eckart":
         return separable_eckart(r, R, pes)[..., None, None]
+    if pes.get("kind") == "product_eckart":
+        return product_eckart(r, R, cosg, masses, pes)[..., None, None]
     mA, mB, mC = masses
     rAB, rBC, rAC = bond_distances(r, R, cosg, mA, mB, mC)
     v11 = leps(rAB, rBC, rAC, pes["D_eV"], pes["beta"], pes["re"], pes["delta"])
@@ -105,6 +107,45 @@ def potential_matrix(r, R, cosg, masses, pes):
 def eckart_barrier(R, V0_eV, alpha, Rb):
     """Symmetric Eckart barrier V0 sech^2(alpha (R - Rb)) in hartree."""
     return V0_eV * EV / np.cosh(alpha * (R - Rb)) ** 2
+
+
+def product_jacobi_lengths(r, R, cosg, masses, arrangement):
+    """(r', R'): lengths of the product Jacobi vectors at reactant Jacobi points.
+
+    With B at the origin, C = r (along z) and A = (m_C/M_BC) r + R at angle gamma to r:
+      "AC+B": r' = |C - A|, R' = |B - X_AC|;   "AB+C": r' = |B - A|, R' = |C - X_AB|,
+    X_.. the centre of mass of the product diatom.
+    """
+    mA, mB, mC = masses
+    r, R, cosg = np.broadcast_arrays(np.asarray(r, float), np.asarray(R, float),
+                                     np.asarray(cosg, float))
+    sing = np.sqrt(np.maximum(1.0 - cosg * cosg, 0.0))
+    Ax, Az = R * sing, mC / (mB + mC) * r + R * cosg       # A; B = (0, 0); C = (0, r)
+    if arrangement == "AC+B":
+        rp = np.hypot(Ax, r - Az)
+        Xx, Xz = mA * Ax / (mA + mC), (mA * Az + mC * r) / (mA + mC)
+        Rp = np.hypot(Xx, Xz)
+    elif arrangement == "AB+C":
+        rp = np.hypot(Ax, Az)
+        Xx, Xz = mA * Ax / (mA + mB), mA * Az / (mA + mB)
+        Rp = np.hypot(Xx, r - Xz)
+    else:
+        raise ValueError("arrangement must be 'AC+B' or 'AB+C'")
+    return rp, Rp
+
+
+def product_eckart(r, R, cosg, masses, pes):
+    """Test surface separable in PRODUCT Jacobi coordinates: an Eckart barrier in R' plus
+    the diatomic Morse curve in r' (arrangement pes["arrangement"]).
+
+    A product-arrangement packet in one diatomic state (v', j') keeps it, and its
+    transmission through the barrier is the textbook Eckart closed form in R' with the
+    product reduced mass mu' (the rotational terms conserve j' because V does not
+    depend on gamma').
+    """
+    rp, Rp = product_jacobi_lengths(r, R, cosg, masses, pes["arrangement"])
+    return (eckart_barrier(Rp, pes["V0_eV"], pes["alpha"], pes["Rb"])
+            + morse(rp, pes["D_eV"], pes["beta"], pes["re"]))
 
 
 def separable_eckart(r, R, pes):

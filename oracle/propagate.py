@@ -54,13 +54,17 @@ def damping_profile(x, xI, A, n):
 def damping_grid(H: GridHamiltonian, absorber: dict):
     """D[k, m] = exp(-phi_r(r_k)) exp(-phi_R(R_m)).
 
-    Test option ``RI_low``/``AR_low``: an extra absorber below R = RI_low (used only
-    when the flux is taken in R, so that the transmitted part is absorbed too).
+    Test options ``RI_low``/``AR_low`` and ``rI_low``/``Ar_low``: an extra absorber below
+    R = RI_low (used only when the flux is taken in R, so that the transmitted part is
+    absorbed too), or below r = rI_low (a product-arrangement packet whose R' runs
+    along r).
     """
     DR = damping_profile(H.R, absorber["RI"], absorber["AR"], absorber["nR"])
     if absorber.get("RI_low") is not None:
         DR = DR * damping_profile(-H.R, -absorber["RI_low"], absorber["AR_low"], absorber["nR"])
     Dr = damping_profile(H.r, absorber["rI"], absorber["Ar"], absorber["nr"])
+    if absorber.get("rI_low") is not None:
+        Dr = Dr * damping_profile(-H.r, -absorber["rI_low"], absorber["Ar_low"], absorber["nr"])
     return Dr[:, None] * DR[None, :]
 
 
@@ -278,16 +282,7 @@ def propagate(cfg: dict, nsteps=None, H: GridHamiltonian = None, flux_axis="r",
                  theta=theta, info=info, H=H, states=states)
     a = incoming_amplitude(H, info["g_tilde"], Ecol)
     res["a"] = a
-    # Psi_E = [1/(2 pi dE sin theta)] sum_k c_k q_k
-    pref = 1.0 / (2.0 * np.pi * H.dE[bj][:, None] * np.sin(th_blk))   # [nblk, nE]
-    flux = np.zeros((len(H.Js), len(Ecol)))
-    for b in range(H.nblk):
-        PsiE = pref[b][:, None, None] * A[b]
-        dPsiE = pref[b][:, None, None] * B[b]
-        flux[bj[b]] += np.sum(np.imag(np.conj(PsiE) * dPsiE), axis=(1, 2))
-    mass = H.m if flux_axis == "r" else H.mu
-    res["flux_sum"] = flux
-    res["P_total"] = (2.0 * np.pi / mass) * flux / np.abs(a)[None, :] ** 2
+    res["flux_sum"], res["P_total"] = total_probability(H, A, B, theta, a, flux_axis)
     if channels:
         pref_c = 1.0 / (2.0 * np.pi * H.dE[chan_J][:, None] * np.sin(theta[chan_J]))
         CE = pref_c * Cc
@@ -302,20 +297,57 @@ def propagate(cfg: dict, nsteps=None, H: GridHamiltonian = None, flux_axis="r",
             key = (iJ, L, v, j)
             res["P_inel"][key] = res["P_inel"].get(key, 0.0) + s2
     if prod:
-        # product channels: |S|^2 = (2 pi K' / mu') |C_E|^2 / |a|^2, summed over Omega'
-        res["P_prod"] = {}
         res["prod_channels"] = [pa.channels(iJ) for iJ in range(len(H.Js))]
         res["C_prod_raw"] = Cp
-        for iJ in range(len(H.Js)):
-            pref_p = 1.0 / (2.0 * np.pi * H.dE[iJ] * np.sin(theta[iJ]))
-            for ic, (L, v, j, op, e) in enumerate(pa.channels(iJ)):
-                K2 = 2.0 * pa.mu_p * (Etot - e)
-                Kp = np.sqrt(np.where(K2 > 0, K2, 0.0))
-                s2 = np.where(K2 > 0, 2.0 * np.pi * Kp / pa.mu_p * np.abs(pref_p * Cp[iJ][ic]) ** 2
-                              / np.abs(a) ** 2, 0.0)
-                key = (iJ, L, v, j)
-                res["P_prod"][key] = res["P_prod"].get(key, 0.0) + s2
+        res["P_prod"] = product_probabilities(H, pa, Cp, theta, Etot, a)
     return res
+
+
+def total_probability(H: GridHamiltonian, A, B, theta, a, flux_axis="r"):
+    """Total reaction probability from the flux through the cut (Section 2.4,
+    Eq. total-flux, with the reading of the module header).
+
+    A[b, E, ...], B[b, E, ...] are the Chebyshev sums sum_k (2 - delta_k0) exp(-i k theta)
+    of psi_k and d psi_k / dx on the cut of every block b (x = r, or R for the test
+    option), theta[iJ, E] the Chebyshev angles, a[E] the incoming amplitude:
+      Psi_E = A / (2 pi dE sin theta),  dPsi_E = B / (2 pi dE sin theta),
+      P(E) = (2 pi / m_x) Im sum_(b, cut) conj(Psi_E) dPsi_E / |a|^2,
+    m_x the reduced mass of the cut's coordinate (m for r, mu for R). Returns the raw
+    flux sum [nJ, nE] and P [nJ, nE].
+    """
+    bj = H.block_J_index()
+    nE = theta.shape[1]
+    pref = 1.0 / (2.0 * np.pi * H.dE[bj][:, None] * np.sin(theta[bj]))   # [nblk, nE]
+    flux = np.zeros((len(H.Js), nE))
+    for b in range(H.nblk):
+        PsiE = pref[b][:, None, None] * A[b]
+        dPsiE = pref[b][:, None, None] * B[b]
+        flux[bj[b]] += np.sum(np.imag(np.conj(PsiE) * dPsiE), axis=(1, 2))
+    mass = H.m if flux_axis == "r" else H.mu
+    return flux, (2.0 * np.pi / mass) * flux / np.abs(a)[None, :] ** 2
+
+
+def product_probabilities(H: GridHamiltonian, pa: ProductAnalysis, Cp, theta, Etot, a):
+    """State-resolved product probabilities (Section 2.4, Eq. S-matrix-from-chebyshev).
+
+    Cp[iJ][c, E] are the Chebyshev sums sum_k (2 - delta_k0) exp(-i k theta) C_c(k) of
+    the product-channel overlaps, theta[iJ, E] the Chebyshev angles, Etot[E] the total
+    energies and a[E] the incoming amplitude. Per channel c = (Lambda', v', j', Omega'):
+      C_E(c) = C_c / (2 pi dE sin theta),  K' = sqrt(2 mu' (E - e_c)),
+      |S_c|^2 = (2 pi K' / mu') |C_E(c)|^2 / |a|^2  (0 for a closed channel),
+    and the result per (iJ, Lambda', v', j') is the sum of |S_c|^2 over Omega'.
+    """
+    out = {}
+    for iJ in range(len(H.Js)):
+        pref_p = 1.0 / (2.0 * np.pi * H.dE[iJ] * np.sin(theta[iJ]))
+        for ic, (L, v, j, op, e) in enumerate(pa.channels(iJ)):
+            K2 = 2.0 * pa.mu_p * (Etot - e)
+            Kp = np.sqrt(np.where(K2 > 0, K2, 0.0))
+            s2 = np.where(K2 > 0, 2.0 * np.pi * Kp / pa.mu_p * np.abs(pref_p * Cp[iJ][ic]) ** 2
+                          / np.abs(a) ** 2, 0.0)
+            key = (iJ, L, v, j)
+            out[key] = out.get(key, 0.0) + s2
+    return out
 
 
 def time_domain_packet(states, t, E0, dE):
