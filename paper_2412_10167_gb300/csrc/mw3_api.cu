@@ -138,8 +138,12 @@ struct mw3_ctx {
   int nchan = 0;
   std::vector<int> chan_block, chan_row, chan_col, chan_v, chan_j, chan_om, chan_lam, chan_iJ;
   std::vector<double> chan_eps;
+  // flux-cut ring (the context's precision): per J 2 ncut columns (psi, dpsi)
   std::vector<long> colbase, ncols, ncut, accoff;
   long NC = 0, max_cols = 0, acc_size = 0;
+  // channel ring (FP64 in both precisions): per J the reactant, then the product channels
+  std::vector<long> colbase_c, ncols_c, accoff_c;
+  long NCc = 0, max_cols_c = 0, accc_size = 0;
 
   // product channels (mw3_set_products)
   bool prod_on = false;
@@ -917,7 +921,9 @@ int mw3_init_packet(mw3_ctx* ctx, const mw3_packet_desc* d) {
   ctx->norm_trace.clear();
   if (ctx->stage < 3) ctx->stage = 3;
   if (ctx->stage >= 5) {
-    if ((st = dzero(ctx, "acc")) || (st = dzero(ctx, "cut")) || (st = dzero(ctx, "d_iter"))) return st;
+    if ((st = dzero(ctx, "acc")) || (st = dzero(ctx, "cut")) || (st = dzero(ctx, "accc")) ||
+        (st = dzero(ctx, "cutc")) || (st = dzero(ctx, "d_iter")))
+      return st;
     if (!ctx->host_only) CK(cudaStreamSynchronize(ctx->stream));
   }
   return MW3_OK;
@@ -1151,11 +1157,15 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
   ctx->ncols.assign(ctx->nJ, 0);
   ctx->ncut.assign(ctx->nJ, 0);
   ctx->accoff.assign(ctx->nJ, 0);
-  long col = 0, acc = 0, maxc = 0;
+  ctx->colbase_c.assign(ctx->nJ, 0);
+  ctx->ncols_c.assign(ctx->nJ, 0);
+  ctx->accoff_c.assign(ctx->nJ, 0);
+  long col = 0, acc = 0, maxc = 0, colc = 0, accc = 0, maxcc = 0;
   for (int iJ = 0; iJ < ctx->nJ; ++iJ) {
     const long b0 = ctx->J_first_block[iJ], b1 = ctx->J_first_block[iJ + 1];
     const long nc = (b1 - b0) * ng * ctx->NR;
     ctx->colbase[iJ] = col;
+    ctx->colbase_c[iJ] = colc;
     ctx->ncut[iJ] = nc;
     for (long b = b0; b < b1; ++b) ctx->blocks[b].cutcol = (int)(col + (b - b0) * ng * ctx->NR);
     long nch = 0;
@@ -1173,7 +1183,7 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
           auto& ec = cache[key];
           for (int v = 0; v <= d->vmax; ++v) {
             ctx->chan_block.push_back((int)b);
-            ctx->chan_col.push_back((int)(col + 2 * nc + nch));
+            ctx->chan_col.push_back((int)(colc + nch));
             ctx->chan_v.push_back(v);
             ctx->chan_j.push_back(j);
             ctx->chan_om.push_back(B.omega);
@@ -1193,28 +1203,46 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
       const long p0 = ctx->prod_first[iJ];
       nchp = ctx->prod_first[iJ + 1] - p0;
       for (auto& g : ctx->prod_groups)
-        if (g.c0 >= p0 && g.c0 < p0 + nchp) g.col0 = (int)(col + 2 * nc + nch + (g.c0 - p0));
+        if (g.c0 >= p0 && g.c0 < p0 + nchp) g.col0 = (int)(colc + nch + (g.c0 - p0));
     }
-    ctx->ncols[iJ] = 2 * nc + nch + nchp;
+    ctx->ncols[iJ] = 2 * nc;
     ctx->accoff[iJ] = acc;
     acc += 2L * nE * ctx->ncols[iJ];
     maxc = std::max(maxc, ctx->ncols[iJ]);
     col += ((ctx->ncols[iJ] + 3) / 4) * 4;
+    ctx->ncols_c[iJ] = nch + nchp;
+    ctx->accoff_c[iJ] = accc;
+    accc += 2L * nE * ctx->ncols_c[iJ];
+    maxcc = std::max(maxcc, ctx->ncols_c[iJ]);
+    colc += ((ctx->ncols_c[iJ] + 3) / 4) * 4;
   }
   ctx->nchan = (int)ctx->chan_block.size();
   ctx->NC = col;
   ctx->max_cols = maxc;
   ctx->acc_size = acc;
+  ctx->NCc = colc;
+  ctx->max_cols_c = maxcc;
+  ctx->accc_size = accc;
   int st;
   const int kb = ctx->tune.kb;
   if ((st = upload_raw(ctx, "blocks", ctx->blocks))) return st;
   if ((st = dalloc(ctx, "cut", (size_t)kb * ctx->NC * ctx->rs())) || (st = dzero(ctx, "cut"))) return st;
   if ((st = dalloc(ctx, "acc", (size_t)acc * 8)) || (st = dzero(ctx, "acc"))) return st;
   if ((st = dalloc(ctx, "ph", (size_t)ctx->nJ * 2 * nE * kb * ctx->rs()))) return st;
+  // channel ring, its FP64 accumulators and (mixed form) its FP64 phase matrix
+  if ((st = dalloc(ctx, "cutc", (size_t)kb * std::max(ctx->NCc, 4L) * 8)) || (st = dzero(ctx, "cutc")))
+    return st;
+  if ((st = dalloc(ctx, "accc", (size_t)std::max(accc, 1L) * 8)) || (st = dzero(ctx, "accc"))) return st;
+  if (ctx->precision != MW3_FP64 &&
+      (st = dalloc(ctx, "ph64", (size_t)ctx->nJ * 2 * nE * kb * 8)))
+    return st;
   if ((st = upload_real(ctx, "theta", ctx->theta, true))) return st;
   if ((st = upload_real(ctx, "wpsi", ctx->wpsi)) || (st = upload_real(ctx, "wdpsi", ctx->wdpsi))) return st;
   if ((st = upload_raw(ctx, "colbase", ctx->colbase)) || (st = upload_raw(ctx, "ncols", ctx->ncols)) ||
       (st = upload_raw(ctx, "ncut", ctx->ncut)) || (st = upload_raw(ctx, "accoff", ctx->accoff)))
+    return st;
+  if ((st = upload_raw(ctx, "colbase_c", ctx->colbase_c)) ||
+      (st = upload_raw(ctx, "ncols_c", ctx->ncols_c)) || (st = upload_raw(ctx, "accoff_c", ctx->accoff_c)))
     return st;
   {
     std::vector<int> nci(ctx->nJ);
@@ -1223,7 +1251,7 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
   }
   if ((st = dalloc(ctx, "qcol", (size_t)ctx->nblk * ng * nr * ctx->rs()))) return st;
   if (ctx->nchan > 0) {
-    if ((st = upload_real(ctx, "P", P)) || (st = upload_raw(ctx, "chan_block", ctx->chan_block)) ||
+    if ((st = upload_real(ctx, "P", P, true)) || (st = upload_raw(ctx, "chan_block", ctx->chan_block)) ||
         (st = upload_raw(ctx, "chan_row", ctx->chan_row)) ||
         (st = upload_raw(ctx, "chan_col", ctx->chan_col)))
       return st;
@@ -1239,11 +1267,15 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
     }
     if ((st = upload_raw(ctx, "p_jl", ctx->prod_jl)) || (st = upload_raw(ctx, "p_chan", ctx->prod_chan)))
       return st;
-    if ((st = upload_raw(ctx, "p_idx", ctx->prod_idx)) || (st = upload_real(ctx, "p_w", ctx->prod_w)) ||
-        (st = upload_real(ctx, "p_pl", ctx->prod_pl)) || (st = upload_real(ctx, "p_T", ctx->prod_T)) ||
-        (st = upload_real(ctx, "p_jac", ctx->prod_jac)) || (st = upload_real(ctx, "p_W", ctx->prod_W)) ||
+    // the projection runs in FP64 in both precisions: only the Legendre rows, which multiply
+    // the state inside the blocked partial sums, take the state's precision
+    if ((st = upload_raw(ctx, "p_idx", ctx->prod_idx)) ||
+        (st = upload_real(ctx, "p_w", ctx->prod_w, true)) ||
+        (st = upload_real(ctx, "p_pl", ctx->prod_pl)) || (st = upload_real(ctx, "p_T", ctx->prod_T, true)) ||
+        (st = upload_real(ctx, "p_jac", ctx->prod_jac, true)) ||
+        (st = upload_real(ctx, "p_W", ctx->prod_W, true)) ||
         (st = upload_raw(ctx, "p_groups", ctx->prod_groups)) ||
-        (st = dalloc(ctx, "p_v", ctx->prod_groups.size() * (size_t)ctx->prod_nn * ctx->rs())))
+        (st = dalloc(ctx, "p_v", ctx->prod_groups.size() * (size_t)ctx->prod_nn * 8)))
       return st;
   }
   if ((st = dalloc(ctx, "d_iter", 8))) return st;
@@ -1271,7 +1303,9 @@ namespace {
 template <typename real>
 struct Bufs {
   real *q[2], *t, *u, *V, *T, *Tt, *coef, *fR, *fr, *DR, *Dr, *lamR, *lamr, *wpsi, *wdpsi, *cut,
-      *qcol, *P, *ph;
+      *qcol, *ph;
+  double *P, *cutc, *ph64, *accc;
+  long *colbase_c, *ncols_c, *accoff_c;
   void *twR, *phR, *twr, *phr;
   DevBlock* blocks;
   DevJ* dj;
@@ -1301,8 +1335,15 @@ Bufs<real> bufs(mw3_ctx* ctx) {
   b.wdpsi = (real*)dptr(ctx, "wdpsi");
   b.cut = (real*)dptr(ctx, "cut");
   b.qcol = (real*)dptr(ctx, "qcol");
-  b.P = (real*)dptr(ctx, "P");
+  b.P = (double*)dptr(ctx, "P");
   b.ph = (real*)dptr(ctx, "ph");
+  b.cutc = (double*)dptr(ctx, "cutc");
+  // FP64 phases of the channel ring: the flux ring's own in the FP64 form
+  b.ph64 = std::is_same<real, double>::value ? (double*)b.ph : (double*)dptr(ctx, "ph64");
+  b.accc = (double*)dptr(ctx, "accc");
+  b.colbase_c = (long*)dptr(ctx, "colbase_c");
+  b.ncols_c = (long*)dptr(ctx, "ncols_c");
+  b.accoff_c = (long*)dptr(ctx, "accoff_c");
   b.twR = dptr(ctx, "twR");
   b.phR = dptr(ctx, "phR");
   b.twr = dptr(ctx, "twr");
@@ -1372,6 +1413,7 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
   const long nrows = (long)ctx->nblk * ctx->ng * ctx->nr;
   const bool analysis = (mode == 0) && ctx->stage >= 5;
   real* cut_slot = analysis ? B.cut + (long)slot * ctx->NC : nullptr;
+  double* cutc_slot = analysis ? B.cutc + (long)slot * ctx->NCc : nullptr;
   {
     Timer tm(ctx, 0, timed);
     LK(launch_kinetic_rows<real>(qk, B.t, nrows, ctx->planR, B.twR, B.phR, B.lamR,
@@ -1461,19 +1503,19 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
   if (analysis && ctx->nchan > 0) {
     Timer tm(ctx, 4, timed);
     LK(launch_channels<real>(B.qcol, B.P, B.chan_block, B.chan_row, B.chan_col, ctx->nchan,
-                             ctx->ng, ctx->nr, B.d_iter, slot, ctx->an.kmin, cut_slot, st));
+                             ctx->ng, ctx->nr, B.d_iter, slot, ctx->an.kmin, cutc_slot, st));
     tm.stop();
   }
   if (analysis && ctx->prod_on) {
     Timer tm(ctx, 8, timed);
     LK(launch_products<real>(qk, ctx->ng, ctx->nr, ctx->NR, ctx->prod_nn,
-                             (const int*)dptr(ctx, "p_idx"), (const real*)dptr(ctx, "p_w"),
+                             (const int*)dptr(ctx, "p_idx"), (const double*)dptr(ctx, "p_w"),
                              (const real*)dptr(ctx, "p_pl"), ctx->prod_ltop,
-                             (const real*)dptr(ctx, "p_T"), (const real*)dptr(ctx, "p_jac"),
+                             (const double*)dptr(ctx, "p_T"), (const double*)dptr(ctx, "p_jac"),
                              (const ProdGroup*)dptr(ctx, "p_groups"), (const int*)dptr(ctx, "p_jl"),
-                             (int)ctx->prod_jl.size(), ctx->prod_max_nom, (real*)dptr(ctx, "p_v"),
-                             (const real*)dptr(ctx, "p_W"), (const int2*)dptr(ctx, "p_chan"),
-                             (int)ctx->prod_first[ctx->nJ], cut_slot, st));
+                             (int)ctx->prod_jl.size(), ctx->prod_max_nom, (double*)dptr(ctx, "p_v"),
+                             (const double*)dptr(ctx, "p_W"), (const int2*)dptr(ctx, "p_chan"),
+                             (int)ctx->prod_first[ctx->nJ], cutc_slot, st));
     tm.stop();
   }
   if (!tc) {
@@ -1498,6 +1540,14 @@ int flush(mw3_ctx* ctx, int nvalid, bool timed) {
   } else {
     LK(launch_sums_flush<real>(B.ph, B.cut, ctx->NC, ctx->tune.kb, ctx->nJ, ctx->an.nE,
                                B.colbase, B.ncols, B.accoff, ctx->max_cols, B.acc, st));
+  }
+  // channel overlaps: FP64 ring, FP64 phases, FP64 GEMM into their own accumulators
+  if (ctx->max_cols_c > 0) {
+    if (!std::is_same<real, double>::value)
+      LK(launch_phases<double>(B.theta, ctx->nJ, ctx->an.nE, ctx->tune.kb, nvalid, B.d_iter,
+                               B.ph64, st));
+    LK(launch_sums_flush<double>(B.ph64, B.cutc, ctx->NCc, ctx->tune.kb, ctx->nJ, ctx->an.nE,
+                                 B.colbase_c, B.ncols_c, B.accoff_c, ctx->max_cols_c, B.accc, st));
   }
   LK(launch_advance(B.d_iter, nvalid, st));
   tm.stop();
@@ -1696,10 +1746,10 @@ int mw3_product_probabilities(mw3_ctx* ctx, double* P) {
   for (int iJ = 0; iJ < nJ; ++iJ) {
     const long p0 = ctx->prod_first[iJ], np = ctx->prod_first[iJ + 1] - p0;
     if (np <= 0) continue;
-    const long first = ctx->ncols[iJ] - np;           // local column of the first product channel
+    const long first = ctx->ncols_c[iJ] - np;         // local column of the first product channel
     std::vector<double> A((size_t)2 * nE * np);
-    const double* src = (const double*)dptr(ctx, "acc") + ctx->accoff[iJ] + first;
-    CK(cudaMemcpy2DAsync(A.data(), np * 8, src, ctx->ncols[iJ] * 8, np * 8, 2 * nE,
+    const double* src = (const double*)dptr(ctx, "accc") + ctx->accoff_c[iJ] + first;
+    CK(cudaMemcpy2DAsync(A.data(), np * 8, src, ctx->ncols_c[iJ] * 8, np * 8, 2 * nE,
                          cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     for (long c = 0; c < np; ++c) {
@@ -1748,12 +1798,16 @@ int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel)
     std::fill(Pinel, Pinel + (size_t)nJ * ne * nv * nj * nE, 0.0);
     // channel columns only: per J a [2 nE x nchan_J] block of the accumulator
     std::vector<std::vector<double>> chA(nJ);
+    // reactant channels: the first columns of each J's block of the channel accumulators
+    auto nreact = [&](int iJ) {
+      return ctx->ncols_c[iJ] - (ctx->prod_on ? ctx->prod_first[iJ + 1] - ctx->prod_first[iJ] : 0L);
+    };
     for (int iJ = 0; iJ < nJ; ++iJ) {
-      const long nch = ctx->ncols[iJ] - 2 * ctx->ncut[iJ];
+      const long nch = nreact(iJ);
       chA[iJ].assign((size_t)2 * nE * std::max(nch, 1L), 0.0);
       if (nch <= 0) continue;
-      const double* src = (const double*)dptr(ctx, "acc") + ctx->accoff[iJ] + 2 * ctx->ncut[iJ];
-      CK(cudaMemcpy2DAsync(chA[iJ].data(), nch * 8, src, ctx->ncols[iJ] * 8, nch * 8, 2 * nE,
+      const double* src = (const double*)dptr(ctx, "accc") + ctx->accoff_c[iJ];
+      CK(cudaMemcpy2DAsync(chA[iJ].data(), nch * 8, src, ctx->ncols_c[iJ] * 8, nch * 8, 2 * nE,
                            cudaMemcpyDeviceToHost, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1767,12 +1821,12 @@ int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel)
         fJE[(size_t)iJ * nE + e] = 2.0 * M_PI / ctx->mu * pref * pref / a2[e];
       }
     std::vector<long> nchJ(nJ);
-    for (int iJ = 0; iJ < nJ; ++iJ) nchJ[iJ] = ctx->ncols[iJ] - 2 * ctx->ncut[iJ];
+    for (int iJ = 0; iJ < nJ; ++iJ) nchJ[iJ] = nreact(iJ);
     std::vector<long> lcol(ctx->nchan);
     std::vector<size_t> obase(ctx->nchan);
     for (int c = 0; c < ctx->nchan; ++c) {
       const int iJ = ctx->chan_iJ[c];
-      lcol[c] = ctx->chan_col[c] - ctx->colbase[iJ] - 2 * ctx->ncut[iJ];
+      lcol[c] = ctx->chan_col[c] - ctx->colbase_c[iJ];
       obase[c] = ((((size_t)iJ * ne + ctx->chan_lam[c]) * nv + ctx->chan_v[c]) * nj + ctx->chan_j[c]) * nE;
     }
     for (int e = 0; e < nE; ++e) {
@@ -1872,20 +1926,24 @@ int mw3_checkpoint_save(mw3_ctx* ctx, const char* path) {
   // raw device state (FBR coefficients in the context's precision), no conversion
   const size_t nb = (size_t)ctx->nblk * ctx->npts * ctx->rs();
   std::vector<char> q(nb), qp(nb);
-  std::vector<double> acc(ctx->acc_size);
+  std::vector<double> acc(ctx->acc_size), accc(ctx->accc_size);
   CK(cudaMemcpyAsync(q.data(), dptr(ctx, state_name(ctx, true)), nb, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(qp.data(), dptr(ctx, state_name(ctx, false)), nb, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(acc.data(), dptr(ctx, "acc"), acc.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (!accc.empty())
+    CK(cudaMemcpyAsync(accc.data(), dptr(ctx, "accc"), accc.size() * 8, cudaMemcpyDeviceToHost,
+                       ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   std::ofstream f(path, std::ios::binary);
   if (!f) return ctx->fail(MW3_ERR_IO, std::string("cannot open ") + path);
-  const uint64_t magic = 0x4d57334350543032ULL;  // "MW3CPT02"
-  const uint64_t hdr[6] = {magic, (uint64_t)ctx->nblk, (uint64_t)ctx->npts, (uint64_t)ctx->acc_size,
-                           (uint64_t)ctx->iter, (uint64_t)ctx->precision};
+  const uint64_t magic = 0x4d57334350543033ULL;  // "MW3CPT03"
+  const uint64_t hdr[7] = {magic, (uint64_t)ctx->nblk, (uint64_t)ctx->npts, (uint64_t)ctx->acc_size,
+                           (uint64_t)ctx->iter, (uint64_t)ctx->precision, (uint64_t)ctx->accc_size};
   f.write((const char*)hdr, sizeof(hdr));
   f.write(q.data(), nb);
   f.write(qp.data(), nb);
   f.write((const char*)acc.data(), acc.size() * 8);
+  f.write((const char*)accc.data(), accc.size() * 8);
   const uint64_t nt = ctx->norm_trace.size();
   f.write((const char*)&nt, 8);
   f.write((const char*)ctx->norm_trace.data(), nt * 8);
@@ -1898,18 +1956,19 @@ int mw3_checkpoint_load(mw3_ctx* ctx, const char* path) {
   if (ctx->stage < 5 || ctx->host_only) return ctx->fail(MW3_ERR_STATE, "set up the context first");
   std::ifstream f(path, std::ios::binary);
   if (!f) return ctx->fail(MW3_ERR_IO, std::string("cannot open ") + path);
-  uint64_t hdr[6];
+  uint64_t hdr[7];
   f.read((char*)hdr, sizeof(hdr));
-  if (!f || hdr[0] != 0x4d57334350543032ULL || hdr[1] != (uint64_t)ctx->nblk ||
+  if (!f || hdr[0] != 0x4d57334350543033ULL || hdr[1] != (uint64_t)ctx->nblk ||
       hdr[2] != (uint64_t)ctx->npts || hdr[3] != (uint64_t)ctx->acc_size ||
-      hdr[5] != (uint64_t)ctx->precision)
+      hdr[5] != (uint64_t)ctx->precision || hdr[6] != (uint64_t)ctx->accc_size)
     return ctx->fail(MW3_ERR_IO, "checkpoint does not match this configuration");
   const size_t nb = (size_t)ctx->nblk * ctx->npts * ctx->rs();
   std::vector<char> q(nb), qp(nb);
-  std::vector<double> acc(ctx->acc_size);
+  std::vector<double> acc(ctx->acc_size), accc(ctx->accc_size);
   f.read(q.data(), nb);
   f.read(qp.data(), nb);
   f.read((char*)acc.data(), acc.size() * 8);
+  f.read((char*)accc.data(), accc.size() * 8);
   uint64_t nt = 0;
   f.read((char*)&nt, 8);
   std::vector<double> tr(nt);
@@ -1918,6 +1977,9 @@ int mw3_checkpoint_load(mw3_ctx* ctx, const char* path) {
   CK(cudaMemcpyAsync(dptr(ctx, state_name(ctx, true)), q.data(), nb, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(dptr(ctx, state_name(ctx, false)), qp.data(), nb, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(dptr(ctx, "acc"), acc.data(), acc.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  if (!accc.empty())
+    CK(cudaMemcpyAsync(dptr(ctx, "accc"), accc.data(), accc.size() * 8, cudaMemcpyHostToDevice,
+                       ctx->stream));
   ctx->iter = (long)hdr[4];
   long it = ctx->iter;
   CK(cudaMemcpyAsync(dptr(ctx, "d_iter"), &it, 8, cudaMemcpyHostToDevice, ctx->stream));

@@ -306,18 +306,18 @@ cudaError_t launch_advance(long* d_iter, long n, cudaStream_t st) {
 // chi already divided by sqrt(dR); qcol holds the FBR coefficients at R_inf.
 template <typename real>
 __global__ void __launch_bounds__(128) k_channels(const real* __restrict__ qcol,
-                                                  const real* __restrict__ chi,
+                                                  const double* __restrict__ chi,
                                                   const int* __restrict__ chan_block,
                                                   const int* __restrict__ chan_row,
                                                   const int* __restrict__ chan_col, int ng, int nr,
                                                   const long* __restrict__ d_iter, int slot,
-                                                  long kmin, real* __restrict__ cut) {
+                                                  long kmin, double* __restrict__ cut) {
   __shared__ double red[128];
   const int c = blockIdx.x;
-  const real* p = chi + (long)c * nr;
+  const double* p = chi + (long)c * nr;
   const real* x = qcol + ((long)chan_block[c] * ng + chan_row[c]) * nr;
   double s = 0;
-  for (int i = threadIdx.x; i < nr; i += blockDim.x) s += (double)p[i] * (double)x[i];
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) s += p[i] * (double)x[i];
   red[threadIdx.x] = s;
   __syncthreads();
   for (int w = 64; w > 0; w >>= 1) {
@@ -326,14 +326,14 @@ __global__ void __launch_bounds__(128) k_channels(const real* __restrict__ qcol,
   }
   if (threadIdx.x == 0) {
     const long k = *d_iter + slot;
-    cut[chan_col[c]] = (k >= kmin) ? (real)red[0] : (real)0;
+    cut[chan_col[c]] = (k >= kmin) ? red[0] : 0.0;
   }
 }
 
 template <typename real>
-cudaError_t launch_channels(const real* qcol, const real* chi, const int* chan_block,
+cudaError_t launch_channels(const real* qcol, const double* chi, const int* chan_block,
                             const int* chan_row, const int* chan_col, int nchan, int ng, int nr,
-                            const long* d_iter, int slot, long kmin, real* cut_slot,
+                            const long* d_iter, int slot, long kmin, double* cut_slot,
                             cudaStream_t st) {
   if (nchan <= 0) return cudaSuccess;
   k_channels<real><<<nchan, 128, 0, st>>>(qcol, chi, chan_block, chan_row, chan_col, ng, nr,
@@ -431,9 +431,9 @@ cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* ac
   template cudaError_t launch_sums_flush<real>(const real*, const real*, long, int, int, int, \
                                                const long*, const long*, const long*, long,   \
                                                double*, cudaStream_t);                        \
-  template cudaError_t launch_channels<real>(const real*, const real*, const int*,            \
+  template cudaError_t launch_channels<real>(const real*, const double*, const int*,          \
                                              const int*, const int*, int, int, int,           \
-                                             const long*, int, long, real*, cudaStream_t);    \
+                                             const long*, int, long, double*, cudaStream_t);  \
   template cudaError_t launch_norms<real>(const real*, const long*, int, double*, int,        \
                                           double*, cudaStream_t);
 

@@ -102,11 +102,12 @@ cudaError_t launch_gamma_update(const real* u, const real* T, const DevBlock* bl
                                 const real* Dr, const DevJ* dj, real alpha, real beta, int mode,
                                 real* out, cudaStream_t st);
 
-// cut[chan_col[c]] = sum_kr chi[c][kr] qcol[block(c)][row(c)][kr]  (0 before kmin)
+// cut[chan_col[c]] = sum_kr chi[c][kr] qcol[block(c)][row(c)][kr]  (0 before kmin), in FP64
+// (products and sum) whatever the state's precision; cut is the FP64 channel ring.
 template <typename real>
-cudaError_t launch_channels(const real* qcol, const real* chi, const int* chan_block,
+cudaError_t launch_channels(const real* qcol, const double* chi, const int* chan_block,
                             const int* chan_row, const int* chan_col, int nchan, int ng, int nr,
-                            const long* d_iter, int slot, long kmin, real* cut_slot,
+                            const long* d_iter, int slot, long kmin, double* cut_slot,
                             cudaStream_t st);
 
 template <typename real>
@@ -139,13 +140,16 @@ struct ProdGroup {
 };
 
 // jl_group[iJ * nelec + L] = index of the Omega' = 0 group of (J, Lambda'); chan[c] =
-// (group, cut column) of product channel c; vbuf holds [groups][nn].
+// (group, cut column) of product channel c; vbuf holds [groups][nn]. The projection is
+// accumulated in FP64 whatever the state's precision: the state (real) times the Legendre
+// rows (real) in partial sums of eight rows, FP64 across them and in every later stage
+// (stencil weights, helicity rotation, Jacobian, channel dots); cut is the FP64 channel ring.
 template <typename real>
 cudaError_t launch_products(const real* q, int ng, int nr, int NR, int nn, const int* idx,
-                            const real* w, const real* pl, int ltop, const real* T,
-                            const real* jac, const ProdGroup* groups, const int* jl_group,
-                            int njl, int max_nom, real* vbuf, const real* W, const int2* chan,
-                            int nchan, real* cut_slot, cudaStream_t st);
+                            const double* w, const real* pl, int ltop, const double* T,
+                            const double* jac, const ProdGroup* groups, const int* jl_group,
+                            int njl, int max_nom, double* vbuf, const double* W, const int2* chan,
+                            int nchan, double* cut_slot, cudaStream_t st);
 
 // Fused tensor-core angular step (mw3_tc.cu), FP32 state, ngamma padded to kp <= 112.
 struct TcArgs {

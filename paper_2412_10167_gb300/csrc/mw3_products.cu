@@ -1,6 +1,12 @@
 // Product-channel overlaps of q_k on the surface R' = R'_inf (Section 2.4,
 // Eq. Chebyshev-products-overlaps), per Chebyshev iteration, into the cut ring.
 //
+// The projection is kept in FP64 whatever the state's precision (the asymptotic
+// projections of the mixed form): the state times the Legendre rows in partial sums of
+// eight rows (each product and partial sum in the state's precision), FP64 across the
+// partials, the stencil weights, the helicity rotation, the Jacobian and the channel dots,
+// and an FP64 overlap into the FP64 channel ring.
+//
 // Two launches per step:
 //   k_prod_nodes  u_Omega = sum_(a,c) wR_a wr_c sum_i P-bar_(Omega + i)^Omega(cos gamma_v)
 //                           c^(J,Omega,Lambda')_i(r_(k_c), R_(m_a))
@@ -17,8 +23,8 @@
 namespace mw3 {
 namespace {
 
-template <typename real>
-__device__ __forceinline__ real warp_sum(real s) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T s) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
@@ -28,20 +34,22 @@ __device__ __forceinline__ real warp_sum(real s) {
 // (J, Omega = w, Lambda') at the node. Lane l takes stencil point (a, c) =
 // (l & 3, (l >> 2) & 3) of the rows i = l >> 4, l >> 4 + 2, ...: one load instruction
 // covers two rows of the 4 x 4 stencil (8 short segments of 4 consecutive R values).
+// A lane's rows are summed eight at a time (eight loads in flight, one partial in the
+// state's precision) and the partials in FP64.
 // Then thread Omega' of the CTA rotates the helicities at the node:
 //   v[g(J, Lambda', Omega')][v] = jac_v sum_Omega T_v[Omega'][Omega] u_Omega.
 template <typename real>
 __global__ void __launch_bounds__(1024) k_prod_nodes(const real* __restrict__ q, int ng, int nr,
                                                      int NR, int nn,
                                                      const int* __restrict__ idx,
-                                                     const real* __restrict__ w,
+                                                     const double* __restrict__ w,
                                                      const real* __restrict__ pl, int ltop,
-                                                     const real* __restrict__ T,
-                                                     const real* __restrict__ jac,
+                                                     const double* __restrict__ T,
+                                                     const double* __restrict__ jac,
                                                      const ProdGroup* __restrict__ groups,
                                                      const int* __restrict__ jl_group,
-                                                     real* __restrict__ vout) {
-  __shared__ real us[32];
+                                                     double* __restrict__ vout) {
+  __shared__ double us[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int v = blockIdx.x;
   const int g0 = jl_group[blockIdx.y];
@@ -54,43 +62,46 @@ __global__ void __launch_bounds__(1024) k_prod_nodes(const real* __restrict__ q,
     const real* src = q + (long)b * ng * plane + (long)idx[v * 8 + 4 + c] * NR + idx[v * 8 + a];
     const real* P = pl + ((long)v * ltop + warp) * ng;
     const int nrow = ng - warp;            // angular functions of helicity Omega = warp
-    real s0 = 0, s1 = 0, s2 = 0, s3 = 0;   // four independent chains: loads in flight
+    double acc = 0.0;
     int i = sub;
-    for (; i + 6 < nrow; i += 8) {
-      s0 += P[i] * src[(long)i * plane];
-      s1 += P[i + 2] * src[(long)(i + 2) * plane];
-      s2 += P[i + 4] * src[(long)(i + 4) * plane];
-      s3 += P[i + 6] * src[(long)(i + 6) * plane];
+    for (; i + 14 < nrow; i += 16) {
+      real x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = src[(long)(i + 2 * u) * plane];
+      real part = P[i] * x[0];
+#pragma unroll
+      for (int u = 1; u < 8; ++u) part += P[i + 2 * u] * x[u];
+      acc += (double)part;
     }
-    for (; i < nrow; i += 2) s0 += P[i] * src[(long)i * plane];
-    real s = (s0 + s1) + (s2 + s3);
-    s *= w[v * 8 + a] * w[v * 8 + 4 + c];
+    real part = 0;
+    for (; i < nrow; i += 2) part += P[i] * src[(long)i * plane];
+    acc += (double)part;
+    double s = acc * (w[v * 8 + a] * w[v * 8 + 4 + c]);
     s = warp_sum(s);
     if (lane == 0) us[warp] = s;
   }
   __syncthreads();
   const int op = threadIdx.x;
   if (op < nom && groups[g0 + op].op == op) {
-    const real* Tv = T + G.toff + ((long)v * nom + op) * nom;
-    real s = 0;
+    const double* Tv = T + G.toff + ((long)v * nom + op) * nom;
+    double s = 0;
     for (int om = 0; om < nom; ++om) s += Tv[om] * us[om];
     vout[(long)(g0 + op) * nn + v] = jac[v] * s;
   }
 }
 
 // One warp per channel: C_c = sum_v W[c][v] v'[group(c)][v], written to its cut column.
-template <typename real>
-__global__ void __launch_bounds__(256) k_prod_dots(const real* __restrict__ vin, int nn,
-                                                   const real* __restrict__ W,
+__global__ void __launch_bounds__(256) k_prod_dots(const double* __restrict__ vin, int nn,
+                                                   const double* __restrict__ W,
                                                    const int2* __restrict__ chan, int nchan,
-                                                   real* __restrict__ cut) {
+                                                   double* __restrict__ cut) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * 8 + warp;
   if (c >= nchan) return;
   const int2 gc = chan[c];   // (group, cut column)
-  const real* Wc = W + (long)c * nn;
-  const real* vg = vin + (long)gc.x * nn;
-  real s = 0;
+  const double* Wc = W + (long)c * nn;
+  const double* vg = vin + (long)gc.x * nn;
+  double s = 0;
   for (int n = lane; n < nn; n += 32) s += Wc[n] * vg[n];
   s = warp_sum(s);
   if (lane == 0) cut[gc.y] = s;
@@ -100,24 +111,24 @@ __global__ void __launch_bounds__(256) k_prod_dots(const real* __restrict__ vin,
 
 template <typename real>
 cudaError_t launch_products(const real* q, int ng, int nr, int NR, int nn, const int* idx,
-                            const real* w, const real* pl, int ltop, const real* T,
-                            const real* jac, const ProdGroup* groups, const int* jl_group,
-                            int njl, int max_nom, real* vbuf, const real* W, const int2* chan,
-                            int nchan, real* cut_slot, cudaStream_t st) {
+                            const double* w, const real* pl, int ltop, const double* T,
+                            const double* jac, const ProdGroup* groups, const int* jl_group,
+                            int njl, int max_nom, double* vbuf, const double* W, const int2* chan,
+                            int nchan, double* cut_slot, cudaStream_t st) {
   if (nchan == 0) return cudaSuccess;
   dim3 g1((unsigned)nn, (unsigned)njl);
   k_prod_nodes<real><<<g1, 32 * max_nom, 0, st>>>(q, ng, nr, NR, nn, idx, w, pl, ltop, T, jac,
                                                   groups, jl_group, vbuf);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_prod_dots<real><<<(nchan + 7) / 8, 256, 0, st>>>(vbuf, nn, W, chan, nchan, cut_slot);
+  k_prod_dots<<<(nchan + 7) / 8, 256, 0, st>>>(vbuf, nn, W, chan, nchan, cut_slot);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_products<float>(const float*, int, int, int, int, const int*,
-                                            const float*, const float*, int, const float*,
-                                            const float*, const ProdGroup*, const int*, int, int,
-                                            float*, const float*, const int2*, int, float*,
+                                            const double*, const float*, int, const double*,
+                                            const double*, const ProdGroup*, const int*, int, int,
+                                            double*, const double*, const int2*, int, double*,
                                             cudaStream_t);
 template cudaError_t launch_products<double>(const double*, int, int, int, int, const int*,
                                              const double*, const double*, int, const double*,
