@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=3)
+    # accuracy gate of the headline: mixed against the FP64 GPU path from the initial packet
+    # (0 skips it; the configured length of the workload is 12000 iterations)
+    ap.add_argument("--accuracy-steps", type=int, default=1280)
     return ap.parse_args()
 
 
@@ -315,6 +318,31 @@ def run_ours(args, rank, world, local):
     pf.close()
     del pf
 
+    # ---- accuracy of the mixed form: both forms from the initial packet for the same count
+    accuracy = None
+    if args.accuracy_steps > 0 and rank == 0:
+        res = {}
+        for prec in ("mixed", "fp64"):
+            pa = mw3.Propagator(cfg, device=local, precision=prec)
+            pa.propagate(args.accuracy_steps)
+            _, Pt_, Pin_ = pa.probabilities()
+            res[prec] = (Pt_, Pin_, pa.product_probabilities(), pa.norm_trace()[-1][0])
+            pa.close()
+            del pa
+        (mt, mi, mp, _), (ft, fi, fp_, fnorm) = res["mixed"], res["fp64"]
+        d = {"total": float(np.max(np.abs(mt - ft))),
+             "reactant_channels": float(np.max(np.abs(mi - fi))),
+             "product_channels": float(np.max(np.abs(mp - fp_)))}
+        accuracy = {
+            "iterations": args.accuracy_steps,
+            "against": "FP64 GPU path (equal to the FP64 oracle to 1e-8 in the parity tests)",
+            "max_abs_dP": d, "gate": 1e-4, "pass": max(d.values()) <= 1e-4,
+            "fp64_range": {"P_total": [float(ft.min()), float(ft.max())],
+                           "reactant_channel_sum_max": float(fi.sum(axis=(1, 2, 3)).max()),
+                           "product_channel_sum_max": float(fp_.sum(axis=(1, 2, 3)).max())},
+            "fp64_final_norm": float(fnorm),
+        }
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -333,7 +361,7 @@ def run_ours(args, rank, world, local):
         fp64_peak = mw3.mw3_measure_peak(local, 0)
     except Exception:
         pass
-    ncols_total = 2 * nblk * g["ngamma"] * g["NR"] + 484
+    ncols_total = 2 * nblk * g["ngamma"] * g["NR"]   # the flux-cut columns of the ring
     bound, amount = kernel_roofline(dom, es, npts, nblk, g["ngamma"], 1, 500, kb, ncols_total)
     if bound == "alu":
         ach = amount / (avg_ms * 1e-3) / 1e12
@@ -385,6 +413,7 @@ def run_ours(args, rank, world, local):
         "clocks": clocks,
         "e2e": {"value": world * e2e_steps / te, "unit": "steps/s", "h2d_bytes_per_step": 2 * vec_bytes,
                 "d2h_bytes_per_step": 500 * 8 * 2},
+        "accuracy": accuracy,
         "cpu_baseline": cpu,
         "fp32_fma_peak_tflops": fp32_peak,
         "fp64_fma_peak_tflops": fp64_peak,
