@@ -87,7 +87,7 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0, 1, 4, 1};
+  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1};
   int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   int kh = 0;          // parity-split operand size, resident form (0: not applicable)
@@ -1868,7 +1868,8 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
   } else if (k == "use_graph") {
     ctx->tune.use_graph = v != 0;
   } else if (k == "kin_warp") {
-    ctx->tune.kin_warp = v != 0;
+    if (v < 0 || v > 2) return ctx->fail(MW3_ERR_BAD_ARG, "kin_warp is 0, 1 or 2");
+    ctx->tune.kin_warp = (int)v;
   } else if (k == "flush_tc") {
     ctx->tune.flush_tc = v != 0;
   } else if (k == "tc_persist") {

@@ -63,7 +63,8 @@ struct Tuning {
   int kb;           // Chebyshev iterations per energy-sum flush (ring depth)
   int use_graph;    // capture full chunks as CUDA graphs
   int use_tc;       // tensor-core gamma transform (mixed precision only)
-  int kin_warp;     // warp-register FFT kinetic kernels where the line length allows
+  int kin_warp;     // kinetic kernels where the line length allows: 2 half-warp form (FP32,
+                    // N = 128, 192, 256; else as 1), 1 warp-register FFT, 0 shared-memory FFT
   int tc_persist;   // persistent tensor-core angular step (operands in tensor memory)
   int flush_tc;     // energy-sum flush on the tensor cores (mixed precision)
 };

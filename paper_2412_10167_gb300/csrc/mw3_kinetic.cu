@@ -312,12 +312,12 @@ bool kinetic_rows_fixed(int N, const T* q, T* t, long nrows, const void* tw, con
 template <typename T>
 bool kinetic_rows_warp(int N, const T* q, T* t, long nrows, const void* tw, const void* ph,
                        const T* lam, const DevBlock* blocks, int ng, int nr, cudaStream_t st,
-                       cudaError_t* err);
+                       cudaError_t* err, int form);
 template <typename T>
 bool kinetic_cols_warp(int N, const T* q, T* t, long nplanes, int NR, const void* tw,
                        const void* ph, const T* lam, int C, int ng, const T* wpsi,
                        const T* wdpsi, T* cut, const DevBlock* blocks, const int* ncut_J,
-                       int m_inf, T* qcol, cudaStream_t st, cudaError_t* err);
+                       int m_inf, T* qcol, cudaStream_t st, cudaError_t* err, int form);
 template <typename T>
 bool kinetic_cols_fixed(int N, const T* q, T* t, long nplanes, int NR, const void* tw,
                         const void* ph, const T* lam, int C, int ng, const T* wpsi,
@@ -331,7 +331,8 @@ cudaError_t launch_kinetic_rows(const real* q, real* t, long nrows, const FFTPla
                                 cudaStream_t st) {
   cudaError_t err = cudaSuccess;
   if (warp_fft &&
-      kinetic_rows_warp<real>(plan.N, q, t, nrows, tw, ph, lam, blocks, ng, nr, st, &err))
+      kinetic_rows_warp<real>(plan.N, q, t, nrows, tw, ph, lam, blocks, ng, nr, st, &err,
+                              warp_fft))
     return err;
   if (kinetic_rows_fixed<real>(plan.N, q, t, nrows, tw, ph, lam, pairs, blocks, ng, nr, st, &err))
     return err;
@@ -361,7 +362,8 @@ cudaError_t launch_kinetic_cols(const real* q, real* t, long nplanes, int nr, in
                                 cudaStream_t st) {
   cudaError_t err = cudaSuccess;
   if (warp_fft && kinetic_cols_warp<real>(plan.N, q, t, nplanes, NR, tw, ph, lam, ctile, ng, wpsi,
-                                          wdpsi, cut_slot, blocks, ncut_J, m_inf, qcol, st, &err))
+                                          wdpsi, cut_slot, blocks, ncut_J, m_inf, qcol, st, &err,
+                                          warp_fft))
     return err;
   if (kinetic_cols_fixed<real>(plan.N, q, t, nplanes, NR, tw, ph, lam, ctile, ng, wpsi, wdpsi,
                                cut_slot, blocks, ncut_J, m_inf, qcol, st, &err))

@@ -560,12 +560,388 @@ bool cols_w(const T* q, T* t, long nplanes, int NR, const void* tw, const void* 
   }
 }
 
+
+// ===================================================================== half-warp form
+// FP32 lines of length N = 16 * N1 (N1 = 8, 12, 16). One line pair per half-warp: lane t
+// (t < 16) holds the elements n = 16 n1 + t (n1 < N1) of the packed sequence z = a + i b
+// (after the sign and permutation of the DST-via-FFT). With n = 16 n1 + n2 and
+// k = k1 + N1 k2 the forward transform is
+//   Z[k1 + N1 k2] = sum_n2 w_16^(n2 k2) [ w_N^(n2 k1) sum_n1 z[16 n1 + n2] w_N1^(n1 k1) ]:
+// an N1-point DFT over n1 in registers on lane n2, the twiddle, an exchange through the
+// pair's own shared-memory storage, and a 16-point DFT over n2 on lane k1 < N1, which then
+// holds Z[k1 + N1 k2] in slot k2. After the spectral scale W_k = sigma_k Z_k + f_k Z_(N-k)
+// (the partner read back from shared memory) the inverse runs the same steps mirrored
+// (16-point DFT over k2 on lane k1, twiddle w_N^(-n2 k1), exchange, N1-point DFT over k1
+// on lane n2), so lane t ends with element 16 n1 + t and every value returns to the
+// location it was read from. Exchange slot of (lane a, index b): ((a + b) mod 16) + 16 b,
+// so the 16 lanes of an exchange access 16 different banks. Lane synchronisation is per
+// half-warp (the two halves of a warp may run different pairs, or one of them none), so
+// the caller's blockDim.x is a multiple of 32 and each pair's 16 lanes are one half-warp.
+template <int N1>
+__device__ __forceinline__ int hw_xj(int a, int b) {
+  return ((a + b) & 15) + 16 * b;
+}
+
+// tw16[j * 16 + t] = w_N^(t j) (j < 16), sig[k] = sigma_k, fk[k] = f_k (shared memory)
+template <int N1>
+__device__ __forceinline__ void hw_pair_kinetic(float* __restrict__ xa, float* __restrict__ xb,
+                                                int st, int t, const cpx<float>* tw16,
+                                                const float* sig, const cpx<float>* fk) {
+  constexpr int N = 16 * N1;
+  // the 16 lanes of this half-warp only: the other half may work on another pair or none
+  const unsigned hm = 0xffffu << (threadIdx.x & 16);
+  cpx<float> v[16];
+#pragma unroll
+  for (int n1 = 0; n1 < N1; ++n1) {
+    const int n = 16 * n1 + t;
+    const int i = n < N / 2 ? 2 * n : 2 * (N - 1 - n) + 1;
+    const float s = (i & 1) ? -1.0f : 1.0f;
+    v[n1] = {s * xa[i * st], s * xb[i * st]};
+  }
+  dftR<float, N1>(v, -1.0f);
+#pragma unroll
+  for (int k1 = 1; k1 < N1; ++k1) v[k1] = cm(v[k1], tw16[k1 * 16 + t]);
+  __syncwarp(hm);                        // every lane's loads precede the exchange writes
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    const int j = hw_xj<N1>(t, k1);
+    xa[j * st] = v[k1].x;
+    xb[j * st] = v[k1].y;
+  }
+  __syncwarp(hm);
+  if (t < N1) {
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) {
+      const int j = hw_xj<N1>(n2, t);
+      v[n2] = {xa[j * st], xb[j * st]};
+    }
+    dftR<float, 16>(v, -1.0f);         // v[k2] = Z[t + N1 k2]
+  }
+  __syncwarp(hm);
+  if (t < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+      const int k = t + N1 * k2;
+      xa[k * st] = v[k2].x;
+      xb[k * st] = v[k2].y;
+    }
+  }
+  __syncwarp(hm);
+  if (t < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+      const int k = t + N1 * k2;
+      const int p = k == 0 ? 0 : N - k;
+      const cpx<float> fz = cm(fk[k], cpx<float>{xa[p * st], xb[p * st]});
+      const float sg = sig[k];
+      v[k2] = {sg * v[k2].x + fz.x, sg * v[k2].y + fz.y};
+    }
+    dftR<float, 16>(v, 1.0f);          // over k2: v[n2]
+#pragma unroll
+    for (int n2 = 1; n2 < 16; ++n2) v[n2] = cmc(v[n2], tw16[n2 * 16 + t]);   // w_N^(-n2 t)
+  }
+  __syncwarp(hm);                        // every partner read precedes the exchange writes
+  if (t < N1) {
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) {
+      const int j = hw_xj<N1>(n2, t);
+      xa[j * st] = v[n2].x;
+      xb[j * st] = v[n2].y;
+    }
+  }
+  __syncwarp(hm);
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    const int j = hw_xj<N1>(t, k1);
+    v[k1] = {xa[j * st], xb[j * st]};
+  }
+  dftR<float, N1>(v, 1.0f);            // v[n1] = element 16 n1 + t
+  __syncwarp(hm);                        // every exchange read precedes the result writes
+#pragma unroll
+  for (int n1 = 0; n1 < N1; ++n1) {
+    const int n = 16 * n1 + t;
+    const int i = n < N / 2 ? 2 * n : 2 * (N - 1 - n) + 1;
+    const float s = (i & 1) ? -1.0f : 1.0f;
+    xa[i * st] = s * v[n1].x;
+    xb[i * st] = s * v[n1].y;
+  }
+}
+
+// Per-CTA tables of the half-warp form (FP32): twiddles w_N^(t j) for t, j < 16 and the
+// spectral scale of every natural index k (same definitions as load_tables).
+template <int N1>
+struct HwTables {
+  cpx<float> tw16[256];
+  cpx<float> fk[16 * N1];
+  float sig[16 * N1];
+};
+
+template <int N1>
+__device__ __forceinline__ void hw_load_tables(HwTables<N1>& tb, const cpx<float>* __restrict__ twg,
+                                               const cpx<float>* __restrict__ phg,
+                                               const float* __restrict__ lamg) {
+  constexpr int N = 16 * N1;
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+    const int j = e >> 4, t = e & 15;
+    tb.tw16[e] = twg[(t * j) % N];
+  }
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const float lr = lamg[N - k], li = lamg[k];
+    const cpx<float> e1 = phg[k];
+    const cpx<float> e2 = {e1.x * e1.x - e1.y * e1.y, -2.0f * e1.x * e1.y};
+    const float dl = 0.5f * (lr - li);
+    tb.sig[k] = 0.5f * (lr + li);
+    tb.fk[k] = {dl * e2.x, dl * e2.y};
+  }
+}
+
+// R direction, persistent: blocks of 32 rows (16 line pairs, one per half-warp of the 256
+// threads), the next block copied into the second buffer with cp.async while this one
+// transforms. Row pitch N + 8 floats: the rows of the two half-warps of a warp start 16
+// banks apart, so their exchanges do not collide.
+template <int N1>
+__global__ void __launch_bounds__(256) k_rows_hw(const float* __restrict__ q, float* __restrict__ t,
+                                                 long nrows, const cpx<float>* __restrict__ twg,
+                                                 const cpx<float>* __restrict__ phg,
+                                                 const float* __restrict__ lamg,
+                                                 const DevBlock* __restrict__ blocks, int ng,
+                                                 int nr) {
+  constexpr int N = 16 * N1;
+  constexpr int ROWS = 32;
+  constexpr int P = N + 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  HwTables<N1>& tb = *reinterpret_cast<HwTables<N1>*>(smem_raw);
+  float* tiles = reinterpret_cast<float*>(smem_raw + ((sizeof(HwTables<N1>) + 15) / 16) * 16);
+  __shared__ int live[ROWS];
+  hw_load_tables<N1>(tb, twg, phg, lamg);
+  const long nrb = (nrows + ROWS - 1) / ROWS;
+  auto prefetch = [&](long rb, int buf) {
+    if (rb < nrb) {
+      const long row0 = rb * ROWS;
+      const int nv = (int)min((long)ROWS, nrows - row0) * (N / 4);
+      const float* src = q + row0 * N;
+      float* dst = tiles + buf * ROWS * P;
+      for (int e = threadIdx.x; e < nv; e += blockDim.x) {
+        const int r = e / (N / 4), c4 = (e - r * (N / 4)) * 4;
+        cp_async16_ca<float>(dst + r * P + c4, src + (long)r * N + c4);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  const int hw = threadIdx.x >> 4, lane = threadIdx.x & 15;
+  int buf = 0;
+  prefetch(blockIdx.x, 0);
+  for (long rb = blockIdx.x; rb < nrb; rb += gridDim.x, buf ^= 1) {
+    __syncthreads();                              // the other buffer's last readers are done
+    prefetch(rb + gridDim.x, buf ^ 1);
+    const long row0 = rb * ROWS;
+    if (threadIdx.x < ROWS) {
+      const long row = row0 + threadIdx.x;
+      const long plane = row / nr;
+      live[threadIdx.x] = row < nrows && (int)(plane % ng) < blocks[plane / ng].nrow;
+    }
+    asm volatile("cp.async.wait_group 1;" ::: "memory");   // this block's rows
+    __syncthreads();
+    float* tile = tiles + buf * ROWS * P;
+    // a pair never straddles planes (nr is even), so one flag covers both rows
+    if (live[2 * hw]) hw_pair_kinetic<N1>(tile + 2 * hw * P, tile + (2 * hw + 1) * P, 1, lane,
+                                          tb.tw16, tb.sig, tb.fk);
+    __syncthreads();
+    const int nv = (int)min((long)ROWS, nrows - row0) * (N / 4);
+    for (int e = threadIdx.x; e < nv; e += blockDim.x) {
+      const int r = e / (N / 4), c4 = (e - r * (N / 4)) * 4;
+      if (live[r])
+        *reinterpret_cast<float4*>(t + (row0 + r) * N + c4) =
+            *reinterpret_cast<const float4*>(tile + r * P + c4);
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// r direction: one CTA = one (block, gamma) plane and 32 columns [c0, c0 + 32); N = nr.
+// Tile [N][33]: with the odd pitch, the 16 rows of an exchange fall in 16 banks, and the
+// column pairs of a warp's two half-warps, (w, w + 8) and (w + 16, w + 24), start 16 banks
+// apart. Flux cut (4-way split over r) and the R_inf column come from the tile first.
+template <int N1>
+__global__ void __launch_bounds__(256) k_cols_hw(
+    const float* __restrict__ q, float* __restrict__ t, int NR, const cpx<float>* __restrict__ twg,
+    const cpx<float>* __restrict__ phg, const float* __restrict__ lamg, int ng,
+    const float* __restrict__ wpsi, const float* __restrict__ wdpsi, float* __restrict__ cut,
+    const DevBlock* __restrict__ blocks, const int* __restrict__ ncut_J, int m_inf,
+    float* __restrict__ qcol) {
+  constexpr int N = 16 * N1;
+  constexpr int C = 32;
+  constexpr int LD = C + 1;
+  constexpr int NOUT = 2 * C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  HwTables<N1>& tb = *reinterpret_cast<HwTables<N1>*>(smem_raw);
+  float* tile = reinterpret_cast<float*>(smem_raw + sizeof(HwTables<N1>));   // [N][C + 1]
+  float* part = tile + N * LD;                                               // [4][2C]
+  const long plane = blockIdx.y;
+  const int b = (int)(plane / ng);
+  const int n = (int)(plane - (long)b * ng);
+  if (n >= blocks[b].nrow) return;
+  hw_load_tables<N1>(tb, twg, phg, lamg);
+  const int c0 = blockIdx.x * C;
+  const float* qp = q + plane * (long)N * NR;
+  float* tp = t + plane * (long)N * NR;
+  constexpr int NV = N * C / 4;                                 // 16-byte vectors per tile
+  constexpr int PERV = (NV + 255) / 256;
+  constexpr int CHV = PERV < 8 ? PERV : 8;                      // loads in flight per thread
+  const bool vec = (NR % 4) == 0;
+  for (int u0 = 0; u0 < PERV; u0 += CHV) {
+    float4 z[CHV];
+#pragma unroll
+    for (int u = 0; u < CHV; ++u) {
+      const int e = threadIdx.x + 256 * (u0 + u);
+      const int kr = e / (C / 4), m = c0 + (e % (C / 4)) * 4;
+      if (e < NV && m < NR) {
+        if (vec) {
+          z[u] = *reinterpret_cast<const float4*>(qp + (long)kr * NR + m);
+        } else {
+          const float* s = qp + (long)kr * NR + m;
+          z[u] = make_float4(s[0], m + 1 < NR ? s[1] : 0.0f, m + 2 < NR ? s[2] : 0.0f,
+                             m + 3 < NR ? s[3] : 0.0f);
+        }
+      } else {
+        z[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CHV; ++u) {
+      const int e = threadIdx.x + 256 * (u0 + u);
+      if (e < NV) {
+        float* dst = tile + (e / (C / 4)) * LD + (e % (C / 4)) * 4;
+        dst[0] = z[u].x;
+        dst[1] = z[u].y;
+        dst[2] = z[u].z;
+        dst[3] = z[u].w;
+      }
+    }
+  }
+  __syncthreads();
+  if (cut != nullptr) {
+    constexpr int SEG = (N + 3) / 4;
+    for (int o = threadIdx.x; o < 4 * NOUT; o += blockDim.x) {
+      const int seg = o / NOUT, oc = o % NOUT, c = oc >> 1;
+      const float* w = (oc & 1) ? wdpsi : wpsi;
+      float s = 0;
+      const int k0 = seg * SEG, k1 = min(N, k0 + SEG);
+      for (int kr = k0; kr < k1; ++kr) s += w[kr] * tile[kr * LD + c];
+      part[seg * NOUT + oc] = s;
+    }
+  }
+  if (qcol != nullptr && m_inf >= c0 && m_inf < c0 + C) {
+    for (int kr = threadIdx.x; kr < N; kr += blockDim.x) qcol[plane * N + kr] = tile[kr * LD + (m_inf - c0)];
+  }
+  __syncthreads();
+  if (cut != nullptr) {
+    const DevBlock B = blocks[b];
+    const long ncut = ncut_J[B.iJ];
+    for (int oc = threadIdx.x; oc < NOUT; oc += blockDim.x) {
+      const int m = c0 + (oc >> 1);
+      if (m >= NR) continue;
+      const float s = ((part[oc] + part[NOUT + oc]) + part[2 * NOUT + oc]) + part[3 * NOUT + oc];
+      cut[B.cutcol + (long)(oc & 1) * ncut + (long)n * NR + m] = s;
+    }
+  }
+  {
+    const int h = threadIdx.x >> 4, lane = threadIdx.x & 15;
+    const int ca = (h >> 1) + 16 * (h & 1);
+    hw_pair_kinetic<N1>(tile + ca, tile + ca + 8, LD, lane, tb.tw16, tb.sig, tb.fk);
+  }
+  __syncthreads();
+  for (int u0 = 0; u0 < PERV; u0 += CHV) {
+    float4 z[CHV];
+#pragma unroll
+    for (int u = 0; u < CHV; ++u) {
+      const int e = threadIdx.x + 256 * (u0 + u);
+      const int kr = e / (C / 4), m = c0 + (e % (C / 4)) * 4;
+      z[u] = (vec && e < NV && m < NR) ? *reinterpret_cast<const float4*>(tp + (long)kr * NR + m)
+                                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int u = 0; u < CHV; ++u) {
+      const int e = threadIdx.x + 256 * (u0 + u);
+      const int kr = e / (C / 4), m = c0 + (e % (C / 4)) * 4;
+      if (e < NV && m < NR) {
+        const float* src = tile + kr * LD + (e % (C / 4)) * 4;
+        if (vec) {
+          float4 o = z[u];
+          o.x += src[0];
+          o.y += src[1];
+          o.z += src[2];
+          o.w += src[3];
+          *reinterpret_cast<float4*>(tp + (long)kr * NR + m) = o;
+        } else {
+          for (int v = 0; v < 4 && m + v < NR; ++v) tp[(long)kr * NR + m + v] += src[v];
+        }
+      }
+    }
+  }
+}
+
+template <int N1>
+bool rows_hw(const float* q, float* t, long nrows, const void* tw, const void* ph,
+             const float* lam, const DevBlock* blocks, int ng, int nr, cudaStream_t st,
+             cudaError_t* err) {
+  constexpr int N = 16 * N1;
+  const size_t sm = ((sizeof(HwTables<N1>) + 15) / 16) * 16 + 2 * 32 * (size_t)(N + 8) * sizeof(float);
+  static bool attr = false;
+  static int nsm = 0, per_sm = 1;
+  if (!attr) {
+    cudaFuncSetAttribute(k_rows_hw<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_hw<N1>, 256, sm);
+    per_sm = std::max(per_sm, 1);
+    attr = true;
+  }
+  const long nrb = (nrows + 31) / 32;
+  const unsigned grid = (unsigned)std::min<long>(nrb, (long)std::max(nsm, 1) * per_sm);
+  k_rows_hw<N1><<<grid, 256, sm, st>>>(q, t, nrows, static_cast<const cpx<float>*>(tw),
+                                       static_cast<const cpx<float>*>(ph), lam, blocks, ng, nr);
+  *err = cudaGetLastError();
+  return true;
+}
+
+template <int N1>
+bool cols_hw(const float* q, float* t, long nplanes, int NR, const void* tw, const void* ph,
+             const float* lam, int ng, const float* wpsi, const float* wdpsi, float* cut,
+             const DevBlock* blocks, const int* ncut_J, int m_inf, float* qcol, cudaStream_t st,
+             cudaError_t* err) {
+  constexpr int N = 16 * N1;
+  const size_t sm = sizeof(HwTables<N1>) + sizeof(float) * ((size_t)N * 33 + 8 * 32);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cols_hw<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  dim3 grid((unsigned)((NR + 31) / 32), (unsigned)nplanes);
+  k_cols_hw<N1><<<grid, 256, sm, st>>>(q, t, NR, static_cast<const cpx<float>*>(tw),
+                                       static_cast<const cpx<float>*>(ph), lam, ng, wpsi, wdpsi,
+                                       cut, blocks, ncut_J, m_inf, qcol);
+  *err = cudaGetLastError();
+  return true;
+}
+
 }  // namespace
 
 template <typename T>
 bool kinetic_rows_warp(int N, const T* q, T* t, long nrows, const void* tw, const void* ph,
                        const T* lam, const DevBlock* blocks, int ng, int nr, cudaStream_t st,
-                       cudaError_t* err) {
+                       cudaError_t* err, int form) {
+  if constexpr (sizeof(T) == 4) {
+    if (form >= 2) {
+      switch (N) {
+        case 128: return rows_hw<8>(q, t, nrows, tw, ph, lam, blocks, ng, nr, st, err);
+        case 192: return rows_hw<12>(q, t, nrows, tw, ph, lam, blocks, ng, nr, st, err);
+        case 256: return rows_hw<16>(q, t, nrows, tw, ph, lam, blocks, ng, nr, st, err);
+        default: break;
+      }
+    }
+  }
   switch (N) {
 #define CASE(R) \
   case 32 * R: return rows_w<T, R>(q, t, nrows, tw, ph, lam, blocks, ng, nr, st, err);
@@ -579,7 +955,20 @@ template <typename T>
 bool kinetic_cols_warp(int N, const T* q, T* t, long nplanes, int NR, const void* tw,
                        const void* ph, const T* lam, int C, int ng, const T* wpsi,
                        const T* wdpsi, T* cut, const DevBlock* blocks, const int* ncut_J,
-                       int m_inf, T* qcol, cudaStream_t st, cudaError_t* err) {
+                       int m_inf, T* qcol, cudaStream_t st, cudaError_t* err, int form) {
+  if constexpr (sizeof(T) == 4) {
+    if (form >= 2) {
+      switch (N) {
+#define HW(n1)                                                                             \
+  case 16 * n1:                                                                            \
+    return cols_hw<n1>(q, t, nplanes, NR, tw, ph, lam, ng, wpsi, wdpsi, cut, blocks, ncut_J, \
+                       m_inf, qcol, st, err);
+        HW(8) HW(12) HW(16)
+#undef HW
+        default: break;
+      }
+    }
+  }
   switch (N) {
 #define CASE(R)                                                                              \
   case 32 * R:                                                                               \
@@ -593,17 +982,17 @@ bool kinetic_cols_warp(int N, const T* q, T* t, long nplanes, int NR, const void
 
 template bool kinetic_rows_warp<float>(int, const float*, float*, long, const void*, const void*,
                                        const float*, const DevBlock*, int, int, cudaStream_t,
-                                       cudaError_t*);
+                                       cudaError_t*, int);
 template bool kinetic_rows_warp<double>(int, const double*, double*, long, const void*,
                                         const void*, const double*, const DevBlock*, int, int,
-                                        cudaStream_t, cudaError_t*);
+                                        cudaStream_t, cudaError_t*, int);
 template bool kinetic_cols_warp<float>(int, const float*, float*, long, int, const void*,
                                        const void*, const float*, int, int, const float*,
                                        const float*, float*, const DevBlock*, const int*, int,
-                                       float*, cudaStream_t, cudaError_t*);
+                                       float*, cudaStream_t, cudaError_t*, int);
 template bool kinetic_cols_warp<double>(int, const double*, double*, long, int, const void*,
                                         const void*, const double*, int, int, const double*,
                                         const double*, double*, const DevBlock*, const int*, int,
-                                        double*, cudaStream_t, cudaError_t*);
+                                        double*, cudaStream_t, cudaError_t*, int);
 
 }  // namespace mw3

@@ -73,12 +73,17 @@ WARP_CASES = {
     "w256x32": W.shrunk(W.C2, "w256x32", NR=256, nr=32, ngamma=6, J=[1], omega_max=1, nE=8),
     "w72x256": W.shrunk(W.C2, "w72x256", NR=72, nr=256, ngamma=5, J=[0], omega_max=0, nE=8),
     "w384x512": W.shrunk(W.C2, "w384x512", NR=384, nr=512, ngamma=4, J=[1], omega_max=1, nE=8),
+    # half-warp form (FP32, N = 128, 192, 256): a partial last 32-row block (nrows = 432),
+    # a column count that is not a multiple of 4 (scalar tile loads), dead rows of Omega > 0
+    "h256x36": W.shrunk(W.C2, "h256x36", NR=256, nr=36, ngamma=6, J=[1], omega_max=1, nE=8),
+    "h30x128": W.shrunk(W.C2, "h30x128", NR=30, nr=128, ngamma=6, J=[1], omega_max=1, nE=8),
+    "h192x256": W.shrunk(W.C2, "h192x256", NR=192, nr=256, ngamma=5, J=[2], omega_max=2, nE=8),
 }
 
 
 @pytest.mark.parametrize("name", list(WARP_CASES))
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("warp", [1, 0])
+@pytest.mark.parametrize("warp", [2, 1, 0])
 def test_warp_fft_kinetic_matches_oracle(name, prec, warp):
     cfg = WARP_CASES[name]
     pr = mw3().Propagator(cfg, precision=prec, tuning={"kin_warp": warp})
