@@ -3,8 +3,9 @@ Chebyshev iterations and print the step rate and the summed probabilities.
 
   python -m paper_2412_10167_gb300.run --config c2 --precision mixed --steps 3
 
-Configurations: c1, c2, c3, c4 (the full workloads) and c1, c2s, c3s, c4s (their
-parity-sized copies). The step rate printed here is wall-clock around
+Configurations: c1, c2, c3, c4 (the full workloads), c1, c2s, c3s, c4s (their
+parity-sized copies) and c2p (the config-2 grid with 8 blocks and 16 energies, the
+kernel-profiling case). The step rate printed here is wall-clock around
 mw3_propagate (synchronous) and includes graph capture on the first full chunk; the
 timed measurement is bench.py.
 """
@@ -30,6 +31,7 @@ def main(argv=None):
     args = ap.parse_args(argv)
     table = dict(W.CONFIGS)
     table.update(W.SMALL)
+    table.update(W.PROFILE)
     cfg = table[args.config]
     tuning = json.loads(args.tuning) if args.tuning else None
     pr = mw3.Propagator(cfg, precision=args.precision, tuning=tuning)

@@ -145,6 +145,12 @@ C4_SMALL = shrunk(C4, "h_dh_j40_60x48x30", NR=60, nr=48, ngamma=30, omega_max=4,
                   steps=80, nE=40, kmin=20, products=dict(_PRODUCTS_SMALL, Rinf=8.0))
 SMALL = {"c1": C1, "c2s": C2_SMALL, "c3s": C3_SMALL, "c4s": C4_SMALL}
 
+# Kernel-profiling case: the config-2 grid and step with 8 helicity blocks (J = 7), so a
+# state vector (151 MB) still exceeds the 129 MB L2, and 16 energies, so the whole context
+# holds about 1 GB on the device.
+C2_PROFILE = shrunk(C2, "h_dh_j7_256x192x96_16E", J=[7], omega_max=7, nE=16)
+PROFILE = {"c2p": C2_PROFILE}
+
 # Line lengths outside the library's compile-time FFT sizes (runtime-plan kernels).
 C_ODD = shrunk(C2, "h_dh_j3_30x18x10", NR=30, nr=18, ngamma=10, J=[3], omega_max=3, steps=60,
                nE=16, kmin=10)
