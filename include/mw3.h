@@ -239,6 +239,24 @@ int mw3_apply_hs(mw3_ctx* ctx, const double* q, double* out);
  * (n <= mw3_iteration); returns the count written. */
 long mw3_norm_trace(mw3_ctx* ctx, double* out, long n);
 
+/* Photodissociation analysis (Section 2.3.2, Eqs. initial-photo-wvp, fourier-transform and
+ * chebyshev-transform; Section 2.5, Eq. spectrum). The initial packet d.e |Psi_bound>,
+ * projected onto the final state's body-fixed functions, is supplied by the caller as the
+ * state (mw3_set_state at k = 0). mw3_enable_autocorrelation then keeps a device copy of
+ * that state as Psi(k=0) and makes every later iteration add one FP64 inner product per J,
+ * C_k = <Psi(0)|Psi(k)> (k = 0, 1, ...; read back at each ring boundary). It returns
+ * MW3_ERR_STATE unless the analysis is set and the context is at k = 0; mw3_init_packet
+ * switches it off. The autocorrelation is not part of checkpoints.
+ *   mw3_autocorrelation: C[k * nJ + iJ] for k < min(n, recorded); returns the count.
+ *   mw3_photo_spectrum:  a0[iJ * nE + e] = (1/pi) sum_k (2 - delta_k0) cos(k arccos E_s)
+ *                        C_k / (dE sqrt(1 - E_s^2)), E_s = (E[e] - E0_J)/dE_J, for total
+ *                        energies E (hartree) inside each J's spectral range (else
+ *                        MW3_ERR_BAD_ARG); host FP64, caller-owned arrays. The cross
+ *                        section of Eq. spectrum is proportional to h nu times a0. */
+int mw3_enable_autocorrelation(mw3_ctx* ctx);
+long mw3_autocorrelation(mw3_ctx* ctx, double* C, long n);
+int mw3_photo_spectrum(mw3_ctx* ctx, const double* E, int nE, double* a0);
+
 /* Sizes and scaling constants: nblocks, points per block, E0 and dE per J. */
 int mw3_sizes(const mw3_ctx* ctx, long* nblocks, long* points_per_block);
 int mw3_spectral_range(const mw3_ctx* ctx, double* E0, double* dE);

@@ -41,8 +41,8 @@ namespace {
 
 const char* kKernelNames[] = {"kinetic_rows", "kinetic_cols", "gamma_to_dvr", "gamma_update",
                               "channels",     "norms",        "sums_flush",   "angular_tc",
-                              "products"};
-constexpr int kNumKernels = 9;
+                              "products",     "autocorrelation"};
+constexpr int kNumKernels = 10;
 
 struct DevBuf {
   void* p = nullptr;
@@ -169,6 +169,10 @@ struct mw3_ctx {
   int cur = 0;         // d_q[cur] holds q_k
   std::vector<double> norm_trace;  // [iter][nJ], ||q_k||^2 for k = 1..iter
   double norm0 = 1.0;
+  // photodissociation analysis: C_k = <q_0|q_k> per J, k = 0..iter-1, after
+  // mw3_enable_autocorrelation stored q_0
+  bool ac_on = false;
+  std::vector<double> ac_trace;    // [k][nJ]
 
   // graphs
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -919,6 +923,8 @@ int mw3_init_packet(mw3_ctx* ctx, const mw3_packet_desc* d) {
   if ((st = upload_state_fbr(ctx, ctx->q0.data()))) return st;
   ctx->iter = 0;
   ctx->norm_trace.clear();
+  ctx->ac_on = false;
+  ctx->ac_trace.clear();
   if (ctx->stage < 3) ctx->stage = 3;
   if (ctx->stage >= 5) {
     if ((st = dzero(ctx, "acc")) || (st = dzero(ctx, "cut")) || (st = dzero(ctx, "accc")) ||
@@ -1523,6 +1529,13 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
     LK(launch_norms<real>(qkm1, B.J_begin, ctx->nJ, B.npartial, 256, B.normbuf + (long)slot * ctx->nJ, st));
     tm.stop();
   }
+  if (ctx->ac_on) {   // C_k = <q_0|q_k> of each J, FP64, for k = iter + slot
+    Timer tm(ctx, 9, timed);
+    LK(launch_dots<real>(qk, (const real*)dptr(ctx, "ac0"), B.J_begin, ctx->nJ,
+                         (double*)dptr(ctx, "acpart"), 64,
+                         (double*)dptr(ctx, "acbuf") + (long)slot * ctx->nJ, st));
+    tm.stop();
+  }
   ctx->cur = 1 - ctx->cur;
   return MW3_OK;
 }
@@ -1566,8 +1579,13 @@ int chunk(mw3_ctx* ctx, int n, bool timed) {
 }
 
 int check_norms(mw3_ctx* ctx, int n) {
-  std::vector<double> h((size_t)n * ctx->nJ);
+  std::vector<double> h((size_t)n * ctx->nJ), ac;
   CK(cudaMemcpyAsync(h.data(), dptr(ctx, "normbuf"), h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (ctx->ac_on) {
+    ac.resize((size_t)n * ctx->nJ);
+    CK(cudaMemcpyAsync(ac.data(), dptr(ctx, "acbuf"), ac.size() * 8, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  }
   int tc_err = 0;
   if (dptr(ctx, "tc_err"))
     CK(cudaMemcpyAsync(&tc_err, dptr(ctx, "tc_err"), 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1575,6 +1593,7 @@ int check_norms(mw3_ctx* ctx, int n) {
   collect_times(ctx);
   if (tc_err) return ctx->fail(MW3_ERR_TIMEOUT, "tensor-core step: an mbarrier wait timed out");
   ctx->norm_trace.insert(ctx->norm_trace.end(), h.begin(), h.end());
+  ctx->ac_trace.insert(ctx->ac_trace.end(), ac.begin(), ac.end());
   for (double v : h)
     if (!(v <= 1.5 * ctx->norm0)) return ctx->fail(MW3_ERR_DIVERGED, "||q_k||^2 > 1.5 ||q_0||^2");
   return MW3_OK;
@@ -1698,6 +1717,57 @@ int mw3_get_state(mw3_ctx* ctx, double* q, double* qprev) {
   int st = transform_download(ctx, state_name(ctx, true), q);
   if (st) return st;
   if (qprev) return transform_download(ctx, state_name(ctx, false), qprev);
+  return MW3_OK;
+}
+
+int mw3_enable_autocorrelation(mw3_ctx* ctx) {
+  if (!ctx) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 5) return ctx->fail(MW3_ERR_STATE, "mw3_set_analysis first");
+  if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
+  if (ctx->iter != 0) return ctx->fail(MW3_ERR_STATE, "the autocorrelation starts at k = 0");
+  cudaSetDevice(ctx->device);
+  const size_t bytes = (size_t)ctx->nblk * ctx->npts * ctx->rs();
+  int st;
+  if ((st = dalloc(ctx, "ac0", bytes)) || (st = dalloc(ctx, "acpart", (size_t)ctx->nJ * 64 * 8)) ||
+      (st = dalloc(ctx, "acbuf", (size_t)ctx->tune.kb * ctx->nJ * 8)))
+    return st;
+  CK(cudaMemcpyAsync(dptr(ctx, "ac0"), dptr(ctx, state_name(ctx, true)), bytes,
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (auto& g : ctx->graph)   // the captured steps do not contain the extra dot
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  ctx->ac_on = true;
+  ctx->ac_trace.clear();
+  return MW3_OK;
+}
+
+long mw3_autocorrelation(mw3_ctx* ctx, double* C, long n) {
+  if (!ctx || !C || n < 0) return MW3_ERR_BAD_ARG;
+  const long have = (long)ctx->ac_trace.size() / std::max(1, ctx->nJ);
+  const long cnt = std::min(n, have);
+  std::copy(ctx->ac_trace.begin(), ctx->ac_trace.begin() + cnt * ctx->nJ, C);
+  return cnt;
+}
+
+int mw3_photo_spectrum(mw3_ctx* ctx, const double* E, int nE, double* a0) {
+  if (!ctx || !E || !a0 || nE < 0) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
+  const int nJ = ctx->nJ;
+  const long N = (long)ctx->ac_trace.size() / std::max(1, nJ);
+  for (int iJ = 0; iJ < nJ; ++iJ)
+    for (int e = 0; e < nE; ++e) {
+      const double Es = (E[e] - ctx->E0[iJ]) / ctx->dE[iJ];
+      if (!(Es > -1.0 && Es < 1.0))
+        return ctx->fail(MW3_ERR_BAD_ARG, "energy outside the spectral range of H");
+      const double th = std::acos(Es);
+      double s = 0;
+      for (long k = 0; k < N; ++k)   // (2 - delta_k0) cos(k theta) C_k, k theta formed in FP64
+        s += (k == 0 ? 1.0 : 2.0) * std::cos((double)k * th) * ctx->ac_trace[(size_t)k * nJ + iJ];
+      a0[(size_t)iJ * nE + e] = s / (M_PI * ctx->dE[iJ] * std::sqrt(1.0 - Es * Es));
+    }
   return MW3_OK;
 }
 
@@ -1868,7 +1938,7 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
   } else if (k == "use_graph") {
     ctx->tune.use_graph = v != 0;
   } else if (k == "kin_warp") {
-    if (v < 0 || v > 2) return ctx->fail(MW3_ERR_BAD_ARG, "kin_warp is 0, 1 or 2");
+    if (v < 0 || v > 3) return ctx->fail(MW3_ERR_BAD_ARG, "kin_warp is 0, 1, 2 or 3");
     ctx->tune.kin_warp = (int)v;
   } else if (k == "flush_tc") {
     ctx->tune.flush_tc = v != 0;

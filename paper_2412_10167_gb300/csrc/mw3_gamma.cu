@@ -369,6 +369,31 @@ __global__ void __launch_bounds__(256) k_norm_partial(const real* __restrict__ q
   if (threadIdx.x == 0) partial[(long)iJ * nchunk + blockIdx.x] = red[0];
 }
 
+// partial[iJ][chunk] = sum of a*b over a fixed contiguous chunk of J's range, in FP64
+// whatever the precision of a and b (the autocorrelation of the photodissociation analysis).
+template <typename real>
+__global__ void __launch_bounds__(256) k_dot_partial(const real* __restrict__ a,
+                                                     const real* __restrict__ b,
+                                                     const long* __restrict__ J_begin,
+                                                     int nchunk, double* __restrict__ partial) {
+  __shared__ double red[256];
+  const int iJ = blockIdx.y;
+  const long beg = J_begin[iJ], end = J_begin[iJ + 1];
+  const long len = end - beg;
+  const long per = (len + nchunk - 1) / nchunk;
+  const long lo = beg + per * blockIdx.x;
+  const long hi = (lo + per < end) ? lo + per : end;
+  double s = 0;
+  for (long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += (double)a[i] * (double)b[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(long)iJ * nchunk + blockIdx.x] = red[0];
+}
+
 __global__ void k_norm_final(const double* __restrict__ partial, int nchunk, double* out) {
   const int iJ = blockIdx.x;
   if (threadIdx.x == 0) {
@@ -382,6 +407,16 @@ template <typename real>
 cudaError_t launch_norms(const real* q, const long* J_begin, int nJ, double* partial,
                          int nchunk, double* out, cudaStream_t st) {
   k_norm_partial<real><<<dim3(nchunk, nJ), 256, 0, st>>>(q, J_begin, nchunk, partial);
+  k_norm_final<<<nJ, 32, 0, st>>>(partial, nchunk, out);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_dots(const real* a, const real* b, const long* J_begin, int nJ,
+                        double* partial, int nchunk, double* out, cudaStream_t st) {
+  k_dot_partial<real><<<dim3(nchunk, nJ), 256, 0, st>>>(a, b, J_begin, nchunk, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   k_norm_final<<<nJ, 32, 0, st>>>(partial, nchunk, out);
   return cudaGetLastError();
 }
@@ -435,7 +470,9 @@ cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* ac
                                              const int*, const int*, int, int, int,           \
                                              const long*, int, long, double*, cudaStream_t);  \
   template cudaError_t launch_norms<real>(const real*, const long*, int, double*, int,        \
-                                          double*, cudaStream_t);
+                                          double*, cudaStream_t);                             \
+  template cudaError_t launch_dots<real>(const real*, const real*, const long*, int, double*, \
+                                         int, double*, cudaStream_t);
 
 MW3_INST(double)
 MW3_INST(float)

@@ -63,8 +63,10 @@ struct Tuning {
   int kb;           // Chebyshev iterations per energy-sum flush (ring depth)
   int use_graph;    // capture full chunks as CUDA graphs
   int use_tc;       // tensor-core gamma transform (mixed precision only)
-  int kin_warp;     // kinetic kernels where the line length allows: 2 half-warp form (FP32,
-                    // N = 128, 192, 256; else as 1), 1 warp-register FFT, 0 shared-memory FFT
+  int kin_warp;     // kinetic kernels where the line length allows: 2 and 3 half-warp form
+                    // (FP32, N = 128, 192, 256; else as 1; 3 exchanges the spectral partners
+                    // by shuffles, 2 through shared memory), 1 warp-register FFT, 0
+                    // shared-memory FFT
   int tc_persist;   // persistent tensor-core angular step (operands in tensor memory)
   int flush_tc;     // energy-sum flush on the tensor cores (mixed precision)
 };
@@ -114,6 +116,11 @@ cudaError_t launch_channels(const real* qcol, const double* chi, const int* chan
 template <typename real>
 cudaError_t launch_norms(const real* q, const long* J_begin, int nJ, double* partial,
                          int nchunk, double* out, cudaStream_t st);
+
+// out[iJ] = sum over J's element range of a * b, in FP64 (partial: [nJ][nchunk])
+template <typename real>
+cudaError_t launch_dots(const real* a, const real* b, const long* J_begin, int nJ,
+                        double* partial, int nchunk, double* out, cudaStream_t st);
 
 template <typename real>
 cudaError_t launch_phases(const double* theta, int nJ, int nE, int kb, int nvalid,

@@ -573,35 +573,40 @@ bool cols_w(const T* q, T* t, long nplanes, int NR, const void* tw, const void* 
 // (the partner read back from shared memory) the inverse runs the same steps mirrored
 // (16-point DFT over k2 on lane k1, twiddle w_N^(-n2 k1), exchange, N1-point DFT over k1
 // on lane n2), so lane t ends with element 16 n1 + t and every value returns to the
-// location it was read from. Exchange slot of (lane a, index b): ((a + b) mod 16) + 16 b,
-// so the 16 lanes of an exchange access 16 different banks. Lane synchronisation is per
+// location it was read from. Exchange slot of (lane a, index b): (a xor b) + 16 b, so the
+// 16 lanes of an exchange access 16 different banks. The partner values of the spectral
+// scale come by shuffles within the half-warp. Lane synchronisation is per
 // half-warp (the two halves of a warp may run different pairs, or one of them none), so
 // the caller's blockDim.x is a multiple of 32 and each pair's 16 lanes are one half-warp.
 template <int N1>
 __device__ __forceinline__ int hw_xj(int a, int b) {
-  return ((a + b) & 15) + 16 * b;
+  return (a ^ b) + 16 * b;
 }
 
-// tw16[j * 16 + t] = w_N^(t j) (j < 16), sig[k] = sigma_k, fk[k] = f_k (shared memory)
-template <int N1>
+// tw16[j * 16 + t] = w_N^(t j) (j < 16), sig[k] = sigma_k, fk[k] = f_k (shared memory).
+// Element n = 16 n1 + t of the packed sequence sits at i = 2n for n1 < N1/2 (sign +) and
+// at i = 2N - 1 - 2n for n1 >= N1/2 (sign -), so its address is lane-base + constant.
+template <int N1, bool SHFL>
 __device__ __forceinline__ void hw_pair_kinetic(float* __restrict__ xa, float* __restrict__ xb,
                                                 int st, int t, const cpx<float>* tw16,
                                                 const float* sig, const cpx<float>* fk) {
   constexpr int N = 16 * N1;
   // the 16 lanes of this half-warp only: the other half may work on another pair or none
   const unsigned hm = 0xffffu << (threadIdx.x & 16);
+  float* const pa_lo = xa + 2 * t * st;                 // i = 32 n1 + 2t
+  float* const pb_lo = xb + 2 * t * st;
+  float* const pa_hi = xa + (2 * N - 1 - 2 * t) * st;   // i = 2N - 1 - 32 n1 - 2t
+  float* const pb_hi = xb + (2 * N - 1 - 2 * t) * st;
   cpx<float> v[16];
 #pragma unroll
   for (int n1 = 0; n1 < N1; ++n1) {
-    const int n = 16 * n1 + t;
-    const int i = n < N / 2 ? 2 * n : 2 * (N - 1 - n) + 1;
-    const float s = (i & 1) ? -1.0f : 1.0f;
-    v[n1] = {s * xa[i * st], s * xb[i * st]};
+    if (n1 < N1 / 2) v[n1] = {pa_lo[32 * n1 * st], pb_lo[32 * n1 * st]};
+    else v[n1] = {-pa_hi[-32 * n1 * st], -pb_hi[-32 * n1 * st]};
   }
   dftR<float, N1>(v, -1.0f);
 #pragma unroll
   for (int k1 = 1; k1 < N1; ++k1) v[k1] = cm(v[k1], tw16[k1 * 16 + t]);
-  __syncwarp(hm);                        // every lane's loads precede the exchange writes
+  __syncwarp(hm);                      // every lane's loads precede the exchange writes
 #pragma unroll
   for (int k1 = 0; k1 < N1; ++k1) {
     const int j = hw_xj<N1>(t, k1);
@@ -617,30 +622,55 @@ __device__ __forceinline__ void hw_pair_kinetic(float* __restrict__ xa, float* _
     }
     dftR<float, 16>(v, -1.0f);         // v[k2] = Z[t + N1 k2]
   }
-  __syncwarp(hm);
-  if (t < N1) {
+  // spectral scale; the partner Z[N - k] of lane t, slot k2 is slot 15 - k2 of lane N1 - t
+  // (lane 0: its own slot (16 - k2) mod 16), fetched by shuffles (SHFL) or written to and
+  // read back from the pair's storage
+  if constexpr (!SHFL) {
+    __syncwarp(hm);
+    if (t < N1) {
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const int k = t + N1 * k2;
+        xa[k * st] = v[k2].x;
+        xb[k * st] = v[k2].y;
+      }
+    }
+    __syncwarp(hm);
+    if (t < N1) {
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const int k = t + N1 * k2;
+        const int p = k == 0 ? 0 : N - k;
+        const cpx<float> fz = cm(fk[k], cpx<float>{xa[p * st], xb[p * st]});
+        const float sg = sig[k];
+        v[k2] = {sg * v[k2].x + fz.x, sg * v[k2].y + fz.y};
+      }
+    }
+  } else {
+    // every partner is read from the unscaled values z (a register copy), never from a slot
+    // that this loop has already overwritten
+    cpx<float> z[16];
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) z[k2] = v[k2];
+    const int src = ((t == 0 || t >= N1) ? t : N1 - t) | (threadIdx.x & 16);
 #pragma unroll
     for (int k2 = 0; k2 < 16; ++k2) {
-      const int k = t + N1 * k2;
-      xa[k * st] = v[k2].x;
-      xb[k * st] = v[k2].y;
+      const cpx<float> far = {__shfl_sync(hm, z[15 - k2].x, src), __shfl_sync(hm, z[15 - k2].y, src)};
+      const cpx<float> zp = t == 0 ? z[(16 - k2) & 15] : far;
+      if (t < N1) {
+        const int k = t + N1 * k2;
+        const cpx<float> fz = cm(fk[k], zp);
+        const float sg = sig[k];
+        v[k2] = {sg * z[k2].x + fz.x, sg * z[k2].y + fz.y};
+      }
     }
   }
-  __syncwarp(hm);
   if (t < N1) {
-#pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) {
-      const int k = t + N1 * k2;
-      const int p = k == 0 ? 0 : N - k;
-      const cpx<float> fz = cm(fk[k], cpx<float>{xa[p * st], xb[p * st]});
-      const float sg = sig[k];
-      v[k2] = {sg * v[k2].x + fz.x, sg * v[k2].y + fz.y};
-    }
     dftR<float, 16>(v, 1.0f);          // over k2: v[n2]
 #pragma unroll
     for (int n2 = 1; n2 < 16; ++n2) v[n2] = cmc(v[n2], tw16[n2 * 16 + t]);   // w_N^(-n2 t)
   }
-  __syncwarp(hm);                        // every partner read precedes the exchange writes
+  __syncwarp(hm);                      // every exchange read precedes the exchange writes
   if (t < N1) {
 #pragma unroll
     for (int n2 = 0; n2 < 16; ++n2) {
@@ -656,14 +686,16 @@ __device__ __forceinline__ void hw_pair_kinetic(float* __restrict__ xa, float* _
     v[k1] = {xa[j * st], xb[j * st]};
   }
   dftR<float, N1>(v, 1.0f);            // v[n1] = element 16 n1 + t
-  __syncwarp(hm);                        // every exchange read precedes the result writes
+  __syncwarp(hm);                      // every exchange read precedes the result writes
 #pragma unroll
   for (int n1 = 0; n1 < N1; ++n1) {
-    const int n = 16 * n1 + t;
-    const int i = n < N / 2 ? 2 * n : 2 * (N - 1 - n) + 1;
-    const float s = (i & 1) ? -1.0f : 1.0f;
-    xa[i * st] = s * v[n1].x;
-    xb[i * st] = s * v[n1].y;
+    if (n1 < N1 / 2) {
+      pa_lo[32 * n1 * st] = v[n1].x;
+      pb_lo[32 * n1 * st] = v[n1].y;
+    } else {
+      pa_hi[-32 * n1 * st] = -v[n1].x;
+      pb_hi[-32 * n1 * st] = -v[n1].y;
+    }
   }
 }
 
@@ -699,8 +731,8 @@ __device__ __forceinline__ void hw_load_tables(HwTables<N1>& tb, const cpx<float
 // threads), the next block copied into the second buffer with cp.async while this one
 // transforms. Row pitch N + 8 floats: the rows of the two half-warps of a warp start 16
 // banks apart, so their exchanges do not collide.
-template <int N1>
-__global__ void __launch_bounds__(256) k_rows_hw(const float* __restrict__ q, float* __restrict__ t,
+template <int N1, bool SHFL>
+__global__ void __launch_bounds__(256, 3) k_rows_hw(const float* __restrict__ q, float* __restrict__ t,
                                                  long nrows, const cpx<float>* __restrict__ twg,
                                                  const cpx<float>* __restrict__ phg,
                                                  const float* __restrict__ lamg,
@@ -744,8 +776,8 @@ __global__ void __launch_bounds__(256) k_rows_hw(const float* __restrict__ q, fl
     __syncthreads();
     float* tile = tiles + buf * ROWS * P;
     // a pair never straddles planes (nr is even), so one flag covers both rows
-    if (live[2 * hw]) hw_pair_kinetic<N1>(tile + 2 * hw * P, tile + (2 * hw + 1) * P, 1, lane,
-                                          tb.tw16, tb.sig, tb.fk);
+    if (live[2 * hw]) hw_pair_kinetic<N1, SHFL>(tile + 2 * hw * P, tile + (2 * hw + 1) * P, 1, lane,
+                                                tb.tw16, tb.sig, tb.fk);
     __syncthreads();
     const int nv = (int)min((long)ROWS, nrows - row0) * (N / 4);
     for (int e = threadIdx.x; e < nv; e += blockDim.x) {
@@ -762,7 +794,7 @@ __global__ void __launch_bounds__(256) k_rows_hw(const float* __restrict__ q, fl
 // Tile [N][33]: with the odd pitch, the 16 rows of an exchange fall in 16 banks, and the
 // column pairs of a warp's two half-warps, (w, w + 8) and (w + 16, w + 24), start 16 banks
 // apart. Flux cut (4-way split over r) and the R_inf column come from the tile first.
-template <int N1>
+template <int N1, bool SHFL>
 __global__ void __launch_bounds__(256) k_cols_hw(
     const float* __restrict__ q, float* __restrict__ t, int NR, const cpx<float>* __restrict__ twg,
     const cpx<float>* __restrict__ phg, const float* __restrict__ lamg, int ng,
@@ -848,7 +880,7 @@ __global__ void __launch_bounds__(256) k_cols_hw(
   {
     const int h = threadIdx.x >> 4, lane = threadIdx.x & 15;
     const int ca = (h >> 1) + 16 * (h & 1);
-    hw_pair_kinetic<N1>(tile + ca, tile + ca + 8, LD, lane, tb.tw16, tb.sig, tb.fk);
+    hw_pair_kinetic<N1, SHFL>(tile + ca, tile + ca + 8, LD, lane, tb.tw16, tb.sig, tb.fk);
   }
   __syncthreads();
   for (int u0 = 0; u0 < PERV; u0 += CHV) {
@@ -881,7 +913,7 @@ __global__ void __launch_bounds__(256) k_cols_hw(
   }
 }
 
-template <int N1>
+template <int N1, bool SHFL>
 bool rows_hw(const float* q, float* t, long nrows, const void* tw, const void* ph,
              const float* lam, const DevBlock* blocks, int ng, int nr, cudaStream_t st,
              cudaError_t* err) {
@@ -890,23 +922,23 @@ bool rows_hw(const float* q, float* t, long nrows, const void* tw, const void* p
   static bool attr = false;
   static int nsm = 0, per_sm = 1;
   if (!attr) {
-    cudaFuncSetAttribute(k_rows_hw<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_rows_hw<N1, SHFL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_hw<N1>, 256, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_hw<N1, SHFL>, 256, sm);
     per_sm = std::max(per_sm, 1);
     attr = true;
   }
   const long nrb = (nrows + 31) / 32;
   const unsigned grid = (unsigned)std::min<long>(nrb, (long)std::max(nsm, 1) * per_sm);
-  k_rows_hw<N1><<<grid, 256, sm, st>>>(q, t, nrows, static_cast<const cpx<float>*>(tw),
+  k_rows_hw<N1, SHFL><<<grid, 256, sm, st>>>(q, t, nrows, static_cast<const cpx<float>*>(tw),
                                        static_cast<const cpx<float>*>(ph), lam, blocks, ng, nr);
   *err = cudaGetLastError();
   return true;
 }
 
-template <int N1>
+template <int N1, bool SHFL>
 bool cols_hw(const float* q, float* t, long nplanes, int NR, const void* tw, const void* ph,
              const float* lam, int ng, const float* wpsi, const float* wdpsi, float* cut,
              const DevBlock* blocks, const int* ncut_J, int m_inf, float* qcol, cudaStream_t st,
@@ -915,11 +947,11 @@ bool cols_hw(const float* q, float* t, long nplanes, int NR, const void* tw, con
   const size_t sm = sizeof(HwTables<N1>) + sizeof(float) * ((size_t)N * 33 + 8 * 32);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_cols_hw<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_cols_hw<N1, SHFL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
   dim3 grid((unsigned)((NR + 31) / 32), (unsigned)nplanes);
-  k_cols_hw<N1><<<grid, 256, sm, st>>>(q, t, NR, static_cast<const cpx<float>*>(tw),
+  k_cols_hw<N1, SHFL><<<grid, 256, sm, st>>>(q, t, NR, static_cast<const cpx<float>*>(tw),
                                        static_cast<const cpx<float>*>(ph), lam, ng, wpsi, wdpsi,
                                        cut, blocks, ncut_J, m_inf, qcol);
   *err = cudaGetLastError();
@@ -934,10 +966,14 @@ bool kinetic_rows_warp(int N, const T* q, T* t, long nrows, const void* tw, cons
                        cudaError_t* err, int form) {
   if constexpr (sizeof(T) == 4) {
     if (form >= 2) {
+      const bool sh = form == 3;
       switch (N) {
-        case 128: return rows_hw<8>(q, t, nrows, tw, ph, lam, blocks, ng, nr, st, err);
-        case 192: return rows_hw<12>(q, t, nrows, tw, ph, lam, blocks, ng, nr, st, err);
-        case 256: return rows_hw<16>(q, t, nrows, tw, ph, lam, blocks, ng, nr, st, err);
+#define HW(n1)                                                                               \
+  case 16 * n1:                                                                              \
+    return sh ? rows_hw<n1, true>(q, t, nrows, tw, ph, lam, blocks, ng, nr, st, err)         \
+              : rows_hw<n1, false>(q, t, nrows, tw, ph, lam, blocks, ng, nr, st, err);
+        HW(8) HW(12) HW(16)
+#undef HW
         default: break;
       }
     }
@@ -958,11 +994,14 @@ bool kinetic_cols_warp(int N, const T* q, T* t, long nplanes, int NR, const void
                        int m_inf, T* qcol, cudaStream_t st, cudaError_t* err, int form) {
   if constexpr (sizeof(T) == 4) {
     if (form >= 2) {
+      const bool sh = form == 3;
       switch (N) {
-#define HW(n1)                                                                             \
-  case 16 * n1:                                                                            \
-    return cols_hw<n1>(q, t, nplanes, NR, tw, ph, lam, ng, wpsi, wdpsi, cut, blocks, ncut_J, \
-                       m_inf, qcol, st, err);
+#define HW(n1)                                                                                \
+  case 16 * n1:                                                                               \
+    return sh ? cols_hw<n1, true>(q, t, nplanes, NR, tw, ph, lam, ng, wpsi, wdpsi, cut, blocks, \
+                                  ncut_J, m_inf, qcol, st, err)                               \
+              : cols_hw<n1, false>(q, t, nplanes, NR, tw, ph, lam, ng, wpsi, wdpsi, cut,      \
+                                   blocks, ncut_J, m_inf, qcol, st, err);
         HW(8) HW(12) HW(16)
 #undef HW
         default: break;

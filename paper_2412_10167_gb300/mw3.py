@@ -97,6 +97,10 @@ _SIGS = {
     "mw3_set_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mw3_apply_hs": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mw3_norm_trace": (C.c_long, [C.c_void_p, C.POINTER(C.c_double), C.c_long]),
+    "mw3_enable_autocorrelation": (C.c_int, [C.c_void_p]),
+    "mw3_autocorrelation": (C.c_long, [C.c_void_p, C.POINTER(C.c_double), C.c_long]),
+    "mw3_photo_spectrum": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int,
+                                     C.POINTER(C.c_double)]),
     "mw3_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_long), C.POINTER(C.c_long)]),
     "mw3_spectral_range": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mw3_reference_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -385,6 +389,27 @@ class Propagator:
         out = np.zeros((max(n, 0), nJ))
         cnt = lib.mw3_norm_trace(self.ctx, _dp(out), n)
         return out[:cnt]
+
+    def enable_autocorrelation(self):
+        """Keep the current state as Psi(k=0) and record C_k = <Psi(0)|Psi(k)> per J."""
+        _check(self.ctx, lib.mw3_enable_autocorrelation(self.ctx))
+
+    def autocorrelation(self):
+        """C[k, iJ] for the recorded iterations k = 0 .. iteration - 1."""
+        nJ = len(self.cfg["J"])
+        n = self.iteration
+        out = np.zeros((max(n, 0), nJ))
+        cnt = lib.mw3_autocorrelation(self.ctx, _dp(out), n)
+        if cnt < 0:
+            _check(self.ctx, int(cnt))
+        return out[:cnt]
+
+    def photo_spectrum(self, E):
+        """a0(E) per J (Eq. chebyshev-transform) at total energies E (hartree)."""
+        E = np.ascontiguousarray(np.asarray(E, dtype=np.float64))
+        out = np.zeros((len(self.cfg["J"]), len(E)))
+        _check(self.ctx, lib.mw3_photo_spectrum(self.ctx, _dp(E), len(E), _dp(out)))
+        return out
 
     def set_tuning(self, key, value):
         _check(self.ctx, lib.mw3_set_tuning(self.ctx, key.encode(), int(value)))

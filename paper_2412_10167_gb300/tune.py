@@ -2,8 +2,9 @@
 
 For a workload's grid shape and precision it times short propagations through the
 library's own per-kernel CUDA-event timers (mw3_kernel_times) over a sweep of
-  kin_warp    half-warp FFT kinetic kernels (2), warp-register ones (1) or the
-              shared-memory ones (0),
+  kin_warp    half-warp FFT kinetic kernels (2: spectral partners through shared
+              memory, 3: by shuffles), warp-register ones (1) or the shared-memory
+              ones (0),
   rows_pairs  line pairs per CTA of the R-direction kinetic kernel,
   cols_tile   R columns per CTA of the r-direction kinetic kernel,
   kb          iterations per energy-sum flush (ring depth),
@@ -22,7 +23,7 @@ from . import mw3
 DEFAULT_CACHE = os.environ.get("MW3_TUNE_CACHE",
                                os.path.join(os.path.expanduser("~"), ".cache", "mw3_tuning.json"))
 
-SWEEP = dict(kin_warp=[2, 1, 0], rows_pairs=[2, 4, 8, 16], cols_tile=[8, 16, 32, 64],
+SWEEP = dict(kin_warp=[2, 3, 1, 0], rows_pairs=[2, 4, 8, 16], cols_tile=[8, 16, 32, 64],
              kb=[32, 64, 128])
 CONTROLS = dict(kin_warp=["kinetic_rows", "kinetic_cols"], rows_pairs=["kinetic_rows"],
                 cols_tile=["kinetic_cols"], kb=["sums_flush"])

@@ -83,7 +83,7 @@ WARP_CASES = {
 
 @pytest.mark.parametrize("name", list(WARP_CASES))
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("warp", [2, 1, 0])
+@pytest.mark.parametrize("warp", [3, 2, 1, 0])
 def test_warp_fft_kinetic_matches_oracle(name, prec, warp):
     cfg = WARP_CASES[name]
     pr = mw3().Propagator(cfg, precision=prec, tuning={"kin_warp": warp})
