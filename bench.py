@@ -27,6 +27,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "h_dh_j10_256x192x96_11omega"
+# the headline is config 2; --config times another workload with the same line
+WORKLOADS = {"c2": WORKLOAD, "c3": "two_state_j0to30_192x128x64_164blocks",
+             "c4": "h_dh_j40_512x384x180_21omega"}
 
 
 def parse():
@@ -42,8 +45,18 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=3)
     # accuracy gate of the headline: mixed against the FP64 GPU path from the initial packet
     # (0 skips it; the configured length of the workload is 12000 iterations)
-    ap.add_argument("--accuracy-steps", type=int, default=1280)
-    return ap.parse_args()
+    ap.add_argument("--accuracy-steps", type=int, default=None,
+                    help="default 1280 for config 2, 0 (skipped) for the others")
+    ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS),
+                    help="workload (config 2 is the headline; config 3 and 4 are timed the "
+                         "same way, without the CPU baseline unless --cpu-baseline)")
+    ap.add_argument("--cpu-baseline", action="store_true")
+    a = ap.parse_args()
+    if a.accuracy_steps is None:
+        a.accuracy_steps = 1280 if a.config == "c2" else 0
+    if a.config != "c2" and not a.cpu_baseline:
+        a.no_cpu_baseline = True
+    return a
 
 
 def dist_env():
@@ -241,9 +254,11 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    cfg = W.C2
+    cfg = W.CONFIGS[args.config]
     g = cfg["grid"]
-    nblk = 11
+    nelec = cfg["nelec"]
+    nblk = sum(min(J, cfg["omega_max"]) + 1 for J in cfg["J"]) * nelec
+    nE = cfg["analysis"]["nE"]
     npts = g["NR"] * g["nr"] * g["ngamma"]
 
     from paper_2412_10167_gb300 import dist as mdist
@@ -362,7 +377,8 @@ def run_ours(args, rank, world, local):
     except Exception:
         pass
     ncols_total = 2 * nblk * g["ngamma"] * g["NR"]   # the flux-cut columns of the ring
-    bound, amount = kernel_roofline(dom, es, npts, nblk, g["ngamma"], 1, 500, kb, ncols_total)
+    bound, amount = kernel_roofline(dom, es, npts, nblk, g["ngamma"], nelec, nE, kb,
+                                    ncols_total)
     if bound == "alu":
         ach = amount / (avg_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -399,9 +415,11 @@ def run_ours(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64sums",
         "data": "synthetic (Sato LEPS H+DH surface, deterministic packet)",
-        "config": {"workload": WORKLOAD, "grid": [g["NR"], g["nr"], g["ngamma"]], "J": 10,
-                   "blocks": nblk, "energies": 500, "kb": kb,
-                   "l2": "state vectors 208 MB each (> 129 MB L2), no flush needed",
+        "config": {"workload": WORKLOADS[args.config], "grid": [g["NR"], g["nr"], g["ngamma"]],
+                   "J": cfg["J"] if len(cfg["J"]) > 1 else cfg["J"][0], "electronic_states": nelec,
+                   "blocks": nblk, "energies": nE, "kb": kb,
+                   "l2": f"state vectors {nblk * npts * 4 / 1e6:.0f} MB each (> 129 MB L2), "
+                         "no flush needed",
                    "parallelism": f"replicas x{world}"},
         "grid_pts_omega_per_s": value * npts * nblk,
         "fp64": {"value": fp64_rate, "unit": "steps/s", "steps": args.fp64_steps,
@@ -412,7 +430,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": world * e2e_steps / te, "unit": "steps/s", "h2d_bytes_per_step": 2 * vec_bytes,
-                "d2h_bytes_per_step": 500 * 8 * 2},
+                "d2h_bytes_per_step": nE * 8 * 2 * len(cfg["J"])},
         "accuracy": accuracy,
         "cpu_baseline": cpu,
         "fp32_fma_peak_tflops": fp32_peak,

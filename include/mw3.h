@@ -257,6 +257,19 @@ int mw3_enable_autocorrelation(mw3_ctx* ctx);
 long mw3_autocorrelation(mw3_ctx* ctx, double* C, long n);
 int mw3_photo_spectrum(mw3_ctx* ctx, const double* E, int nE, double* a0);
 
+/* Time-domain packets (Section 2.2, Eqs. wvf-chebyshev and chebyshev-expansion-constants):
+ * Psi(t_j) = sum_k f_k(t_j) Psi(k), f_k(t) = (2 - delta_k0) exp(-i E0 t) (-i)^k J_k(t dE)
+ * (hbar = 1, E0 and dE of each J), for nt times t[j] >= 0 (atomic units). Enabled at k = 0
+ * (MW3_ERR_STATE otherwise, or before mw3_set_analysis); every later iteration k < K adds
+ * its term to FP64 accumulators on the device (2 nt state vectors of FP64), where K is the
+ * first index beyond which every |J_k(t_j dE)| < 1e-17 (Bessel functions by Miller's
+ * backward recurrence). The packets are exact for the undamped recursion once K
+ * iterations have run. mw3_init_packet switches the accumulation off.
+ *   mw3_time_packets: out[(j * 2 + c) * nblocks * ppb + ...] grid values (c = 0 real,
+ *                     1 imaginary part), host FP64, caller-owned; *kmax = K (may be NULL). */
+int mw3_enable_time_packets(mw3_ctx* ctx, int nt, const double* t);
+int mw3_time_packets(mw3_ctx* ctx, double* out, long* kmax);
+
 /* Sizes and scaling constants: nblocks, points per block, E0 and dE per J. */
 int mw3_sizes(const mw3_ctx* ctx, long* nblocks, long* points_per_block);
 int mw3_spectral_range(const mw3_ctx* ctx, double* E0, double* dE);

@@ -41,8 +41,8 @@ namespace {
 
 const char* kKernelNames[] = {"kinetic_rows", "kinetic_cols", "gamma_to_dvr", "gamma_update",
                               "channels",     "norms",        "sums_flush",   "angular_tc",
-                              "products",     "autocorrelation"};
-constexpr int kNumKernels = 10;
+                              "products",     "autocorrelation", "time_packets"};
+constexpr int kNumKernels = 11;
 
 struct DevBuf {
   void* p = nullptr;
@@ -173,6 +173,10 @@ struct mw3_ctx {
   // mw3_enable_autocorrelation stored q_0
   bool ac_on = false;
   std::vector<double> ac_trace;    // [k][nJ]
+  // time-domain packets: Psi(t_j) = sum_(k < tp_K) f_k(t_j) q_k accumulated in FP64 (FBR)
+  bool tp_on = false;
+  int tp_nt = 0;
+  long tp_K = 0;
 
   // graphs
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -925,6 +929,7 @@ int mw3_init_packet(mw3_ctx* ctx, const mw3_packet_desc* d) {
   ctx->norm_trace.clear();
   ctx->ac_on = false;
   ctx->ac_trace.clear();
+  ctx->tp_on = false;
   if (ctx->stage < 3) ctx->stage = 3;
   if (ctx->stage >= 5) {
     if ((st = dzero(ctx, "acc")) || (st = dzero(ctx, "cut")) || (st = dzero(ctx, "accc")) ||
@@ -1529,6 +1534,13 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
     LK(launch_norms<real>(qkm1, B.J_begin, ctx->nJ, B.npartial, 256, B.normbuf + (long)slot * ctx->nJ, st));
     tm.stop();
   }
+  if (ctx->tp_on) {   // Psi(t_j) += f_k(t_j) q_k, k = iter + slot
+    Timer tm(ctx, 10, timed);
+    LK(launch_time_accum<real>(qk, (long)ctx->nblk * ctx->npts, ctx->npts, B.blocks,
+                               (const double*)dptr(ctx, "tp_f"), ctx->nJ, ctx->tp_nt, ctx->tp_K,
+                               B.d_iter, slot, (double*)dptr(ctx, "tp_acc"), st));
+    tm.stop();
+  }
   if (ctx->ac_on) {   // C_k = <q_0|q_k> of each J, FP64, for k = iter + slot
     Timer tm(ctx, 9, timed);
     LK(launch_dots<real>(qk, (const real*)dptr(ctx, "ac0"), B.J_begin, ctx->nJ,
@@ -1741,6 +1753,90 @@ int mw3_enable_autocorrelation(mw3_ctx* ctx) {
     }
   ctx->ac_on = true;
   ctx->ac_trace.clear();
+  return MW3_OK;
+}
+
+int mw3_enable_time_packets(mw3_ctx* ctx, int nt, const double* t) {
+  if (!ctx || nt < 1 || !t) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 5) return ctx->fail(MW3_ERR_STATE, "mw3_set_analysis first");
+  if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
+  if (ctx->iter != 0) return ctx->fail(MW3_ERR_STATE, "the time-domain sums start at k = 0");
+  for (int j = 0; j < nt; ++j)
+    if (!(t[j] >= 0.0 && t[j] < 1e12)) return ctx->fail(MW3_ERR_BAD_ARG, "times must be >= 0");
+  cudaSetDevice(ctx->device);
+  // f_k(t) = (2 - delta_k0) exp(-i E0 t) (-i)^k J_k(t dE) per (J, t_j), up to the last k
+  // at which some |J_k| is above 1e-17 (beyond it the terms are below FP64 resolution)
+  const int nJ = ctx->nJ;
+  std::vector<std::vector<double>> Js((size_t)nJ * nt);
+  long K = 1;
+  for (int iJ = 0; iJ < nJ; ++iJ)
+    for (int j = 0; j < nt; ++j) {
+      const double x = t[j] * ctx->dE[iJ];
+      std::vector<double>& b = Js[(size_t)iJ * nt + j];
+      bessel_j_sequence(x, (int)(x + 60.0 + 15.0 * std::cbrt(x)), b);
+      for (long k = (long)b.size() - 1; k >= 0; --k)
+        if (std::fabs(b[k]) > 1e-17) {
+          K = std::max(K, k + 1);
+          break;
+        }
+    }
+  std::vector<double> f((size_t)K * nJ * nt * 2, 0.0);
+  for (long k = 0; k < K; ++k)
+    for (int iJ = 0; iJ < nJ; ++iJ)
+      for (int j = 0; j < nt; ++j) {
+        const std::vector<double>& b = Js[(size_t)iJ * nt + j];
+        const double jk = k < (long)b.size() ? b[k] : 0.0;
+        const double w = (k == 0 ? 1.0 : 2.0) * jk;
+        const double ph = -ctx->E0[iJ] * t[j];
+        const double c = std::cos(ph), sn = std::sin(ph);
+        // (-i)^k: 1, -i, -1, i
+        const double pr = (k % 4 == 0) ? 1.0 : (k % 4 == 2 ? -1.0 : 0.0);
+        const double pi_ = (k % 4 == 1) ? -1.0 : (k % 4 == 3 ? 1.0 : 0.0);
+        const size_t o = (((size_t)k * nJ + iJ) * nt + j) * 2;
+        f[o] = w * (c * pr - sn * pi_);
+        f[o + 1] = w * (c * pi_ + sn * pr);
+      }
+  int st;
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  if ((st = upload_real(ctx, "tp_f", f, true))) return st;
+  if ((st = dalloc(ctx, "tp_acc", (size_t)nt * 2 * n * 8)) || (st = dzero(ctx, "tp_acc"))) return st;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (auto& g : ctx->graph)   // the captured steps do not contain the accumulation
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  ctx->tp_nt = nt;
+  ctx->tp_K = K;
+  ctx->tp_on = true;
+  return MW3_OK;
+}
+
+int mw3_time_packets(mw3_ctx* ctx, double* out, long* kmax) {
+  if (!ctx || !out) return MW3_ERR_BAD_ARG;
+  if (!ctx->tp_on) return ctx->fail(MW3_ERR_STATE, "mw3_enable_time_packets first");
+  cudaSetDevice(ctx->device);
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  const int ng = ctx->ng;
+  int st;
+  if (!ctx->buf.count("Tt64")) {   // FP64 (T^Omega)^T for the FBR -> grid transform
+    std::vector<double> Ttall;
+    for (auto& Tm : ctx->T)
+      for (int a = 0; a < ng; ++a)
+        for (int b = 0; b < ng; ++b) Ttall.push_back(Tm[(size_t)b * ng + a]);
+    if ((st = upload_real(ctx, "Tt64", Ttall, true))) return st;
+  }
+  if ((st = dalloc(ctx, "tp_tmp", n * 8))) return st;
+  for (int c = 0; c < 2 * ctx->tp_nt; ++c) {
+    LK(launch_gamma_forward<double>((const double*)dptr(ctx, "tp_acc") + (size_t)c * n,
+                                    (double*)dptr(ctx, "tp_tmp"), (const double*)dptr(ctx, "Tt64"),
+                                    (const DevBlock*)dptr(ctx, "blocks"), ctx->nblk, ng, ctx->ncol,
+                                    ctx->stream));
+    CK(cudaMemcpyAsync(out + (size_t)c * n, dptr(ctx, "tp_tmp"), n * 8, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (kmax) *kmax = ctx->tp_K;
   return MW3_OK;
 }
 

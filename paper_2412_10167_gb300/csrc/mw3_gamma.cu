@@ -394,6 +394,31 @@ __global__ void __launch_bounds__(256) k_dot_partial(const real* __restrict__ a,
   if (threadIdx.x == 0) partial[(long)iJ * nchunk + blockIdx.x] = red[0];
 }
 
+// Time-domain packets (Eqs. wvf-chebyshev, chebyshev-expansion-constants): for iteration
+// k = *d_iter + slot < K, acc[j][0 or 1][e] += Re or Im f_k(t_j) q_k[e], with f[k][iJ][j]
+// (complex FP64) the coefficient of element e's J; the sums are FP64 whatever the state's
+// precision. One thread per element, grid-stride.
+template <typename real>
+__global__ void __launch_bounds__(256) k_time_accum(const real* __restrict__ q, long n, long npts,
+                                                    const DevBlock* __restrict__ blocks,
+                                                    const double* __restrict__ f, int nJ, int nt,
+                                                    long K, const long* __restrict__ d_iter,
+                                                    int slot, double* __restrict__ acc) {
+  const long k = *d_iter + slot;
+  if (k >= K) return;
+  const double* fk = f + (size_t)k * nJ * nt * 2;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x) {
+    const double x = (double)q[e];
+    const int iJ = blocks[e / npts].iJ;
+    for (int j = 0; j < nt; ++j) {
+      const double fr = fk[((size_t)iJ * nt + j) * 2], fi = fk[((size_t)iJ * nt + j) * 2 + 1];
+      acc[((size_t)j * 2) * n + e] += fr * x;
+      acc[((size_t)j * 2 + 1) * n + e] += fi * x;
+    }
+  }
+}
+
 __global__ void k_norm_final(const double* __restrict__ partial, int nchunk, double* out) {
   const int iJ = blockIdx.x;
   if (threadIdx.x == 0) {
@@ -408,6 +433,16 @@ cudaError_t launch_norms(const real* q, const long* J_begin, int nJ, double* par
                          int nchunk, double* out, cudaStream_t st) {
   k_norm_partial<real><<<dim3(nchunk, nJ), 256, 0, st>>>(q, J_begin, nchunk, partial);
   k_norm_final<<<nJ, 32, 0, st>>>(partial, nchunk, out);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_time_accum(const real* q, long n, long npts, const DevBlock* blocks,
+                              const double* f, int nJ, int nt, long K, const long* d_iter,
+                              int slot, double* acc, cudaStream_t st) {
+  const long nb = (n + 255) / 256;
+  k_time_accum<real><<<(unsigned)(nb < 8192 ? nb : 8192), 256, 0, st>>>(q, n, npts, blocks, f, nJ,
+                                                                         nt, K, d_iter, slot, acc);
   return cudaGetLastError();
 }
 
@@ -472,7 +507,10 @@ cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* ac
   template cudaError_t launch_norms<real>(const real*, const long*, int, double*, int,        \
                                           double*, cudaStream_t);                             \
   template cudaError_t launch_dots<real>(const real*, const real*, const long*, int, double*, \
-                                         int, double*, cudaStream_t);
+                                         int, double*, cudaStream_t);                         \
+  template cudaError_t launch_time_accum<real>(const real*, long, long, const DevBlock*,      \
+                                               const double*, int, int, long, const long*,    \
+                                               int, double*, cudaStream_t);
 
 MW3_INST(double)
 MW3_INST(float)

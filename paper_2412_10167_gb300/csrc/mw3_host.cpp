@@ -330,8 +330,6 @@ void helicity_transform(int J, int nom, double beta, int sa, int sc, std::vector
     }
 }
 
-}  // namespace mw3
-
 // --------------------------------------------------------------- LEPS surface
 extern "C" int mw3_pes_leps(double r, double R, double cosg, double* potmat, void* user) {
   const mw3_leps_params* P = static_cast<const mw3_leps_params*>(user);
@@ -373,3 +371,38 @@ extern "C" int mw3_pes_leps(double r, double R, double cosg, double* potmat, voi
   potmat[3] = v22;
   return 0;
 }
+
+// J_k(x), k = 0..n-1: the recurrence J_(k-1) = (2k/x) J_k - J_(k+1) run downwards from an
+// index well above both n and x (where J is negligible) with arbitrary small start values is
+// stable in that direction (Miller's algorithm); the sequence is then scaled so that
+// J_0 + 2 (J_2 + J_4 + ...) = 1, the generating-function identity at angle 0.
+void bessel_j_sequence(double x, int n, std::vector<double>& J) {
+  J.assign(std::max(n, 0), 0.0);
+  if (n <= 0) return;
+  if (x == 0.0) {
+    J[0] = 1.0;
+    return;
+  }
+  const double m = std::max((double)n, x);
+  int top = (int)(m + 40.0 + 12.0 * std::cbrt(m));
+  top += top & 1;
+  std::vector<double> t((size_t)top + 1, 0.0);
+  double jk1 = 0.0, jk = 1e-280;   // J_(top+1), J_top up to a common factor
+  t[top] = jk;
+  for (int k = top; k >= 1; --k) {
+    const double jm = (2.0 * k / x) * jk - jk1;
+    jk1 = jk;
+    jk = jm;
+    t[k - 1] = jm;
+    if (std::fabs(jm) > 1e250) {   // rescale everything computed so far
+      for (int i = k - 1; i <= top; ++i) t[i] *= 1e-250;
+      jk *= 1e-250;
+      jk1 *= 1e-250;
+    }
+  }
+  double s = t[0];
+  for (int i = 2; i <= top; i += 2) s += 2.0 * t[i];
+  for (int k = 0; k < n; ++k) J[k] = t[k] / s;
+}
+
+}  // namespace mw3

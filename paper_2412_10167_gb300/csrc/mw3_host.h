@@ -31,6 +31,10 @@ void product_point(const double masses[3], int arrangement, double Rp, double rp
                    double* R, double* r, double* cosg, double* beta, int* sa, int* sc);
 // Wigner d^J_(m'm)(beta).
 double wigner_small_d(int J, int mp, int m, double beta);
+
+// Bessel functions of the first kind J_0(x) .. J_(n-1)(x) for x >= 0 (Miller's backward
+// recurrence normalised by J_0 + 2 sum_m J_2m = 1).
+void bessel_j_sequence(double x, int n, std::vector<double>& J);
 // Helicity transform of the parity-adapted blocks Omega = 0..nom-1 (parity (-1)^J):
 // T[op * nom + om] with Phi'_op = sum_om T[op][om] Phi_om.
 void helicity_transform(int J, int nom, double beta, int sa, int sc, std::vector<double>& T);

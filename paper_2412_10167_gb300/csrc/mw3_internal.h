@@ -117,6 +117,13 @@ template <typename real>
 cudaError_t launch_norms(const real* q, const long* J_begin, int nJ, double* partial,
                          int nchunk, double* out, cudaStream_t st);
 
+// acc[j][0/1][e] += Re/Im f[k][iJ(e)][j] q[e] for k = *d_iter + slot < K (time-domain
+// packets; FP64 sums and coefficients)
+template <typename real>
+cudaError_t launch_time_accum(const real* q, long n, long npts, const DevBlock* blocks,
+                              const double* f, int nJ, int nt, long K, const long* d_iter,
+                              int slot, double* acc, cudaStream_t st);
+
 // out[iJ] = sum over J's element range of a * b, in FP64 (partial: [nJ][nchunk])
 template <typename real>
 cudaError_t launch_dots(const real* a, const real* b, const long* J_begin, int nJ,

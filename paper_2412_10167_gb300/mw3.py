@@ -98,6 +98,8 @@ _SIGS = {
     "mw3_apply_hs": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mw3_norm_trace": (C.c_long, [C.c_void_p, C.POINTER(C.c_double), C.c_long]),
     "mw3_enable_autocorrelation": (C.c_int, [C.c_void_p]),
+    "mw3_enable_time_packets": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "mw3_time_packets": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
     "mw3_autocorrelation": (C.c_long, [C.c_void_p, C.POINTER(C.c_double), C.c_long]),
     "mw3_photo_spectrum": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int,
                                      C.POINTER(C.c_double)]),
@@ -393,6 +395,20 @@ class Propagator:
     def enable_autocorrelation(self):
         """Keep the current state as Psi(k=0) and record C_k = <Psi(0)|Psi(k)> per J."""
         _check(self.ctx, lib.mw3_enable_autocorrelation(self.ctx))
+
+    def enable_time_packets(self, times):
+        """Accumulate Psi(t) = sum_k f_k(t) q_k for the given times (atomic units) from k = 0."""
+        t = np.ascontiguousarray(np.asarray(times, dtype=np.float64))
+        self._tp_nt = len(t)
+        _check(self.ctx, lib.mw3_enable_time_packets(self.ctx, len(t), _dp(t)))
+
+    def time_packets(self):
+        """(Psi(t_j) as complex grid values [nt, nblocks, ngamma, nr, NR], K)."""
+        out = np.zeros((self._tp_nt, 2, int(np.prod(self.shape))))
+        K = C.c_long(0)
+        _check(self.ctx, lib.mw3_time_packets(self.ctx, _dp(out), C.byref(K)))
+        psi = out[:, 0] + 1j * out[:, 1]
+        return psi.reshape((self._tp_nt,) + self.shape), K.value
 
     def autocorrelation(self):
         """C[k, iJ] for the recorded iterations k = 0 .. iteration - 1."""

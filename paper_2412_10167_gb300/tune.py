@@ -7,6 +7,11 @@ library's own per-kernel CUDA-event timers (mw3_kernel_times) over a sweep of
               ones (0),
   rows_pairs  line pairs per CTA of the R-direction kinetic kernel,
   cols_tile   R columns per CTA of the r-direction kinetic kernel,
+  tc_persist  form of the tensor-core angular step (mixed precision): 4 tile-major
+              parity-split (one electronic state), 2 group-major parity-split,
+              1 persistent without the split, 0 one tile per CTA (the library falls
+              back to the nearest form a shape supports),
+  flush_tc    energy-sum flush on the tensor cores (1) or the CUDA cores (0),
   kb          iterations per energy-sum flush (ring depth),
 and keeps, for each knob, the value with the lowest time of the kernels it
 controls. Results are cached in a JSON file keyed by the shape, so a later
@@ -24,9 +29,11 @@ DEFAULT_CACHE = os.environ.get("MW3_TUNE_CACHE",
                                os.path.join(os.path.expanduser("~"), ".cache", "mw3_tuning.json"))
 
 SWEEP = dict(kin_warp=[2, 3, 1, 0], rows_pairs=[2, 4, 8, 16], cols_tile=[8, 16, 32, 64],
-             kb=[32, 64, 128])
+             tc_persist=[4, 2, 1, 0], flush_tc=[1, 0], kb=[32, 64, 128])
 CONTROLS = dict(kin_warp=["kinetic_rows", "kinetic_cols"], rows_pairs=["kinetic_rows"],
-                cols_tile=["kinetic_cols"], kb=["sums_flush"])
+                cols_tile=["kinetic_cols"],
+                tc_persist=["angular_tc", "gamma_to_dvr", "gamma_update"],
+                flush_tc=["sums_flush"], kb=["sums_flush"])
 
 
 def shape_key(cfg: dict, precision: str) -> str:

@@ -84,3 +84,31 @@ def test_autocorrelation_state_checks():
         pr.enable_autocorrelation()
     assert e.value.code == -7
     pr.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_time_packets_match_oracle(prec):
+    """Time-domain packets (Eqs. wvf-chebyshev, chebyshev-expansion-constants) accumulated
+    on the device against the oracle's Bessel sum of the same iterates, undamped: they also
+    keep the norm of the initial packet (the reconstruction is exp(-iHt) Psi_0)."""
+    import copy
+    from paper_2412_10167_gb300 import mw3
+    cfg = copy.deepcopy(W.C2_SMALL)
+    cfg["absorber"] = dict(cfg["absorber"], AR=0.0, Ar=0.0)
+    H = GridHamiltonian(cfg)
+    q0 = H.project(W.random_unit_state(H.shape, 21))
+    t = np.array([7.0, 35.0]) / H.dE[0]
+    pr = mw3.Propagator(cfg, precision=prec)
+    pr.set_state(q0)
+    pr.enable_time_packets(t)
+    pr.propagate(150)
+    psi, K = pr.time_packets()
+    assert 35 < K < 150
+    D = np.ones((1, 1) + H.shape[2:])
+    states = [q0] + [qn for _, _, qn in P.chebyshev_iterates(H, q0, D, K - 1)]
+    tol = 1e-10 if prec == "fp64" else 2e-5
+    for j, tj in enumerate(t):
+        ref = P.time_domain_packet(states, tj, H.E0[0], H.dE[0])
+        assert np.linalg.norm(psi[j] - ref) <= tol
+        assert abs(np.linalg.norm(psi[j]) - 1.0) <= tol
+    pr.close()
