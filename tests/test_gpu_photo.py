@@ -97,6 +97,7 @@ def test_time_packets_match_oracle(prec):
     cfg["absorber"] = dict(cfg["absorber"], AR=0.0, Ar=0.0)
     H = GridHamiltonian(cfg)
     q0 = H.project(W.random_unit_state(H.shape, 21))
+    q0 /= np.linalg.norm(q0)                   # unit norm inside the blocks' span
     t = np.array([7.0, 35.0]) / H.dE[0]
     pr = mw3.Propagator(cfg, precision=prec)
     pr.set_state(q0)
