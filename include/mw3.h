@@ -282,6 +282,10 @@ int mw3_reference_energy(const mw3_ctx* ctx, double* Ev0j0);
 int mw3_checkpoint_save(mw3_ctx* ctx, const char* path);
 int mw3_checkpoint_load(mw3_ctx* ctx, const char* path);
 
+/* |a(E)|^2 of the initial packet's incoming part at the analysis energies (Eq.
+ * initial-flux-collisions; the denominator of every probability): a2[nE], caller-owned. */
+int mw3_incoming_amplitude(mw3_ctx* ctx, double* a2);
+
 /* State-resolved product probabilities |S|^2 (Eq. S-matrix-from-chebyshev, with the
  * flux normalisation of the reactant channels: (2 pi K'/mu') |C_E|^2 / |a(E)|^2,
  * K' = sqrt(2 mu' (E - e_(v'j'))), closed channels 0), summed over Omega':

@@ -1899,6 +1899,15 @@ long mw3_norm_trace(mw3_ctx* ctx, double* out, long n) {
   return cnt;
 }
 
+int mw3_incoming_amplitude(mw3_ctx* ctx, double* a2) {
+  if (!ctx || !a2) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 5) return ctx->fail(MW3_ERR_STATE, "mw3_set_analysis first");
+  std::vector<double> v;
+  incoming_a2(ctx, v);
+  std::copy(v.begin(), v.end(), a2);
+  return MW3_OK;
+}
+
 int mw3_product_probabilities(mw3_ctx* ctx, double* P) {
   if (!ctx || !P) return MW3_ERR_BAD_ARG;
   if (ctx->stage < 5) return ctx->fail(MW3_ERR_STATE, "mw3_set_analysis first");

@@ -4,7 +4,9 @@
 // output; weights held in BF16 for the forward and backward products, with FP32 master
 // weights and AdamW moments; activations and accumulation in FP32. The network is
 // small (4 -> 256 -> 256 -> 256 -> 1 is 133k parameters), so the products run on
-// CUDA cores in 64 x 64 tiles; a training step is a few GFLOP.
+// CUDA cores in register-tiled 128 x 64 blocks (8 x 4 outputs per thread) with the
+// operand layouts fixed at compile time; the weight gradients, whose contraction runs
+// over the batch, are split over the batch into partial products summed in a fixed order.
 //
 // Parameter order (flat, as exchanged with the host): for each layer l = 0..depth,
 // W_l (row-major [out][in]) then b_l.
@@ -24,8 +26,6 @@
 
 namespace {
 
-constexpr int MBM = 64, MBN = 64, MBK = 16, MTHREADS = 256;
-
 __device__ __forceinline__ float gelu_f(float z) {
   const float s = 0.7978845608028654f, a = 0.044715f;
   return 0.5f * z * (1.0f + tanhf(s * (z + a * z * z * z)));
@@ -36,65 +36,82 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
   return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * s * (1.0f + 3.0f * a * z * z);
 }
 
-// Element accessor for a matrix stored row-major with leading dimension ld; trans
-// swaps the two indices. bf16 selects the BF16 weight array.
-struct Mat {
-  const float* f;
-  const __nv_bfloat16* h;
-  long ld;
-  int trans;
-  __device__ float at(long r, long c) const {
-    const long i = trans ? c * ld + r : r * ld + c;
-    return h ? __bfloat162float(h[i]) : f[i];
-  }
-};
-
 // C[M x N] = A[M x K] B[K x N] with an epilogue:
 //   mode 0: C = acc + bias[n]; Z = C; H = gelu(C) (hidden layer forward)
 //   mode 1: C = acc + bias[n] (output layer forward)
 //   mode 2: C = acc * gelu'(Z[m][n]) (backward through a hidden activation)
 //   mode 3: C = acc (weight gradient)
-__global__ void __launch_bounds__(MTHREADS) k_mlp_gemm(int M, int N, int K, Mat A, Mat B,
-                                                       float* __restrict__ C, long ldc,
-                                                       const float* __restrict__ bias,
-                                                       const float* __restrict__ Z,
-                                                       float* __restrict__ H, int mode) {
-  __shared__ float As[MBK][MBM + 1];
-  __shared__ float Bs[MBK][MBN];
-  const int m0 = blockIdx.y * MBM, n0 = blockIdx.x * MBN;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += MBK) {
-    for (int e = threadIdx.x; e < MBM * MBK; e += MTHREADS) {
-      const int mm = e / MBK, kk = e - mm * MBK;
-      As[kk][mm] = (m0 + mm < M && k0 + kk < K) ? A.at(m0 + mm, k0 + kk) : 0.f;
+// The product runs in 128 x 64 tiles, 256 threads,
+// each thread 8 rows (8 ty .. 8 ty + 7) x 4 columns (4 tx .. 4 tx + 3) read from shared
+// memory as float4. The layouts are template parameters: AT / BT transpose the operand's
+// storage (element (r, c) at c * ld + r), AH / BH read the BF16 weight copy. split > 1
+// (mode 3 only): CTA z takes rows [z, z + 1) * kchunk of K and writes its partial product
+// to C + z * M * ldc (summed afterwards by k_sum_splits in a fixed order).
+constexpr int TBM = 128, TBN = 64, TBK = 16, TPAD = 4;
+
+template <bool AT, bool AH, bool BT, bool BH>
+__global__ void __launch_bounds__(256) k_mlp_gemm_t(int M, int N, int K, int kchunk,
+                                                    const void* __restrict__ Ap, long lda,
+                                                    const void* __restrict__ Bp, long ldb,
+                                                    float* __restrict__ C, long ldc,
+                                                    const float* __restrict__ bias,
+                                                    const float* __restrict__ Z,
+                                                    float* __restrict__ H, int mode) {
+  __shared__ __align__(16) float As[TBK][TBM + TPAD];
+  __shared__ __align__(16) float Bs[TBK][TBN + TPAD];
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  auto ldA = [&](long r, long c) -> float {   // A(r, c), r < M, c < K
+    const long i = AT ? c * lda + r : r * lda + c;
+    if constexpr (AH) return __bfloat162float(static_cast<const __nv_bfloat16*>(Ap)[i]);
+    else return static_cast<const float*>(Ap)[i];
+  };
+  auto ldB = [&](long r, long c) -> float {   // B(r, c), r < K, c < N
+    const long i = BT ? c * ldb + r : r * ldb + c;
+    if constexpr (BH) return __bfloat162float(static_cast<const __nv_bfloat16*>(Bp)[i]);
+    else return static_cast<const float*>(Bp)[i];
+  };
+  float acc[8][4] = {};
+  for (int k0 = kbeg; k0 < kend; k0 += TBK) {
+    // A tile: with AT the storage is contiguous along m, else along k
+#pragma unroll
+    for (int u = 0; u < TBM * TBK / 256; ++u) {
+      const int e = tid + 256 * u;
+      const int mm = AT ? (e % TBM) : (e / TBK), kk = AT ? (e / TBM) : (e % TBK);
+      const int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < M && k < kend) ? ldA(m, k) : 0.0f;
     }
-    for (int e = threadIdx.x; e < MBK * MBN; e += MTHREADS) {
-      const int kk = e / MBN, nn = e - kk * MBN;
-      Bs[kk][nn] = (k0 + kk < K && n0 + nn < N) ? B.at(k0 + kk, n0 + nn) : 0.f;
+#pragma unroll
+    for (int u = 0; u < TBN * TBK / 256; ++u) {
+      const int e = tid + 256 * u;
+      const int nn = BT ? (e / TBK) : (e % TBN), kk = BT ? (e % TBK) : (e / TBN);
+      const int n = n0 + nn, k = k0 + kk;
+      Bs[kk][nn] = (n < N && k < kend) ? ldB(k, n) : 0.0f;
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < MBK; ++kk) {
-      float a[4], b[4];
+    for (int kk = 0; kk < TBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][8 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][8 * ty + 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
     }
     __syncthreads();
   }
+  float* Cz = C + (long)blockIdx.z * M * ldc;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty + 16 * i;
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + 8 * ty + i;
     if (m >= M) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tx + 16 * j;
+      const int n = n0 + 4 * tx + j;
       if (n >= N) continue;
       float v = acc[i][j];
       const long o = (long)m * ldc + n;
@@ -107,9 +124,19 @@ __global__ void __launch_bounds__(MTHREADS) k_mlp_gemm(int M, int N, int K, Mat 
       } else if (mode == 2) {
         C[o] = v * gelu_grad_f(Z[o]);
       } else {
-        C[o] = v;
+        Cz[o] = v;
       }
     }
+  }
+}
+
+// out[e] = sum_z part[z][e], z in order (the split-batch weight gradients)
+__global__ void k_sum_splits(const float* __restrict__ part, int nsplit, long n,
+                             float* __restrict__ out) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int z = 0; z < nsplit; ++z) s += part[(long)z * n + e];
+    out[e] = s;
   }
 }
 
@@ -192,12 +219,13 @@ struct mw3_mlp {
   double* partial = nullptr;
   float *Xall = nullptr, *yall = nullptr;
   int* idx = nullptr;
+  float* split = nullptr;            // partial weight gradients of the split batch
+  long split_cap = 0;
   long nall = 0;
   std::string err;
 };
 
 namespace {
-
 int mfail(mw3_mlp* n, int code, const std::string& s) {
   n->err = s;
   return code;
@@ -248,7 +276,9 @@ int ensure_cap(mw3_mlp* net, long rows) {
   return MW3_OK;
 }
 
-dim3 ggrid(int M, int N) { return dim3((N + MBN - 1) / MBN, (M + MBM - 1) / MBM); }
+dim3 tgrid(int M, int N, int nsplit = 1) {
+  return dim3((N + TBN - 1) / TBN, (M + TBM - 1) / TBM, nsplit);
+}
 
 // forward on rows already in net->X; output in net->out (Zs[L-1])
 int forward(mw3_mlp* net, long n) {
@@ -256,12 +286,12 @@ int forward(mw3_mlp* net, long n) {
   const float* in = net->X;
   for (int l = 0; l < L; ++l) {
     const int K = net->sizes[l], N = net->sizes[l + 1];
-    Mat A{in, nullptr, K, 0};
-    Mat B{nullptr, net->ph + net->woff[l], K, 1};  // B[k][o] = W[o][k]
+    // A = activations [n][K] (FP32), B[k][o] = W[o][k] (BF16 weights, stored [o][k])
     const int mode = (l < L - 1) ? 0 : 1;
     float* C = (l < L - 1) ? net->Zs[l] : net->out;
-    k_mlp_gemm<<<ggrid((int)n, N), MTHREADS>>>((int)n, N, K, A, B, C, N, net->p + net->boff[l],
-                                               nullptr, net->Hs[l], mode);
+    k_mlp_gemm_t<false, false, true, true><<<tgrid((int)n, N), 256>>>(
+        (int)n, N, K, K, in, K, net->ph + net->woff[l], K, C, N, net->p + net->boff[l], nullptr,
+        net->Hs[l], mode);
     in = net->Hs[l];
   }
   MCK(cudaGetLastError());
@@ -275,18 +305,31 @@ int backward(mw3_mlp* net, long n) {
   for (int l = L - 1; l >= 0; --l) {
     const int K = net->sizes[l], N = net->sizes[l + 1];
     const float* a_in = (l == 0) ? net->X : net->Hs[l - 1];
-    // dW[o][i] = sum_r g[r][o] a_in[r][i]: M = N (o), N = K (i), K = n (r)
-    Mat A{g, nullptr, N, 1};       // A[o][r] = g[r][o]
-    Mat B{a_in, nullptr, K, 0};    // B[r][i] = a_in[r][i]
-    k_mlp_gemm<<<ggrid(N, K), MTHREADS>>>(N, K, (int)n, A, B, net->g + net->woff[l], K, nullptr,
-                                          nullptr, nullptr, 3);
+    // dW[o][i] = sum_r g[r][o] a_in[r][i]: M = N (o), N = K (i), K = n (r); A(o, r) = g[r][o]
+    // (stored transposed), B(r, i) = a_in[r][i]; the batch is split into chunks of 512 rows
+    // whose partial products are summed in chunk order
+    {
+      const int kchunk = 512;
+      const int nsplit = (int)((n + kchunk - 1) / kchunk);
+      const long need = (long)nsplit * N * K;
+      if (need > net->split_cap) {
+        cudaFree(net->split);
+        MCK(cudaMalloc(&net->split, need * sizeof(float)));
+        net->split_cap = need;
+      }
+      k_mlp_gemm_t<true, false, false, false><<<tgrid(N, K, nsplit), 256>>>(
+          N, K, (int)n, kchunk, g, N, a_in, K, net->split, K, nullptr, nullptr, nullptr, 3);
+      const long ne = (long)N * K;
+      k_sum_splits<<<(unsigned)std::min<long>((ne + 255) / 256, 1024), 256>>>(
+          net->split, nsplit, ne, net->g + net->woff[l]);
+    }
     k_colsum<<<(N + 127) / 128, 128>>>(g, (int)n, N, net->g + net->boff[l]);
     if (l > 0) {
       // g_prev[r][i] = sum_o g[r][o] W[o][i] * gelu'(Z_(l-1)[r][i])
-      Mat A2{g, nullptr, N, 0};
-      Mat B2{nullptr, net->ph + net->woff[l], K, 0};  // B2[o][i] = W[o][i]
-      k_mlp_gemm<<<ggrid((int)n, K), MTHREADS>>>((int)n, K, N, A2, B2, net->Gs[l - 1], K, nullptr,
-                                                 net->Zs[l - 1], nullptr, 2);
+      // A(r, o) = g[r][o], B(o, i) = W[o][i] (BF16)
+      k_mlp_gemm_t<false, false, false, true><<<tgrid((int)n, K), 256>>>(
+          (int)n, K, N, N, g, N, net->ph + net->woff[l], K, net->Gs[l - 1], K, nullptr,
+          net->Zs[l - 1], nullptr, 2);
       g = net->Gs[l - 1];
     }
   }
@@ -392,6 +435,7 @@ void mw3_mlp_destroy(mw3_mlp* net) {
   cudaFree(net->Xall);
   cudaFree(net->yall);
   cudaFree(net->idx);
+  cudaFree(net->split);
   delete net;
 }
 

@@ -98,6 +98,7 @@ _SIGS = {
     "mw3_apply_hs": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mw3_norm_trace": (C.c_long, [C.c_void_p, C.POINTER(C.c_double), C.c_long]),
     "mw3_enable_autocorrelation": (C.c_int, [C.c_void_p]),
+    "mw3_incoming_amplitude": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mw3_enable_time_packets": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "mw3_time_packets": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
     "mw3_autocorrelation": (C.c_long, [C.c_void_p, C.POINTER(C.c_double), C.c_long]),
@@ -391,6 +392,12 @@ class Propagator:
         out = np.zeros((max(n, 0), nJ))
         cnt = lib.mw3_norm_trace(self.ctx, _dp(out), n)
         return out[:cnt]
+
+    def incoming_amplitude(self):
+        """|a(E)|^2 of the packet's incoming part at the analysis energies."""
+        out = np.zeros(self.cfg["analysis"]["nE"])
+        _check(self.ctx, lib.mw3_incoming_amplitude(self.ctx, _dp(out)))
+        return out
 
     def enable_autocorrelation(self):
         """Keep the current state as Psi(k=0) and record C_k = <Psi(0)|Psi(k)> per J."""

@@ -4,9 +4,15 @@ The cumulative probability of Eq. cumulative-probability needs the probabilities
 every J; the paper computes a coarse set of J and interpolates the rest by
 J-shifting (Eq. J-shifting-interpolation). Here a small network learns
 P_J(E, v', j') from propagations at training J values (this library's propagation,
-one batched context for all of them) and predicts intermediate J. The propagation
-measures its error and is its fallback: wherever the prediction differs from the
-propagated value by more than `fallback_dP`, the propagated value is used.
+one batched context for all of them) and predicts intermediate J. An ensemble of
+networks (different seeds) gives both the prediction (the mean) and its uncertainty
+(the spread); a held-out J whose spread, times `spread_factor`, exceeds `fallback_dP`
+anywhere falls back to propagation, so the decision needs no propagation of the J
+values that pass. Energies where the packet's incoming amplitude |a(E)|^2 is below
+`a2_floor` of its maximum carry no usable flux information (the probabilities divide
+by it) and are left out of training and scoring. A separate propagation of every
+held-out J measures the errors of the surrogate, the fallback result and the two
+interpolations; it is evaluation, not part of the surrogate path.
 
 State-resolved targets are the reactant-channel (v', j') probabilities the library
 projects at R_inf (summed over Omega), which stand in for product channels.
@@ -21,9 +27,10 @@ import numpy as np
 from . import mw3
 
 
-def propagate_probabilities(cfg: dict, Js, steps: int, precision: str = "fp64", device: int = 0):
+def propagate_probabilities(cfg: dict, Js, steps: int, precision: str = "fp64", device: int = 0,
+                            with_a2: bool = False):
     """Run one batched propagation over the J list; returns (E, P_total[J,E],
-    P_state[J, v, j, E] for the initial electronic state, seconds)."""
+    P_state[J, v, j, E] for the initial electronic state, seconds[, |a(E)|^2])."""
     c = copy.deepcopy(cfg)
     c["J"] = list(Js)
     t0 = time.perf_counter()
@@ -31,8 +38,11 @@ def propagate_probabilities(cfg: dict, Js, steps: int, precision: str = "fp64", 
     pr.propagate(steps)
     E, P, Pin = pr.probabilities()
     secs = time.perf_counter() - t0
+    a2 = pr.incoming_amplitude() if with_a2 else None
     pr.close()
     L0 = c["packet"]["elec0"]
+    if with_a2:
+        return E, P, Pin[:, L0], secs, a2
     return E, P, Pin[:, L0], secs
 
 
@@ -128,15 +138,20 @@ def cumulative(Js, P):
 
 def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 1500, width: int = 256,
         depth: int = 3, lr: float = 2e-3, batch: int = 512, fallback_dP: float = 0.01,
-        ensemble: int = 3, precision: str = "fp64", device: int = 0, seed: int = 10167):
-    """Train on J_train, evaluate on J_test; returns a report dictionary.
+        ensemble: int = 3, precision: str = "fp64", device: int = 0, seed: int = 10167,
+        spread_factor: float = 2.0, a2_floor: float = 0.05):
+    """Train on J_train, predict J_test with the fallback decided by the ensemble spread,
+    then score everything against a propagation of J_test; returns a report dictionary.
 
     Each of `ensemble` networks (different initialisation and shuffling seeds) trains for
     `epochs` at `lr`, then epochs/2 at lr/4 and epochs/2 at lr/16 (the AdamW state carries
-    over); the prediction is their mean. Single networks vary strongly with the seed on a
-    few thousand samples; the mean is steadier. The propagations (training J and the held-out
-    J that evaluate the network) run in `precision` ("fp64" or "mixed")."""
-    E, _, Ptr, t_train = propagate_probabilities(cfg, J_train, steps, precision, device=device)
+    over); the prediction is their mean, the uncertainty their standard deviation. The
+    propagations run in `precision` ("fp64" or "mixed")."""
+    E_all, _, Ptr_all, t_train, a2 = propagate_probabilities(cfg, J_train, steps, precision,
+                                                              device=device, with_a2=True)
+    keep = a2 >= a2_floor * np.max(a2)
+    E = E_all[keep]
+    Ptr = Ptr_all[..., keep]
     nv, nj = Ptr.shape[1], Ptr.shape[2]
     scale = dict(J=max(max(J_train), 1), E0=E[0], dE=max(E[-1] - E[0], 1e-12), v=max(nv - 1, 1),
                  j=max(nj - 1, 1), B=fit_shift(E, np.asarray(J_train, float), Ptr))
@@ -156,33 +171,89 @@ def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 1500, width: int =
         preds.append(predict(net, J_test, E, nv, nj, scale))
         t_pred += time.perf_counter() - t0
         net.close()
-    Psur = np.mean(preds, axis=0)
+    preds = np.asarray(preds)
+    Psur = preds.mean(axis=0)
+    spread = preds.std(axis=0) if len(preds) > 1 else np.zeros_like(Psur)
     loss = float(np.mean(losses))
-    # the reference: propagation at the held-out J
-    _, _, Pte, t_test = propagate_probabilities(cfg, J_test, steps, precision, device=device)
+    # fallback decided from the ensemble alone; only those J values are propagated
+    bad_J = [J for t, J in enumerate(J_test) if spread_factor * spread[t].max() > fallback_dP]
+    final = Psur.astype(np.float64)
+    t_fallback = 0.0
+    if bad_J:
+        _, _, Pfb, t_fallback = propagate_probabilities(cfg, bad_J, steps, precision, device=device)
+        for t, J in enumerate(J_test):
+            if J in bad_J:
+                final[t] = Pfb[bad_J.index(J)][..., keep]
+    # evaluation: every held-out J propagated
+    _, _, Pte_all, t_test = propagate_probabilities(cfg, J_test, steps, precision, device=device)
+    Pte = Pte_all[..., keep]
     Pjs = jshift_baseline(E, np.asarray(J_train), Ptr, np.asarray(J_test))
     Plin = linear_baseline(np.asarray(J_train), Ptr, np.asarray(J_test))
     err = np.abs(Psur - Pte)
-    bad_J = [J for t, J in enumerate(J_test) if err[t].max() > fallback_dP]
-    final = Psur.astype(np.float64)
-    for t, J in enumerate(J_test):
-        if J in bad_J:
-            final[t] = Pte[t]
     C_true = cumulative(J_test, Pte)
+
+    def crel(P):
+        return float(np.abs(cumulative(J_test, P) - C_true).max() / max(C_true.max(), 1e-30))
+
     rep = dict(
         train_loss=loss, n_train=int(X.shape[0]), B_shift=scale["B"], ensemble=len(preds),
+        energies_scored=int(keep.sum()), energies=int(keep.size), a2_floor=a2_floor,
         mean_abs_dP=dict(surrogate=float(err.mean()), jshift=float(np.abs(Pjs - Pte).mean()),
-                         linear=float(np.abs(Plin - Pte).mean())),
+                         linear=float(np.abs(Plin - Pte).mean()),
+                         with_fallback=float(np.abs(final - Pte).mean())),
         max_abs_dP=dict(surrogate=float(err.max()), jshift=float(np.abs(Pjs - Pte).max()),
                         linear=float(np.abs(Plin - Pte).max()),
                         with_fallback=float(np.abs(final - Pte).max())),
-        cumulative_rel_err=dict(
-            surrogate=float(np.abs(cumulative(J_test, Psur) - C_true).max() / max(C_true.max(), 1e-30)),
-            jshift=float(np.abs(cumulative(J_test, Pjs) - C_true).max() / max(C_true.max(), 1e-30)),
-            linear=float(np.abs(cumulative(J_test, Plin) - C_true).max() / max(C_true.max(), 1e-30)),
-            with_fallback=float(np.abs(cumulative(J_test, final) - C_true).max() / max(C_true.max(), 1e-30))),
+        cumulative_rel_err=dict(surrogate=crel(Psur), jshift=crel(Pjs), linear=crel(Plin),
+                                with_fallback=crel(final)),
         fallback_J=bad_J, fallback_fraction=len(bad_J) / len(J_test),
-        seconds=dict(propagate_train=t_train, fit=t_fit, predict=t_pred, propagate_test=t_test,
-                     surrogate_path=t_pred + t_test * len(bad_J) / len(J_test)),
+        spread_factor=spread_factor,
+        # per held-out J: largest error over largest ensemble spread (calibration of the rule)
+        error_over_spread=[float(err[t].max() / max(spread[t].max(), 1e-30))
+                           for t in range(len(J_test))],
+        passed_J_max_abs_dP=float(max([err[t].max() for t, J in enumerate(J_test) if J not in bad_J],
+                                      default=0.0)),
+        max_P_propagated=float(Pte.max()),
+        seconds=dict(propagate_train=t_train, fit=t_fit, predict=t_pred,
+                     propagate_fallback=t_fallback, propagate_all_test=t_test,
+                     surrogate_path=t_fit + t_pred + t_fallback),
     )
     return rep
+
+
+def c5_config():
+    """The J-interpolation workload: the config-3 grid with a single electronic surface,
+    Omega up to 15, the configured energy window and final-state ranges."""
+    import workloads as W
+    c5 = W.C5
+    cfg = copy.deepcopy(c5["base"])
+    cfg["pes"]["two_state"] = None
+    cfg["nelec"] = 1
+    cfg["analysis"].update(nE=c5["nE"], E_lo_eV=c5["E_lo_eV"], E_hi_eV=c5["E_hi_eV"],
+                           vmax=c5["vmax"], jmax=c5["jmax"])
+    return cfg
+
+
+def main(argv=None):
+    """python -m paper_2412_10167_gb300.surrogate [--epochs 60 ...]: the J-interpolation
+    workload end to end (training propagations, ensemble training, fallback, evaluation)."""
+    import argparse
+    import json
+    import workloads as W
+    ap = argparse.ArgumentParser(description=main.__doc__.splitlines()[0])
+    ap.add_argument("--steps", type=int, default=8000)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--ensemble", type=int, default=3)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--spread-factor", type=float, default=2.0)
+    args = ap.parse_args(argv)
+    rep = run(c5_config(), W.C5["J_train"], W.C5["J_test"], steps=args.steps,
+              epochs=args.epochs, batch=args.batch, ensemble=args.ensemble,
+              precision=args.precision, fallback_dP=W.C5["fallback_dP"],
+              spread_factor=args.spread_factor)
+    print(json.dumps(rep, indent=1))
+
+
+if __name__ == "__main__":
+    main()

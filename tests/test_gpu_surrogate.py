@@ -83,7 +83,10 @@ def test_surrogate_pipeline_against_propagation():
     rep = surrogate.run(cfg, J_train=list(range(0, 25, 4)), J_test=list(range(2, 23, 4)),
                         steps=600, epochs=1500, width=256, depth=3, batch=512, ensemble=3)
     print(json.dumps(rep, indent=1))
-    # the propagation fallback bounds every final probability error
-    assert rep["max_abs_dP"]["with_fallback"] <= 0.01 + 1e-12
     assert np.isfinite(rep["mean_abs_dP"]["surrogate"])
     assert rep["train_loss"] < 1e-2
+    # the fallback is decided by the ensemble spread without propagating the held-out J
+    assert 0.0 <= rep["fallback_fraction"] <= 1.0
+    # the J values the spread let through and the fallback result are scored as they are
+    assert rep["max_abs_dP"]["with_fallback"] <= rep["max_abs_dP"]["surrogate"] + 1e-12
+    assert rep["seconds"]["surrogate_path"] >= rep["seconds"]["fit"]
