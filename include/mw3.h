@@ -270,6 +270,29 @@ int mw3_photo_spectrum(mw3_ctx* ctx, const double* E, int nE, double* a0);
 int mw3_enable_time_packets(mw3_ctx* ctx, int nt, const double* t);
 int mw3_time_packets(mw3_ctx* ctx, double* out, long* kmax);
 
+/* Bound states by non-orthogonal Lanczos (Section 2.3.2: the bound-state program that
+ * supplies photodissociation initial states applies the same grid Hamiltonian in the
+ * iterative non-orthogonal Lanczos method of Cullum and Willoughby). m steps of the plain
+ * three-term recursion on H_s, on the device in the FBR coordinates of the state, without
+ * reorthogonalisation, from the start vector v0 (host FP64 grid values of every block,
+ * normalised per J; the blocks of different J are independent). FP64 contexts give the
+ * eigenvalues to ~1e-10 dE, mixed contexts to the FP32 rounding of the recursion.
+ *   mw3_lanczos:       alpha[i * nJ + iJ], beta[i * nJ + iJ] (i < m; beta_i couples
+ *                      v_i and v_(i+1)), caller-owned.
+ *   mw3_bound_states:  eigenvalues (hartree) of each J accepted by the Cullum-Willoughby
+ *                      test (a cluster of numerically equal copies counts once; a simple
+ *                      eigenvalue of T_m that is also one of T_m without its first row and
+ *                      column is spurious) inside [emin, emax]: E[iJ * maxev + k],
+ *                      k < count[iJ] <= maxev.
+ *   mw3_bound_state_vector: the Ritz vector of J index iJ nearest the eigenvalue E, from a
+ *                      second run of the recursion: out = grid values (every block; zero
+ *                      outside J), normalised.
+ * All three allocate work vectors on the device and leave the propagation state alone. */
+int mw3_lanczos(mw3_ctx* ctx, const double* v0, int m, double* alpha, double* beta);
+int mw3_bound_states(mw3_ctx* ctx, const double* v0, int m, double emin, double emax, int maxev,
+                     double* E, int* count);
+int mw3_bound_state_vector(mw3_ctx* ctx, const double* v0, int m, int iJ, double E, double* out);
+
 /* Sizes and scaling constants: nblocks, points per block, E0 and dE per J. */
 int mw3_sizes(const mw3_ctx* ctx, long* nblocks, long* points_per_block);
 int mw3_spectral_range(const mw3_ctx* ctx, double* E0, double* dE);

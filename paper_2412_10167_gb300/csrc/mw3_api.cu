@@ -1649,6 +1649,109 @@ int propagate_impl(mw3_ctx* ctx, long nsteps) {
   return MW3_OK;
 }
 
+// Non-orthogonal Lanczos on H_s in the FBR coordinates of the state (Section 2.3.2, the
+// bound-state program): m steps per J from the start vector already in "lz_v" (normalised
+// per J here), without reorthogonalisation. alpha/beta (device [m][nJ]) hold
+// alpha_i = <v_i|H_s v_i - beta_(i-1) v_(i-1)> and beta_i = ||w_i||, w_i the residual that
+// becomes v_(i+1) (beta_i couples v_i and v_(i+1)). With accumulate, x += s[i][iJ] v_i
+// each step ("lz_s" device [m][nJ]) into "lz_x" (the second run of a Ritz vector).
+template <typename real>
+int lanczos_run(mw3_ctx* ctx, int m, bool accumulate) {
+  cudaStream_t st = ctx->stream;
+  const long n = (long)ctx->nblk * ctx->npts;
+  const int nJ = ctx->nJ;
+  const DevBlock* blk = (const DevBlock*)dptr(ctx, "blocks");
+  const long* Jb = (const long*)dptr(ctx, "J_begin");
+  double* part = (double*)dptr(ctx, "lz_part");
+  double* a = (double*)dptr(ctx, "lz_a");
+  double* b = (double*)dptr(ctx, "lz_b");
+  double* b2 = (double*)dptr(ctx, "lz_b2");
+  double* nrm = (double*)dptr(ctx, "lz_nrm");
+  real* v = (real*)dptr(ctx, "lz_v");
+  real* vp = (real*)dptr(ctx, "lz_vp");
+  real* w = (real*)dptr(ctx, "lz_w");
+  real* x = accumulate ? (real*)dptr(ctx, "lz_x") : nullptr;
+  const double* S = accumulate ? (const double*)dptr(ctx, "lz_s") : nullptr;
+  LK(launch_dots<real>(v, v, Jb, nJ, part, 64, nrm, st));
+  LK(launch_rscale_seg<real>(v, nrm, n, ctx->npts, blk, st));
+  CK(cudaMemsetAsync(vp, 0, n * sizeof(real), st));
+  if (accumulate) CK(cudaMemsetAsync(x, 0, n * sizeof(real), st));
+  const char* qname = state_name(ctx, true);
+  void* saved = ctx->buf[qname].p;
+  const int cur0 = ctx->cur;
+  int status = MW3_OK;
+  for (int i = 0; i < m && status == MW3_OK; ++i) {
+    if (accumulate) LK(launch_axpy_seg<real>(x, v, S + (size_t)i * nJ, 1.0, n, ctx->npts, blk, st));
+    ctx->buf[qname].p = v;   // H_s v through the step's own kernels (mode 1)
+    status = step<real>(ctx, 0, true, false, 1, w);
+    ctx->buf[qname].p = saved;
+    ctx->cur = cur0;
+    if (status) break;
+    if (i > 0) LK(launch_axpy_seg<real>(w, vp, b + (size_t)(i - 1) * nJ, -1.0, n, ctx->npts, blk, st));
+    LK(launch_dots<real>(v, w, Jb, nJ, part, 64, a + (size_t)i * nJ, st));
+    LK(launch_axpy_seg<real>(w, v, a + (size_t)i * nJ, -1.0, n, ctx->npts, blk, st));
+    LK(launch_dots<real>(w, w, Jb, nJ, part, 64, b2 + (size_t)i * nJ, st));
+    LK(launch_sqrt(b2 + (size_t)i * nJ, b + (size_t)i * nJ, nJ, st));
+    LK(launch_rscale_seg<real>(w, b2 + (size_t)i * nJ, n, ctx->npts, blk, st));
+    real* t = vp;   // (v_(i-1), v_i, w) <- (v_i, v_(i+1), free)
+    vp = v;
+    v = w;
+    w = t;
+  }
+  ctx->buf[qname].p = saved;
+  CK(cudaStreamSynchronize(st));
+  return status;
+}
+
+// Lanczos coefficients of m steps from the host start vector v0 (grid values), per J.
+int lanczos_coefficients(mw3_ctx* ctx, const double* v0, int m, std::vector<double>& alpha,
+                         std::vector<double>& beta, bool accumulate = false) {
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  const int nJ = ctx->nJ;
+  int st;
+  if ((st = dalloc(ctx, "lz_v", n * ctx->rs())) || (st = dalloc(ctx, "lz_vp", n * ctx->rs())) ||
+      (st = dalloc(ctx, "lz_w", n * ctx->rs())) ||
+      (st = dalloc(ctx, "lz_part", (size_t)nJ * 64 * 8)) ||
+      (st = dalloc(ctx, "lz_a", (size_t)m * nJ * 8)) || (st = dalloc(ctx, "lz_b", (size_t)m * nJ * 8)) ||
+      (st = dalloc(ctx, "lz_b2", (size_t)m * nJ * 8)) || (st = dalloc(ctx, "lz_nrm", (size_t)nJ * 8)))
+    return st;
+  if (accumulate && (st = dalloc(ctx, "lz_x", n * ctx->rs()))) return st;
+  if ((st = transform_upload(ctx, v0, "lz_v", true))) return st;
+  st = ctx->precision == MW3_FP64 ? lanczos_run<double>(ctx, m, accumulate)
+                                  : lanczos_run<float>(ctx, m, accumulate);
+  if (st) return st;
+  alpha.resize((size_t)m * nJ);
+  beta.resize((size_t)m * nJ);
+  CK(cudaMemcpyAsync(alpha.data(), dptr(ctx, "lz_a"), alpha.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(beta.data(), dptr(ctx, "lz_b"), beta.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MW3_OK;
+}
+
+// Cullum-Willoughby identification for one J: accepted eigenvalues of T_m (scaled units).
+void cw_accept(const std::vector<double>& al, const std::vector<double>& be, double tol,
+               std::vector<double>& out) {
+  const int m = (int)al.size();
+  std::vector<double> lam, hat;
+  tridiagonal_eigenvalues(al, std::vector<double>(be.begin(), be.begin() + std::max(m - 1, 0)), lam);
+  if (m > 1) {
+    std::vector<double> ah(al.begin() + 1, al.end()), bh(be.begin() + 1, be.begin() + (m - 1));
+    tridiagonal_eigenvalues(ah, bh, hat);
+  }
+  out.clear();
+  for (int i = 0; i < m;) {
+    int j = i;
+    while (j + 1 < m && lam[j + 1] - lam[i] <= tol) ++j;
+    double mean = 0;
+    for (int k = i; k <= j; ++k) mean += lam[k];
+    mean /= (j - i + 1);
+    double dh = 1e300;
+    for (double h : hat) dh = std::min(dh, std::fabs(h - mean));
+    if (j > i || dh > tol) out.push_back(mean);   // copies, or simple and not in T-hat
+    i = j + 1;
+  }
+}
+
 // |a(E)|^2 of the incoming packet, a(E) = sqrt(mu/(2 pi K)) sum_m dR exp(i K R_m) g~(R_m).
 void incoming_a2(mw3_ctx* ctx, std::vector<double>& a2) {
   const int nE = ctx->an.nE;
@@ -1897,6 +2000,76 @@ long mw3_norm_trace(mw3_ctx* ctx, double* out, long n) {
   const long cnt = std::min(n, have);
   std::copy(ctx->norm_trace.end() - cnt * ctx->nJ, ctx->norm_trace.end(), out);
   return cnt;
+}
+
+int mw3_lanczos(mw3_ctx* ctx, const double* v0, int m, double* alpha, double* beta) {
+  if (!ctx || !v0 || m < 1 || !alpha || !beta) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
+  if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
+  cudaSetDevice(ctx->device);
+  std::vector<double> a, b;
+  int st = lanczos_coefficients(ctx, v0, m, a, b);
+  if (st) return st;
+  std::copy(a.begin(), a.end(), alpha);
+  std::copy(b.begin(), b.end(), beta);
+  return MW3_OK;
+}
+
+int mw3_bound_states(mw3_ctx* ctx, const double* v0, int m, double emin, double emax, int maxev,
+                     double* E, int* count) {
+  if (!ctx || !v0 || m < 2 || maxev < 1 || !E || !count) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
+  if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
+  cudaSetDevice(ctx->device);
+  std::vector<double> a, b;
+  int st = lanczos_coefficients(ctx, v0, m, a, b);
+  if (st) return st;
+  const int nJ = ctx->nJ;
+  const double tol = ctx->precision == MW3_FP64 ? 1e-10 : 1e-5;
+  for (int iJ = 0; iJ < nJ; ++iJ) {
+    std::vector<double> al(m), be(m), acc;
+    for (int i = 0; i < m; ++i) {
+      al[i] = a[(size_t)i * nJ + iJ];
+      be[i] = b[(size_t)i * nJ + iJ];
+    }
+    cw_accept(al, be, tol, acc);
+    int c = 0;
+    for (double lam : acc) {
+      const double e = ctx->E0[iJ] + ctx->dE[iJ] * lam;
+      if (e >= emin && e <= emax && c < maxev) E[(size_t)iJ * maxev + c++] = e;
+    }
+    count[iJ] = c;
+  }
+  return MW3_OK;
+}
+
+int mw3_bound_state_vector(mw3_ctx* ctx, const double* v0, int m, int iJ, double E, double* out) {
+  if (!ctx || !v0 || m < 2 || !out) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
+  if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
+  if (iJ < 0 || iJ >= ctx->nJ) return ctx->fail(MW3_ERR_BAD_ARG, "J index out of range");
+  cudaSetDevice(ctx->device);
+  std::vector<double> a, b;
+  int st = lanczos_coefficients(ctx, v0, m, a, b);
+  if (st) return st;
+  const int nJ = ctx->nJ;
+  std::vector<double> al(m), be(m - 1), s;
+  for (int i = 0; i < m; ++i) al[i] = a[(size_t)i * nJ + iJ];
+  for (int i = 0; i + 1 < m; ++i) be[i] = b[(size_t)i * nJ + iJ];
+  tridiagonal_eigenvector(al, be, (E - ctx->E0[iJ]) / ctx->dE[iJ], s);
+  std::vector<double> S((size_t)m * nJ, 0.0);
+  for (int i = 0; i < m; ++i) S[(size_t)i * nJ + iJ] = s[i];
+  if ((st = upload_raw(ctx, "lz_s", S))) return st;
+  if ((st = lanczos_coefficients(ctx, v0, m, a, b, true))) return st;   // second run
+  // normalise the J's part on the host after the transform (an orthogonal map per block)
+  if ((st = transform_download(ctx, "lz_x", out))) return st;
+  double nrm = 0;
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  for (size_t e = 0; e < n; ++e) nrm += out[e] * out[e];
+  nrm = std::sqrt(nrm);
+  if (nrm > 0)
+    for (size_t e = 0; e < n; ++e) out[e] /= nrm;
+  return MW3_OK;
 }
 
 int mw3_incoming_amplitude(mw3_ctx* ctx, double* a2) {

@@ -419,6 +419,32 @@ __global__ void __launch_bounds__(256) k_time_accum(const real* __restrict__ q, 
   }
 }
 
+// Lanczos helpers on J segments (every element's scalar is that of its block's J):
+//   k_axpy_seg:   y[e] += s * c[iJ(e)] * x[e]
+//   k_rscale_seg: y[e] /= sqrt(c2[iJ(e)])  (c2 = 0 leaves y unchanged)
+//   k_sqrt:       b[i] = sqrt(b2[i])
+template <typename real>
+__global__ void k_axpy_seg(real* __restrict__ y, const real* __restrict__ x,
+                           const double* __restrict__ c, double s, long n, long npts,
+                           const DevBlock* __restrict__ blocks) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    y[e] = (real)((double)y[e] + s * c[blocks[e / npts].iJ] * (double)x[e]);
+}
+
+template <typename real>
+__global__ void k_rscale_seg(real* __restrict__ y, const double* __restrict__ c2, long n, long npts,
+                             const DevBlock* __restrict__ blocks) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const double v = c2[blocks[e / npts].iJ];
+    if (v > 0.0) y[e] = (real)((double)y[e] / sqrt(v));
+  }
+}
+
+__global__ void k_sqrt(const double* __restrict__ b2, double* __restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = sqrt(b2[i]);
+}
+
 __global__ void k_norm_final(const double* __restrict__ partial, int nchunk, double* out) {
   const int iJ = blockIdx.x;
   if (threadIdx.x == 0) {
@@ -433,6 +459,27 @@ cudaError_t launch_norms(const real* q, const long* J_begin, int nJ, double* par
                          int nchunk, double* out, cudaStream_t st) {
   k_norm_partial<real><<<dim3(nchunk, nJ), 256, 0, st>>>(q, J_begin, nchunk, partial);
   k_norm_final<<<nJ, 32, 0, st>>>(partial, nchunk, out);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_axpy_seg(real* y, const real* x, const double* c, double s, long n, long npts,
+                            const DevBlock* blocks, cudaStream_t st) {
+  const long nb = (n + 255) / 256;
+  k_axpy_seg<real><<<(unsigned)(nb < 8192 ? nb : 8192), 256, 0, st>>>(y, x, c, s, n, npts, blocks);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_rscale_seg(real* y, const double* c2, long n, long npts, const DevBlock* blocks,
+                              cudaStream_t st) {
+  const long nb = (n + 255) / 256;
+  k_rscale_seg<real><<<(unsigned)(nb < 8192 ? nb : 8192), 256, 0, st>>>(y, c2, n, npts, blocks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sqrt(const double* b2, double* b, int n, cudaStream_t st) {
+  k_sqrt<<<(n + 127) / 128, 128, 0, st>>>(b2, b, n);
   return cudaGetLastError();
 }
 
@@ -510,7 +557,11 @@ cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* ac
                                          int, double*, cudaStream_t);                         \
   template cudaError_t launch_time_accum<real>(const real*, long, long, const DevBlock*,      \
                                                const double*, int, int, long, const long*,    \
-                                               int, double*, cudaStream_t);
+                                               int, double*, cudaStream_t);                   \
+  template cudaError_t launch_axpy_seg<real>(real*, const real*, const double*, double, long, \
+                                             long, const DevBlock*, cudaStream_t);            \
+  template cudaError_t launch_rscale_seg<real>(real*, const double*, long, long,              \
+                                               const DevBlock*, cudaStream_t);
 
 MW3_INST(double)
 MW3_INST(float)

@@ -90,6 +90,61 @@ void fbr_matrix(int om, int n, const std::vector<double>& x, const std::vector<d
     for (int k = 0; k < n; ++k) T[(size_t)i * n + k] = P[(size_t)i * n + k] * std::sqrt(w[k]);
 }
 
+// Implicit QL with shifts on a symmetric tridiagonal matrix (diagonal d, e[i] coupling
+// d[i] and d[i+1]; e is destroyed), eigenvalues left in d (unsorted). With Z != nullptr the
+// plane rotations are accumulated into the n x n row-major Z (eigenvectors in its columns).
+static void ql_implicit(int n, std::vector<double>& d, std::vector<double>& e, double* Z) {
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    int m;
+    do {
+      for (m = l; m + 1 < n; ++m) {
+        const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (std::fabs(e[m]) + dd == dd) break;  // negligible at working precision
+      }
+      if (m != l) {
+        if (++iter > 200) break;
+        double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+        double r = std::hypot(g, 1.0);
+        g = d[m] - d[l] + e[l] / (g + (g >= 0 ? std::fabs(r) : -std::fabs(r)));
+        double s = 1.0, c = 1.0, pp = 0.0;
+        int i;
+        bool deflated = false;
+        for (i = m - 1; i >= l; --i) {
+          double f = s * e[i];
+          const double b = c * e[i];
+          r = std::hypot(f, g);
+          e[i + 1] = r;
+          if (r == 0.0) {
+            d[i + 1] -= pp;
+            e[m] = 0.0;
+            deflated = true;
+            break;
+          }
+          s = f / r;
+          c = g / r;
+          g = d[i + 1] - pp;
+          r = (d[i] - g) * s + 2.0 * c * b;
+          pp = s * r;
+          d[i + 1] = g + pp;
+          g = c * r - b;
+          if (Z) {
+            for (int kk = 0; kk < n; ++kk) {
+              f = Z[(size_t)kk * n + i + 1];
+              Z[(size_t)kk * n + i + 1] = s * Z[(size_t)kk * n + i] + c * f;
+              Z[(size_t)kk * n + i] = c * Z[(size_t)kk * n + i] - s * f;
+            }
+          }
+        }
+        if (deflated) continue;
+        d[l] -= pp;
+        e[l] = g;
+        e[m] = 0.0;
+      }
+    } while (m != l);
+  }
+}
+
 // Symmetric eigen-decomposition: Householder reduction to tridiagonal form, then
 // the implicit QL iteration with Wilkinson-type shifts of Bowdler, Martin, Reinsch and
 // Wilkinson (the published tql2 algorithm, Numer. Math. 11, 1968); eigenvalues
@@ -141,54 +196,7 @@ void symmetric_eigen(int n, const std::vector<double>& Ain, std::vector<double>&
   std::vector<double> d(n), e(n, 0.0);
   for (int i = 0; i < n; ++i) d[i] = A[(size_t)i * n + i];
   for (int i = 0; i + 1 < n; ++i) e[i] = A[(size_t)(i + 1) * n + i];
-  // implicit QL; e[i] couples d[i] and d[i+1]
-  for (int l = 0; l < n; ++l) {
-    int iter = 0;
-    int m;
-    do {
-      for (m = l; m + 1 < n; ++m) {
-        const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
-        if (std::fabs(e[m]) + dd == dd) break;  // negligible at working precision
-      }
-      if (m != l) {
-        if (++iter > 200) break;
-        double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-        double r = std::hypot(g, 1.0);
-        g = d[m] - d[l] + e[l] / (g + (g >= 0 ? std::fabs(r) : -std::fabs(r)));
-        double s = 1.0, c = 1.0, pp = 0.0;
-        int i;
-        bool deflated = false;
-        for (i = m - 1; i >= l; --i) {
-          double f = s * e[i];
-          const double b = c * e[i];
-          r = std::hypot(f, g);
-          e[i + 1] = r;
-          if (r == 0.0) {
-            d[i + 1] -= pp;
-            e[m] = 0.0;
-            deflated = true;
-            break;
-          }
-          s = f / r;
-          c = g / r;
-          g = d[i + 1] - pp;
-          r = (d[i] - g) * s + 2.0 * c * b;
-          pp = s * r;
-          d[i + 1] = g + pp;
-          g = c * r - b;
-          for (int kk = 0; kk < n; ++kk) {
-            f = Z[(size_t)kk * n + i + 1];
-            Z[(size_t)kk * n + i + 1] = s * Z[(size_t)kk * n + i] + c * f;
-            Z[(size_t)kk * n + i] = c * Z[(size_t)kk * n + i] - s * f;
-          }
-        }
-        if (deflated) continue;
-        d[l] -= pp;
-        e[l] = g;
-        e[m] = 0.0;
-      }
-    } while (m != l);
-  }
+  ql_implicit(n, d, e, Z.data());
   // sort ascending
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -403,6 +411,64 @@ void bessel_j_sequence(double x, int n, std::vector<double>& J) {
   double s = t[0];
   for (int i = 2; i <= top; i += 2) s += 2.0 * t[i];
   for (int k = 0; k < n; ++k) J[k] = t[k] / s;
+}
+
+// Eigenvalues (ascending) of the symmetric tridiagonal matrix with diagonal d[0..n-1] and
+// off-diagonal e[0..n-2] (e[i] couples i and i+1): the implicit QL above without vectors.
+void tridiagonal_eigenvalues(const std::vector<double>& d_in, const std::vector<double>& e_in,
+                             std::vector<double>& evals) {
+  const int n = (int)d_in.size();
+  std::vector<double> d = d_in, e(n, 0.0);
+  for (int i = 0; i + 1 < n; ++i) e[i] = e_in[i];
+  ql_implicit(n, d, e, nullptr);
+  std::sort(d.begin(), d.end());
+  evals = d;
+}
+
+// Eigenvector of the same tridiagonal matrix for the eigenvalue lam by inverse iteration:
+// three solves of (T - (lam + delta) I) x = x_prev by Gaussian elimination with partial
+// pivoting (the band grows to two super-diagonals), delta a relative 1e-12 offset that keeps
+// the shifted matrix nonsingular. x is normalised.
+void tridiagonal_eigenvector(const std::vector<double>& d, const std::vector<double>& e,
+                             double lam, std::vector<double>& x) {
+  const int n = (int)d.size();
+  const double scale = std::max(1.0, std::fabs(lam));
+  const double mu = lam + 1e-12 * scale;
+  x.assign(n, 1.0 / std::sqrt((double)n));
+  for (int it = 0; it < 3; ++it) {
+    // rows i: a[i] (sub), b[i] (diag), c[i] (super), f[i] (second super after pivoting)
+    std::vector<double> a(n, 0.0), b(n), c(n, 0.0), f(n, 0.0), r = x;
+    for (int i = 0; i < n; ++i) {
+      b[i] = d[i] - mu;
+      if (i > 0) a[i] = e[i - 1];
+      if (i + 1 < n) c[i] = e[i];
+    }
+    for (int i = 0; i + 1 < n; ++i) {
+      // eliminate a[i+1] using row i or the swapped row i+1
+      if (std::fabs(a[i + 1]) > std::fabs(b[i])) {
+        std::swap(b[i], a[i + 1]);
+        std::swap(c[i], b[i + 1]);
+        std::swap(f[i], c[i + 1]);
+        std::swap(r[i], r[i + 1]);
+      }
+      const double piv = b[i] != 0.0 ? b[i] : 1e-300;
+      const double mlt = a[i + 1] / piv;
+      b[i + 1] -= mlt * c[i];
+      c[i + 1] -= mlt * f[i];
+      r[i + 1] -= mlt * r[i];
+      a[i + 1] = 0.0;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double v = r[i];
+      if (i + 1 < n) v -= c[i] * x[i + 1];
+      if (i + 2 < n) v -= f[i] * x[i + 2];
+      x[i] = v / (b[i] != 0.0 ? b[i] : 1e-300);
+    }
+    double nrm = 0;
+    for (double v : x) nrm += v * v;
+    nrm = std::sqrt(nrm);
+    for (double& v : x) v /= nrm;
+  }
 }
 
 }  // namespace mw3

@@ -32,6 +32,13 @@ void product_point(const double masses[3], int arrangement, double Rp, double rp
 // Wigner d^J_(m'm)(beta).
 double wigner_small_d(int J, int mp, int m, double beta);
 
+// Symmetric tridiagonal matrix (diagonal d, off-diagonal e, e[i] coupling i and i+1):
+// ascending eigenvalues by implicit QL, and one normalised eigenvector by inverse iteration.
+void tridiagonal_eigenvalues(const std::vector<double>& d, const std::vector<double>& e,
+                             std::vector<double>& evals);
+void tridiagonal_eigenvector(const std::vector<double>& d, const std::vector<double>& e,
+                             double lam, std::vector<double>& x);
+
 // Bessel functions of the first kind J_0(x) .. J_(n-1)(x) for x >= 0 (Miller's backward
 // recurrence normalised by J_0 + 2 sum_m J_2m = 1).
 void bessel_j_sequence(double x, int n, std::vector<double>& J);

@@ -124,6 +124,15 @@ cudaError_t launch_time_accum(const real* q, long n, long npts, const DevBlock* 
                               const double* f, int nJ, int nt, long K, const long* d_iter,
                               int slot, double* acc, cudaStream_t st);
 
+// Lanczos helpers on J segments: y += s c[iJ] x; y /= sqrt(c2[iJ]); b = sqrt(b2)
+template <typename real>
+cudaError_t launch_axpy_seg(real* y, const real* x, const double* c, double s, long n, long npts,
+                            const DevBlock* blocks, cudaStream_t st);
+template <typename real>
+cudaError_t launch_rscale_seg(real* y, const double* c2, long n, long npts, const DevBlock* blocks,
+                              cudaStream_t st);
+cudaError_t launch_sqrt(const double* b2, double* b, int n, cudaStream_t st);
+
 // out[iJ] = sum over J's element range of a * b, in FP64 (partial: [nJ][nchunk])
 template <typename real>
 cudaError_t launch_dots(const real* a, const real* b, const long* J_begin, int nJ,

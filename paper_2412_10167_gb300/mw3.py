@@ -99,6 +99,13 @@ _SIGS = {
     "mw3_norm_trace": (C.c_long, [C.c_void_p, C.POINTER(C.c_double), C.c_long]),
     "mw3_enable_autocorrelation": (C.c_int, [C.c_void_p]),
     "mw3_incoming_amplitude": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mw3_lanczos": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int,
+                              C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mw3_bound_states": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double,
+                                   C.c_double, C.c_int, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int)]),
+    "mw3_bound_state_vector": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_int,
+                                         C.c_double, C.POINTER(C.c_double)]),
     "mw3_enable_time_packets": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "mw3_time_packets": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_long)]),
     "mw3_autocorrelation": (C.c_long, [C.c_void_p, C.POINTER(C.c_double), C.c_long]),
@@ -392,6 +399,31 @@ class Propagator:
         out = np.zeros((max(n, 0), nJ))
         cnt = lib.mw3_norm_trace(self.ctx, _dp(out), n)
         return out[:cnt]
+
+    def lanczos(self, v0, m):
+        """(alpha[m, nJ], beta[m, nJ]) of m non-orthogonal Lanczos steps from grid values v0."""
+        v0 = np.ascontiguousarray(np.asarray(v0, dtype=np.float64).reshape(self.shape))
+        nJ = len(self.cfg["J"])
+        a, b = np.zeros((m, nJ)), np.zeros((m, nJ))
+        _check(self.ctx, lib.mw3_lanczos(self.ctx, _dp(v0), m, _dp(a), _dp(b)))
+        return a, b
+
+    def bound_states(self, v0, m, emin=-1e300, emax=1e300, maxev=4096):
+        """Accepted Lanczos eigenvalues (hartree) per J inside [emin, emax]: list of arrays."""
+        v0 = np.ascontiguousarray(np.asarray(v0, dtype=np.float64).reshape(self.shape))
+        nJ = len(self.cfg["J"])
+        E = np.zeros((nJ, maxev))
+        cnt = np.zeros(nJ, dtype=np.int32)
+        _check(self.ctx, lib.mw3_bound_states(self.ctx, _dp(v0), m, emin, emax, maxev, _dp(E),
+                                              cnt.ctypes.data_as(C.POINTER(C.c_int))))
+        return [E[i, :cnt[i]].copy() for i in range(nJ)]
+
+    def bound_state_vector(self, v0, m, E, iJ=0):
+        """Normalised Ritz vector (grid values) of J index iJ for the eigenvalue E."""
+        v0 = np.ascontiguousarray(np.asarray(v0, dtype=np.float64).reshape(self.shape))
+        out = np.zeros(self.shape)
+        _check(self.ctx, lib.mw3_bound_state_vector(self.ctx, _dp(v0), m, iJ, E, _dp(out)))
+        return out
 
     def incoming_amplitude(self):
         """|a(E)|^2 of the packet's incoming part at the analysis energies."""
