@@ -87,7 +87,7 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1};
+  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1, 1};
   int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   int kh = 0;          // parity-split operand size, resident form (0: not applicable)
@@ -1490,6 +1490,7 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
       a.persistent = 1;
     }
     a.nsm = ctx->nsm;
+    a.tma = ctx->tune.tc_tma;
     int tc = 32;
     while (tc < 2 * ctx->nelec * ctx->kp) tc *= 2;
     a.tmem_cols = a.persistent ? 512 : tc;
@@ -2220,6 +2221,9 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
     ctx->tune.kin_warp = (int)v;
   } else if (k == "flush_tc") {
     ctx->tune.flush_tc = v != 0;
+  } else if (k == "tc_tma") {
+    ctx->tune.tc_tma = v != 0;
+    drop_graphs();
   } else if (k == "tc_persist") {
     if (v < 0 || v > 4) return ctx->fail(MW3_ERR_BAD_ARG, "tc_persist must be in 0..4");
     ctx->tune.tc_persist = (int)v;
@@ -2244,6 +2248,7 @@ long mw3_get_tuning(const mw3_ctx* ctx, const char* key) {
   if (k == "use_graph") return ctx->tune.use_graph;
   if (k == "kin_warp") return ctx->tune.kin_warp;
   if (k == "tc_persist") return ctx->tune.tc_persist;
+  if (k == "tc_tma") return ctx->tune.tc_tma;
   if (k == "flush_tc") return ctx->tune.flush_tc;
   if (k == "use_tc") return ctx->stage >= 2 ? ctx->tune.use_tc : (ctx->tc_user != 0);
   return MW3_ERR_BAD_ARG;

@@ -1376,8 +1376,8 @@ constexpr size_t tc5_smem() {
          (size_t)2 * KH * 8 * 4 + 64;
 }
 
-template <int KH>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
+template <int KH, bool TMA>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   constexpr int kh = KH;
   constexpr size_t bb = (size_t)KH * KH * 4;
@@ -1390,6 +1390,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
   double* red = reinterpret_cast<double*>(mbar + 2);
   float* cfs = reinterpret_cast<float*>(red + 16);           // [2 kh][8] coefficients
   float* redf = reinterpret_cast<float*>(red);                // per-warp sums of squares
+  // TMA form: one barrier per tile buffer (0 cs, 1 ts, 2 ps), each completing once per copy
+  uint64_t* tbar = reinterpret_cast<uint64_t*>(cfs + 2 * kh * 8);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q = warp & 3;
@@ -1410,6 +1412,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(mb));
+    if constexpr (TMA) {
+      for (int w = 0; w < 3; ++w)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(tbar + w)));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1426,12 +1432,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
   const long u1 = (long)(blockIdx.x + 1) * total / gridDim.x;
   auto unit_tile = [&](long u) { return (int)(u / ngr); };
   auto unit_block = [&](long u) { return (int)(u - (long)(u / ngr) * ngr); };
-  auto stage = [&](float* dst, const float* src, int nrow, long col0) {
-    const int nch = nrow * (TC_M / 4);
-    for (int e = tid; e < nch; e += TC_THREADS) {
-      const int i = e / (TC_M / 4);
-      const int c4 = (e - i * (TC_M / 4)) * 4;
-      if (col0 + c4 < a.ncol) cp_async16(dst + i * TC_M + c4, src + (long)i * a.ncol + col0 + c4);
+  // tile copies: rows [0, nrow) of block b's plane, columns [col0, col0 + 128). TMA form:
+  // thread 0 issues ceil(nrow / 16) boxes of 16 x 128 into dst and arms the buffer's barrier
+  // with their bytes (columns past the grid arrive as zeros; rows past nrow are not read)
+  bool ok = true;                          // no bounded wait has expired
+  bool tpend[3] = {false, false, false};   // a copy into buffer w is in flight
+  uint32_t tph[3] = {0u, 0u, 0u};
+  auto stage = [&](int which, float* dst, const float* src, int b, int nrow, long col0) {
+    if constexpr (TMA) {
+      const CUtensorMap* map = which == 0 ? &a.tm_ck : (which == 1 ? &a.tm_t : &a.tm_ckm1);
+      const int nbox = (nrow + 15) / 16;
+      if (tid == 0) {
+        const uint32_t bar = smem_u32(tbar + which);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)(nbox * 16 * TC_M * 4))
+                     : "memory");
+        for (int x = 0; x < nbox; ++x) {
+          const int row = b * a.ng + 16 * x;
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst + 16 * x * TC_M)),
+              "l"(reinterpret_cast<uint64_t>(map)), "r"((int)col0), "r"(row), "r"(bar)
+              : "memory");
+        }
+      }
+      tpend[which] = true;
+    } else {
+      (void)which;
+      (void)b;
+      const int nch = nrow * (TC_M / 4);
+      for (int e = tid; e < nch; e += TC_THREADS) {
+        const int i = e / (TC_M / 4);
+        const int c4 = (e - i * (TC_M / 4)) * 4;
+        if (col0 + c4 < a.ncol) cp_async16(dst + i * TC_M + c4, src + (long)i * a.ncol + col0 + c4);
+      }
+    }
+  };
+  // TMA form: a CTA-uniform bounded wait for buffer w's copy (if one is in flight)
+  auto wait_tile = [&](int which) {
+    if constexpr (TMA) {
+      if (tpend[which]) {
+        ok = __syncthreads_and(mbar_wait(smem_u32(tbar + which), tph[which]) ? 1 : 0) != 0;
+        tph[which] ^= 1u;
+        tpend[which] = false;
+      }
     }
   };
   // matrices k0 (buffer 0) and k0 + 1 (buffer 1) of unit u, as one copy group
@@ -1446,14 +1490,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   uint32_t phase = 0;
-  bool ok = true;
   // both parities' MMAs of one GEMM (even: A even x buffer 0, odd: A odd x buffer 1), issued
   // once the copy groups it needs have landed (all, or all but the newest: visible to the tensor
   // core) and the operand stores to tensor memory are complete; the wait comes later, so that
   // CUDA-core work overlaps the MMAs
   auto issue_mma2 = [&](uint32_t de, uint32_t dodd, bool one_pending) {
     tmem_st_wait();
-    if (one_pending) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    // TMA form: the only cp.async group in flight is the half matrices this GEMM needs
+    if (one_pending && !TMA) asm volatile("cp.async.wait_group 1;" ::: "memory");
     else asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1478,13 +1522,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
   // Copy groups, in commit order: [c(u)] during GEMM 1 of unit u-1, [t(u), G1e G1o(u)] after
   // GEMM 2 of unit u-1, [c_(k-1)(u)] after the result of unit u-1 is written, [G2e G2o(u)]
   // after GEMM 1 of unit u; the first unit's three come from here.
+  // (TMA form: the tile copies complete on their own barriers; only the half-matrix groups
+  // remain cp.async groups.)
   const int b00 = u0 < u1 ? unit_block(u0) : 0;
   const long c00 = u0 < u1 ? (long)unit_tile(u0) * TC_M : 0;
-  if (u0 < u1) stage(cs, a.ck + (long)b00 * a.npts, a.blocks[b00].nrow, c00);
+  if (u0 < u1) stage(0, cs, a.ck + (long)b00 * a.npts, b00, a.blocks[b00].nrow, c00);
   asm volatile("cp.async.commit_group;" ::: "memory");
-  if (u0 < u1) stage(ts, a.t + (long)b00 * a.npts, a.blocks[b00].nrow, c00);
+  if (u0 < u1) stage(1, ts, a.t + (long)b00 * a.npts, b00, a.blocks[b00].nrow, c00);
   issue_b2(u0, 0);
-  if (u0 < u1 && a.mode == 0) stage(ps, a.ckm1 + (long)b00 * a.npts, a.blocks[b00].nrow, c00);
+  if (u0 < u1 && a.mode == 0)
+    stage(2, ps, a.ckm1 + (long)b00 * a.npts, b00, a.blocks[b00].nrow, c00);
   asm volatile("cp.async.commit_group;" ::: "memory");
 
   float va[nq], vb[nq];
@@ -1508,8 +1555,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     const bool up_chip = B0.up >= 0 && B0.up == b + 1 && u + 1 < u1 && unit_tile(u + 1) == tile;
 
     __syncthreads();   // previous unit's readers of ts, ps, cs and tensor memory are done
-    asm volatile("cp.async.wait_group 2;" ::: "memory");   // this unit's c tile
-    __syncthreads();
+    if constexpr (TMA) {
+      wait_tile(0);                                         // this unit's c tile
+      if (!ok) break;
+    } else {
+      asm volatile("cp.async.wait_group 2;" ::: "memory");   // this unit's c tile
+      __syncthreads();
+    }
     // ---- GEMM 1 operands (both parities) and the raw c tile, from shared memory
 #pragma unroll
     for (int s0 = 0; s0 < nq; s0 += 4) {
@@ -1540,7 +1592,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     issue_mma2(tE, tO, true);                     // [t G1e G1o](u) landed; [c_(k-1)](u) may not
     if (u + 1 < u1) {
       const int bn = unit_block(u + 1);
-      stage(cs, a.ck + (long)bn * a.npts, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
+      stage(0, cs, a.ck + (long)bn * a.npts, bn, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     if (tid < ng) {   // the block's five coefficient rows, interleaved per row i
@@ -1593,6 +1645,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     //   H_s c = invdE (w + r) - e0s c,  c_(k+1) = D (alpha H_s c - beta D c_(k-1)),
     // so the result is k1 w + r2 with r2 written over c_(k-1) in shared memory.
     issue_mma2(tE, tO, false);                    // c(u+1), c_(k-1)(u), G2e G2o(u) landed
+    if constexpr (TMA) {   // the tiles the remainder reads: t(u), c_(k-1)(u), c(u+1) if on chip
+      wait_tile(1);
+      if (a.mode == 0) wait_tile(2);
+      if (up_chip) wait_tile(0);
+      if (!ok) break;
+    }
     const float invdE = a.dj[B0.iJ].invdE_f, e0s = a.dj[B0.iJ].e0s_f;
     const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
     const float k1 = a.mode == 1 ? invdE : D * a.alpha * invdE;
@@ -1652,7 +1710,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     // t is free: the next unit's t with its G1e G1o, one group
     if (u + 1 < u1) {
       const int bn = unit_block(u + 1);
-      stage(ts, a.t + (long)bn * a.npts, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
+      stage(1, ts, a.t + (long)bn * a.npts, bn, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
     }
     issue_b2(u + 1, 0);
 
@@ -1689,13 +1747,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
     float ws = ssf;
     for (int o = 16; o > 0; o >>= 1) ws += __shfl_down_sync(0xffffffffu, ws, o);
     if (lane == 0) redf[warp] = ws;
+    // the remainder written into ps by these threads precedes the copy engine's next write
+    if constexpr (TMA) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     // c_(k-1) is free: the next unit's
     if (u + 1 < u1 && a.mode == 0) {
       const int bn = unit_block(u + 1);
-      stage(ps, a.ckm1 + (long)bn * a.npts, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
+      stage(2, ps, a.ckm1 + (long)bn * a.npts, bn, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     if (warp == 0) {
@@ -1709,6 +1769,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(TcArgs a) {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (!ok && tid == 0) atomicExch(a.err, 1);
   drain_expired(ok, mb, phase ^ 1u);   // ok is CTA-uniform; the failed wait toggled phase
+  if constexpr (TMA) {   // no tile copy may still be writing shared memory when the CTA ends
+    for (int w = 0; w < 3; ++w)
+      if (tpend[w]) (void)mbar_wait(smem_u32(tbar + w), tph[w]);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) {
@@ -1989,18 +2053,23 @@ static cudaError_t launch_tc4(const TcArgs& a, cudaStream_t st) {
   }
 }
 
-template <int KH>
-static cudaError_t launch_tc5_inst(const TcArgs& args, cudaStream_t st) {
+template <int KH, bool TMA>
+static cudaError_t launch_tc5_tma(const TcArgs& args, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_angular_tc5<KH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_angular_tc5<KH, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          227 * 1024);
     attr = true;
   }
   const long total = (long)args.ngroups * args.ntiles;
   const unsigned grid = (unsigned)std::min<long>(total, args.nsm);
-  k_angular_tc5<KH><<<grid, TC_THREADS, tc5_smem<KH>(), st>>>(args);
+  k_angular_tc5<KH, TMA><<<grid, TC_THREADS, tc5_smem<KH>(), st>>>(args);
   return cudaGetLastError();
+}
+
+template <int KH>
+static cudaError_t launch_tc5_inst(const TcArgs& args, cudaStream_t st) {
+  return args.tma ? launch_tc5_tma<KH, true>(args, st) : launch_tc5_tma<KH, false>(args, st);
 }
 
 static cudaError_t launch_tc5(const TcArgs& a, cudaStream_t st) {
@@ -2043,11 +2112,52 @@ static cudaError_t launch_tc_ne(const TcArgs& a, dim3 grid, cudaStream_t st) {
   }
 }
 
+// cuTensorMapEncodeTiled through the driver's entry point (the library does not link libcuda)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                        &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// A [rows x ncol] FP32 matrix (row stride ncol) as a 2-D tensor map with 128 x 16 boxes,
+// no swizzle (shared-memory layout [16][128], the tile layout of the angular step), zero fill
+// beyond the edges.
+static bool tile_map(CUtensorMap* map, const float* base, long ncol, long rows) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc || !base || (ncol * 4) % 16 != 0) return false;
+  const cuuint64_t dim[2] = {(cuuint64_t)ncol, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)ncol * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_M, 16u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dim, stride, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begin, int nJ,
                               double* norm_out, cudaStream_t st) {
   cudaError_t e;
   if (args.persistent == 4) {
-    e = launch_tc5(args, st);
+    if (args.tma) {   // tile copies by the tensor memory accelerator when the maps encode
+      TcArgs a = args;
+      const long rows = (long)ngroups * args.ng;   // one electronic state: one block per group
+      a.tma = tile_map(&a.tm_ck, a.ck, a.ncol, rows) && tile_map(&a.tm_t, a.t, a.ncol, rows) &&
+              (a.mode != 0 || tile_map(&a.tm_ckm1, a.ckm1, a.ncol, rows));
+      e = launch_tc5(a, st);
+    } else {
+      e = launch_tc5(args, st);
+    }
   } else if (args.persistent == 3) {
     e = launch_tc4(args, st);
   } else if (args.persistent == 2) {

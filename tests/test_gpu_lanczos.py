@@ -27,9 +27,18 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
+def gpu_tiny_cfg():
+    """The oracle pin's tiny grid with an analysis surface inside it (the library sets up
+    the analysis with every context)."""
+    cfg = tiny_cfg()
+    cfg["analysis"] = dict(rstar=3.0, E_lo_eV=0.3, E_hi_eV=1.0, nE=4, Rinf=7.0, vmax=0, jmax=0,
+                           kmin=0)
+    return cfg
+
+
 def test_lanczos_full_spectrum_tiny_grid():
     from paper_2412_10167_gb300 import mw3
-    cfg = tiny_cfg()
+    cfg = gpu_tiny_cfg()
     H = GridHamiltonian(cfg)
     exact = span_spectrum(H)
     distinct = exact[np.concatenate(([True], np.diff(exact) > 1e-9 * H.dE[0]))]
