@@ -87,7 +87,7 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1, 1};
+  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1, 0};
   int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   int kh = 0;          // parity-split operand size, resident form (0: not applicable)

@@ -1433,7 +1433,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
   auto unit_tile = [&](long u) { return (int)(u / ngr); };
   auto unit_block = [&](long u) { return (int)(u - (long)(u / ngr) * ngr); };
   // tile copies: rows [0, nrow) of block b's plane, columns [col0, col0 + 128). TMA form:
-  // thread 0 issues ceil(nrow / 16) boxes of 16 x 128 into dst and arms the buffer's barrier
+  // thread 64 issues ceil(nrow / 8) boxes of 8 x 128 into dst and arms the buffer's barrier
   // with their bytes (columns past the grid arrive as zeros; rows past nrow are not read)
   bool ok = true;                          // no bounded wait has expired
   bool tpend[3] = {false, false, false};   // a copy into buffer w is in flight
@@ -1441,17 +1441,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
   auto stage = [&](int which, float* dst, const float* src, int b, int nrow, long col0) {
     if constexpr (TMA) {
       const CUtensorMap* map = which == 0 ? &a.tm_ck : (which == 1 ? &a.tm_t : &a.tm_ckm1);
-      const int nbox = (nrow + 15) / 16;
-      if (tid == 0) {
+      const int nbox = (nrow + 7) / 8;
+      if (tid == 64) {   // a thread of its own: threads 0 and 32 issue the MMAs
         const uint32_t bar = smem_u32(tbar + which);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"((uint32_t)(nbox * 16 * TC_M * 4))
+                     "r"((uint32_t)(nbox * 8 * TC_M * 4))
                      : "memory");
         for (int x = 0; x < nbox; ++x) {
-          const int row = b * a.ng + 16 * x;
+          const int row = b * a.ng + 8 * x;
           asm volatile(
               "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-              " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst + 16 * x * TC_M)),
+              " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst + 8 * x * TC_M)),
               "l"(reinterpret_cast<uint64_t>(map)), "r"((int)col0), "r"(row), "r"(bar)
               : "memory");
         }
@@ -1468,14 +1468,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
       }
     }
   };
-  // TMA form: a CTA-uniform bounded wait for buffer w's copy (if one is in flight)
-  auto wait_tile = [&](int which) {
+  // TMA form: bounded waits for the copies of the buffers in `mask` that are in flight,
+  // combined into one CTA-wide vote (ok stays CTA-uniform)
+  auto wait_tiles = [&](int mask) {
     if constexpr (TMA) {
-      if (tpend[which]) {
-        ok = __syncthreads_and(mbar_wait(smem_u32(tbar + which), tph[which]) ? 1 : 0) != 0;
-        tph[which] ^= 1u;
-        tpend[which] = false;
-      }
+      int good = 1, any = 0;
+      for (int w = 0; w < 3; ++w)
+        if ((mask >> w & 1) && tpend[w]) {
+          good &= mbar_wait(smem_u32(tbar + w), tph[w]) ? 1 : 0;
+          tph[w] ^= 1u;
+          tpend[w] = false;
+          any = 1;
+        }
+      if (any) ok = __syncthreads_and(good) != 0;
     }
   };
   // matrices k0 (buffer 0) and k0 + 1 (buffer 1) of unit u, as one copy group
@@ -1556,7 +1561,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
 
     __syncthreads();   // previous unit's readers of ts, ps, cs and tensor memory are done
     if constexpr (TMA) {
-      wait_tile(0);                                         // this unit's c tile
+      wait_tiles(1);                                        // this unit's c tile
       if (!ok) break;
     } else {
       asm volatile("cp.async.wait_group 2;" ::: "memory");   // this unit's c tile
@@ -1646,9 +1651,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
     // so the result is k1 w + r2 with r2 written over c_(k-1) in shared memory.
     issue_mma2(tE, tO, false);                    // c(u+1), c_(k-1)(u), G2e G2o(u) landed
     if constexpr (TMA) {   // the tiles the remainder reads: t(u), c_(k-1)(u), c(u+1) if on chip
-      wait_tile(1);
-      if (a.mode == 0) wait_tile(2);
-      if (up_chip) wait_tile(0);
+      wait_tiles(2 | (a.mode == 0 ? 4 : 0) | (up_chip ? 1 : 0));
       if (!ok) break;
     }
     const float invdE = a.dj[B0.iJ].invdE_f, e0s = a.dj[B0.iJ].e0s_f;
@@ -2130,15 +2133,15 @@ static EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// A [rows x ncol] FP32 matrix (row stride ncol) as a 2-D tensor map with 128 x 16 boxes,
-// no swizzle (shared-memory layout [16][128], the tile layout of the angular step), zero fill
+// A [rows x ncol] FP32 matrix (row stride ncol) as a 2-D tensor map with 128 x 8 boxes,
+// no swizzle (shared-memory layout [8][128], the tile layout of the angular step), zero fill
 // beyond the edges.
 static bool tile_map(CUtensorMap* map, const float* base, long ncol, long rows) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc || !base || (ncol * 4) % 16 != 0) return false;
   const cuuint64_t dim[2] = {(cuuint64_t)ncol, (cuuint64_t)rows};
   const cuuint64_t stride[1] = {(cuuint64_t)ncol * 4};
-  const cuuint32_t box[2] = {(cuuint32_t)TC_M, 16u};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_M, 8u};
   const cuuint32_t estr[2] = {1u, 1u};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dim, stride, box,
              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

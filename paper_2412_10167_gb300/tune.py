@@ -11,6 +11,8 @@ library's own per-kernel CUDA-event timers (mw3_kernel_times) over a sweep of
               parity-split (one electronic state), 2 group-major parity-split,
               1 persistent without the split, 0 one tile per CTA (the library falls
               back to the nearest form a shape supports),
+  tc_tma      tile copies of the tile-major angular step by the tensor memory
+              accelerator (1) or cp.async (0),
   flush_tc    energy-sum flush on the tensor cores (1) or the CUDA cores (0),
   kb          iterations per energy-sum flush (ring depth),
 and keeps, for each knob, the value with the lowest time of the kernels it
@@ -29,10 +31,10 @@ DEFAULT_CACHE = os.environ.get("MW3_TUNE_CACHE",
                                os.path.join(os.path.expanduser("~"), ".cache", "mw3_tuning.json"))
 
 SWEEP = dict(kin_warp=[2, 3, 1, 0], rows_pairs=[2, 4, 8, 16], cols_tile=[8, 16, 32, 64],
-             tc_persist=[4, 2, 1, 0], flush_tc=[1, 0], kb=[32, 64, 128])
+             tc_persist=[4, 2, 1, 0], tc_tma=[0, 1], flush_tc=[1, 0], kb=[32, 64, 128])
 CONTROLS = dict(kin_warp=["kinetic_rows", "kinetic_cols"], rows_pairs=["kinetic_rows"],
                 cols_tile=["kinetic_cols"],
-                tc_persist=["angular_tc", "gamma_to_dvr", "gamma_update"],
+                tc_persist=["angular_tc", "gamma_to_dvr", "gamma_update"], tc_tma=["angular_tc"],
                 flush_tc=["sums_flush"], kb=["sums_flush"])
 
 

@@ -81,3 +81,22 @@ def test_mixed_graph_replay_equals_eager_bitwise(name, cfg):
         pr.close()
     for a, b in zip(runs[0], runs[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("name,cfg", [
+    ("ng96", W.shrunk(W.C2, "g96", NR=40, nr=36, ngamma=96, J=[4], omega_max=4, steps=40, nE=16,
+                      kmin=10)),
+    ("c2s", W.C2_SMALL),
+])
+def test_tma_tile_copies_equal_cp_async(name, cfg):
+    """The tile-major angular step with its c, t and c_(k-1) tiles copied by the tensor memory
+    accelerator (2-D tensor maps, ragged last tile filled with zeros) gives the same bits as
+    the cp.async copies: the arithmetic is identical, only the copy engine differs."""
+    runs = []
+    for tma in (1, 0):
+        pr = mw3().Propagator(cfg, precision="mixed", tuning={"tc_tma": tma, "tc_persist": 4})
+        pr.propagate(40)
+        runs.append(pr.state())
+        pr.close()
+    for a, b in zip(runs[0], runs[1]):
+        assert np.array_equal(a, b)
