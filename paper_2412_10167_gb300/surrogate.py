@@ -14,8 +14,11 @@ by it) and are left out of training and scoring. A separate propagation of every
 held-out J measures the errors of the surrogate, the fallback result and the two
 interpolations; it is evaluation, not part of the surrogate path.
 
-State-resolved targets are the reactant-channel (v', j') probabilities the library
-projects at R_inf (summed over Omega), which stand in for product channels.
+State-resolved targets are the product-channel probabilities P_J(E, v', j') (summed over
+Omega') of the initial electronic state when the workload enables product channels, else
+the reactant-channel (v, j) probabilities projected at R_inf. (At high J the reactant
+surface at R_inf = 11.5 bohr is not asymptotic, the centrifugal term there is 0.16 eV at
+J = 46, and its elastic |S|^2 exceeds 1; the product surface has no such channel.)
 """
 from __future__ import annotations
 
@@ -30,20 +33,23 @@ from . import mw3
 def propagate_probabilities(cfg: dict, Js, steps: int, precision: str = "fp64", device: int = 0,
                             with_a2: bool = False):
     """Run one batched propagation over the J list; returns (E, P_total[J,E],
-    P_state[J, v, j, E] for the initial electronic state, seconds[, |a(E)|^2])."""
+    P_state[J, v, j, E] for the initial electronic state (product channels when enabled),
+    seconds[, |a(E)|^2])."""
     c = copy.deepcopy(cfg)
     c["J"] = list(Js)
     t0 = time.perf_counter()
     pr = mw3.Propagator(c, device=device, precision=precision)
     pr.propagate(steps)
-    E, P, Pin = pr.probabilities()
+    E, P, Pst = pr.probabilities()
+    if c["analysis"].get("products"):
+        Pst = pr.product_probabilities()
     secs = time.perf_counter() - t0
     a2 = pr.incoming_amplitude() if with_a2 else None
     pr.close()
     L0 = c["packet"]["elec0"]
     if with_a2:
-        return E, P, Pin[:, L0], secs, a2
-    return E, P, Pin[:, L0], secs
+        return E, P, Pst[:, L0], secs, a2
+    return E, P, Pst[:, L0], secs
 
 
 def features(J, E, v, j, scale):
