@@ -224,6 +224,8 @@ def kernel_roofline(kernel, es, npts, nblk, ng, nelec, nE, kb, ncols):
         return "hbm", 2 * vec                   # read c_k, write t
     if kernel == "kinetic_cols":
         return "hbm", 3 * vec                   # read c_k, read + write t
+    if kernel == "kinetic_radial":
+        return "hbm", 2 * vec                   # read c_k, write t (both radial terms)
     if kernel == "gamma_to_dvr":
         return "alu", 2.0 * ng * ng * (npts // ng) * nblk
     if kernel == "gamma_update":

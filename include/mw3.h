@@ -331,8 +331,18 @@ int mw3_product_probabilities(mw3_ctx* ctx, double* P);
  *                streamed parity split.
  *   "flush_tc"   0/1: energy-sum flush on the tensor cores in MW3_MIXED (split-TF32 within
  *                a flush, FP64 accumulators); default 1
- *   "kin_warp"   0/1: warp-register FFT kinetic kernels for line lengths 32 R
- *                (R = 1, 2, 3, 4, 6, 8, 12, 16; FP64 up to R = 8); default 1
+ *   "kin_warp"   radial kinetic kernels: 2 (default) and 3 the half-warp FFT form in
+ *                MW3_MIXED for line lengths 128, 192, 256 (spectral partners through
+ *                shared memory, or by shuffles), else as 1; 1 warp-register FFT kernels for
+ *                line lengths 32 R (R = 1, 2, 3, 4, 6, 8, 12, 16; FP64 up to R = 8); 0 the
+ *                shared-memory FFT kernels
+ *   "kin_fused"  with kin_warp 2 in MW3_MIXED, both radial kinetic terms, the flux cut and
+ *                the R_inf column in one launch of thread-block clusters, each cluster one
+ *                (block, i) plane (NR and nr in {128, 192, 256}): 1 cluster size chosen by
+ *                the library, 2, 4 or 8 that size, 0 (default) the two separate kernels;
+ *                shapes without a fused form use the separate kernels
+ *   "tc_tma"     0/1: tile copies of the tile-major angular step by the tensor memory
+ *                accelerator (2-D tensor maps) instead of cp.async; default 0
  * Values outside a key's range return MW3_ERR_BAD_ARG. mw3_get_tuning reads a key. */
 int mw3_set_tuning(mw3_ctx* ctx, const char* key, long value);
 long mw3_get_tuning(const mw3_ctx* ctx, const char* key);

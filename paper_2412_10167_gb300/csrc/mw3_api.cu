@@ -41,8 +41,8 @@ namespace {
 
 const char* kKernelNames[] = {"kinetic_rows", "kinetic_cols", "gamma_to_dvr", "gamma_update",
                               "channels",     "norms",        "sums_flush",   "angular_tc",
-                              "products",     "autocorrelation", "time_packets"};
-constexpr int kNumKernels = 11;
+                              "products",     "autocorrelation", "time_packets", "kinetic_radial"};
+constexpr int kNumKernels = 12;
 
 struct DevBuf {
   void* p = nullptr;
@@ -87,7 +87,7 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1, 0};
+  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1, 0, 0};
   int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   int kh = 0;          // parity-split operand size, resident form (0: not applicable)
@@ -1425,21 +1425,46 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
   const bool analysis = (mode == 0) && ctx->stage >= 5;
   real* cut_slot = analysis ? B.cut + (long)slot * ctx->NC : nullptr;
   double* cutc_slot = analysis ? B.cutc + (long)slot * ctx->NCc : nullptr;
-  {
-    Timer tm(ctx, 0, timed);
-    LK(launch_kinetic_rows<real>(qk, B.t, nrows, ctx->planR, B.twR, B.phR, B.lamR,
-                                 ctx->tune.rows_pairs, B.blocks, ctx->ng, ctx->nr,
-                                 ctx->tune.kin_warp, st));
-    tm.stop();
+  // both radial terms in one launch where a fused shape applies (FP32, half-warp form with
+  // the spectral partners through shared memory)
+  bool fused = false;
+  if constexpr (std::is_same<real, float>::value) {
+    if (ctx->tune.kin_warp == 2 && ctx->tune.kin_fused) {
+      const long nplanes = (long)ctx->nblk * ctx->ng;
+      auto radial = [&](const float* qin, cudaError_t* e) {
+        return kinetic_radial_fused(ctx->NR, ctx->nr, ctx->tune.kin_fused, qin, B.t, nplanes,
+                                    B.twR, B.phR, B.lamR, B.twr, B.phr, B.lamr, ctx->ng, B.wpsi,
+                                    B.wdpsi, cut_slot, B.blocks, B.ncut_i,
+                                    analysis ? ctx->m_inf : -1, analysis ? B.qcol : nullptr, st,
+                                    e);
+      };
+      cudaError_t e = cudaSuccess;
+      if (radial(nullptr, &e)) {
+        Timer tm(ctx, 11, timed);
+        radial(qk, &e);
+        LK(e);
+        tm.stop();
+        fused = true;
+      }
+    }
   }
-  {
-    Timer tm(ctx, 1, timed);
-    LK(launch_kinetic_cols<real>(qk, B.t, (long)ctx->nblk * ctx->ng, ctx->nr, ctx->NR, ctx->planr,
-                                 B.twr, B.phr, B.lamr, ctx->tune.cols_tile, ctx->ng, B.wpsi,
-                                 B.wdpsi, cut_slot, B.blocks, B.ncut_i,
-                                 analysis ? ctx->m_inf : -1, analysis ? B.qcol : nullptr,
-                                 ctx->tune.kin_warp, st));
-    tm.stop();
+  if (!fused) {
+    {
+      Timer tm(ctx, 0, timed);
+      LK(launch_kinetic_rows<real>(qk, B.t, nrows, ctx->planR, B.twR, B.phR, B.lamR,
+                                   ctx->tune.rows_pairs, B.blocks, ctx->ng, ctx->nr,
+                                   ctx->tune.kin_warp, st));
+      tm.stop();
+    }
+    {
+      Timer tm(ctx, 1, timed);
+      LK(launch_kinetic_cols<real>(qk, B.t, (long)ctx->nblk * ctx->ng, ctx->nr, ctx->NR,
+                                   ctx->planr, B.twr, B.phr, B.lamr, ctx->tune.cols_tile, ctx->ng,
+                                   B.wpsi, B.wdpsi, cut_slot, B.blocks, B.ncut_i,
+                                   analysis ? ctx->m_inf : -1, analysis ? B.qcol : nullptr,
+                                   ctx->tune.kin_warp, st));
+      tm.stop();
+    }
   }
   const bool tc = std::is_same<real, float>::value && ctx->tc_ok && ctx->tune.use_tc;
   if (tc) {
@@ -2219,6 +2244,10 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
   } else if (k == "kin_warp") {
     if (v < 0 || v > 3) return ctx->fail(MW3_ERR_BAD_ARG, "kin_warp is 0, 1, 2 or 3");
     ctx->tune.kin_warp = (int)v;
+  } else if (k == "kin_fused") {
+    if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8)
+      return ctx->fail(MW3_ERR_BAD_ARG, "kin_fused is 0, 1 (automatic), 2, 4 or 8");
+    ctx->tune.kin_fused = (int)v;
   } else if (k == "flush_tc") {
     ctx->tune.flush_tc = v != 0;
   } else if (k == "tc_tma") {
@@ -2249,6 +2278,7 @@ long mw3_get_tuning(const mw3_ctx* ctx, const char* key) {
   if (k == "kin_warp") return ctx->tune.kin_warp;
   if (k == "tc_persist") return ctx->tune.tc_persist;
   if (k == "tc_tma") return ctx->tune.tc_tma;
+  if (k == "kin_fused") return ctx->tune.kin_fused;
   if (k == "flush_tc") return ctx->tune.flush_tc;
   if (k == "use_tc") return ctx->stage >= 2 ? ctx->tune.use_tc : (ctx->tc_user != 0);
   return MW3_ERR_BAD_ARG;

@@ -70,6 +70,11 @@ struct Tuning {
                     // shared-memory FFT
   int tc_persist;   // persistent tensor-core angular step (operands in tensor memory)
   int flush_tc;     // energy-sum flush on the tensor cores (mixed precision)
+  int kin_fused;    // both radial kinetic terms in one launch (FP32, kin_warp = 2, half-warp
+                    // line lengths in both directions): 0 separate kernels (the default:
+                    // 0.302 against 0.310 ms per step on config 2, where both forms are
+                    // bound by instruction issue), 1 automatic cluster size, 2/4/8 that many
+                    // CTAs per (block, i) plane
   int tc_tma;       // tile-major angular step: tile copies by TMA (1) or cp.async (0, the
                     // default: 0.380 against 0.399 ms per step on config 2)
 };
@@ -91,6 +96,17 @@ cudaError_t launch_kinetic_cols(const real* q, real* t, long nplanes, int nr, in
                                 const DevBlock* blocks, const int* ncut_J,
                                 // column at R_inf for channel projections
                                 int m_inf, real* qcol, int warp_fft, cudaStream_t st);
+
+// t = K_R c + K_r c for every live plane in one launch of CS-CTA clusters, with the flux cut
+// and the R_inf column (mw3_radial.cu). Returns false (nothing enqueued) where no fused
+// shape applies; q == nullptr only asks. cs = 1 picks the cluster size.
+bool kinetic_radial_fused(int NR, int nr, int cs, const float* q, float* t, long nplanes,
+                          const void* twR, const void* phR, const float* lamR, const void* twr,
+                          const void* phr, const float* lamr, int ng, const float* wpsi,
+                          const float* wdpsi, float* cut, const DevBlock* blocks,
+                          const int* ncut_J, int m_inf, float* qcol, cudaStream_t st,
+                          cudaError_t* err);
+int radial_fused_default_cs(int NR, int nr);
 
 // out[b] = Tmat[omega(b)] in[b] (per block [ng x ng] x [ng x ncol]); Tmat is T (DVR ->
 // FBR) or its transpose (FBR -> DVR), zero-padded to ng x ng.

@@ -5,6 +5,8 @@ library's own per-kernel CUDA-event timers (mw3_kernel_times) over a sweep of
   kin_warp    half-warp FFT kinetic kernels (2: spectral partners through shared
               memory, 3: by shuffles), warp-register ones (1) or the shared-memory
               ones (0),
+  kin_fused   both radial terms in one launch of thread-block clusters (1 cluster size
+              chosen by the library, 2/4/8 that size) or the two kernels (0),
   rows_pairs  line pairs per CTA of the R-direction kinetic kernel,
   cols_tile   R columns per CTA of the r-direction kinetic kernel,
   tc_persist  form of the tensor-core angular step (mixed precision): 4 tile-major
@@ -30,9 +32,10 @@ from . import mw3
 DEFAULT_CACHE = os.environ.get("MW3_TUNE_CACHE",
                                os.path.join(os.path.expanduser("~"), ".cache", "mw3_tuning.json"))
 
-SWEEP = dict(kin_warp=[2, 3, 1, 0], rows_pairs=[2, 4, 8, 16], cols_tile=[8, 16, 32, 64],
+SWEEP = dict(kin_warp=[2, 3, 1, 0], kin_fused=[0, 1, 2, 4, 8], rows_pairs=[2, 4, 8, 16], cols_tile=[8, 16, 32, 64],
              tc_persist=[4, 2, 1, 0], tc_tma=[0, 1], flush_tc=[1, 0], kb=[32, 64, 128])
-CONTROLS = dict(kin_warp=["kinetic_rows", "kinetic_cols"], rows_pairs=["kinetic_rows"],
+RADIAL = ["kinetic_rows", "kinetic_cols", "kinetic_radial"]
+CONTROLS = dict(kin_warp=RADIAL, kin_fused=RADIAL, rows_pairs=["kinetic_rows"],
                 cols_tile=["kinetic_cols"],
                 tc_persist=["angular_tc", "gamma_to_dvr", "gamma_update"], tc_tma=["angular_tc"],
                 flush_tc=["sums_flush"], kb=["sums_flush"])

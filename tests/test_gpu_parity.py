@@ -86,7 +86,7 @@ WARP_CASES = {
 @pytest.mark.parametrize("warp", [3, 2, 1, 0])
 def test_warp_fft_kinetic_matches_oracle(name, prec, warp):
     cfg = WARP_CASES[name]
-    pr = mw3().Propagator(cfg, precision=prec, tuning={"kin_warp": warp})
+    pr = mw3().Propagator(cfg, precision=prec, tuning={"kin_warp": warp, "kin_fused": 0})
     H = GridHamiltonian(cfg)
     q = H.project(W.random_state(H.shape, 77))
     ref = H.apply_Hs(q)
