@@ -228,13 +228,20 @@ def propagate(cfg: dict, nsteps=None, H: GridHamiltonian = None, flux_axis="r",
     Returns a Result with q_N, q_(N-1), the raw sums A (psi) and B (dpsi) per
     energy and cut point, the channel sums, the norm trace ||q_k||^2 (k = 0..N),
     and the derived probabilities. ``q0`` replaces the initial packet as the first
-    iterate (the packet still defines a(E) and the energy grid).
+    iterate (the packet still defines a(E) and the energy grid). ``cfg["pcb"]`` (the
+    packet's arrangement and its diatom's sine DVR) starts from the products-coordinate
+    packet of pcb.py instead, with its closed-form a(E).
     """
     if H is None:
         H = GridHamiltonian(cfg)
     N = cfg["steps"] if nsteps is None else int(nsteps)
     an = cfg["analysis"]
-    qp, info = initial_packet(H, cfg["packet"])
+    pcb_src = cfg.get("pcb")
+    if pcb_src:     # products-coordinate-based start (pcb.py): the grid is the product arrangement
+        from . import pcb
+        qp, info = pcb.pcb_packet(H, cfg["packet"], pcb_src)
+    else:
+        qp, info = initial_packet(H, cfg["packet"])
     q0 = qp if q0 is None else np.asarray(q0, dtype=float)
     D = damping_grid(H, cfg["absorber"])[None, None, :, :]
     Ecol, Etot, theta = energy_grid(H, an, info["E_v0j0"])
@@ -280,7 +287,10 @@ def propagate(cfg: dict, nsteps=None, H: GridHamiltonian = None, flux_axis="r",
     q, q_prev = q_next, q
     res = Result(q=q, q_prev=q_prev, A=A, B=B, norms=np.array(norms), Ecol=Ecol, Etot=Etot,
                  theta=theta, info=info, H=H, states=states)
-    a = incoming_amplitude(H, info["g_tilde"], Ecol)
+    if pcb_src:
+        a = pcb.incoming_amplitude(info["packet_function"], Ecol)
+    else:
+        a = incoming_amplitude(H, info["g_tilde"], Ecol)
     res["a"] = a
     res["flux_sum"], res["P_total"] = total_probability(H, A, B, theta, a, flux_axis)
     if channels:
