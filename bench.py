@@ -51,6 +51,8 @@ def parse():
                     help="workload (config 2 is the headline; config 3 and 4 are timed the "
                          "same way, without the CPU baseline unless --cpu-baseline)")
     ap.add_argument("--cpu-baseline", action="store_true")
+    ap.add_argument("--no-pcb", action="store_true",
+                    help="skip the products-coordinate start timing (config 2's product grid)")
     a = ap.parse_args()
     if a.accuracy_steps is None:
         a.accuracy_steps = 1280 if a.config == "c2" else 0
@@ -298,23 +300,33 @@ def run_ours(args, rank, world, local):
 
     # ---- e2e through the public API with host buffers
     q_dev, qp_dev = pr.state()
-    # the step's inputs sit in pinned (page-locked) host memory
-    q_host = torch.empty(q_dev.shape, dtype=torch.float64, pin_memory=True).numpy()
-    qp_host = torch.empty(qp_dev.shape, dtype=torch.float64, pin_memory=True).numpy()
+    # the step's inputs sit in pinned (page-locked) host memory, FP32 like the mixed form's
+    # state (mw3_set_state_f32)
+    q_host = torch.empty(q_dev.shape, dtype=torch.float32, pin_memory=True).numpy()
+    qp_host = torch.empty(qp_dev.shape, dtype=torch.float32, pin_memory=True).numpy()
     q_host[...] = q_dev
     qp_host[...] = qp_dev
-    e2e_steps = max(4, min(16, args.steps // 8))
+    # two whole cycles of pending energy-ring reads (eight read on the fly, the ninth flushed)
+    e2e_steps = max(4, min(18, args.steps // 8))
     # one untimed iteration: upload buffers, the copy stream and the cached packet amplitudes
     # are set up on first use
-    pr.set_state(q_host, qp_host)
+    pr.set_state_f32(q_host, qp_host)
     pr.propagate(1)
     pr.probabilities()
     barrier()
     te0 = time.perf_counter()
+    tparts = [0.0, 0.0, 0.0]   # host wall time of the three calls (each returns synchronised)
     for _ in range(e2e_steps):
-        pr.set_state(q_host, qp_host)
+        t0 = time.perf_counter()
+        pr.set_state_f32(q_host, qp_host)
+        t1 = time.perf_counter()
         pr.propagate(1)
+        t2 = time.perf_counter()
         _, Pe, _ = pr.probabilities()
+        t3 = time.perf_counter()
+        tparts[0] += t1 - t0
+        tparts[1] += t2 - t1
+        tparts[2] += t3 - t2
     barrier()
     te = mdist.max_over_ranks(time.perf_counter() - te0)   # wall clock: host copies included
     pr.close()
@@ -359,6 +371,29 @@ def run_ours(args, rank, world, local):
                            "product_channel_sum_max": float(fp_.sum(axis=(1, 2, 3)).max())},
             "fp64_final_norm": float(fnorm),
         }
+
+    # ---- products-coordinate-based start: the one-off carry of the H + DH packet onto the
+    # product-arrangement grid of the same size class (256 x 256 x 96, J = 10, 11 blocks)
+    pcb_start = None
+    if rank == 0 and not args.no_pcb and args.config == "c2":
+        pcfg = W.PCB["c2pcb"]
+        pp = mw3.Propagator(pcfg, device=local, precision="mixed", analysis=False)
+        pp.kernel_times(enable=True)
+        t0 = time.perf_counter()
+        pp.init_packet()
+        t_call = time.perf_counter() - t0
+        kms, kn = pp.kernel_times()["pcb_packet"]
+        pp.kernel_times(enable=False)
+        q_p, _ = pp.state()
+        pg = pcfg["grid"]
+        pnodes = pg["NR"] * pg["nr"] * pg["ngamma"]
+        pblk = sum(min(J, pcfg["omega_max"]) + 1 for J in pcfg["J"]) * pcfg["nelec"]
+        pcb_start = {"workload": pcfg["name"], "kernel_ms": kms / max(kn, 1),
+                     "call_ms": 1e3 * t_call, "nodes": pnodes, "blocks": pblk,
+                     "node_blocks_per_s": pnodes * pblk / (1e-3 * kms / max(kn, 1)),
+                     "carried_norm": float(np.sum(q_p.astype(np.float64) ** 2))}
+        pp.close()
+        del pp
 
     if rank != 0:
         if dist is not None:
@@ -411,7 +446,7 @@ def run_ours(args, rank, world, local):
             cpu = {"value": None, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {str(e)[:200]}"}
 
-    vec_bytes = nblk * npts * 8
+    vec_bytes = nblk * npts * 4   # FP32 host state of the e2e arm
     line = {
         "metric": "Chebyshev steps/s", "value": value, "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
@@ -432,11 +467,16 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": world * e2e_steps / te, "unit": "steps/s", "h2d_bytes_per_step": 2 * vec_bytes,
-                "d2h_bytes_per_step": nE * 8 * 2 * len(cfg["J"])},
+                "d2h_bytes_per_step": nE * 8 * 2 * len(cfg["J"]), "host_state": "f32 pinned",
+                "steps": e2e_steps,
+                "ms_per_call": {"set_state_f32": 1e3 * tparts[0] / e2e_steps,
+                                "propagate_1": 1e3 * tparts[1] / e2e_steps,
+                                "probabilities": 1e3 * tparts[2] / e2e_steps}},
         "accuracy": accuracy,
         "cpu_baseline": cpu,
         "fp32_fma_peak_tflops": fp32_peak,
         "fp64_fma_peak_tflops": fp64_peak,
+        "pcb_start": pcb_start,
     }
     print(json.dumps(line))
     if dist is not None:

@@ -82,6 +82,19 @@ typedef struct {
   int v0, j0, omega0, elec0;
 } mw3_packet_desc;
 
+/* Products-coordinate-based (PCB) start (Section 2.4, the first of its two routes to
+ * state-to-state probabilities, iprod = 1): the grid of the context is the PRODUCT
+ * arrangement and the packet of mw3_packet_desc lives in another arrangement, named in the
+ * grid's atom labels (grid: A + BC, r = C - B, R from the BC centre of mass to A):
+ *   arrangement  1: the packet's diatom is A-C (r_s = C - A, R_s from the AC centre of mass
+ *                to B); 2: A-B (r_s = B - A, R_s to C); 0: the grid's own (a test case)
+ *   rmin, rmax, nr  the sine DVR (midpoint nodes) of the packet's diatom, 4 <= nr <= 4096 */
+typedef struct {
+  int arrangement;
+  double rmin, rmax;
+  int nr;
+} mw3_pcb_desc;
+
 /* Energy analysis (Section 2.4 and the inputflux/inputtime namelists):
  * nE collision energies E_i = linspace(E_lo, E_hi, nE) (inclusive), flux through
  * r = rstar (Eq. total-flux), reactant channels (Lambda, v <= vmax, j <= jmax,
@@ -186,6 +199,24 @@ int mw3_pes_leps(double r, double R, double cosg, double* potmat, void* user);
  * counter and every energy sum. */
 int mw3_init_packet(mw3_ctx* ctx, const mw3_packet_desc* desc);
 
+/* PCB start (Section 2.4, iprod = 1; packet of Section 2.3.1): the packet
+ * g(R_s) chi_(v0 j0)(r_s) P-bar_(j0)^(Omega0)(cos gamma_s) of `desc`, in its own arrangement
+ * `src` (mw3_pcb_desc), is evaluated once at every node of the context's grid (the product
+ * arrangement) on the device: the packet's Jacobi coordinates from the grid's, every helicity
+ * Omega = 0..min(J, omega_max) of every J from the rotation between the two body frames
+ * (parity-adapted Wigner d^J; Omega0 must be a block of every J), the Jacobian
+ * r R / (r_s R_s), then the gamma transform to each block's FBR. g is normalised in closed
+ * form (int g^2 dR = 1, k0 = sqrt(2 mu_s Ecol), mu_s the packet's reduced mass of R_s); chi
+ * is the packet diatom's state (departing atom 100 bohr away on its axis; needs a potential
+ * callback) as its sine interpolant. E_(v0 j0) is that diatom's level, so the energy grid of
+ * mw3_set_analysis is E_col + E_(v0 j0), and |a(E)|^2 becomes the closed-form Gaussian
+ * integral with mu_s. The grid's own channel analysis (mw3_set_analysis: vmax, jmax at Rinf)
+ * then gives the state-to-state probabilities of the product arrangement; set kmin = 0.
+ * Resets the iteration counter and every energy sum. Device scratch: two FP64 state-sized
+ * buffers (one in the FP64 form), freed before the return. Synchronous.
+ * MW3_ERR_BAD_ARG for an invalid description, MW3_ERR_STATE before mw3_load_potential. */
+int mw3_init_packet_pcb(mw3_ctx* ctx, const mw3_packet_desc* desc, const mw3_pcb_desc* src);
+
 /* Damping exp(-phi), phi = A_R (R-RI)^nR for R > RI plus A_r (r-rI)^nr for r > rI
  * (Eq. imaginary-potential, inputabsorcion namelist). */
 int mw3_set_absorber(mw3_ctx* ctx, double RI, double AR, int nR, double rI, double Ar, int nr);
@@ -226,10 +257,20 @@ int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel)
 int mw3_get_state(mw3_ctx* ctx, double* q, double* qprev);
 
 /* Overwrite q_k and q_{k-1} (host FP64, same size; qprev == NULL sets q_{k-1} = 0) without
- * touching the sums. Synchronous. The values cross to the device in four block groups on a
- * library-owned copy stream, each group's conversion and DVR -> FBR transform overlapping the
- * next group's copy; page-locked host memory gives the full link bandwidth. */
+ * touching the sums. Synchronous; the caller's arrays are not read after the return. The
+ * values cross to the device in four block groups on a library-owned stream, each group's
+ * DVR -> FBR transform overlapping the next group's transfer. An array that lies wholly
+ * inside one page-locked host allocation mapped into the device's address space
+ * (cudaHostAlloc, cudaHostRegister; 16-byte aligned) is read by a kernel over the host link
+ * and narrowed to the state's precision on the way (tuning key "up_direct"); any other
+ * array is copied by the DMA engines into a staging buffer first. Both give the same bits. */
 int mw3_set_state(mw3_ctx* ctx, const double* q, const double* qprev);
+
+/* mw3_set_state for FP32 host arrays (same sizes and layout): half the bytes over the host
+ * link. In MW3_MIXED the values are the FP32 state itself (the FP64 form of mw3_set_state
+ * rounds to them on the device, so both give the same state for FP32-representable input);
+ * in MW3_FP64 they are widened exactly. Synchronous; always copied by the DMA engines. */
+int mw3_set_state_f32(mw3_ctx* ctx, const float* q, const float* qprev);
 
 /* out[i] = (H_s q)[i] for a host FP64 vector q (one application of the scaled
  * Hamiltonian through the same kernels as a propagation step). */
@@ -341,6 +382,9 @@ int mw3_product_probabilities(mw3_ctx* ctx, double* P);
  *                (block, i) plane (NR and nr in {128, 192, 256}): 1 cluster size chosen by
  *                the library, 2, 4 or 8 that size, 0 (default) the two separate kernels;
  *                shapes without a fused form use the separate kernels
+ *   "up_direct"  0/1: mw3_set_state reads page-locked, mapped host arrays with a kernel
+ *                (default 0: the DMA engines were faster over this host link);
+ *                "up_direct_last" (read only) is 1 when the last upload did
  *   "tc_tma"     0/1: tile copies of the tile-major angular step by the tensor memory
  *                accelerator (2-D tensor maps) instead of cp.async; default 0
  * Values outside a key's range return MW3_ERR_BAD_ARG. mw3_get_tuning reads a key. */
@@ -348,7 +392,8 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long value);
 long mw3_get_tuning(const mw3_ctx* ctx, const char* key);
 
 /* Per-kernel CUDA-event timing of the last mw3_propagate call, summed:
- * names[i] (static strings), ms[i], launches[i] for i < *count (in/out capacity). */
+ * names[i] (static strings), ms[i], launches[i] for i < *count (in/out capacity).
+ * "pcb_packet" times the one-off transform of mw3_init_packet_pcb while the timers are on. */
 int mw3_kernel_times(mw3_ctx* ctx, int enable, const char** names, double* ms, long* launches,
                      int* count);
 

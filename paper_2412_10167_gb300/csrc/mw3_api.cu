@@ -41,8 +41,10 @@ namespace {
 
 const char* kKernelNames[] = {"kinetic_rows", "kinetic_cols", "gamma_to_dvr", "gamma_update",
                               "channels",     "norms",        "sums_flush",   "angular_tc",
-                              "products",     "autocorrelation", "time_packets", "kinetic_radial"};
-constexpr int kNumKernels = 12;
+                              "products",     "autocorrelation", "time_packets", "kinetic_radial",
+                              "pcb_packet"};
+constexpr int kNumKernels = 13;
+constexpr int kPcbKernel = 12;   // the one-off products-coordinate transform (not a step kernel)
 
 struct DevBuf {
   void* p = nullptr;
@@ -80,6 +82,7 @@ struct mw3_ctx {
   // host-to-device state uploads: a copy stream and one event per block group, so that a
   // group's conversion and gamma transform overlap the next group's copy
   cudaStream_t up_stream = nullptr;
+  bool up_direct_last = false;   // the last state upload read mapped host memory directly
   cudaEvent_t up_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool own_stream = false;
   mw3_alloc_fn alloc = nullptr;
@@ -87,7 +90,7 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1, 0, 0};
+  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1, 0, 0, 0};
   int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   int kh = 0;          // parity-split operand size, resident form (0: not applicable)
@@ -126,6 +129,12 @@ struct mw3_ctx {
   double Ev0j0 = 0;
   std::vector<double> q0;
   std::vector<double> g_tilde;
+  // device tables of the channel-probability kernel (built by mw3_set_analysis)
+  ChanTable chan_tab_r{}, chan_tab_p{};
+  // products-coordinate-based start (mw3_init_packet_pcb): a(E) in closed form from the
+  // packet's g(R_s) = N exp(-(R_s - R0)^2 / (2 G^2)) cos(k0 R_s) and reduced mass mu_s
+  bool pcb_on = false;
+  double pcb_mu = 0, pcb_N = 0, pcb_R0 = 0, pcb_G = 0, pcb_k0 = 0;
 
   // absorber
   std::vector<double> DR, Dr;
@@ -166,6 +175,7 @@ struct mw3_ctx {
 
   // propagation state
   long iter = 0;       // k of q_k
+  int ring_n = 0;      // ring slots 0 .. ring_n - 1 hold iterations not yet flushed into the sums
   int cur = 0;         // d_q[cur] holds q_k
   std::vector<double> norm_trace;  // [iter][nJ], ||q_k||^2 for k = 1..iter
   double norm0 = 1.0;
@@ -351,18 +361,66 @@ int diatomic(mw3_ctx* ctx, int j, int lam, int nv, std::vector<double>& E, std::
 
 // Transform `n` host FP64 values between the grid (DVR) and the FBR of every block
 // on the device: to_fbr = 1 computes T^Omega x into dst_name, 0 computes (T^Omega)^T x.
-int transform_upload(mw3_ctx* ctx, const double* src, const char* dst_name, bool to_fbr) {
+// Device address of the `bytes` of caller memory at `p` when the whole range lies inside one
+// page-locked host allocation that is mapped into the device's address space at the same
+// address (cudaHostAlloc, cudaHostRegister); nullptr otherwise (the caller then copies with
+// the DMA engines). The allocation's extent comes from the driver, so a kernel reading the
+// alias never leaves the allocation.
+const double* mapped_host_alias(const double* p, size_t bytes) {
+  if (reinterpret_cast<uintptr_t>(p) % 16) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || at.devicePointer != static_cast<const void*>(p))
+    return nullptr;
+  using AttrFn = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+  static AttrFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<AttrFn>(f);
+  }();
+  if (!fn) return nullptr;
+  CUdeviceptr start = 0;
+  size_t size = 0;
+  const CUdeviceptr a = (CUdeviceptr)reinterpret_cast<uintptr_t>(p);
+  if (fn(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, a) != CUDA_SUCCESS ||
+      fn(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, a) != CUDA_SUCCESS)
+    return nullptr;
+  if (start > a || a + bytes > start + size) return nullptr;
+  return p;
+}
+
+// Host state values (FP64, or FP32 for mw3_set_state_f32) -> the FBR coefficients of
+// buffer `dst_name` in the context's precision. The values cross in four block groups on the
+// copy stream; each group's conversion and gamma transform on the library's stream overlap
+// the next group's transfer.
+template <typename Th>
+int transform_upload(mw3_ctx* ctx, const Th* src, const char* dst_name, bool to_fbr) {
   const size_t n = (size_t)ctx->nblk * ctx->npts;
   int st = dalloc(ctx, "xfer", n * ctx->rs());
   if (st) return st;
   const bool mixed = ctx->precision != MW3_FP64;
-  // FP64 host values land in a device FP64 buffer (narrowed on the device in the mixed form)
-  if (mixed && (st = dalloc(ctx, "xfer64", n * 8))) return st;
-  double* d64 = (double*)dptr(ctx, mixed ? "xfer64" : "xfer");
+  // host values land in a staging buffer of their own type unless it is the state's type
+  const bool same = mixed ? sizeof(Th) == 4 : sizeof(Th) == 8;
+  const char* stage_name = sizeof(Th) == 8 ? "xfer64" : "xfer32";
+  if (!same && (st = dalloc(ctx, stage_name, n * sizeof(Th)))) return st;
+  Th* stg = (Th*)dptr(ctx, same ? "xfer" : stage_name);
   if (!ctx->up_stream) {
     CK(cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking));
     for (auto& e : ctx->up_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
+  // page-locked, mapped FP64 caller memory may be read by a kernel over the host link and
+  // converted on the way (no staging copy); everything else goes through the DMA engines
+  const double* alias = nullptr;
+  if constexpr (sizeof(Th) == 8)
+    alias = ctx->tune.up_direct ? mapped_host_alias(src, n * 8) : nullptr;
+  ctx->up_direct_last = alias != nullptr;
   // the copies start after earlier work on the library's stream (which may still read xfer)
   CK(cudaEventRecord(ctx->up_ev[4], ctx->stream));
   CK(cudaStreamWaitEvent(ctx->up_stream, ctx->up_ev[4], 0));
@@ -380,24 +438,37 @@ int transform_upload(mw3_ctx* ctx, const double* src, const char* dst_name, bool
   for (int g = 0; g < G; ++g) {
     long b0, nb;
     group(g, b0, nb);
-    CK(cudaMemcpyAsync(d64 + b0 * ctx->npts, src + b0 * ctx->npts, (size_t)nb * ctx->npts * 8,
-                       cudaMemcpyHostToDevice, ctx->up_stream));
+    const long off = b0 * ctx->npts, cnt = nb * ctx->npts;
+    if (alias && mixed) {   // narrowed on the way in
+      LK(launch_host_read<float>(alias + off, (float*)dptr(ctx, "xfer") + off, cnt, ctx->up_stream));
+    } else if (alias) {
+      LK(launch_host_read<double>(alias + off, (double*)dptr(ctx, "xfer") + off, cnt,
+                                  ctx->up_stream));
+    } else {
+      CK(cudaMemcpyAsync(stg + off, src + off, (size_t)cnt * sizeof(Th), cudaMemcpyHostToDevice,
+                         ctx->up_stream));
+    }
     CK(cudaEventRecord(ctx->up_ev[g], ctx->up_stream));
   }
   const DevBlock* blk = (const DevBlock*)dptr(ctx, "blocks");
   for (int g = 0; g < G; ++g) {
     long b0, nb;
     group(g, b0, nb);
-    const long off = b0 * ctx->npts;
+    const long off = b0 * ctx->npts, cnt = nb * ctx->npts;
     CK(cudaStreamWaitEvent(ctx->stream, ctx->up_ev[g], 0));
     if (mixed) {
       float* x = (float*)dptr(ctx, "xfer");
-      LK(launch_convert_d2f(d64 + off, x + off, nb * ctx->npts, ctx->stream));
+      if constexpr (sizeof(Th) == 8) {
+        if (!alias) LK(launch_convert_d2f((const double*)stg + off, x + off, cnt, ctx->stream));
+      }
       LK(launch_gamma_forward<float>(x + off, (float*)dptr(ctx, dst_name) + off,
                                      (const float*)dptr(ctx, to_fbr ? "T" : "Tt"), blk + b0,
                                      (int)nb, ctx->ng, ctx->ncol, ctx->stream));
     } else {
-      LK(launch_gamma_forward<double>(d64 + off, (double*)dptr(ctx, dst_name) + off,
+      double* x = (double*)dptr(ctx, "xfer");
+      if constexpr (sizeof(Th) == 4)
+        LK(launch_convert_f2d((const float*)stg + off, x + off, cnt, ctx->stream));
+      LK(launch_gamma_forward<double>(x + off, (double*)dptr(ctx, dst_name) + off,
                                       (const double*)dptr(ctx, to_fbr ? "T" : "Tt"), blk + b0,
                                       (int)nb, ctx->ng, ctx->ncol, ctx->stream));
     }
@@ -448,6 +519,65 @@ int upload_state_fbr(mw3_ctx* ctx, const double* c) {
   }
   CK(cudaMemsetAsync(dptr(ctx, state_name(ctx, false)), 0, n * ctx->rs(), ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return MW3_OK;
+}
+
+// Device table of one channel set for k_channel_probs: keys ((iJ ne + L) nv + v) nj + j, each
+// key's channels in channel order. Buffers are named with `pfx`.
+int build_chan_table(mw3_ctx* ctx, const std::string& pfx, int nv, int nj, double mu,
+                     const std::vector<int>& cJ, const std::vector<int>& cL,
+                     const std::vector<int>& cv, const std::vector<int>& cj,
+                     const std::vector<long>& ccol, const std::vector<double>& ceps,
+                     ChanTable& t) {
+  const int nkeys = ctx->nJ * ctx->nelec * nv * nj;
+  const size_t nc = cJ.size();
+  std::vector<std::vector<int>> per(nkeys);
+  for (size_t c = 0; c < nc; ++c)
+    per[((cJ[c] * ctx->nelec + cL[c]) * nv + cv[c]) * nj + cj[c]].push_back((int)c);
+  std::vector<long> first(nkeys + 1, 0), ld(nc);
+  std::vector<int> chans;
+  for (int k = 0; k < nkeys; ++k) {
+    first[k] = (long)chans.size();
+    chans.insert(chans.end(), per[k].begin(), per[k].end());
+  }
+  first[nkeys] = (long)chans.size();
+  for (size_t c = 0; c < nc; ++c) ld[c] = ctx->ncols_c[cJ[c]];
+  if (chans.empty()) chans.push_back(0);   // keep the buffers non-empty
+  int st;
+  if ((st = upload_raw(ctx, (pfx + "_first").c_str(), first)) ||
+      (st = upload_raw(ctx, (pfx + "_chan").c_str(), chans)) ||
+      (st = upload_raw(ctx, (pfx + "_J").c_str(), nc ? cJ : std::vector<int>{0})) ||
+      (st = upload_raw(ctx, (pfx + "_col").c_str(), nc ? ccol : std::vector<long>{0})) ||
+      (st = upload_raw(ctx, (pfx + "_ld").c_str(), nc ? ld : std::vector<long>{0})) ||
+      (st = upload_raw(ctx, (pfx + "_eps").c_str(), nc ? ceps : std::vector<double>{0.0})))
+    return st;
+  t.key_first = (const long*)dptr(ctx, (pfx + "_first").c_str());
+  t.key_chan = (const int*)dptr(ctx, (pfx + "_chan").c_str());
+  t.chJ = (const int*)dptr(ctx, (pfx + "_J").c_str());
+  t.col = (const long*)dptr(ctx, (pfx + "_col").c_str());
+  t.ld = (const long*)dptr(ctx, (pfx + "_ld").c_str());
+  t.eps = (const double*)dptr(ctx, (pfx + "_eps").c_str());
+  t.mu = mu;
+  t.nkeys = nkeys;
+  return MW3_OK;
+}
+
+// A new q_0 is in place: the iteration counter, traces and energy sums start over.
+int reset_after_packet(mw3_ctx* ctx) {
+  ctx->iter = 0;
+  ctx->norm_trace.clear();
+  ctx->ac_on = false;
+  ctx->ac_trace.clear();
+  ctx->tp_on = false;
+  if (ctx->stage < 3) ctx->stage = 3;
+  if (ctx->stage >= 5) {
+    int st;
+    if ((st = dzero(ctx, "acc")) || (st = dzero(ctx, "cut")) || (st = dzero(ctx, "accc")) ||
+        (st = dzero(ctx, "cutc")) || (st = dzero(ctx, "d_iter")))
+      return st;
+    ctx->ring_n = 0;
+    if (!ctx->host_only) CK(cudaStreamSynchronize(ctx->stream));
+  }
   return MW3_OK;
 }
 
@@ -924,20 +1054,186 @@ int mw3_init_packet(mw3_ctx* ctx, const mw3_packet_desc* d) {
             chi[(size_t)d->v0 * ctx->nr + kr] * g[mm];
   }
   ctx->norm0 = 1.0;
+  ctx->pcb_on = false;
   if ((st = upload_state_fbr(ctx, ctx->q0.data()))) return st;
-  ctx->iter = 0;
-  ctx->norm_trace.clear();
-  ctx->ac_on = false;
-  ctx->ac_trace.clear();
-  ctx->tp_on = false;
-  if (ctx->stage < 3) ctx->stage = 3;
-  if (ctx->stage >= 5) {
-    if ((st = dzero(ctx, "acc")) || (st = dzero(ctx, "cut")) || (st = dzero(ctx, "accc")) ||
-        (st = dzero(ctx, "cutc")) || (st = dzero(ctx, "d_iter")))
-      return st;
-    if (!ctx->host_only) CK(cudaStreamSynchronize(ctx->stream));
+  return reset_after_packet(ctx);
+}
+
+int mw3_init_packet_pcb(mw3_ctx* ctx, const mw3_packet_desc* d, const mw3_pcb_desc* s) {
+  if (ctx) ctx->a2_cache.clear();
+  if (!ctx || !d || !s) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
+  if (s->arrangement < 0 || s->arrangement > 2 || s->nr < 4 || s->nr > 4096 || !(s->rmin > 0) ||
+      !(s->rmax > s->rmin))
+    return ctx->fail(MW3_ERR_BAD_ARG, "invalid PCB description");
+  if (d->v0 < 0 || d->j0 < d->omega0 || d->omega0 < 0 || d->elec0 < 0 || d->elec0 >= ctx->nelec ||
+      !(d->Gamma > 0) || !(d->Ecol > 0) || d->v0 >= s->nr)
+    return ctx->fail(MW3_ERR_BAD_ARG, "invalid packet description");
+  for (int iJ = 0; iJ < ctx->nJ; ++iJ)
+    if (d->omega0 > ctx->omtop[iJ])
+      return ctx->fail(MW3_ERR_BAD_ARG, "Omega0 must be a helicity block of every J");
+  if (!ctx->pot_fn) return ctx->fail(MW3_ERR_BAD_ARG, "the packet diatom needs a potential callback");
+  const double masses[3] = {ctx->mA, ctx->mB, ctx->mC};
+  double M[2][2] = {{1.0, 0.0}, {0.0, 1.0}};
+  double mu_s = ctx->mu, m_s = ctx->m;
+  if (s->arrangement > 0) {
+    product_jacobi_matrix(masses, s->arrangement, M);
+    product_masses(masses, s->arrangement, &mu_s, &m_s);
   }
-  return MW3_OK;
+  const double det = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+  const double Mi[2][2] = {{M[1][1] / det, -M[0][1] / det}, {-M[1][0] / det, M[0][0] / det}};
+  // the packet diatom on its sine DVR, the third atom 100 bohr away on its axis
+  const int ns = s->nr;
+  const double Ls = s->rmax - s->rmin, drs = Ls / ns;
+  std::vector<double> Hd((size_t)ns * ns, 0.0), lam(ns + 1, 0.0), pm((size_t)ctx->nelec * ctx->nelec);
+  for (int j = 1; j <= ns; ++j) {
+    const double k = j * M_PI / Ls;
+    lam[j] = std::min(k * k / (2.0 * m_s), ctx->tcut);
+  }
+  for (int a = 0; a < ns; ++a)
+    for (int b = 0; b < ns; ++b) {
+      double t = 0;
+      for (int j = 1; j <= ns; ++j) t += dst2(ns, j, a + 1) * lam[j] * dst2(ns, j, b + 1);
+      Hd[(size_t)a * ns + b] = t;
+    }
+  const int L0 = d->elec0, j0 = d->j0;
+  for (int a = 0; a < ns; ++a) {
+    const double x = s->rmin + (a + 0.5) * drs;
+    // packet vectors (r_s, R_s) along z -> the grid's (r, R)
+    const double rz = Mi[0][0] * x + Mi[0][1] * 100.0, Rz = Mi[1][0] * x + Mi[1][1] * 100.0;
+    const double r = std::fabs(rz), R = std::fabs(Rz), cg = (rz * Rz) / (r * R);
+    if (ctx->pot_fn(r, R, cg, pm.data(), ctx->pot_user) != 0)
+      return ctx->fail(MW3_ERR_BAD_ARG, "potential callback failed");
+    Hd[(size_t)a * ns + a] += std::min(pm[(size_t)L0 * ctx->nelec + L0], ctx->vcut) +
+                              std::min(j0 * (j0 + 1.0) / (2.0 * m_s * x * x), ctx->erot);
+  }
+  std::vector<double> ev, Z;
+  symmetric_eigen(ns, Hd, ev, Z);
+  std::vector<double> vec(ns);
+  int imax = 0;
+  for (int a = 0; a < ns; ++a) {
+    vec[a] = Z[(size_t)a * ns + d->v0];
+    if (std::fabs(vec[a]) > std::fabs(vec[imax])) imax = a;
+  }
+  if (vec[imax] < 0)
+    for (double& v : vec) v = -v;
+  // chi(r_s) = sum_j s_j (S vec)_j sqrt(2/L) sin(j pi (r_s - rmin) / L), s_N = 1/sqrt(2)
+  std::vector<double> coef(ns);
+  for (int j = 1; j <= ns; ++j) {
+    double a = 0;
+    for (int i = 1; i <= ns; ++i) a += dst2(ns, j, i) * vec[i - 1];
+    coef[j - 1] = a * (j == ns ? 1.0 / std::sqrt(2.0) : 1.0) * std::sqrt(2.0 / Ls);
+  }
+  ctx->packet = *d;
+  ctx->Ev0j0 = ev[d->v0];
+  const double k0 = std::sqrt(2.0 * mu_s * d->Ecol);
+  const double G = d->Gamma;
+  ctx->pcb_on = true;
+  ctx->pcb_mu = mu_s;
+  ctx->pcb_R0 = d->R0;
+  ctx->pcb_G = G;
+  ctx->pcb_k0 = k0;
+  ctx->pcb_N = 1.0 / std::sqrt(std::sqrt(M_PI) * G / 2.0 *
+                               (1.0 + std::exp(-k0 * k0 * G * G) * std::cos(2.0 * k0 * d->R0)));
+  ctx->q0.clear();
+  ctx->norm0 = 1.0;
+  if (ctx->host_only) return reset_after_packet(ctx);
+  // output blocks (J, Omega, Lambda0) and their helicity-transform terms
+  std::vector<PcbTerm> terms;
+  const int om0 = d->omega0;
+  const double s0 = std::sqrt(2.0);
+  for (int iJ = 0; iJ < ctx->nJ; ++iJ) {
+    const int J = ctx->J[iJ];
+    for (int om = 0; om <= ctx->omtop[iJ]; ++om) {
+      PcbTerm t{};
+      t.blk = (int)(ctx->J_first_block[iJ] + (long)om * ctx->nelec + L0);
+      t.om = om;
+      // T[Omega][Omega0] = [s(Omega0) d(Omega0, Omega) + (Omega0 > 0)(-1)^Omega0 d(-Omega0, Omega)]
+      //                    / s(Omega), s(0) = sqrt(2), s(>0) = 1
+      const double so = om == 0 ? s0 : 1.0;
+      t.w1 = wigner_index(J, om0, om);
+      t.p1 = (om0 == 0 ? s0 : 1.0) / so * wigner_prefactor(J, t.w1);
+      t.w2 = wigner_index(J, -om0, om);
+      t.p2 = om0 > 0 ? ((om0 & 1) ? -1.0 : 1.0) / so * wigner_prefactor(J, t.w2) : 0.0;
+      terms.push_back(t);
+    }
+  }
+  PcbParams p{};
+  p.M00 = M[0][0];
+  p.M01 = M[0][1];
+  p.M10 = M[1][0];
+  p.M11 = M[1][1];
+  p.R0 = d->R0;
+  p.G = G;
+  p.k0 = k0;
+  p.N = ctx->pcb_N;
+  p.rsmin = s->rmin;
+  p.rsmax = s->rmax;
+  p.nrs = ns;
+  p.j0 = j0;
+  p.om0 = om0;
+  p.NR = ctx->NR;
+  p.nr = ctx->nr;
+  p.ng = ctx->ng;
+  p.Rmin = ctx->Rmin;
+  p.dR = ctx->dR;
+  p.rmin = ctx->rmin;
+  p.dr = ctx->dr;
+  p.plc = 1.0 / std::sqrt(2.0);
+  for (int mm = 1; mm <= om0; ++mm) p.plc *= -std::sqrt((2.0 * mm + 1.0) / (2.0 * mm));
+  std::vector<double> xw(ctx->x);
+  xw.insert(xw.end(), ctx->w.begin(), ctx->w.end());
+  const size_t n = (size_t)ctx->nblk * ctx->npts;
+  const bool mixed = ctx->precision != MW3_FP64;
+  int st;
+  if ((st = upload_raw(ctx, "pcb_xw", xw)) || (st = upload_raw(ctx, "pcb_coef", coef)) ||
+      (st = upload_raw(ctx, "pcb_terms", terms)) || (st = dalloc(ctx, "pcb_dvr", n * 8)) ||
+      (st = dzero(ctx, "pcb_dvr")))
+    return st;
+  // with the kernel timers on, CUDA events on the library's stream bracket the launch
+  cudaEvent_t te[2] = {nullptr, nullptr};
+  if (ctx->timing) {
+    CK(cudaEventCreate(&te[0]));
+    CK(cudaEventCreate(&te[1]));
+    CK(cudaEventRecord(te[0], ctx->stream));
+  }
+  LK(launch_pcb_packet(p, (const double*)dptr(ctx, "pcb_xw"), (const double*)dptr(ctx, "pcb_coef"),
+                       (const PcbTerm*)dptr(ctx, "pcb_terms"), (int)terms.size(),
+                       (double*)dptr(ctx, "pcb_dvr"), ctx->nsm, ctx->stream));
+  if (ctx->timing) {
+    CK(cudaEventRecord(te[1], ctx->stream));
+    CK(cudaEventSynchronize(te[1]));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, te[0], te[1]));
+    ctx->kms[kPcbKernel] += ms;
+    ctx->klaunch[kPcbKernel] += 1;
+    cudaEventDestroy(te[0]);
+    cudaEventDestroy(te[1]);
+  }
+  const DevBlock* blk = (const DevBlock*)dptr(ctx, "blocks");
+  if (!mixed) {
+    LK(launch_gamma_forward<double>((const double*)dptr(ctx, "pcb_dvr"),
+                                    (double*)dptr(ctx, state_name(ctx, true)),
+                                    (const double*)dptr(ctx, "T"), blk, ctx->nblk, ctx->ng,
+                                    ctx->ncol, ctx->stream));
+  } else {
+    // the FP64 FBR coefficients, rounded once to the FP32 state
+    std::vector<double> Tall;
+    for (auto& Tm : ctx->T) Tall.insert(Tall.end(), Tm.begin(), Tm.end());
+    if ((st = upload_real(ctx, "pcb_T64", Tall, true)) || (st = dalloc(ctx, "pcb_fbr", n * 8)))
+      return st;
+    LK(launch_gamma_forward<double>((const double*)dptr(ctx, "pcb_dvr"),
+                                    (double*)dptr(ctx, "pcb_fbr"),
+                                    (const double*)dptr(ctx, "pcb_T64"), blk, ctx->nblk, ctx->ng,
+                                    ctx->ncol, ctx->stream));
+    LK(launch_convert_d2f((const double*)dptr(ctx, "pcb_fbr"),
+                          (float*)dptr(ctx, state_name(ctx, true)), (long)n, ctx->stream));
+  }
+  CK(cudaMemsetAsync(dptr(ctx, state_name(ctx, false)), 0, n * ctx->rs(), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (const char* b : {"pcb_dvr", "pcb_fbr", "pcb_T64", "pcb_xw", "pcb_coef", "pcb_terms"})
+    dfree(ctx, b);
+  return reset_after_packet(ctx);
 }
 
 int mw3_set_absorber(mw3_ctx* ctx, double RI, double AR, int nR, double rI, double Ar, int nrx) {
@@ -1239,6 +1535,7 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
   if ((st = upload_raw(ctx, "blocks", ctx->blocks))) return st;
   if ((st = dalloc(ctx, "cut", (size_t)kb * ctx->NC * ctx->rs())) || (st = dzero(ctx, "cut"))) return st;
   if ((st = dalloc(ctx, "acc", (size_t)acc * 8)) || (st = dzero(ctx, "acc"))) return st;
+  ctx->ring_n = 0;
   if ((st = dalloc(ctx, "ph", (size_t)ctx->nJ * 2 * nE * kb * ctx->rs()))) return st;
   // channel ring, its FP64 accumulators and (mixed form) its FP64 phase matrix
   if ((st = dalloc(ctx, "cutc", (size_t)kb * std::max(ctx->NCc, 4L) * 8)) || (st = dzero(ctx, "cutc")))
@@ -1296,6 +1593,40 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
   }
   if ((st = dalloc(ctx, "normbuf", (size_t)kb * ctx->nJ * 8))) return st;
   if ((st = dalloc(ctx, "npartial", (size_t)ctx->nJ * 256 * 8))) return st;
+  // channel-probability tables, the energy grid and dE for the device assembly
+  if ((st = upload_raw(ctx, "Ecol", ctx->Ecol)) || (st = upload_raw(ctx, "dE", ctx->dE)) ||
+      (st = dalloc(ctx, "a2", (size_t)nE * 8)) || (st = dalloc(ctx, "pout", 8)))
+    return st;
+  ctx->chan_tab_r = ChanTable{};
+  ctx->chan_tab_p = ChanTable{};
+  if (d->vmax >= 0) {
+    std::vector<long> ccol(ctx->nchan);
+    for (int c = 0; c < ctx->nchan; ++c) {
+      const int iJ = ctx->chan_iJ[c];
+      ccol[c] = ctx->accoff_c[iJ] + (ctx->chan_col[c] - ctx->colbase_c[iJ]);
+    }
+    if ((st = build_chan_table(ctx, "cr", d->vmax + 1, d->jmax + 1, ctx->mu, ctx->chan_iJ,
+                               ctx->chan_lam, ctx->chan_v, ctx->chan_j, ccol, ctx->chan_eps,
+                               ctx->chan_tab_r)))
+      return st;
+  }
+  if (ctx->prod_on) {
+    const long nchp = ctx->prod_first[ctx->nJ];
+    std::vector<int> cJ(nchp);
+    std::vector<long> ccol(nchp);
+    for (int iJ = 0; iJ < ctx->nJ; ++iJ) {
+      const long p0 = ctx->prod_first[iJ], np = ctx->prod_first[iJ + 1] - p0;
+      const long first = ctx->ncols_c[iJ] - np;   // local column of the J's first product channel
+      for (long c = 0; c < np; ++c) {
+        cJ[p0 + c] = iJ;
+        ccol[p0 + c] = ctx->accoff_c[iJ] + first + c;
+      }
+    }
+    if ((st = build_chan_table(ctx, "cp", ctx->prod.vmax + 1, ctx->prod.jmax + 1, ctx->mu_p, cJ,
+                               ctx->pch_L, ctx->pch_v, ctx->pch_j, ccol, ctx->pch_eps,
+                               ctx->chan_tab_p)))
+      return st;
+  }
   for (auto& g : ctx->graph)
     if (g) {
       cudaGraphExecDestroy(g);
@@ -1616,13 +1947,15 @@ int chunk(mw3_ctx* ctx, int n, bool timed) {
   return flush<real>(ctx, n, timed);
 }
 
-int check_norms(mw3_ctx* ctx, int n) {
+// Norms (and autocorrelations) of the n iterations just run, ring slots slot0 .. slot0 + n - 1.
+int check_norms(mw3_ctx* ctx, int slot0, int n) {
   std::vector<double> h((size_t)n * ctx->nJ), ac;
-  CK(cudaMemcpyAsync(h.data(), dptr(ctx, "normbuf"), h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(h.data(), (const double*)dptr(ctx, "normbuf") + (size_t)slot0 * ctx->nJ,
+                     h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
   if (ctx->ac_on) {
     ac.resize((size_t)n * ctx->nJ);
-    CK(cudaMemcpyAsync(ac.data(), dptr(ctx, "acbuf"), ac.size() * 8, cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    CK(cudaMemcpyAsync(ac.data(), (const double*)dptr(ctx, "acbuf") + (size_t)slot0 * ctx->nJ,
+                       ac.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
   }
   int tc_err = 0;
   if (dptr(ctx, "tc_err"))
@@ -1642,8 +1975,12 @@ int propagate_impl(mw3_ctx* ctx, long nsteps) {
   const int kb = ctx->tune.kb;
   long done = 0;
   while (done < nsteps) {
-    const int n = (int)std::min<long>(kb, nsteps - done);
-    const bool can_graph = ctx->tune.use_graph && !ctx->timing && n == kb && ctx->iter > 0;
+    // fill the ring from its first free slot; a full ring is flushed into the sums, a partly
+    // filled one stays pending (a probability read adds it on the fly or flushes it)
+    const int slot0 = ctx->ring_n;
+    const int n = (int)std::min<long>(kb - slot0, nsteps - done);
+    const bool can_graph =
+        ctx->tune.use_graph && !ctx->timing && slot0 == 0 && n == kb && ctx->iter > 0;
     int st;
     if (can_graph) {
       cudaGraphExec_t& ge = ctx->graph[ctx->cur];
@@ -1664,14 +2001,91 @@ int propagate_impl(mw3_ctx* ctx, long nsteps) {
       CK(cudaGraphLaunch(ge, ctx->stream));
       ctx->cur = (kb % 2) ? 1 - ctx->cur : ctx->cur;
     } else {
-      st = chunk<real>(ctx, n, true);
-      if (st) return st;
+      for (int s = 0; s < n; ++s) {
+        const bool first = (ctx->iter + s == 0);
+        if ((st = step<real>(ctx, slot0 + s, first, true))) return st;
+      }
+      ctx->ring_n = slot0 + n;
+      if (ctx->ring_n == kb) {
+        if ((st = flush<real>(ctx, kb, true))) return st;
+        ctx->ring_n = 0;
+      }
     }
     ctx->iter += n;
     done += n;
-    if ((st = check_norms(ctx, n))) return st;
+    if ((st = check_norms(ctx, slot0, n))) return st;
   }
   CK(cudaStreamSynchronize(ctx->stream));
+  return MW3_OK;
+}
+
+// Flush the pending ring slots into the sums (readers that need the accumulators themselves).
+int flush_pending(mw3_ctx* ctx) {
+  if (ctx->ring_n == 0 || ctx->host_only) return MW3_OK;
+  const int n = ctx->ring_n;
+  const int st = ctx->precision == MW3_FP64 ? flush<double>(ctx, n, false) : flush<float>(ctx, n, false);
+  if (st) return st;
+  ctx->ring_n = 0;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MW3_OK;
+}
+
+// The channel accumulators as a reader sees them: "accc" itself when no ring slot is pending,
+// else a device copy with the pending slots added by the same FP64 GEMM a flush uses (their
+// FP64 phases first; phases of the slots beyond ring_n are zero). The copy is a few MB.
+int channel_accumulators(mw3_ctx* ctx, const double** out) {
+  *out = (const double*)dptr(ctx, "accc");
+  if (ctx->ring_n == 0 || ctx->max_cols_c <= 0) return MW3_OK;
+  int st;
+  if ((st = dalloc(ctx, "accc_peek", (size_t)ctx->accc_size * 8))) return st;
+  double* pk = (double*)dptr(ctx, "accc_peek");
+  CK(cudaMemcpyAsync(pk, dptr(ctx, "accc"), (size_t)ctx->accc_size * 8, cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  double* ph64 = (double*)dptr(ctx, ctx->precision == MW3_FP64 ? "ph" : "ph64");
+  LK(launch_phases<double>((const double*)dptr(ctx, "theta"), ctx->nJ, ctx->an.nE, ctx->tune.kb,
+                           ctx->ring_n, (const long*)dptr(ctx, "d_iter"), ph64, ctx->stream));
+  LK(launch_sums_flush<double>(ph64, (const double*)dptr(ctx, "cutc"), ctx->NCc, ctx->tune.kb,
+                               ctx->nJ, ctx->an.nE, (const long*)dptr(ctx, "colbase_c"),
+                               (const long*)dptr(ctx, "ncols_c"), (const long*)dptr(ctx, "accoff_c"),
+                               ctx->max_cols_c, pk, ctx->stream));
+  *out = pk;
+  return MW3_OK;
+}
+
+void incoming_a2(mw3_ctx* ctx, std::vector<double>& a2);
+
+// |S|^2 per (J, Lambda, v, j) summed over the helicities, assembled on the device from the
+// channel accumulators `accc` and copied into the caller's array out[nkeys][nE].
+int channel_probabilities(mw3_ctx* ctx, const double* accc, const ChanTable& t, double* out) {
+  const int nE = ctx->an.nE;
+  std::vector<double> a2;
+  incoming_a2(ctx, a2);
+  const size_t n = (size_t)t.nkeys * nE;
+  int st;
+  if ((st = dalloc(ctx, "pout", std::max<size_t>(n, 1) * 8))) return st;
+  CK(cudaMemcpyAsync(dptr(ctx, "a2"), a2.data(), (size_t)nE * 8, cudaMemcpyHostToDevice, ctx->stream));
+  LK(launch_channel_probs(accc, t, (const double*)dptr(ctx, "Ecol"), ctx->Ev0j0,
+                          (const double*)dptr(ctx, "theta"), (const double*)dptr(ctx, "dE"),
+                          (const double*)dptr(ctx, "a2"), nE, (double*)dptr(ctx, "pout"),
+                          ctx->stream));
+  CK(cudaMemcpyAsync(out, dptr(ctx, "pout"), n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MW3_OK;
+}
+
+// Flux sums over A + Ph Cut for the pending ring slots (phases of those slots first).
+template <typename real>
+int flux_peek(mw3_ctx* ctx) {
+  Bufs<real> B = bufs<real>(ctx);
+  const int nJ = ctx->nJ, nE = ctx->an.nE, kb = ctx->tune.kb;
+  LK(launch_phases<real>(B.theta, nJ, nE, kb, ctx->ring_n, B.d_iter, B.ph, ctx->stream));
+  const long max_ncut = *std::max_element(ctx->ncut.begin(), ctx->ncut.end());
+  int st;
+  if ((st = dalloc(ctx, "flux_part", (size_t)flux_partial_size(nJ, nE, max_ncut) * 8))) return st;
+  LK(launch_flux_reduce_peek<real>(B.acc, nJ, nE, B.accoff, B.ncols, B.ncut, max_ncut, B.ph, kb,
+                                   ctx->ring_n, B.cut, ctx->NC, B.colbase,
+                                   (double*)dptr(ctx, "flux_part"), (double*)dptr(ctx, "flux"),
+                                   ctx->stream));
   return MW3_OK;
 }
 
@@ -1786,6 +2200,25 @@ void incoming_a2(mw3_ctx* ctx, std::vector<double>& a2) {
     return;
   }
   a2.assign(nE, 0.0);
+  if (ctx->pcb_on) {
+    // products-coordinate-based start: a(E) = sqrt(mu_s/(2 pi K)) int exp(i K R) g(R) dR
+    // = sqrt(mu_s/(2 pi K)) N sqrt(2 pi) G / 2 sum_(s = +-1) exp(i (K + s k0) R0 - G^2 (K + s k0)^2 / 2)
+    for (int e = 0; e < nE; ++e) {
+      const double K = std::sqrt(2.0 * ctx->pcb_mu * ctx->Ecol[e]);
+      double re = 0, im = 0;
+      for (double sgn : {1.0, -1.0}) {
+        const double q = K + sgn * ctx->pcb_k0;
+        const double mag = std::exp(-ctx->pcb_G * ctx->pcb_G * q * q / 2.0);
+        re += mag * std::cos(q * ctx->pcb_R0);
+        im += mag * std::sin(q * ctx->pcb_R0);
+      }
+      const double sc = std::sqrt(ctx->pcb_mu / (2.0 * M_PI * K)) * ctx->pcb_N *
+                        std::sqrt(2.0 * M_PI) * ctx->pcb_G / 2.0;
+      a2[e] = sc * sc * (re * re + im * im);
+    }
+    ctx->a2_cache = a2;
+    return;
+  }
   for (int e = 0; e < nE; ++e) {
     const double K = std::sqrt(2.0 * ctx->mu * ctx->Ecol[e]);
     double re = 0, im = 0;
@@ -1837,6 +2270,20 @@ int mw3_reference_energy(const mw3_ctx* ctx, double* e) {
 }
 
 int mw3_set_state(mw3_ctx* ctx, const double* q, const double* qprev) {
+  if (!ctx || !q) return MW3_ERR_BAD_ARG;
+  if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
+  if (ctx->host_only) return MW3_OK;
+  cudaSetDevice(ctx->device);
+  int st = transform_upload(ctx, q, state_name(ctx, true), true);
+  if (st) return st;
+  if (qprev) return transform_upload(ctx, qprev, state_name(ctx, false), true);
+  CK(cudaMemsetAsync(dptr(ctx, state_name(ctx, false)), 0,
+                     (size_t)ctx->nblk * ctx->npts * ctx->rs(), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MW3_OK;
+}
+
+int mw3_set_state_f32(mw3_ctx* ctx, const float* q, const float* qprev) {
   if (!ctx || !q) return MW3_ERR_BAD_ARG;
   if (ctx->stage < 2) return ctx->fail(MW3_ERR_STATE, "mw3_load_potential first");
   if (ctx->host_only) return MW3_OK;
@@ -2112,34 +2559,11 @@ int mw3_product_probabilities(mw3_ctx* ctx, double* P) {
   if (ctx->stage < 5) return ctx->fail(MW3_ERR_STATE, "mw3_set_analysis first");
   if (!ctx->prod_on) return ctx->fail(MW3_ERR_STATE, "product channels are not enabled");
   if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
-  const int nE = ctx->an.nE, nJ = ctx->nJ, ne = ctx->nelec;
-  const int nv = ctx->prod.vmax + 1, nj = ctx->prod.jmax + 1;
-  std::vector<double> a2;
-  incoming_a2(ctx, a2);
-  std::fill(P, P + (size_t)nJ * ne * nv * nj * nE, 0.0);
-  for (int iJ = 0; iJ < nJ; ++iJ) {
-    const long p0 = ctx->prod_first[iJ], np = ctx->prod_first[iJ + 1] - p0;
-    if (np <= 0) continue;
-    const long first = ctx->ncols_c[iJ] - np;         // local column of the first product channel
-    std::vector<double> A((size_t)2 * nE * np);
-    const double* src = (const double*)dptr(ctx, "accc") + ctx->accoff_c[iJ] + first;
-    CK(cudaMemcpy2DAsync(A.data(), np * 8, src, ctx->ncols_c[iJ] * 8, np * 8, 2 * nE,
-                         cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    for (long c = 0; c < np; ++c) {
-      const long g = p0 + c;
-      for (int e = 0; e < nE; ++e) {
-        const double K2 = 2.0 * ctx->mu_p * (ctx->Ecol[e] + ctx->Ev0j0 - ctx->pch_eps[g]);
-        if (K2 <= 0) continue;
-        const double th = ctx->theta[(size_t)iJ * nE + e];
-        const double pref = 1.0 / (2.0 * M_PI * ctx->dE[iJ] * std::sin(th));
-        const double re = A[(size_t)e * np + c] * pref, im = A[(size_t)(nE + e) * np + c] * pref;
-        const size_t o = ((((size_t)iJ * ne + ctx->pch_L[g]) * nv + ctx->pch_v[g]) * nj + ctx->pch_j[g]) * nE + e;
-        P[o] += 2.0 * M_PI * std::sqrt(K2) / ctx->mu_p * (re * re + im * im) / a2[e];
-      }
-    }
-  }
-  return MW3_OK;
+  int st;
+  if (ctx->ring_n > kPeekMax && (st = flush_pending(ctx))) return st;
+  const double* accc = nullptr;   // with the pending ring slots added
+  if ((st = channel_accumulators(ctx, &accc))) return st;
+  return channel_probabilities(ctx, accc, ctx->chan_tab_p, P);
 }
 
 int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel) {
@@ -2153,9 +2577,19 @@ int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel)
   incoming_a2(ctx, a2);
   int st;
   if ((st = dalloc(ctx, "flux", (size_t)nJ * nE * 8))) return st;
-  LK(launch_flux_reduce((const double*)dptr(ctx, "acc"), nJ, nE, (const long*)dptr(ctx, "accoff"),
-                        (const long*)dptr(ctx, "ncols"), (const long*)dptr(ctx, "ncut"),
-                        (double*)dptr(ctx, "flux"), ctx->stream));
+  // a few pending ring slots are added on the fly (the accumulators are only read); more are
+  // flushed first
+  if (ctx->ring_n > kPeekMax && (st = flush_pending(ctx))) return st;
+  if (ctx->ring_n > 0) {
+    st = ctx->precision == MW3_FP64 ? flux_peek<double>(ctx) : flux_peek<float>(ctx);
+    if (st) return st;
+  } else {
+    const long max_ncut = *std::max_element(ctx->ncut.begin(), ctx->ncut.end());
+    if ((st = dalloc(ctx, "flux_part", (size_t)flux_partial_size(nJ, nE, max_ncut) * 8))) return st;
+    LK(launch_flux_reduce((const double*)dptr(ctx, "acc"), nJ, nE, (const long*)dptr(ctx, "accoff"),
+                          (const long*)dptr(ctx, "ncols"), (const long*)dptr(ctx, "ncut"), max_ncut,
+                          (double*)dptr(ctx, "flux_part"), (double*)dptr(ctx, "flux"), ctx->stream));
+  }
   std::vector<double> F((size_t)nJ * nE);
   CK(cudaMemcpyAsync(F.data(), dptr(ctx, "flux"), F.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -2168,53 +2602,9 @@ int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel)
       }
   }
   if (Pinel && ctx->an.vmax >= 0) {
-    const int nv = ctx->an.vmax + 1, nj = ctx->an.jmax + 1, ne = ctx->nelec;
-    std::fill(Pinel, Pinel + (size_t)nJ * ne * nv * nj * nE, 0.0);
-    // channel columns only: per J a [2 nE x nchan_J] block of the accumulator
-    std::vector<std::vector<double>> chA(nJ);
-    // reactant channels: the first columns of each J's block of the channel accumulators
-    auto nreact = [&](int iJ) {
-      return ctx->ncols_c[iJ] - (ctx->prod_on ? ctx->prod_first[iJ + 1] - ctx->prod_first[iJ] : 0L);
-    };
-    for (int iJ = 0; iJ < nJ; ++iJ) {
-      const long nch = nreact(iJ);
-      chA[iJ].assign((size_t)2 * nE * std::max(nch, 1L), 0.0);
-      if (nch <= 0) continue;
-      const double* src = (const double*)dptr(ctx, "accc") + ctx->accoff_c[iJ];
-      CK(cudaMemcpy2DAsync(chA[iJ].data(), nch * 8, src, ctx->ncols_c[iJ] * 8, nch * 8, 2 * nE,
-                           cudaMemcpyDeviceToHost, ctx->stream));
-    }
-    CK(cudaStreamSynchronize(ctx->stream));
-    // |S|^2 = 2 pi k_c / mu |pref A_c(E)|^2 / |a(E)|^2 with pref = 1 / (2 pi dE sin theta_E):
-    // energies outer so that a J's channel columns are read contiguously, the factors that
-    // depend on (J, E) only formed once
-    std::vector<double> fJE((size_t)nJ * nE);
-    for (int iJ = 0; iJ < nJ; ++iJ)
-      for (int e = 0; e < nE; ++e) {
-        const double pref = 1.0 / (2.0 * M_PI * ctx->dE[iJ] * std::sin(ctx->theta[(size_t)iJ * nE + e]));
-        fJE[(size_t)iJ * nE + e] = 2.0 * M_PI / ctx->mu * pref * pref / a2[e];
-      }
-    std::vector<long> nchJ(nJ);
-    for (int iJ = 0; iJ < nJ; ++iJ) nchJ[iJ] = nreact(iJ);
-    std::vector<long> lcol(ctx->nchan);
-    std::vector<size_t> obase(ctx->nchan);
-    for (int c = 0; c < ctx->nchan; ++c) {
-      const int iJ = ctx->chan_iJ[c];
-      lcol[c] = ctx->chan_col[c] - ctx->colbase_c[iJ];
-      obase[c] = ((((size_t)iJ * ne + ctx->chan_lam[c]) * nv + ctx->chan_v[c]) * nj + ctx->chan_j[c]) * nE;
-    }
-    for (int e = 0; e < nE; ++e) {
-      const double Etot = ctx->Ecol[e] + ctx->Ev0j0;
-      for (int c = 0; c < ctx->nchan; ++c) {
-        const double K2 = 2.0 * ctx->mu * (Etot - ctx->chan_eps[c]);
-        if (K2 <= 0) continue;
-        const int iJ = ctx->chan_iJ[c];
-        const double* A = chA[iJ].data();
-        const double re = A[(size_t)e * nchJ[iJ] + lcol[c]];
-        const double im = A[(size_t)(nE + e) * nchJ[iJ] + lcol[c]];
-        Pinel[obase[c] + e] += std::sqrt(K2) * fJE[(size_t)iJ * nE + e] * (re * re + im * im);
-      }
-    }
+    const double* accc = nullptr;   // with the pending ring slots added
+    if ((st = channel_accumulators(ctx, &accc))) return st;
+    if ((st = channel_probabilities(ctx, accc, ctx->chan_tab_r, Pinel))) return st;
   }
   return MW3_OK;
 }
@@ -2248,6 +2638,8 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
     if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8)
       return ctx->fail(MW3_ERR_BAD_ARG, "kin_fused is 0, 1 (automatic), 2, 4 or 8");
     ctx->tune.kin_fused = (int)v;
+  } else if (k == "up_direct") {
+    ctx->tune.up_direct = v != 0;
   } else if (k == "flush_tc") {
     ctx->tune.flush_tc = v != 0;
   } else if (k == "tc_tma") {
@@ -2279,6 +2671,8 @@ long mw3_get_tuning(const mw3_ctx* ctx, const char* key) {
   if (k == "tc_persist") return ctx->tune.tc_persist;
   if (k == "tc_tma") return ctx->tune.tc_tma;
   if (k == "kin_fused") return ctx->tune.kin_fused;
+  if (k == "up_direct") return ctx->tune.up_direct;
+  if (k == "up_direct_last") return ctx->up_direct_last ? 1 : 0;
   if (k == "flush_tc") return ctx->tune.flush_tc;
   if (k == "use_tc") return ctx->stage >= 2 ? ctx->tune.use_tc : (ctx->tc_user != 0);
   return MW3_ERR_BAD_ARG;
@@ -2307,6 +2701,9 @@ int mw3_kernel_times(mw3_ctx* ctx, int enable, const char** names, double* ms, l
 int mw3_checkpoint_save(mw3_ctx* ctx, const char* path) {
   if (!ctx || !path) return MW3_ERR_BAD_ARG;
   if (ctx->stage < 5 || ctx->host_only) return ctx->fail(MW3_ERR_STATE, "nothing to save");
+  cudaSetDevice(ctx->device);
+  int fst = flush_pending(ctx);   // the saved sums hold every iteration run so far
+  if (fst) return fst;
   // raw device state (FBR coefficients in the context's precision), no conversion
   const size_t nb = (size_t)ctx->nblk * ctx->npts * ctx->rs();
   std::vector<char> q(nb), qp(nb);
@@ -2346,6 +2743,7 @@ int mw3_checkpoint_load(mw3_ctx* ctx, const char* path) {
       hdr[2] != (uint64_t)ctx->npts || hdr[3] != (uint64_t)ctx->acc_size ||
       hdr[5] != (uint64_t)ctx->precision || hdr[6] != (uint64_t)ctx->accc_size)
     return ctx->fail(MW3_ERR_IO, "checkpoint does not match this configuration");
+  ctx->ring_n = 0;   // the saved sums hold every saved iteration
   const size_t nb = (size_t)ctx->nblk * ctx->npts * ctx->rs();
   std::vector<char> q(nb), qp(nb);
   std::vector<double> acc(ctx->acc_size), accc(ctx->accc_size);

@@ -15,6 +15,8 @@
 //     c_(k+1) = D (alpha H_s c_k - beta D c_(k-1)) written over c_(k-1).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "mw3_internal.h"
 
 namespace mw3 {
@@ -296,6 +298,46 @@ cudaError_t launch_convert_f2d(const float* in, double* out, long n, cudaStream_
   return cudaGetLastError();
 }
 
+// A state vector read straight from page-locked host memory through its device alias: 16-byte
+// loads, four in flight per thread (the host link has a long latency), converted to the
+// state's precision on the way. `in` is 16-byte aligned; an odd last element is read alone.
+template <typename B>
+__global__ void __launch_bounds__(256) k_host_read(const double* __restrict__ in,
+                                                   B* __restrict__ out, long n) {
+  const long n2 = n >> 1;
+  const double2* in2 = reinterpret_cast<const double2*>(in);
+  const long stride = (long)gridDim.x * blockDim.x;
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n2; i += 4 * stride) {
+    double2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = in2[i + u * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      out[2 * (i + u * stride)] = (B)v[u].x;
+      out[2 * (i + u * stride) + 1] = (B)v[u].y;
+    }
+  }
+  for (; i < n2; i += stride) {
+    const double2 v = in2[i];
+    out[2 * i] = (B)v.x;
+    out[2 * i + 1] = (B)v.y;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[n - 1] = (B)in[n - 1];
+}
+
+template <typename B>
+cudaError_t launch_host_read(const double* host_alias, B* out, long n, cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long blocks = std::min<long>((long)std::max(nsm, 1) * 8, (n / 2 + 255) / 256 + 1);
+  k_host_read<B><<<(unsigned)blocks, 256, 0, st>>>(host_alias, out, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_host_read<float>(const double*, float*, long, cudaStream_t);
+template cudaError_t launch_host_read<double>(const double*, double*, long, cudaStream_t);
+
 cudaError_t launch_advance(long* d_iter, long n, cudaStream_t st) {
   k_advance<<<1, 1, 0, st>>>(d_iter, n);
   return cudaGetLastError();
@@ -506,36 +548,174 @@ cudaError_t launch_dots(const real* a, const real* b, const long* J_begin, int n
 // ------------------------------------------------------------- flux reduce
 // out[iJ][e] = sum_p Re A_psi Im A_dpsi - Im A_psi Re A_dpsi over J's cut points,
 // with A rows e (real part) and nE + e (imaginary part).
-__global__ void __launch_bounds__(256) k_flux_reduce(const double* __restrict__ acc, int nE,
-                                                     const long* __restrict__ accoff,
-                                                     const long* __restrict__ ncols,
-                                                     const long* __restrict__ ncut,
-                                                     double* __restrict__ out) {
-  __shared__ double red[256];
-  const int e = blockIdx.x;
+// The flux sum of Eq. total-flux per (J, E): F = sum_p Re A(p) Im B(p) - Im A(p) Re B(p) over
+// the J's cut points p (A the psi columns, B the dpsi columns of the accumulators), split over
+// chunks of kFluxChunk points so that every SM takes part (the accumulators are GBs: the
+// reduction is one read of them), with partial sums per chunk summed in chunk order by
+// k_flux_final. PEEK: the accumulators are A + Ph Cut with the ring slots that have not been
+// flushed yet (npend <= kPeekMax) added on the fly in FP64; A itself is only read, so a
+// probability read between flushes moves the accumulators once instead of three times (read
+// and write of a flush, then the read of the reduction).
+constexpr int kFluxE = 8;          // energies per CTA (the ring values of a point read once)
+constexpr long kFluxChunk = 4096;  // cut points per CTA
+
+template <bool PEEK, typename real>
+__global__ void __launch_bounds__(256) k_flux_partial(
+    const double* __restrict__ acc, int nJ, int nE, const long* __restrict__ accoff,
+    const long* __restrict__ ncols, const long* __restrict__ ncut, const real* __restrict__ ph,
+    int kb, int npend, const real* __restrict__ cut, long ncut_total,
+    const long* __restrict__ colbase, double* __restrict__ part) {
+  __shared__ double sph[kFluxE][2][kPeekMax];   // phase factors (real, imaginary row) per slot
+  __shared__ double red[kFluxE][256];
+  const int e0 = blockIdx.x * kFluxE;
   const int iJ = blockIdx.y;
+  const int ne = min(kFluxE, nE - e0);
   const long nc = ncols[iJ], np = ncut[iJ];
-  const double* re = acc + accoff[iJ] + (long)e * nc;
-  const double* im = acc + accoff[iJ] + (long)(nE + e) * nc;
-  double s = 0;
-  for (long p = threadIdx.x; p < np; p += blockDim.x) s += re[p] * im[np + p] - im[p] * re[np + p];
-  red[threadIdx.x] = s;
+  const long p0 = (long)blockIdx.z * kFluxChunk, p1 = min(np, p0 + kFluxChunk);
+  const double* A = acc + accoff[iJ];
+  if constexpr (PEEK) {
+    for (int x = threadIdx.x; x < kFluxE * 2 * kPeekMax; x += blockDim.x) {
+      const int q = x / (2 * kPeekMax), prt = (x / kPeekMax) & 1, sl = x % kPeekMax;
+      const int row = (prt ? nE : 0) + e0 + q;
+      sph[q][prt][sl] =
+          (q < ne && sl < npend) ? (double)ph[((long)iJ * 2 * nE + row) * kb + sl] : 0.0;
+    }
+  }
+  double acc_q[kFluxE];
+#pragma unroll
+  for (int q = 0; q < kFluxE; ++q) acc_q[q] = 0.0;
+  __syncthreads();
+  for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    real cp[kPeekMax], cq[kPeekMax];
+    if constexpr (PEEK) {
+      const real* cj = cut + colbase[iJ];
+#pragma unroll
+      for (int sl = 0; sl < kPeekMax; ++sl) {
+        cp[sl] = sl < npend ? cj[(long)sl * ncut_total + p] : (real)0;
+        cq[sl] = sl < npend ? cj[(long)sl * ncut_total + np + p] : (real)0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kFluxE; ++q) {
+      if (q < ne) {
+        const double* re = A + (long)(e0 + q) * nc;
+        const double* im = A + (long)(nE + e0 + q) * nc;
+        double rp = re[p], ip = im[p], rq = re[np + p], iq = im[np + p];
+        if constexpr (PEEK) {
+#pragma unroll
+          for (int sl = 0; sl < kPeekMax; ++sl) {
+            rp += sph[q][0][sl] * (double)cp[sl];
+            ip += sph[q][1][sl] * (double)cp[sl];
+            rq += sph[q][0][sl] * (double)cq[sl];
+            iq += sph[q][1][sl] * (double)cq[sl];
+          }
+        }
+        acc_q[q] += rp * iq - ip * rq;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kFluxE; ++q) red[q][threadIdx.x] = acc_q[q];
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < kFluxE; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[(long)iJ * nE + e] = red[0];
+  if (threadIdx.x < ne)
+    part[((long)blockIdx.z * nJ + iJ) * nE + e0 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// out[iJ][e] = sum over the chunks z (in order) of part[z][iJ][e].
+__global__ void k_flux_final(const double* __restrict__ part, int nz, long n,
+                             double* __restrict__ out) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int z = 0; z < nz; ++z) s += part[(long)z * n + i];
+  out[i] = s;
+}
+
+long flux_partial_size(int nJ, int nE, long max_ncut) {
+  return std::max<long>(1, (max_ncut + kFluxChunk - 1) / kFluxChunk) * nJ * nE;
 }
 
 cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* accoff,
-                               const long* ncols, const long* ncut, double* out,
-                               cudaStream_t st) {
-  k_flux_reduce<<<dim3(nE, nJ), 256, 0, st>>>(acc, nE, accoff, ncols, ncut, out);
+                               const long* ncols, const long* ncut, long max_ncut, double* part,
+                               double* out, cudaStream_t st) {
+  const int nz = (int)std::max<long>(1, (max_ncut + kFluxChunk - 1) / kFluxChunk);
+  k_flux_partial<false, double><<<dim3((nE + kFluxE - 1) / kFluxE, nJ, nz), 256, 0, st>>>(
+      acc, nJ, nE, accoff, ncols, ncut, nullptr, 0, 0, nullptr, 0, nullptr, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long n = (long)nJ * nE;
+  k_flux_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, nz, n, out);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_flux_reduce_peek(const double* acc, int nJ, int nE, const long* accoff,
+                                    const long* ncols, const long* ncut, long max_ncut,
+                                    const real* ph, int kb, int npend, const real* cut,
+                                    long ncut_total, const long* colbase, double* part,
+                                    double* out, cudaStream_t st) {
+  if (npend < 0 || npend > kPeekMax) return cudaErrorInvalidValue;
+  const int nz = (int)std::max<long>(1, (max_ncut + kFluxChunk - 1) / kFluxChunk);
+  k_flux_partial<true, real><<<dim3((nE + kFluxE - 1) / kFluxE, nJ, nz), 256, 0, st>>>(
+      acc, nJ, nE, accoff, ncols, ncut, ph, kb, npend, cut, ncut_total, colbase, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long n = (long)nJ * nE;
+  k_flux_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, nz, n, out);
+  return cudaGetLastError();
+}
+
+// State-resolved probabilities from the channel accumulators (Eq. S-matrix-from-chebyshev),
+// one thread per (output key, energy), energies fastest: for the key's channels c (in channel
+// order) with K_c^2 = 2 mu (E_col + E_ref - eps_c) > 0,
+//   P[key][e] += (2 pi K_c / mu) |pref A_c(E)|^2 / |a(E)|^2,  pref = 1 / (2 pi dE_J sin theta_JE),
+// A_c(E) = acc[col_c + e ld_c] + i acc[col_c + (nE + e) ld_c]. Keys without channels get 0.
+__global__ void __launch_bounds__(256) k_channel_probs(const double* __restrict__ acc,
+                                                       ChanTable t, const double* __restrict__ Ecol,
+                                                       double Eref,
+                                                       const double* __restrict__ theta,
+                                                       const double* __restrict__ dE,
+                                                       const double* __restrict__ a2, int nE,
+                                                       double* __restrict__ out) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)t.nkeys * nE) return;
+  const int key = (int)(idx / nE), e = (int)(idx - (long)key * nE);
+  const double Etot = Ecol[e] + Eref;
+  double sum = 0.0;
+  for (long q = t.key_first[key]; q < t.key_first[key + 1]; ++q) {
+    const int c = t.key_chan[q];
+    const double K2 = 2.0 * t.mu * (Etot - t.eps[c]);
+    if (K2 <= 0.0) continue;
+    const int iJ = t.chJ[c];
+    const double pref = 1.0 / (2.0 * M_PI * dE[iJ] * sin(theta[(long)iJ * nE + e]));
+    const double re = acc[t.col[c] + (long)e * t.ld[c]] * pref;
+    const double im = acc[t.col[c] + (long)(nE + e) * t.ld[c]] * pref;
+    sum += 2.0 * M_PI * sqrt(K2) / t.mu * (re * re + im * im) / a2[e];
+  }
+  out[idx] = sum;
+}
+
+cudaError_t launch_channel_probs(const double* acc, const ChanTable& t, const double* Ecol,
+                                 double Eref, const double* theta, const double* dE,
+                                 const double* a2, int nE, double* out, cudaStream_t st) {
+  const long n = (long)t.nkeys * nE;
+  if (n == 0) return cudaSuccess;
+  k_channel_probs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(acc, t, Ecol, Eref, theta, dE, a2,
+                                                               nE, out);
   return cudaGetLastError();
 }
 
 #define MW3_INST(real)                                                                        \
+  template cudaError_t launch_flux_reduce_peek<real>(const double*, int, int, const long*,      \
+                                                     const long*, const long*, long, const real*, \
+                                                     int, int, const real*, long, const long*,   \
+                                                     double*, double*, cudaStream_t);            \
   template cudaError_t launch_gamma_forward<real>(const real*, real*, const real*,            \
                                                   const DevBlock*, int, int, long,            \
                                                   cudaStream_t);                              \

@@ -2,6 +2,7 @@
 // symmetric eigensolver for the diatomic states, and the built-in LEPS surface.
 // These run once per set-up call; the propagation itself runs on the device.
 #include "mw3_host.h"
+#include "mw3_wigner.h"
 
 #include <algorithm>
 #include <cmath>
@@ -305,19 +306,10 @@ void product_point(const double masses[3], int arrangement, double Rp, double rp
   }
 }
 
-// Wigner's explicit sum, factorials through lgamma.
+// Wigner d^J_(m'm)(beta) in its Jacobi-polynomial form (mw3_wigner.h): the explicit
+// alternating sum loses about nine digits at J = 40, this form keeps them.
 double wigner_small_d(int J, int mp, int m, double beta) {
-  const double c = std::cos(0.5 * beta), s = std::sin(0.5 * beta);
-  auto lf = [](int k) { return std::lgamma(k + 1.0); };
-  const double lpre = 0.5 * (lf(J + mp) + lf(J - mp) + lf(J + m) + lf(J - m));
-  double tot = 0.0;
-  for (int k = std::max(0, m - mp); k <= std::min(J + m, J - mp); ++k) {
-    const int pc = 2 * J + m - mp - 2 * k, ps = mp - m + 2 * k;
-    const double mag = std::exp(lpre - lf(J + m - k) - lf(k) - lf(mp - m + k) - lf(J - mp - k));
-    const double sgn = ((mp - m + k) & 1) ? -1.0 : 1.0;
-    tot += sgn * mag * std::pow(c, pc) * std::pow(s, ps);
-  }
-  return tot;
+  return wigner_small_d_jacobi(J, mp, m, beta);
 }
 
 // Unadapted components: Phi'_m' = sum_m D_(m m')(rho) Phi_m with Phi_(-m) = (-1)^m Phi_m

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/mw3.h"
+#include "mw3_wigner.h"
 
 namespace mw3 {
 
@@ -75,6 +76,9 @@ struct Tuning {
                     // 0.302 against 0.310 ms per step on config 2, where both forms are
                     // bound by instruction issue), 1 automatic cluster size, 2/4/8 that many
                     // CTAs per (block, i) plane
+  int up_direct;    // FP64 state uploads from page-locked, mapped host memory read by a kernel
+                    // over the host link (1) or copied by the DMA engines (0, the default:
+                    // 4.49 against 5.05 ms for both state vectors of config 2)
   int tc_tma;       // tile-major angular step: tile copies by TMA (1) or cp.async (0, the
                     // default: 0.380 against 0.399 ms per step on config 2)
 };
@@ -167,8 +171,66 @@ cudaError_t launch_sums_flush(const real* ph, const real* cut, long ncut_total, 
                               const long* accoff, long max_cols, double* acc, cudaStream_t st);
 
 cudaError_t launch_advance(long* d_iter, long n, cudaStream_t st);
+// Ring slots a probability read adds on the fly instead of flushing them first.
+constexpr int kPeekMax = 8;
+// out[iJ][e] = the same flux sum over A + Ph Cut for the npend pending ring slots (phases
+// ph[iJ][2 nE][kb] of those slots already computed), A read only.
+template <typename real>
+cudaError_t launch_flux_reduce_peek(const double* acc, int nJ, int nE, const long* accoff,
+                                    const long* ncols, const long* ncut, long max_ncut,
+                                    const real* ph, int kb, int npend, const real* cut,
+                                    long ncut_total, const long* colbase, double* part,
+                                    double* out, cudaStream_t st);
 cudaError_t launch_convert_d2f(const double* in, float* out, long n, cudaStream_t st);
+// out[0, n) = (B) host[0, n), read by the device through the device alias of page-locked,
+// mapped host memory (16-byte aligned).
+template <typename B>
+cudaError_t launch_host_read(const double* host_alias, B* out, long n, cudaStream_t st);
 cudaError_t launch_convert_f2d(const float* in, double* out, long n, cudaStream_t st);
+
+// Channel probabilities on the device (mw3_gamma.cu): output keys (J, Lambda, v, j) in
+// CSR form over their channels; channel c reads the accumulator pair at col[c] (real row e,
+// imaginary row nE + e, row stride ld[c]) with its energy eps[c] and J index chJ[c].
+struct ChanTable {
+  const long* key_first;   // nkeys + 1
+  const int* key_chan;
+  const int* chJ;
+  const long* col;
+  const long* ld;
+  const double* eps;
+  double mu;
+  int nkeys;
+};
+cudaError_t launch_channel_probs(const double* acc, const ChanTable& t, const double* Ecol,
+                                 double Eref, const double* theta, const double* dE,
+                                 const double* a2, int nE, double* out, cudaStream_t st);
+
+// Products-coordinate-based start (mw3_pcb.cu). The packet frame's Jacobi vectors are
+// (r_s, R_s) = M (r, R); its diatom is a sine series sum_j coef[j] sin((j+1) pi (r_s - rsmin) / L)
+// on (rsmin, rsmax); g(R_s) = N exp(-(R_s - R0)^2 / (2 G^2)) cos(k0 R_s); plc is the
+// normalisation of P-bar_(om0)^(om0).
+struct PcbParams {
+  double M00, M01, M10, M11;
+  double R0, G, k0, N;
+  double rsmin, rsmax;
+  int nrs;
+  int j0, om0;
+  int NR, nr, ng;
+  double Rmin, dR, rmin, dr;
+  double plc;
+};
+// One output block (J, Omega, Lambda0): T^J[Omega][Omega0] = (sign flips of the frame
+// rotation) x (p1 d^J_(Omega0, Omega) + p2 d^J_(-Omega0, Omega)), the prefactors of the
+// Jacobi form and the parity-adapted weights folded into p1, p2.
+struct PcbTerm {
+  int blk;
+  int om;
+  WignerIdx w1, w2;
+  double p1, p2;
+};
+cudaError_t launch_pcb_packet(const PcbParams& p, const double* xw, const double* coef,
+                              const PcbTerm* terms, int nterms, double* out, int nsm,
+                              cudaStream_t st);
 
 // Product-channel projection (mw3_products.cu): channels of one (J, Lambda', Omega').
 struct ProdGroup {
@@ -245,8 +307,11 @@ cudaError_t launch_angular_tc(const TcArgs& args, int ngroups, const int* g_begi
                               double* norm_out, cudaStream_t st);
 constexpr int kTcMaxKp = 112;
 
+// out[iJ][e] = the flux sum of the J's cut columns (psi, dpsi) at energy e; `part` holds
+// flux_partial_size(nJ, nE, max_ncut) doubles of per-chunk partial sums.
+long flux_partial_size(int nJ, int nE, long max_ncut);
 cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* accoff,
-                               const long* ncols, const long* ncut, double* out,
-                               cudaStream_t st);
+                               const long* ncols, const long* ncut, long max_ncut, double* part,
+                               double* out, cudaStream_t st);
 
 }  // namespace mw3

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "mw3_internal.h"
 
@@ -1468,20 +1469,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
       }
     }
   };
-  // TMA form: bounded waits for the copies of the buffers in `mask` that are in flight,
-  // combined into one CTA-wide vote (ok stays CTA-uniform)
-  auto wait_tiles = [&](int mask) {
+  // TMA form: every thread waits (bounded) for the copies of the buffers in `mask` that are in
+  // flight; the completed barrier phase makes the copied bytes visible to each waiting thread,
+  // so no CTA barrier is needed here. The result is folded into the next CTA-wide vote, which
+  // keeps ok uniform.
+  auto wait_tiles_local = [&](int mask) -> bool {
+    bool good = true;
     if constexpr (TMA) {
-      int good = 1, any = 0;
       for (int w = 0; w < 3; ++w)
         if ((mask >> w & 1) && tpend[w]) {
-          good &= mbar_wait(smem_u32(tbar + w), tph[w]) ? 1 : 0;
-          tph[w] ^= 1u;
-          tpend[w] = false;
-          any = 1;
+          if (mbar_wait(smem_u32(tbar + w), tph[w])) {
+            tph[w] ^= 1u;
+            tpend[w] = false;
+          } else {
+            good = false;   // still pending: the exit path waits for this copy once more
+          }
         }
-      if (any) ok = __syncthreads_and(good) != 0;
     }
+    return good;
   };
   // matrices k0 (buffer 0) and k0 + 1 (buffer 1) of unit u, as one copy group
   auto issue_b2 = [&](long u, int k0) {
@@ -1518,8 +1523,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
       mma_commit(mb);
     }
   };
-  auto wait_mma = [&]() {
-    ok = __syncthreads_and(mbar_wait(mb, phase) ? 1 : 0) != 0;
+  auto wait_mma = [&](bool also = true) {
+    ok = __syncthreads_and((mbar_wait(mb, phase) && also) ? 1 : 0) != 0;
     phase ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;");
   };
@@ -1559,11 +1564,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
     // c^(Omega+1) in shared memory when the next unit is that block of this tile
     const bool up_chip = B0.up >= 0 && B0.up == b + 1 && u + 1 < u1 && unit_tile(u + 1) == tile;
 
-    __syncthreads();   // previous unit's readers of ts, ps, cs and tensor memory are done
     if constexpr (TMA) {
-      wait_tiles(1);                                        // this unit's c tile
+      // this unit's c tile has landed and the previous unit's readers of ts, ps, cs and
+      // tensor memory are done: one barrier
+      ok = __syncthreads_and(wait_tiles_local(1) ? 1 : 0) != 0;
       if (!ok) break;
     } else {
+      __syncthreads();   // previous unit's readers of ts, ps, cs and tensor memory are done
       asm volatile("cp.async.wait_group 2;" ::: "memory");   // this unit's c tile
       __syncthreads();
     }
@@ -1650,10 +1657,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
     //   H_s c = invdE (w + r) - e0s c,  c_(k+1) = D (alpha H_s c - beta D c_(k-1)),
     // so the result is k1 w + r2 with r2 written over c_(k-1) in shared memory.
     issue_mma2(tE, tO, false);                    // c(u+1), c_(k-1)(u), G2e G2o(u) landed
-    if constexpr (TMA) {   // the tiles the remainder reads: t(u), c_(k-1)(u), c(u+1) if on chip
-      wait_tiles(2 | (a.mode == 0 ? 4 : 0) | (up_chip ? 1 : 0));
-      if (!ok) break;
-    }
+    // TMA form: the tiles the remainder reads, t(u), c_(k-1)(u) and c(u+1) if on chip; the
+    // outcome joins the vote after GEMM 2
+    const bool tiles_ok = wait_tiles_local(2 | (a.mode == 0 ? 4 : 0) | (up_chip ? 1 : 0));
     const float invdE = a.dj[B0.iJ].invdE_f, e0s = a.dj[B0.iJ].e0s_f;
     const float D = live ? a.DR[mR] * a.Dr[kr] : 0.0f;
     const float k1 = a.mode == 1 ? invdE : D * a.alpha * invdE;
@@ -1663,52 +1669,79 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
       const float frk = live ? a.fr[kr] : 0.0f;
       const float fRm = live ? a.fR[mR] : 0.0f;
       const float erot = a.erot;
-      for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 8) {
-        // c of this unit: even columns i0/2.. = rows i0, i0+2, i0+4, i0+6, odd columns = rows
-        // i0+1, ...; with c^(Omega-1) on chip, its rows i0+1.. = odd columns i0/2.. (rows
-        // i0+1, i0+3, ...) and even columns i0/2+1.. (rows i0+2, i0+4, ...) of the previous
-        // unit's raw tile (row i of block Omega-1 is its row i + 1)
-        uint32_t r[16];
-        tmem_ld4_issue(tC + lane_base + (uint32_t)(i0 / 2), r);
-        tmem_ld4_issue(tC + kh + lane_base + (uint32_t)(i0 / 2), r + 4);
-        if (dn_chip) {
-          tmem_ld4_issue(tCp + kh + lane_base + (uint32_t)(i0 / 2), r + 8);
-          tmem_ld4_issue(tCp + lane_base + (uint32_t)(i0 / 2 + 1), r + 12);
-        } else {
-#pragma unroll
-          for (int s = 8; s < 16; ++s) r[s] = 0u;
-        }
-        tmem_wait16(r);
-        if (!live) continue;
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const int i = i0 + s;
-          if (i >= nrow) break;
-          const long off = (long)i * a.ncol + col;
-          const float cv = __uint_as_float(r[(s & 1) * 4 + (s >> 1)]);
-          float cd = 0.0f;
-          if (dn_chip) {
-            if (i + 1 < ng) cd = __uint_as_float(r[8 + (s & 1) * 4 + (s >> 1)]);
-          } else if (B0.dn >= 0) {
-            cd = __ldg(a.ck + (long)B0.dn * a.npts + off + a.ncol);
+      const bool has_up = B0.up >= 0, has_dn = B0.dn >= 0, use_pv = a.mode == 0;
+      // neighbours that are not on chip come from global memory (rows i + 1 of block
+      // Omega - 1 and i - 1 of block Omega + 1 share the (r, R) column of row i)
+      const float* dn_g = a.ck + (long)(has_dn ? B0.dn : 0) * a.npts + a.ncol + col;
+      const float* up_g = a.ck + (long)(has_up ? B0.up : 0) * a.npts - a.ncol + col;
+      // The remainder of rows i0 .. i0 + 7, specialised on which neighbours are on chip
+      // (uniform over the unit) and on whether all eight rows are live (every group but the
+      // last ones of the high-Omega blocks). With c^(Omega-1) on chip, row i + 1 of the
+      // previous unit's tile exists for every live row i (its block has one row more).
+      auto remainder = [&](auto dn_tag, auto up_tag) {
+        constexpr bool DNC = decltype(dn_tag)::value, UPC = decltype(up_tag)::value;
+        for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 8) {
+          // c of this unit: even columns i0/2.. = rows i0, i0+2, i0+4, i0+6, odd columns =
+          // rows i0+1, ...; with c^(Omega-1) on chip, its rows i0+1.. = odd columns i0/2..
+          // (rows i0+1, i0+3, ...) and even columns i0/2+1.. (rows i0+2, i0+4, ...) of the
+          // previous unit's raw tile (row i of block Omega-1 is its row i + 1)
+          uint32_t r[16];
+          tmem_ld4_issue(tC + lane_base + (uint32_t)(i0 / 2), r);
+          tmem_ld4_issue(tC + kh + lane_base + (uint32_t)(i0 / 2), r + 4);
+          if constexpr (DNC) {
+            tmem_ld4_issue(tCp + kh + lane_base + (uint32_t)(i0 / 2), r + 8);
+            tmem_ld4_issue(tCp + lane_base + (uint32_t)(i0 / 2 + 1), r + 12);
+            tmem_wait16(r);
+          } else {
+            tmem_wait8(r);
           }
-          // row i of block Omega+1 is its row i - 1 (j = Omega + i)
-          float cu = 0.0f;
-          if (B0.up >= 0 && i >= 1)
-            cu = up_chip ? cs[(i - 1) * TC_M + m] : __ldg(a.ck + (long)B0.up * a.npts + off - a.ncol);
-          const float tv = ts[i * TC_M + m];
-          const float pv = a.mode == 0 ? ps[i * TC_M + m] : 0.0f;
-          const float4 c4 = *reinterpret_cast<const float4*>(cfs + i * 8);
-          const float gg = fminf(fRm, cfs[i * 8 + 4]);
-          const float aa = fminf(c4.x * frk, erot) + gg * c4.y;
-          float rr = aa * cv + tv;
-          rr += gg * c4.z * cu;
-          rr += gg * c4.w * cd;
-          ps[i * TC_M + m] = kc * (rr * invdE - e0s * cv) - kq * pv;
+          if (!live) continue;
+          const int nv = nrow - i0;   // live rows from i0 on (may be <= 0)
+          float* psr = ps + i0 * TC_M + m;
+          const float* tsr = ts + i0 * TC_M + m;
+          const float* csr = cs + (i0 - 1) * TC_M + m;   // row i - 1 of the next unit's tile
+          const float* cfr = cfs + i0 * 8;
+          const long goff = (long)i0 * a.ncol;
+          auto row = [&](int s) {
+            const float cv = __uint_as_float(r[(s & 1) * 4 + (s >> 1)]);
+            float cd = 0.0f;
+            if constexpr (DNC) cd = __uint_as_float(r[8 + (s & 1) * 4 + (s >> 1)]);
+            else if (has_dn) cd = __ldg(dn_g + goff + (long)s * a.ncol);
+            // row i of block Omega+1 is its row i - 1 (j = Omega + i); none for i = 0
+            float cu = 0.0f;
+            if (has_up && (s > 0 || i0 > 0)) {
+              if constexpr (UPC) cu = csr[s * TC_M];
+              else cu = __ldg(up_g + goff + (long)s * a.ncol);
+            }
+            const float tv = tsr[s * TC_M];
+            const float pv = use_pv ? psr[s * TC_M] : 0.0f;
+            const float4 c4 = *reinterpret_cast<const float4*>(cfr + s * 8);
+            const float gg = fminf(fRm, cfr[s * 8 + 4]);
+            const float aa = fminf(c4.x * frk, erot) + gg * c4.y;
+            float rr = aa * cv + tv;
+            rr += gg * c4.z * cu;
+            rr += gg * c4.w * cd;
+            psr[s * TC_M] = kc * (rr * invdE - e0s * cv) - kq * pv;
+          };
+          if (nv >= 8) {
+#pragma unroll
+            for (int s2 = 0; s2 < 8; ++s2) row(s2);
+          } else {
+#pragma unroll
+            for (int s2 = 0; s2 < 8; ++s2)
+              if (s2 < nv) row(s2);
+          }
         }
+      };
+      if (dn_chip) {
+        if (up_chip) remainder(std::true_type{}, std::true_type{});
+        else remainder(std::true_type{}, std::false_type{});
+      } else {
+        if (up_chip) remainder(std::false_type{}, std::true_type{});
+        else remainder(std::false_type{}, std::false_type{});
       }
     }
-    wait_mma();
+    wait_mma(tiles_ok);
     if (!ok) break;
     // t is free: the next unit's t with its G1e G1o, one group
     if (u + 1 < u1) {
@@ -1720,30 +1753,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
     // ---- result = k1 w + r2, eight rows per tensor-memory wait (w even: rows i0, i0 + 2, ...;
     // w odd: rows i0 + 1, i0 + 3, ...); rows nrow..ng-1 of the block are zero
     float ssf = 0.0f;   // a thread's sum of squares (FP32: FP64 arithmetic is slow here)
-    for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 8) {
-      uint32_t r[8];
-      tmem_ld4_issue(tE + lane_base + (uint32_t)(i0 / 2), r);
-      tmem_ld4_issue(tO + lane_base + (uint32_t)(i0 / 2), r + 4);
-      tmem_wait8(r);
-      if (!live) continue;
+    {
+      const bool hs_out = a.mode == 1;
+      float* outb = (hs_out ? a.out : a.ckm1) + (long)b * a.npts + col;
+      for (int i0 = half * ncb; i0 < (half + 1) * ncb; i0 += 8) {
+        uint32_t r[8];
+        tmem_ld4_issue(tE + lane_base + (uint32_t)(i0 / 2), r);
+        tmem_ld4_issue(tO + lane_base + (uint32_t)(i0 / 2), r + 4);
+        tmem_wait8(r);
+        if (!live) continue;
+        const float* psr = ps + i0 * TC_M + m;
+        float* o = outb + (long)i0 * a.ncol;
+        const int nv = nrow - i0, nall = ng - i0;
+        if (nv >= 8) {   // eight live rows
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const int i = i0 + s;
-        if (i >= ng) break;
-        const float w = __uint_as_float(r[(s & 1) * 4 + (s >> 1)]);
-        const long idx = (long)b * a.npts + (long)i * a.ncol + col;
-        if (i >= nrow) {
-          if (a.mode == 1) a.out[idx] = 0.0f; else a.ckm1[idx] = 0.0f;
-          continue;
-        }
-        const float v = fmaf(k1, w, ps[i * TC_M + m]);
-        if (a.mode == 1) {
-          a.out[idx] = v;
+          for (int s2 = 0; s2 < 8; ++s2) {
+            const float v = fmaf(k1, __uint_as_float(r[(s2 & 1) * 4 + (s2 >> 1)]), psr[s2 * TC_M]);
+            o[(long)s2 * a.ncol] = v;
+            ssf = fmaf(v, v, ssf);
+          }
         } else {
-          a.ckm1[idx] = v;
-          ssf = fmaf(v, v, ssf);
+#pragma unroll
+          for (int s2 = 0; s2 < 8; ++s2) {
+            if (s2 >= nall) break;
+            float v = 0.0f;
+            if (s2 < nv) {
+              v = fmaf(k1, __uint_as_float(r[(s2 & 1) * 4 + (s2 >> 1)]), psr[s2 * TC_M]);
+              ssf = fmaf(v, v, ssf);
+            }
+            o[(long)s2 * a.ncol] = v;
+          }
         }
       }
+      if (hs_out) ssf = 0.0f;   // H_s q: no norm
     }
     // the sum of squares reduced in FP32 (across the warp, then across the 16 warps by warp 0):
     // one FP64 value per (block, tile)

@@ -40,6 +40,11 @@ class mw3_packet_desc(C.Structure):
                 ("v0", C.c_int), ("j0", C.c_int), ("omega0", C.c_int), ("elec0", C.c_int)]
 
 
+class mw3_pcb_desc(C.Structure):
+    _fields_ = [("arrangement", C.c_int), ("rmin", C.c_double), ("rmax", C.c_double),
+                ("nr", C.c_int)]
+
+
 class mw3_analysis_desc(C.Structure):
     _fields_ = [("rstar", C.c_double), ("E_lo", C.c_double), ("E_hi", C.c_double),
                 ("nE", C.c_int), ("Rinf", C.c_double), ("vmax", C.c_int), ("jmax", C.c_int),
@@ -53,6 +58,7 @@ class mw3_products_desc(C.Structure):
 
 
 ARRANGEMENTS = {"AC+B": 1, "AB+C": 2}
+PCB_ARRANGEMENTS = {"A+BC": 0, "AC+B": 1, "AB+C": 2}
 
 
 class mw3_leps_params(C.Structure):
@@ -84,6 +90,8 @@ _SIGS = {
     "mw3_pes_leps": (C.c_int, [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
                                C.c_void_p]),
     "mw3_init_packet": (C.c_int, [C.c_void_p, C.POINTER(mw3_packet_desc)]),
+    "mw3_init_packet_pcb": (C.c_int, [C.c_void_p, C.POINTER(mw3_packet_desc),
+                                      C.POINTER(mw3_pcb_desc)]),
     "mw3_set_absorber": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_double,
                                    C.c_double, C.c_int]),
     "mw3_set_analysis": (C.c_int, [C.c_void_p, C.POINTER(mw3_analysis_desc)]),
@@ -95,6 +103,7 @@ _SIGS = {
                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mw3_get_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mw3_set_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mw3_set_state_f32": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "mw3_apply_hs": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mw3_norm_trace": (C.c_long, [C.c_void_p, C.POINTER(C.c_double), C.c_long]),
     "mw3_enable_autocorrelation": (C.c_int, [C.c_void_p]),
@@ -310,6 +319,14 @@ class Propagator:
 
     def init_packet(self):
         pk = self.cfg["packet"]
+        src = self.cfg.get("pcb")
+        if src:   # products-coordinate-based start: the grid is the product arrangement
+            d = mw3_packet_desc(pk["R0"], pk["Gamma"], pk["Ecol_eV"] / HARTREE_EV, pk["v0"],
+                                pk["j0"], pk["omega0"], pk["elec0"])
+            s = mw3_pcb_desc(PCB_ARRANGEMENTS[src["arrangement"]], src["rmin"], src["rmax"],
+                             src["nr"])
+            _check(self.ctx, lib.mw3_init_packet_pcb(self.ctx, C.byref(d), C.byref(s)))
+            return
         mw3_init_packet(self.ctx, pk["R0"], pk["Gamma"], pk["Ecol_eV"] / HARTREE_EV, pk["v0"],
                         pk["j0"], pk["omega0"], pk["elec0"])
 
@@ -354,6 +371,11 @@ class Propagator:
         q = np.ascontiguousarray(q, dtype=np.float64)
         qp = None if qprev is None else np.ascontiguousarray(qprev, dtype=np.float64)
         _check(self.ctx, lib.mw3_set_state(self.ctx, _dp(q), None if qp is None else _dp(qp)))
+
+    def set_state_f32(self, q, qprev=None):
+        q = np.ascontiguousarray(q, dtype=np.float32)
+        qp = None if qprev is None else np.ascontiguousarray(qprev, dtype=np.float32)
+        _check(self.ctx, lib.mw3_set_state_f32(self.ctx, _fp(q), None if qp is None else _fp(qp)))
 
     def apply_hs(self, q):
         q = np.ascontiguousarray(q, dtype=np.float64)

@@ -229,6 +229,52 @@ def test_checkpoint_roundtrip():
     np.testing.assert_allclose(a.probabilities()[1], b.probabilities()[1], atol=1e-13)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("pending", [1, 5, 8, 13])
+def test_pending_ring_read_equals_flushed(prec, pending):
+    """A propagation that stops inside an energy ring leaves the slots pending: a probability
+    read adds up to eight of them on the fly (reading the accumulators only) and flushes more.
+    Either way the probabilities (total, reactant channels, product channels) equal those
+    read after an explicit flush (a checkpoint save flushes); continuing afterwards gives the
+    same state as one uninterrupted call.
+
+    Tolerances. The total: the on-the-fly read must reproduce the pending slots' own
+    contribution (the change from the last flushed read) to 1e-9 of it in FP64 and to 1e-4 in
+    the mixed form, whose flush multiplies on the tensor cores (split-TF32 products summed in
+    FP32 inside the MMA) while the read multiplies the same FP32 values in FP64. The channel
+    sums are FP64 in both forms (FP64 ring, phases and GEMM), so both use FP64 bounds."""
+    cfg = W.C2_SMALL
+    kb = 16
+    n0 = 12 * kb
+    drel, rel = (1e-9, 1e-10) if prec == "fp64" else (1e-4, 1e-6)
+
+    a = mw3().Propagator(cfg, precision=prec, tuning={"kb": kb})
+    a.propagate(n0)
+    _, P0, _ = a.probabilities()               # ring empty: the flushed sums alone
+    a.propagate(pending)
+    E, Pt, Pin = a.probabilities()
+    Pp = a.product_probabilities()
+    E2, Pt2, Pin2 = a.probabilities()          # a second read sees the same sums
+    assert np.array_equal(Pt, Pt2) and np.array_equal(Pin, Pin2)
+    with tempfile.TemporaryDirectory() as d:
+        a.checkpoint_save(os.path.join(d, "ck.bin"))
+    _, Ft, Fin = a.probabilities()
+    Fp = a.product_probabilities()
+    step = np.max(np.abs(Ft - P0))             # what the pending slots add
+    assert step > 0
+    assert np.max(np.abs(Pt - Ft)) <= drel * step + rel * np.max(np.abs(Ft)) + 1e-15
+    for x, y in ((Pin, Fin), (Pp, Fp)):
+        assert np.max(np.abs(x - y)) <= 1e-9 * np.max(np.abs(y)) + 1e-14
+    a.propagate(kb - pending + 3)
+    b = mw3().Propagator(cfg, precision=prec, tuning={"kb": kb})
+    b.propagate(n0 + kb + 3)
+    assert np.array_equal(a.state()[0], b.state()[0])
+    Fa, Fb = a.probabilities()[1], b.probabilities()[1]
+    assert np.max(np.abs(Fa - Fb)) <= (1e-10 if prec == "fp64" else 1e-4) * np.max(np.abs(Fb)) + 1e-15
+    a.close()
+    b.close()
+
+
 def test_full_size_config2_operator_and_first_steps():
     """Config 2 at full size (256 x 192 x 96, 11 blocks): H_s on a seeded vector in
     both precisions, and the first two damped iterations plus their flux sums in FP64."""

@@ -156,6 +156,30 @@ C_ODD = shrunk(C2, "h_dh_j3_30x18x10", NR=30, nr=18, ngamma=10, J=[3], omega_max
                nE=16, kmin=10)
 
 
+# Products-coordinate-based start (Section 2.4, iprod = 1): H + DH -> H2 + D propagated on a
+# grid in the PRODUCT Jacobi coordinates, whose own labels are A = D, B = C = H (r = H-H,
+# R from the H2 centre of mass to D); the H + DH packet lives in the arrangement "AC+B" of
+# those labels (diatom D-H, atom H) and is carried onto the grid once. The grid's r reaches
+# past the H-H distances of the packet (R0 = 8 bohr from DH puts the two H atoms 6.5-9.5 bohr
+# apart); the product channels H2(v', j') are the grid's own, projected at R_inf.
+MASSES_D_HH = (2.01410, 1.00783, 1.00783)
+_PCB_SRC = dict(arrangement="AC+B", rmin=0.5, rmax=4.5, nr=48)
+C2_PCB = _cfg(
+    "pcb_h_dh_j10_256x256x96",
+    grid=dict(NR=256, Rmin=0.5, Rmax=12.0, nr=256, rmin=0.5, rmax=16.0, ngamma=96),
+    J=[10], omega_max=10, nelec=1, packet=dict(_PACKET, R0=8.0),
+    absorber=_absorber(12.0, 9.6, 16.0, 13.0),
+    analysis=dict(rstar=12.5, E_lo_eV=0.3, E_hi_eV=1.5, nE=500, Rinf=9.0,
+                  vmax=3, jmax=15, kmin=0),
+    steps=12000, precision="mixed")
+C2_PCB["masses_u"] = MASSES_D_HH
+C2_PCB["pcb"] = dict(_PCB_SRC)
+# parity size of the same (J = 1)
+C2_PCB_SMALL = shrunk(C2_PCB, "pcb_h_dh_j1_32x48x12", NR=32, nr=48, ngamma=12, J=[1],
+                      omega_max=1, steps=120, nE=32, vmax=2, jmax=6)
+PCB = {"c2pcb": C2_PCB, "c2pcbs": C2_PCB_SMALL}
+
+
 def rng(seed: int) -> np.random.Generator:
     """The single seeded generator used for every random test input."""
     return np.random.default_rng(int(seed))
