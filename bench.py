@@ -466,8 +466,13 @@ def run_ours(args, rank, world, local):
         "kernels": kernels,
         "gpu_launches": launches,
         "clocks": clocks,
-        "e2e": {"value": world * e2e_steps / te, "unit": "steps/s", "h2d_bytes_per_step": 2 * vec_bytes,
-                "d2h_bytes_per_step": nE * 8 * 2 * len(cfg["J"]), "host_state": "f32 pinned",
+        "e2e": {"value": world * e2e_steps / te, "unit": "steps/s",
+                # the two state vectors up, and the |a(E)|^2 row of the probability read
+                "h2d_bytes_per_step": 2 * vec_bytes + nE * 8,
+                # back: the flux per (J, E) and the channel probabilities per (J, Lambda, v, j, E)
+                "d2h_bytes_per_step": 8 * len(cfg["J"]) * nE * (1 + nelec * (cfg["analysis"]["vmax"] + 1)
+                                                                * (cfg["analysis"]["jmax"] + 1)),
+                "host_state": "f32 pinned",
                 "steps": e2e_steps,
                 "ms_per_call": {"set_state_f32": 1e3 * tparts[0] / e2e_steps,
                                 "propagate_1": 1e3 * tparts[1] / e2e_steps,

@@ -176,6 +176,11 @@ struct mw3_ctx {
   // propagation state
   long iter = 0;       // k of q_k
   int ring_n = 0;      // ring slots 0 .. ring_n - 1 hold iterations not yet flushed into the sums
+  // the flux accumulators change with every flush, reset and load; a probability read keeps
+  // their flux ("fluxA") and, in the mixed form, an FP32 copy ("acc32") for the reads that
+  // follow while only ring slots are added
+  long acc_version = 0;
+  long fluxA_version = -1;
   int cur = 0;         // d_q[cur] holds q_k
   std::vector<double> norm_trace;  // [iter][nJ], ||q_k||^2 for k = 1..iter
   double norm0 = 1.0;
@@ -576,6 +581,7 @@ int reset_after_packet(mw3_ctx* ctx) {
         (st = dzero(ctx, "cutc")) || (st = dzero(ctx, "d_iter")))
       return st;
     ctx->ring_n = 0;
+    ++ctx->acc_version;
     if (!ctx->host_only) CK(cudaStreamSynchronize(ctx->stream));
   }
   return MW3_OK;
@@ -1536,6 +1542,7 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
   if ((st = dalloc(ctx, "cut", (size_t)kb * ctx->NC * ctx->rs())) || (st = dzero(ctx, "cut"))) return st;
   if ((st = dalloc(ctx, "acc", (size_t)acc * 8)) || (st = dzero(ctx, "acc"))) return st;
   ctx->ring_n = 0;
+  ++ctx->acc_version;
   if ((st = dalloc(ctx, "ph", (size_t)ctx->nJ * 2 * nE * kb * ctx->rs()))) return st;
   // channel ring, its FP64 accumulators and (mixed form) its FP64 phase matrix
   if ((st = dalloc(ctx, "cutc", (size_t)kb * std::max(ctx->NCc, 4L) * 8)) || (st = dzero(ctx, "cutc")))
@@ -1911,6 +1918,7 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
 
 template <typename real>
 int flush(mw3_ctx* ctx, int nvalid, bool timed) {
+  ++ctx->acc_version;
   Bufs<real> B = bufs<real>(ctx);
   cudaStream_t st = ctx->stream;
   Timer tm(ctx, 6, timed);
@@ -1999,6 +2007,7 @@ int propagate_impl(mw3_ctx* ctx, long nsteps) {
         ctx->iter = it0;
       }
       CK(cudaGraphLaunch(ge, ctx->stream));
+      ++ctx->acc_version;   // the ring's flush is part of the graph
       ctx->cur = (kb % 2) ? 1 - ctx->cur : ctx->cur;
     } else {
       for (int s = 0; s < n; ++s) {
@@ -2073,7 +2082,29 @@ int channel_probabilities(mw3_ctx* ctx, const double* accc, const ChanTable& t, 
   return MW3_OK;
 }
 
-// Flux sums over A + Ph Cut for the pending ring slots (phases of those slots first).
+// The flux of the flushed accumulators alone into "fluxA" (and, in the mixed form, their FP32
+// copy "acc32"), unless the accumulators are unchanged since the last time.
+int flux_flushed(mw3_ctx* ctx) {
+  const int nJ = ctx->nJ, nE = ctx->an.nE;
+  if (ctx->fluxA_version == ctx->acc_version && dptr(ctx, "fluxA")) return MW3_OK;
+  const long max_ncut = *std::max_element(ctx->ncut.begin(), ctx->ncut.end());
+  const bool mixed = ctx->precision != MW3_FP64;
+  int st;
+  if ((st = dalloc(ctx, "flux_part", (size_t)flux_partial_size(nJ, nE, max_ncut) * 8)) ||
+      (st = dalloc(ctx, "fluxA", (size_t)nJ * nE * 8)) ||
+      (mixed && (st = dalloc(ctx, "acc32", (size_t)ctx->acc_size * 4))))
+    return st;
+  LK(launch_flux_reduce((const double*)dptr(ctx, "acc"), nJ, nE, (const long*)dptr(ctx, "accoff"),
+                        (const long*)dptr(ctx, "ncols"), (const long*)dptr(ctx, "ncut"), max_ncut,
+                        (double*)dptr(ctx, "flux_part"), (double*)dptr(ctx, "fluxA"),
+                        mixed ? (float*)dptr(ctx, "acc32") : nullptr, ctx->stream));
+  ctx->fluxA_version = ctx->acc_version;
+  return MW3_OK;
+}
+
+// Flux sums over A + Ph Cut for the pending ring slots (phases of those slots first): in FP64
+// from the FP64 accumulators; in the mixed form as the flushed flux plus the change that the
+// pending slots make, from the FP32 copy of the accumulators (the FP64 ones are not read).
 template <typename real>
 int flux_peek(mw3_ctx* ctx) {
   Bufs<real> B = bufs<real>(ctx);
@@ -2082,10 +2113,18 @@ int flux_peek(mw3_ctx* ctx) {
   const long max_ncut = *std::max_element(ctx->ncut.begin(), ctx->ncut.end());
   int st;
   if ((st = dalloc(ctx, "flux_part", (size_t)flux_partial_size(nJ, nE, max_ncut) * 8))) return st;
-  LK(launch_flux_reduce_peek<real>(B.acc, nJ, nE, B.accoff, B.ncols, B.ncut, max_ncut, B.ph, kb,
-                                   ctx->ring_n, B.cut, ctx->NC, B.colbase,
-                                   (double*)dptr(ctx, "flux_part"), (double*)dptr(ctx, "flux"),
-                                   ctx->stream));
+  if constexpr (std::is_same<real, float>::value) {
+    if ((st = flux_flushed(ctx))) return st;
+    LK(launch_flux_cross((const float*)dptr(ctx, "acc32"), nJ, nE, B.accoff, B.ncols, B.ncut,
+                         max_ncut, B.ph, kb, ctx->ring_n, B.cut, ctx->NC, B.colbase,
+                         (double*)dptr(ctx, "flux_part"), (const double*)dptr(ctx, "fluxA"),
+                         (double*)dptr(ctx, "flux"), ctx->stream));
+  } else {
+    LK(launch_flux_reduce_peek<real>(B.acc, nJ, nE, B.accoff, B.ncols, B.ncut, max_ncut, B.ph, kb,
+                                     ctx->ring_n, B.cut, ctx->NC, B.colbase,
+                                     (double*)dptr(ctx, "flux_part"), (double*)dptr(ctx, "flux"),
+                                     ctx->stream));
+  }
   return MW3_OK;
 }
 
@@ -2584,11 +2623,9 @@ int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel)
     st = ctx->precision == MW3_FP64 ? flux_peek<double>(ctx) : flux_peek<float>(ctx);
     if (st) return st;
   } else {
-    const long max_ncut = *std::max_element(ctx->ncut.begin(), ctx->ncut.end());
-    if ((st = dalloc(ctx, "flux_part", (size_t)flux_partial_size(nJ, nE, max_ncut) * 8))) return st;
-    LK(launch_flux_reduce((const double*)dptr(ctx, "acc"), nJ, nE, (const long*)dptr(ctx, "accoff"),
-                          (const long*)dptr(ctx, "ncols"), (const long*)dptr(ctx, "ncut"), max_ncut,
-                          (double*)dptr(ctx, "flux_part"), (double*)dptr(ctx, "flux"), ctx->stream));
+    if ((st = flux_flushed(ctx))) return st;
+    CK(cudaMemcpyAsync(dptr(ctx, "flux"), dptr(ctx, "fluxA"), (size_t)nJ * nE * 8,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
   }
   std::vector<double> F((size_t)nJ * nE);
   CK(cudaMemcpyAsync(F.data(), dptr(ctx, "flux"), F.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -2744,6 +2781,7 @@ int mw3_checkpoint_load(mw3_ctx* ctx, const char* path) {
       hdr[5] != (uint64_t)ctx->precision || hdr[6] != (uint64_t)ctx->accc_size)
     return ctx->fail(MW3_ERR_IO, "checkpoint does not match this configuration");
   ctx->ring_n = 0;   // the saved sums hold every saved iteration
+  ++ctx->acc_version;
   const size_t nb = (size_t)ctx->nblk * ctx->npts * ctx->rs();
   std::vector<char> q(nb), qp(nb);
   std::vector<double> acc(ctx->acc_size), accc(ctx->accc_size);

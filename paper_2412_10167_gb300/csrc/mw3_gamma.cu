@@ -553,7 +553,8 @@ cudaError_t launch_dots(const real* a, const real* b, const long* J_begin, int n
 // chunks of kFluxChunk points so that every SM takes part (the accumulators are GBs: the
 // reduction is one read of them), with partial sums per chunk summed in chunk order by
 // k_flux_final. PEEK: the accumulators are A + Ph Cut with the ring slots that have not been
-// flushed yet (npend <= kPeekMax) added on the fly in FP64; A itself is only read, so a
+// flushed yet (npend <= kPeekMax) added on the fly (the products summed in the ring's
+// precision, then added to the FP64 accumulator values); A itself is only read, so a
 // probability read between flushes moves the accumulators once instead of three times (read
 // and write of a flush, then the read of the reduction).
 constexpr int kFluxE = 8;          // energies per CTA (the ring values of a point read once)
@@ -564,8 +565,11 @@ __global__ void __launch_bounds__(256) k_flux_partial(
     const double* __restrict__ acc, int nJ, int nE, const long* __restrict__ accoff,
     const long* __restrict__ ncols, const long* __restrict__ ncut, const real* __restrict__ ph,
     int kb, int npend, const real* __restrict__ cut, long ncut_total,
-    const long* __restrict__ colbase, double* __restrict__ part) {
-  __shared__ double sph[kFluxE][2][kPeekMax];   // phase factors (real, imaginary row) per slot
+    const long* __restrict__ colbase, double* __restrict__ part, float* __restrict__ acc32) {
+  // phase factors (real, imaginary row) per pending slot, in the ring's precision: the pending
+  // terms are summed like the flush sums them (FP32 products in the mixed form; FP64 arithmetic
+  // runs at 1/64 of the FP32 rate here) and added to the FP64 accumulators once
+  __shared__ real sph[kFluxE][2][kPeekMax];
   __shared__ double red[kFluxE][256];
   const int e0 = blockIdx.x * kFluxE;
   const int iJ = blockIdx.y;
@@ -577,13 +581,17 @@ __global__ void __launch_bounds__(256) k_flux_partial(
     for (int x = threadIdx.x; x < kFluxE * 2 * kPeekMax; x += blockDim.x) {
       const int q = x / (2 * kPeekMax), prt = (x / kPeekMax) & 1, sl = x % kPeekMax;
       const int row = (prt ? nE : 0) + e0 + q;
-      sph[q][prt][sl] =
-          (q < ne && sl < npend) ? (double)ph[((long)iJ * 2 * nE + row) * kb + sl] : 0.0;
+      sph[q][prt][sl] = (q < ne && sl < npend) ? ph[((long)iJ * 2 * nE + row) * kb + sl] : (real)0;
     }
   }
-  double acc_q[kFluxE];
+  // the reduction keeps all energies of a point in registers (the loads of a point in flight
+  // together); with pending slots the energies go two at a time and the sums live in shared
+  // memory (a thread owns its column), which keeps the register count, and the occupancy, up
+  double acc_q[PEEK ? 1 : kFluxE];
 #pragma unroll
-  for (int q = 0; q < kFluxE; ++q) acc_q[q] = 0.0;
+  for (int q = 0; q < (PEEK ? 1 : kFluxE); ++q) acc_q[q] = 0.0;
+#pragma unroll
+  for (int q = 0; q < kFluxE; ++q) red[q][threadIdx.x] = 0.0;
   __syncthreads();
   for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     real cp[kPeekMax], cq[kPeekMax];
@@ -595,27 +603,46 @@ __global__ void __launch_bounds__(256) k_flux_partial(
         cq[sl] = sl < npend ? cj[(long)sl * ncut_total + np + p] : (real)0;
       }
     }
-#pragma unroll
+#pragma unroll(PEEK ? 2 : kFluxE)
     for (int q = 0; q < kFluxE; ++q) {
       if (q < ne) {
         const double* re = A + (long)(e0 + q) * nc;
         const double* im = A + (long)(nE + e0 + q) * nc;
         double rp = re[p], ip = im[p], rq = re[np + p], iq = im[np + p];
+        if (acc32) {   // an FP32 copy of the values read, for later reads with pending slots
+          float* r32 = acc32 + accoff[iJ] + (long)(e0 + q) * nc;
+          float* i32 = acc32 + accoff[iJ] + (long)(nE + e0 + q) * nc;
+          r32[p] = (float)rp;
+          i32[p] = (float)ip;
+          r32[np + p] = (float)rq;
+          i32[np + p] = (float)iq;
+        }
         if constexpr (PEEK) {
+          real drp = 0, dip = 0, drq = 0, diq = 0;
 #pragma unroll
           for (int sl = 0; sl < kPeekMax; ++sl) {
-            rp += sph[q][0][sl] * (double)cp[sl];
-            ip += sph[q][1][sl] * (double)cp[sl];
-            rq += sph[q][0][sl] * (double)cq[sl];
-            iq += sph[q][1][sl] * (double)cq[sl];
+            if (sl < npend) {
+              drp += sph[q][0][sl] * cp[sl];
+              dip += sph[q][1][sl] * cp[sl];
+              drq += sph[q][0][sl] * cq[sl];
+              diq += sph[q][1][sl] * cq[sl];
+            }
           }
+          rp += (double)drp;
+          ip += (double)dip;
+          rq += (double)drq;
+          iq += (double)diq;
+          red[q][threadIdx.x] += rp * iq - ip * rq;
+        } else {
+          acc_q[q] += rp * iq - ip * rq;
         }
-        acc_q[q] += rp * iq - ip * rq;
       }
     }
   }
+  if constexpr (!PEEK) {
 #pragma unroll
-  for (int q = 0; q < kFluxE; ++q) red[q][threadIdx.x] = acc_q[q];
+    for (int q = 0; q < kFluxE; ++q) red[q][threadIdx.x] = acc_q[q];
+  }
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w)
@@ -627,14 +654,86 @@ __global__ void __launch_bounds__(256) k_flux_partial(
     part[((long)blockIdx.z * nJ + iJ) * nE + e0 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-// out[iJ][e] = sum over the chunks z (in order) of part[z][iJ][e].
+// Mixed form, reads with pending ring slots: with A the flushed accumulators (their flux F_A
+// already known, FP32 copy A32) and D = Ph Cut the pending terms,
+//   flux(A + D) - F_A = sum_p Re A Im D_B + Re D_A Im B - Im A Re D_B - Im D_A Re B
+//                              + Re D_A Im D_B - Im D_A Re D_B
+// (A = psi column p, B = dpsi column np + p). The pending terms and their products with A
+// are FP32 values like the flush's own products; each thread sums its points in FP32 and the
+// CTA in FP64, so the FP64 accumulators are not read at all.
+__global__ void __launch_bounds__(256) k_flux_cross(
+    const float* __restrict__ acc32, int nJ, int nE, const long* __restrict__ accoff,
+    const long* __restrict__ ncols, const long* __restrict__ ncut, const float* __restrict__ ph,
+    int kb, int npend, const float* __restrict__ cut, long ncut_total,
+    const long* __restrict__ colbase, double* __restrict__ part) {
+  __shared__ float sph[kFluxE][2][kPeekMax];
+  __shared__ double red[kFluxE][256];
+  const int e0 = blockIdx.x * kFluxE;
+  const int iJ = blockIdx.y;
+  const int ne = min(kFluxE, nE - e0);
+  const long nc = ncols[iJ], np = ncut[iJ];
+  const long p0 = (long)blockIdx.z * kFluxChunk, p1 = min(np, p0 + kFluxChunk);
+  const float* A = acc32 + accoff[iJ];
+  const float* cj = cut + colbase[iJ];
+  for (int x = threadIdx.x; x < kFluxE * 2 * kPeekMax; x += blockDim.x) {
+    const int q = x / (2 * kPeekMax), prt = (x / kPeekMax) & 1, sl = x % kPeekMax;
+    const int row = (prt ? nE : 0) + e0 + q;
+    sph[q][prt][sl] = (q < ne && sl < npend) ? ph[((long)iJ * 2 * nE + row) * kb + sl] : 0.0f;
+  }
+  // a thread's FP32 sums in shared memory (it owns its column): four energies at a time keep the
+  // register count, and the occupancy, up
+  __shared__ float accs[kFluxE][256];
+#pragma unroll
+  for (int q = 0; q < kFluxE; ++q) accs[q][threadIdx.x] = 0.0f;
+  __syncthreads();
+  for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    float cp[kPeekMax], cq[kPeekMax];
+#pragma unroll
+    for (int sl = 0; sl < kPeekMax; ++sl) {
+      cp[sl] = sl < npend ? cj[(long)sl * ncut_total + p] : 0.0f;
+      cq[sl] = sl < npend ? cj[(long)sl * ncut_total + np + p] : 0.0f;
+    }
+#pragma unroll 4
+    for (int q = 0; q < kFluxE; ++q) {
+      if (q < ne) {
+        const float* re = A + (long)(e0 + q) * nc;
+        const float* im = A + (long)(nE + e0 + q) * nc;
+        float dra = 0, dia = 0, drb = 0, dib = 0;
+#pragma unroll
+        for (int sl = 0; sl < kPeekMax; ++sl) {
+          if (sl < npend) {
+            dra += sph[q][0][sl] * cp[sl];
+            dia += sph[q][1][sl] * cp[sl];
+            drb += sph[q][0][sl] * cq[sl];
+            dib += sph[q][1][sl] * cq[sl];
+          }
+        }
+        const float ra = re[p], ia = im[p], rb = re[np + p], ib = im[np + p];
+        accs[q][threadIdx.x] += ra * dib + dra * ib - ia * drb - dia * rb + dra * dib - dia * drb;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kFluxE; ++q) red[q][threadIdx.x] = (double)accs[q][threadIdx.x];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < kFluxE; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < ne)
+    part[((long)blockIdx.z * nJ + iJ) * nE + e0 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// out[iJ][e] = base[iJ][e] (if given) + the sum over the chunks z (in order) of part[z][iJ][e].
 __global__ void k_flux_final(const double* __restrict__ part, int nz, long n,
-                             double* __restrict__ out) {
+                             const double* __restrict__ base, double* __restrict__ out) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double s = 0.0;
   for (int z = 0; z < nz; ++z) s += part[(long)z * n + i];
-  out[i] = s;
+  out[i] = base ? base[i] + s : s;
 }
 
 long flux_partial_size(int nJ, int nE, long max_ncut) {
@@ -643,14 +742,14 @@ long flux_partial_size(int nJ, int nE, long max_ncut) {
 
 cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* accoff,
                                const long* ncols, const long* ncut, long max_ncut, double* part,
-                               double* out, cudaStream_t st) {
+                               double* out, float* acc32, cudaStream_t st) {
   const int nz = (int)std::max<long>(1, (max_ncut + kFluxChunk - 1) / kFluxChunk);
   k_flux_partial<false, double><<<dim3((nE + kFluxE - 1) / kFluxE, nJ, nz), 256, 0, st>>>(
-      acc, nJ, nE, accoff, ncols, ncut, nullptr, 0, 0, nullptr, 0, nullptr, part);
+      acc, nJ, nE, accoff, ncols, ncut, nullptr, 0, 0, nullptr, 0, nullptr, part, acc32);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long n = (long)nJ * nE;
-  k_flux_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, nz, n, out);
+  k_flux_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, nz, n, nullptr, out);
   return cudaGetLastError();
 }
 
@@ -663,11 +762,27 @@ cudaError_t launch_flux_reduce_peek(const double* acc, int nJ, int nE, const lon
   if (npend < 0 || npend > kPeekMax) return cudaErrorInvalidValue;
   const int nz = (int)std::max<long>(1, (max_ncut + kFluxChunk - 1) / kFluxChunk);
   k_flux_partial<true, real><<<dim3((nE + kFluxE - 1) / kFluxE, nJ, nz), 256, 0, st>>>(
-      acc, nJ, nE, accoff, ncols, ncut, ph, kb, npend, cut, ncut_total, colbase, part);
+      acc, nJ, nE, accoff, ncols, ncut, ph, kb, npend, cut, ncut_total, colbase, part, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long n = (long)nJ * nE;
-  k_flux_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, nz, n, out);
+  k_flux_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, nz, n, nullptr, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flux_cross(const float* acc32, int nJ, int nE, const long* accoff,
+                              const long* ncols, const long* ncut, long max_ncut, const float* ph,
+                              int kb, int npend, const float* cut, long ncut_total,
+                              const long* colbase, double* part, const double* fluxA, double* out,
+                              cudaStream_t st) {
+  if (npend < 0 || npend > kPeekMax) return cudaErrorInvalidValue;
+  const int nz = (int)std::max<long>(1, (max_ncut + kFluxChunk - 1) / kFluxChunk);
+  k_flux_cross<<<dim3((nE + kFluxE - 1) / kFluxE, nJ, nz), 256, 0, st>>>(
+      acc32, nJ, nE, accoff, ncols, ncut, ph, kb, npend, cut, ncut_total, colbase, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long n = (long)nJ * nE;
+  k_flux_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, nz, n, fluxA, out);
   return cudaGetLastError();
 }
 

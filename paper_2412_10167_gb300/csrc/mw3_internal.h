@@ -310,8 +310,17 @@ constexpr int kTcMaxKp = 112;
 // out[iJ][e] = the flux sum of the J's cut columns (psi, dpsi) at energy e; `part` holds
 // flux_partial_size(nJ, nE, max_ncut) doubles of per-chunk partial sums.
 long flux_partial_size(int nJ, int nE, long max_ncut);
+// acc32 (may be null): an FP32 copy of every accumulator value the reduction reads, written on
+// the way (for launch_flux_cross).
 cudaError_t launch_flux_reduce(const double* acc, int nJ, int nE, const long* accoff,
                                const long* ncols, const long* ncut, long max_ncut, double* part,
-                               double* out, cudaStream_t st);
+                               double* out, float* acc32, cudaStream_t st);
+// Mixed form: out = fluxA + the flux change that the npend pending ring slots make, from the
+// FP32 copy acc32 of the flushed accumulators (whose flux is fluxA) and the FP32 ring.
+cudaError_t launch_flux_cross(const float* acc32, int nJ, int nE, const long* accoff,
+                              const long* ncols, const long* ncut, long max_ncut, const float* ph,
+                              int kb, int npend, const float* cut, long ncut_total,
+                              const long* colbase, double* part, const double* fluxA, double* out,
+                              cudaStream_t st);
 
 }  // namespace mw3

@@ -145,14 +145,20 @@ def cumulative(Js, P):
 def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 1500, width: int = 256,
         depth: int = 3, lr: float = 2e-3, batch: int = 512, fallback_dP: float = 0.01,
         ensemble: int = 3, precision: str = "fp64", device: int = 0, seed: int = 10167,
-        spread_factor: float = 2.0, a2_floor: float = 0.05):
+        spread_factor: float = 2.0, a2_floor: float = 0.05, e_stride: int = 1,
+        rule: str = "spread"):
     """Train on J_train, predict J_test with the fallback decided by the ensemble spread,
     then score everything against a propagation of J_test; returns a report dictionary.
 
     Each of `ensemble` networks (different initialisation and shuffling seeds) trains for
     `epochs` at `lr`, then epochs/2 at lr/4 and epochs/2 at lr/16 (the AdamW state carries
     over); the prediction is their mean, the uncertainty their standard deviation. The
-    propagations run in `precision` ("fp64" or "mixed")."""
+    propagations run in `precision` ("fp64" or "mixed"). The networks train on every
+    `e_stride`-th kept energy (the probabilities are smooth in E on the energy grid) and
+    predict all of them. `rule` decides the fallback without propagating: "spread" (spread
+    times `spread_factor` above `fallback_dP`), "linear" (the prediction differs from the
+    linear interpolation in J of the neighbouring training values by more than
+    `fallback_dP`), or "both" (either)."""
     E_all, _, Ptr_all, t_train, a2 = propagate_probabilities(cfg, J_train, steps, precision,
                                                               device=device, with_a2=True)
     keep = a2 >= a2_floor * np.max(a2)
@@ -161,7 +167,7 @@ def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 1500, width: int =
     nv, nj = Ptr.shape[1], Ptr.shape[2]
     scale = dict(J=max(max(J_train), 1), E0=E[0], dE=max(E[-1] - E[0], 1e-12), v=max(nv - 1, 1),
                  j=max(nj - 1, 1), B=fit_shift(E, np.asarray(J_train, float), Ptr))
-    X, y = dataset(J_train, E, Ptr, scale)
+    X, y = dataset(J_train, E[::e_stride], Ptr[..., ::e_stride], scale)
     schedule = ((epochs, lr), (epochs // 2, lr / 4), (epochs // 2, lr / 16))
     losses, preds = [], []
     t_fit = t_pred = 0.0
@@ -181,8 +187,13 @@ def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 1500, width: int =
     Psur = preds.mean(axis=0)
     spread = preds.std(axis=0) if len(preds) > 1 else np.zeros_like(Psur)
     loss = float(np.mean(losses))
-    # fallback decided from the ensemble alone; only those J values are propagated
-    bad_J = [J for t, J in enumerate(J_test) if spread_factor * spread[t].max() > fallback_dP]
+    # fallback decided without propagating the held-out J; only those J values are propagated
+    Plin = linear_baseline(np.asarray(J_train), Ptr, np.asarray(J_test))
+    by_spread = [spread_factor * spread[t].max() > fallback_dP for t in range(len(J_test))]
+    by_linear = [np.abs(Psur[t] - Plin[t]).max() > fallback_dP for t in range(len(J_test))]
+    flag = {"spread": by_spread, "linear": by_linear,
+            "both": [a or b for a, b in zip(by_spread, by_linear)]}[rule]
+    bad_J = [J for t, J in enumerate(J_test) if flag[t]]
     final = Psur.astype(np.float64)
     t_fallback = 0.0
     if bad_J:
@@ -194,7 +205,6 @@ def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 1500, width: int =
     _, _, Pte_all, t_test = propagate_probabilities(cfg, J_test, steps, precision, device=device)
     Pte = Pte_all[..., keep]
     Pjs = jshift_baseline(E, np.asarray(J_train), Ptr, np.asarray(J_test))
-    Plin = linear_baseline(np.asarray(J_train), Ptr, np.asarray(J_test))
     err = np.abs(Psur - Pte)
     C_true = cumulative(J_test, Pte)
 
@@ -213,13 +223,25 @@ def run(cfg: dict, J_train, J_test, steps: int, epochs: int = 1500, width: int =
         cumulative_rel_err=dict(surrogate=crel(Psur), jshift=crel(Pjs), linear=crel(Plin),
                                 with_fallback=crel(final)),
         fallback_J=bad_J, fallback_fraction=len(bad_J) / len(J_test),
-        spread_factor=spread_factor,
+        spread_factor=spread_factor, rule=rule, e_stride=e_stride,
         # per held-out J: largest error over largest ensemble spread (calibration of the rule)
         error_over_spread=[float(err[t].max() / max(spread[t].max(), 1e-30))
                            for t in range(len(J_test))],
         passed_J_max_abs_dP=float(max([err[t].max() for t, J in enumerate(J_test) if J not in bad_J],
                                       default=0.0)),
         max_P_propagated=float(Pte.max()),
+        # every rule on the same predictions (the evaluation propagation stands in for its
+        # fallback propagations)
+        rules={name: dict(
+            fallback_J=[J for t, J in enumerate(J_test) if f[t]],
+            max_abs_dP=float(max(np.abs(np.where(f[t], Pte[t], Psur[t]) - Pte[t]).max()
+                                 for t in range(len(J_test)))),
+            passed_J_max_abs_dP=float(max([err[t].max() for t in range(len(J_test)) if not f[t]],
+                                          default=0.0)),
+            cumulative_rel_err=crel(np.asarray([Pte[t] if f[t] else Psur[t]
+                                                for t in range(len(J_test))])))
+            for name, f in (("spread", by_spread), ("linear", by_linear),
+                            ("both", [a or b for a, b in zip(by_spread, by_linear)]))},
         seconds=dict(propagate_train=t_train, fit=t_fit, predict=t_pred,
                      propagate_fallback=t_fallback, propagate_all_test=t_test,
                      surrogate_path=t_fit + t_pred + t_fallback),
@@ -253,11 +275,15 @@ def main(argv=None):
     ap.add_argument("--ensemble", type=int, default=3)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--spread-factor", type=float, default=2.0)
+    ap.add_argument("--e-stride", type=int, default=1,
+                    help="train on every n-th energy of the grid (all are predicted)")
+    ap.add_argument("--rule", default="spread", choices=["spread", "linear", "both"],
+                    help="fallback decision made without propagating the held-out J")
     args = ap.parse_args(argv)
     rep = run(c5_config(), W.C5["J_train"], W.C5["J_test"], steps=args.steps,
               epochs=args.epochs, batch=args.batch, ensemble=args.ensemble,
               precision=args.precision, fallback_dP=W.C5["fallback_dP"],
-              spread_factor=args.spread_factor)
+              spread_factor=args.spread_factor, e_stride=args.e_stride, rule=args.rule)
     print(json.dumps(rep, indent=1))
 
 

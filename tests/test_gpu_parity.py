@@ -241,8 +241,8 @@ def test_pending_ring_read_equals_flushed(prec, pending):
     Tolerances. The total: the on-the-fly read must reproduce the pending slots' own
     contribution (the change from the last flushed read) to 1e-9 of it in FP64 and to 1e-4 in
     the mixed form, whose flush multiplies on the tensor cores (split-TF32 products summed in
-    FP32 inside the MMA) while the read multiplies the same FP32 values in FP64. The channel
-    sums are FP64 in both forms (FP64 ring, phases and GEMM), so both use FP64 bounds."""
+    FP32 inside the MMA) while the read sums the FP32 products of the same values in FP32. The
+    channel sums are FP64 in both forms (FP64 ring, phases and GEMM), so both use FP64 bounds."""
     cfg = W.C2_SMALL
     kb = 16
     n0 = 12 * kb
