@@ -14,8 +14,8 @@
 //                 node v (4-point Lagrange stencils in R and r, Legendre series in gamma;
 //                 1/sqrt(dR dr) folded into wR), then the rotated, Jacobian-weighted node
 //                 values v'[Omega'][v] = jac_v sum_Omega T_v[Omega'][Omega] u_Omega.
-//   k_prod_dots   one warp per channel dots v'[Omega'(c)] with the channel's quadrature
-//                 weights W[c][v] and writes the overlap into its cut-ring column.
+//   k_prod_dots   four warps per channel dot v'[Omega'(c)] with the channel's quadrature
+//                 weights W[c][v] and write the overlap into its cut-ring column.
 #include <cuda_runtime.h>
 
 #include "mw3_internal.h"
@@ -90,21 +90,42 @@ __global__ void __launch_bounds__(1024) k_prod_nodes(const real* __restrict__ q,
   }
 }
 
-// One warp per channel: C_c = sum_v W[c][v] v'[group(c)][v], written to its cut column.
+// C_c = sum_v W[c][v] v'[group(c)][v], written to its cut column: four warps per channel
+// (two channels per CTA), each warp a quarter of the nodes with two independent partial sums
+// (the FP64 chain is the latency), then a fixed-order sum of the four warps (deterministic).
+constexpr int kDotWarps = 4;
 __global__ void __launch_bounds__(256) k_prod_dots(const double* __restrict__ vin, int nn,
                                                    const double* __restrict__ W,
                                                    const int2* __restrict__ chan, int nchan,
                                                    double* __restrict__ cut) {
+  __shared__ double part[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * 8 + warp;
-  if (c >= nchan) return;
-  const int2 gc = chan[c];   // (group, cut column)
-  const double* Wc = W + (long)c * nn;
-  const double* vg = vin + (long)gc.x * nn;
-  double s = 0;
-  for (int n = lane; n < nn; n += 32) s += Wc[n] * vg[n];
-  s = warp_sum(s);
-  if (lane == 0) cut[gc.y] = s;
+  const int local = warp / kDotWarps, sub = warp % kDotWarps;
+  const int c = blockIdx.x * (8 / kDotWarps) + local;
+  double s = 0.0;
+  if (c < nchan) {
+    const int2 gc = chan[c];   // (group, cut column)
+    const double* Wc = W + (long)c * nn;
+    const double* vg = vin + (long)gc.x * nn;
+    double s0 = 0.0, s1 = 0.0;
+    int n = sub * 32 + lane;
+    for (; n + 32 * kDotWarps < nn; n += 64 * kDotWarps) {
+      s0 += Wc[n] * vg[n];
+      s1 += Wc[n + 32 * kDotWarps] * vg[n + 32 * kDotWarps];
+    }
+    if (n < nn) s0 += Wc[n] * vg[n];
+    s = warp_sum(s0 + s1);
+  }
+  if (lane == 0) part[warp] = s;
+  __syncthreads();
+  if (threadIdx.x < 8 / kDotWarps) {
+    const int cc = blockIdx.x * (8 / kDotWarps) + threadIdx.x;
+    if (cc < nchan) {
+      double t = 0.0;
+      for (int w = 0; w < kDotWarps; ++w) t += part[threadIdx.x * kDotWarps + w];
+      cut[chan[cc].y] = t;
+    }
+  }
 }
 
 }  // namespace
@@ -121,7 +142,7 @@ cudaError_t launch_products(const real* q, int ng, int nr, int NR, int nn, const
                                                   groups, jl_group, vbuf);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_prod_dots<<<(nchan + 7) / 8, 256, 0, st>>>(vbuf, nn, W, chan, nchan, cut_slot);
+  k_prod_dots<<<(nchan + 1) / 2, 256, 0, st>>>(vbuf, nn, W, chan, nchan, cut_slot);
   return cudaGetLastError();
 }
 

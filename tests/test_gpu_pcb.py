@@ -50,8 +50,20 @@ def heavy_cfg(J, j0, om0, arrangement, masses):
     return cfg
 
 
+def two_state_batch_cfg():
+    """Several J in one batch (Omega blocks 0..min(J, 2)) and two diabatic states, the packet
+    in the second one: the carry fills only that state's blocks, every J with its own d^J."""
+    cfg = copy.deepcopy(W.C2_PCB_SMALL)
+    cfg["J"], cfg["omega_max"], cfg["nelec"] = [0, 2, 3], 2, 2
+    cfg["pes"] = dict(cfg["pes"], two_state=dict(W.TWO_STATE))
+    cfg["packet"] = dict(cfg["packet"], omega0=0, elec0=1)
+    cfg["grid"] = dict(cfg["grid"], ngamma=10)
+    return cfg
+
+
 CASES = {
     "h_dh_small": W.C2_PCB_SMALL,
+    "two_states_J0_2_3": two_state_batch_cfg(),
     "heavyC_AC+B_J2": heavy_cfg(2, 2, 1, "AC+B", (2.0, 1.0, 300.0)),
     "heavyB_AB+C_J2": heavy_cfg(2, 2, 2, "AB+C", (2.0, 300.0, 1.0)),
     "generic_AC+B_J3": heavy_cfg(3, 1, 0, "AC+B", (2.0, 1.3, 30.0)),
