@@ -73,23 +73,45 @@ __global__ void __launch_bounds__(256) k_mlp_gemm_t(int M, int N, int K, int kch
     else return static_cast<const float*>(Bp)[i];
   };
   float acc[8][4] = {};
-  for (int k0 = kbeg; k0 < kend; k0 += TBK) {
-    // A tile: with AT the storage is contiguous along m, else along k
+  // the next K tile is read from global memory into registers while the current one is
+  // multiplied from shared memory, so the loads overlap the arithmetic
+  constexpr int NA = TBM * TBK / 256, NB = TBN * TBK / 256;
+  float ra[NA], rb[NB];
+  auto fetch = [&](int k0) {
 #pragma unroll
-    for (int u = 0; u < TBM * TBK / 256; ++u) {
+    for (int u = 0; u < NA; ++u) {   // with AT the storage is contiguous along m, else along k
       const int e = tid + 256 * u;
       const int mm = AT ? (e % TBM) : (e / TBK), kk = AT ? (e / TBM) : (e % TBK);
       const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < kend) ? ldA(m, k) : 0.0f;
+      ra[u] = (m < M && k < kend) ? ldA(m, k) : 0.0f;
     }
 #pragma unroll
-    for (int u = 0; u < TBN * TBK / 256; ++u) {
+    for (int u = 0; u < NB; ++u) {
       const int e = tid + 256 * u;
       const int nn = BT ? (e / TBK) : (e % TBN), kk = BT ? (e % TBK) : (e / TBN);
       const int n = n0 + nn, k = k0 + kk;
-      Bs[kk][nn] = (n < N && k < kend) ? ldB(k, n) : 0.0f;
+      rb[u] = (n < N && k < kend) ? ldB(k, n) : 0.0f;
     }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const int e = tid + 256 * u;
+      const int mm = AT ? (e % TBM) : (e / TBK), kk = AT ? (e / TBM) : (e % TBK);
+      As[kk][mm] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int e = tid + 256 * u;
+      const int nn = BT ? (e / TBK) : (e % TBN), kk = BT ? (e % TBK) : (e / TBN);
+      Bs[kk][nn] = rb[u];
+    }
+  };
+  if (kbeg < kend) fetch(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += TBK) {
+    stash();
     __syncthreads();
+    if (k0 + TBK < kend) fetch(k0 + TBK);
 #pragma unroll
     for (int kk = 0; kk < TBK; ++kk) {
       const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][8 * ty]);
@@ -171,13 +193,34 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ y
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-// db[o] = sum_r g[r][o] (fixed order over r)
-__global__ void k_colsum(const float* __restrict__ g, int n, int nout, float* __restrict__ db) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= nout) return;
-  float s = 0;
-  for (int r = 0; r < n; ++r) s += g[(long)r * nout + o];
-  db[o] = s;
+// loss[0] = (sum_b partial[b]) / n, the block partials in order (one thread)
+__global__ void k_loss_sum(const double* __restrict__ partial, int nb, double n,
+                           double* __restrict__ loss) {
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partial[b];
+  *loss = s / n;
+}
+
+// db[o] = sum_r g[r][o] in two fixed-order stages: CTA (column tile, row chunk) sums its rows
+// with lane = column (coalesced) and warp = row stride 8, the eight warps in order; then the
+// chunks in order (k_sum_splits).
+constexpr int kColChunk = 512;
+__global__ void __launch_bounds__(256) k_colsum_part(const float* __restrict__ g, int n, int nout,
+                                                     float* __restrict__ part) {
+  __shared__ float red[8][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int o = blockIdx.x * 32 + lane;
+  const int r0 = blockIdx.y * kColChunk, r1 = min(n, r0 + kColChunk);
+  float s = 0.0f;
+  if (o < nout)
+    for (int r = r0 + warp; r < r1; r += 8) s += g[(long)r * nout + o];
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && o < nout) {
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t += red[w][lane];
+    part[(long)blockIdx.y * nout + o] = t;
+  }
 }
 
 // AdamW on FP32 master parameters; refreshes the BF16 copy of weights (wmask = 1).
@@ -323,7 +366,11 @@ int backward(mw3_mlp* net, long n) {
       k_sum_splits<<<(unsigned)std::min<long>((ne + 255) / 256, 1024), 256>>>(
           net->split, nsplit, ne, net->g + net->woff[l]);
     }
-    k_colsum<<<(N + 127) / 128, 128>>>(g, (int)n, N, net->g + net->boff[l]);
+    {
+      const int nchunk = (int)((n + kColChunk - 1) / kColChunk);
+      k_colsum_part<<<dim3((N + 31) / 32, nchunk), 256>>>(g, (int)n, N, net->split);
+      k_sum_splits<<<(N + 255) / 256, 256>>>(net->split, nchunk, N, net->g + net->boff[l]);
+    }
     if (l > 0) {
       // g_prev[r][i] = sum_o g[r][o] W[o][i] * gelu'(Z_(l-1)[r][i])
       // A(r, o) = g[r][o], B(o, i) = W[o][i] (BF16)
@@ -519,29 +566,48 @@ int mw3_mlp_train(mw3_mlp* net, const float* X, const float* y, long n, int epoc
   std::iota(perm.begin(), perm.end(), 0);
   double last = 0;
   const float b1 = 0.9f, b2 = 0.999f;
+  // per-step losses stay on the device until the end of the epoch, so the steps are queued
+  // without a host round trip each
+  const long steps_max = std::max<long>(1, n / batch + 1);
+  double* dloss = nullptr;
+  MCK(cudaMalloc(&dloss, steps_max * sizeof(double)));
+  std::vector<double> hloss(steps_max);
   for (int ep = 0; ep < epochs; ++ep) {
     std::shuffle(perm.begin(), perm.end(), rng);
     MCK(cudaMemcpy(net->idx, perm.data(), n * 4, cudaMemcpyHostToDevice));
-    double sum = 0;
     long cnt = 0;
     for (long r0 = 0; r0 + batch <= n || (r0 == 0 && n < batch); r0 += batch) {
       const long rows = std::min<long>(batch, n - r0);
       k_gather<<<(int)((rows + 255) / 256), 256>>>(net->Xall, net->yall, net->idx + r0, (int)rows,
                                                     net->nin, net->X, net->y);
-      if ((st = forward(net, rows))) return st;
-      const double l = mse_and_grad(net, rows, net->y);
-      if ((st = backward(net, rows))) return st;
+      if ((st = forward(net, rows))) {
+        cudaFree(dloss);
+        return st;
+      }
+      const int nb = (int)((rows + 255) / 256);
+      k_mse<<<nb, 256>>>(net->out, net->y, (int)rows, net->gout, net->partial);
+      k_loss_sum<<<1, 1>>>(net->partial, nb, (double)rows, dloss + cnt);
+      if ((st = backward(net, rows))) {
+        cudaFree(dloss);
+        return st;
+      }
       net->step += 1;
       const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
       k_adamw<<<(int)((net->nparam + 255) / 256), 256>>>(net->p, net->g, net->m, net->v, net->ph,
                                                          net->wmask, net->nparam, (float)lr, b1,
                                                          b2, 1e-8f, (float)wd, c1, c2);
-      sum += l;
       ++cnt;
       if (rows < batch) break;
     }
+    if (cudaMemcpy(hloss.data(), dloss, cnt * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaFree(dloss);
+      return mfail(net, MW3_ERR_CUDA, "mw3_mlp_train: loss read-back failed");
+    }
+    double sum = 0;
+    for (long i = 0; i < cnt; ++i) sum += hloss[i];
     last = cnt ? sum / cnt : 0;
   }
+  cudaFree(dloss);
   MCK(cudaDeviceSynchronize());
   if (final_loss) *final_loss = last;
   return MW3_OK;
