@@ -306,8 +306,9 @@ def run_ours(args, rank, world, local):
     qp_host = torch.empty(qp_dev.shape, dtype=torch.float32, pin_memory=True).numpy()
     q_host[...] = q_dev
     qp_host[...] = qp_dev
-    # two whole cycles of pending energy-ring reads (eight read on the fly, the ninth flushed)
-    e2e_steps = max(4, min(18, args.steps // 8))
+    # two whole cycles of pending energy-ring reads (the mixed form adds up to sixteen pending
+    # iterations on the fly; the seventeenth read flushes)
+    e2e_steps = max(4, min(34, args.steps // 8))
     # one untimed iteration: upload buffers, the copy stream and the cached packet amplitudes
     # are set up on first use
     pr.set_state_f32(q_host, qp_host)

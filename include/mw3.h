@@ -251,9 +251,9 @@ long mw3_iteration(const mw3_ctx* ctx);
  *   Pinel[nJ * nelec * (vmax+1) * (jmax+1) * nE] or NULL: reactant-channel
  *                    probabilities summed over Omega, zero for closed channels.
  * Every iteration run so far counts. Iterations still in the energy ring (a propagation that
- * stopped between flushes) are added on the fly when there are at most eight of them, else
- * flushed first; the |S|^2 assembly runs on the device and only the results are copied
- * back. The flux of the flushed sums is kept until the next flush; in MW3_MIXED the first
+ * stopped between flushes) are added on the fly when there are at most eight (MW3_FP64) or
+ * sixteen (MW3_MIXED) of them, else flushed first; the |S|^2 assembly runs on the device and
+ * only the results are copied back. The flux of the flushed sums is kept until the next flush; in MW3_MIXED the first
  * read after a flush also keeps an FP32 copy of the flux accumulators (half their size) from
  * which later reads add the pending iterations. Synchronous. */
 int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel);

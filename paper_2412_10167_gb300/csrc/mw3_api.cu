@@ -1928,7 +1928,7 @@ int flush(mw3_ctx* ctx, int nvalid, bool timed) {
                        ctx->an.nE, B.colbase, B.ncols, B.accoff, ctx->max_cols, B.acc,
                        (int*)dptr(ctx, "tc_err"), st));
   } else {
-    LK(launch_sums_flush<real>(B.ph, B.cut, ctx->NC, ctx->tune.kb, ctx->nJ, ctx->an.nE,
+    LK(launch_sums_flush<real>(B.ph, B.cut, ctx->NC, ctx->tune.kb, nvalid, ctx->nJ, ctx->an.nE,
                                B.colbase, B.ncols, B.accoff, ctx->max_cols, B.acc, st));
   }
   // channel overlaps: FP64 ring, FP64 phases, FP64 GEMM into their own accumulators
@@ -1936,7 +1936,7 @@ int flush(mw3_ctx* ctx, int nvalid, bool timed) {
     if (!std::is_same<real, double>::value)
       LK(launch_phases<double>(B.theta, ctx->nJ, ctx->an.nE, ctx->tune.kb, nvalid, B.d_iter,
                                B.ph64, st));
-    LK(launch_sums_flush<double>(B.ph64, B.cutc, ctx->NCc, ctx->tune.kb, ctx->nJ, ctx->an.nE,
+    LK(launch_sums_flush<double>(B.ph64, B.cutc, ctx->NCc, ctx->tune.kb, nvalid, ctx->nJ, ctx->an.nE,
                                  B.colbase_c, B.ncols_c, B.accoff_c, ctx->max_cols_c, B.accc, st));
   }
   LK(launch_advance(B.d_iter, nvalid, st));
@@ -2054,6 +2054,7 @@ int channel_accumulators(mw3_ctx* ctx, const double** out) {
   LK(launch_phases<double>((const double*)dptr(ctx, "theta"), ctx->nJ, ctx->an.nE, ctx->tune.kb,
                            ctx->ring_n, (const long*)dptr(ctx, "d_iter"), ph64, ctx->stream));
   LK(launch_sums_flush<double>(ph64, (const double*)dptr(ctx, "cutc"), ctx->NCc, ctx->tune.kb,
+                               ctx->ring_n,
                                ctx->nJ, ctx->an.nE, (const long*)dptr(ctx, "colbase_c"),
                                (const long*)dptr(ctx, "ncols_c"), (const long*)dptr(ctx, "accoff_c"),
                                ctx->max_cols_c, pk, ctx->stream));
@@ -2081,6 +2082,9 @@ int channel_probabilities(mw3_ctx* ctx, const double* accc, const ChanTable& t, 
   CK(cudaStreamSynchronize(ctx->stream));
   return MW3_OK;
 }
+
+// Pending ring slots a probability read adds on the fly (more are flushed first).
+int peek_max(const mw3_ctx* ctx) { return ctx->precision == MW3_FP64 ? kPeekMax : kPeekMaxX; }
 
 // The flux of the flushed accumulators alone into "fluxA" (and, in the mixed form, their FP32
 // copy "acc32"), unless the accumulators are unchanged since the last time.
@@ -2599,7 +2603,7 @@ int mw3_product_probabilities(mw3_ctx* ctx, double* P) {
   if (!ctx->prod_on) return ctx->fail(MW3_ERR_STATE, "product channels are not enabled");
   if (ctx->host_only) return ctx->fail(MW3_ERR_STATE, "host-only context");
   int st;
-  if (ctx->ring_n > kPeekMax && (st = flush_pending(ctx))) return st;
+  if (ctx->ring_n > peek_max(ctx) && (st = flush_pending(ctx))) return st;
   const double* accc = nullptr;   // with the pending ring slots added
   if ((st = channel_accumulators(ctx, &accc))) return st;
   return channel_probabilities(ctx, accc, ctx->chan_tab_p, P);
@@ -2618,7 +2622,7 @@ int mw3_flux_probabilities(mw3_ctx* ctx, double* E, double* Ptot, double* Pinel)
   if ((st = dalloc(ctx, "flux", (size_t)nJ * nE * 8))) return st;
   // a few pending ring slots are added on the fly (the accumulators are only read); more are
   // flushed first
-  if (ctx->ring_n > kPeekMax && (st = flush_pending(ctx))) return st;
+  if (ctx->ring_n > peek_max(ctx) && (st = flush_pending(ctx))) return st;
   if (ctx->ring_n > 0) {
     st = ctx->precision == MW3_FP64 ? flux_peek<double>(ctx) : flux_peek<float>(ctx);
     if (st) return st;

@@ -266,16 +266,18 @@ cudaError_t launch_phases(const double* theta, int nJ, int nE, int kb, int nvali
 }
 
 template <typename real>
-cudaError_t launch_sums_flush(const real* ph, const real* cut, long ncut_total, int kb, int nJ,
-                              int nE, const long* colbase, const long* ncols,
+cudaError_t launch_sums_flush(const real* ph, const real* cut, long ncut_total, int kb, int nvalid,
+                              int nJ, int nE, const long* colbase, const long* ncols,
                               const long* accoff, long max_cols, double* acc,
                               cudaStream_t st) {
+  if (nvalid < 1 || nvalid > kb) return cudaErrorInvalidValue;
   dim3 grid((unsigned)((max_cols + GBN - 1) / GBN), (unsigned)((2 * nE + GBM - 1) / GBM),
             (unsigned)nJ);
-  // M = 2 nE rows, K = kb ring slots, N = columns of each J (checked by the epilogue)
+  // M = 2 nE rows, K = the nvalid filled ring slots (the phases of the others are zero; ph
+  // rows keep their stride kb), N = columns of each J (checked by the epilogue)
   k_gemm<real, real, real><<<grid, GTHREADS, 0, st>>>(
-      2 * nE, max_cols, kb, LoadPh<real>{ph, 2 * nE, kb}, LoadCut<real>{cut, ncut_total, colbase, ncols},
-      EpiAcc<real>{acc, accoff, ncols});
+      2 * nE, max_cols, nvalid, LoadPh<real>{ph, 2 * nE, kb},
+      LoadCut<real>{cut, ncut_total, colbase, ncols}, EpiAcc<real>{acc, accoff, ncols});
   return cudaGetLastError();
 }
 
@@ -666,7 +668,7 @@ __global__ void __launch_bounds__(256) k_flux_cross(
     const long* __restrict__ ncols, const long* __restrict__ ncut, const float* __restrict__ ph,
     int kb, int npend, const float* __restrict__ cut, long ncut_total,
     const long* __restrict__ colbase, double* __restrict__ part) {
-  __shared__ float sph[kFluxE][2][kPeekMax];
+  __shared__ float sph[kFluxE][2][kPeekMaxX];
   __shared__ double red[kFluxE][256];
   const int e0 = blockIdx.x * kFluxE;
   const int iJ = blockIdx.y;
@@ -675,8 +677,8 @@ __global__ void __launch_bounds__(256) k_flux_cross(
   const long p0 = (long)blockIdx.z * kFluxChunk, p1 = min(np, p0 + kFluxChunk);
   const float* A = acc32 + accoff[iJ];
   const float* cj = cut + colbase[iJ];
-  for (int x = threadIdx.x; x < kFluxE * 2 * kPeekMax; x += blockDim.x) {
-    const int q = x / (2 * kPeekMax), prt = (x / kPeekMax) & 1, sl = x % kPeekMax;
+  for (int x = threadIdx.x; x < kFluxE * 2 * kPeekMaxX; x += blockDim.x) {
+    const int q = x / (2 * kPeekMaxX), prt = (x / kPeekMaxX) & 1, sl = x % kPeekMaxX;
     const int row = (prt ? nE : 0) + e0 + q;
     sph[q][prt][sl] = (q < ne && sl < npend) ? ph[((long)iJ * 2 * nE + row) * kb + sl] : 0.0f;
   }
@@ -687,9 +689,9 @@ __global__ void __launch_bounds__(256) k_flux_cross(
   for (int q = 0; q < kFluxE; ++q) accs[q][threadIdx.x] = 0.0f;
   __syncthreads();
   for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    float cp[kPeekMax], cq[kPeekMax];
+    float cp[kPeekMaxX], cq[kPeekMaxX];
 #pragma unroll
-    for (int sl = 0; sl < kPeekMax; ++sl) {
+    for (int sl = 0; sl < kPeekMaxX; ++sl) {
       cp[sl] = sl < npend ? cj[(long)sl * ncut_total + p] : 0.0f;
       cq[sl] = sl < npend ? cj[(long)sl * ncut_total + np + p] : 0.0f;
     }
@@ -700,7 +702,7 @@ __global__ void __launch_bounds__(256) k_flux_cross(
         const float* im = A + (long)(nE + e0 + q) * nc;
         float dra = 0, dia = 0, drb = 0, dib = 0;
 #pragma unroll
-        for (int sl = 0; sl < kPeekMax; ++sl) {
+        for (int sl = 0; sl < kPeekMaxX; ++sl) {
           if (sl < npend) {
             dra += sph[q][0][sl] * cp[sl];
             dia += sph[q][1][sl] * cp[sl];
@@ -775,7 +777,7 @@ cudaError_t launch_flux_cross(const float* acc32, int nJ, int nE, const long* ac
                               int kb, int npend, const float* cut, long ncut_total,
                               const long* colbase, double* part, const double* fluxA, double* out,
                               cudaStream_t st) {
-  if (npend < 0 || npend > kPeekMax) return cudaErrorInvalidValue;
+  if (npend < 0 || npend > kPeekMaxX || npend > kb) return cudaErrorInvalidValue;
   const int nz = (int)std::max<long>(1, (max_ncut + kFluxChunk - 1) / kFluxChunk);
   k_flux_cross<<<dim3((nE + kFluxE - 1) / kFluxE, nJ, nz), 256, 0, st>>>(
       acc32, nJ, nE, accoff, ncols, ncut, ph, kb, npend, cut, ncut_total, colbase, part);
@@ -841,8 +843,8 @@ cudaError_t launch_channel_probs(const double* acc, const ChanTable& t, const do
   template cudaError_t launch_phases<real>(const double*, int, int, int, int, const long*,    \
                                            real*, cudaStream_t);                              \
   template cudaError_t launch_sums_flush<real>(const real*, const real*, long, int, int, int, \
-                                               const long*, const long*, const long*, long,   \
-                                               double*, cudaStream_t);                        \
+                                               int, const long*, const long*, const long*,    \
+                                               long, double*, cudaStream_t);                  \
   template cudaError_t launch_channels<real>(const real*, const double*, const int*,          \
                                              const int*, const int*, int, int, int,           \
                                              const long*, int, long, double*, cudaStream_t);  \

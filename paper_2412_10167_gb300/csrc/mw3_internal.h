@@ -166,13 +166,16 @@ cudaError_t launch_phases(const double* theta, int nJ, int nE, int kb, int nvali
                           const long* d_iter, real* ph, cudaStream_t st);
 
 template <typename real>
-cudaError_t launch_sums_flush(const real* ph, const real* cut, long ncut_total, int kb,
+cudaError_t launch_sums_flush(const real* ph, const real* cut, long ncut_total, int kb, int nvalid,
                               int nJ, int nE, const long* colbase, const long* ncols,
                               const long* accoff, long max_cols, double* acc, cudaStream_t st);
 
 cudaError_t launch_advance(long* d_iter, long n, cudaStream_t st);
 // Ring slots a probability read adds on the fly instead of flushing them first.
 constexpr int kPeekMax = 8;
+// The same for the mixed form's reads, which add only the change of the pending slots from an
+// FP32 copy of the flushed accumulators (launch_flux_cross).
+constexpr int kPeekMaxX = 16;
 // out[iJ][e] = the same flux sum over A + Ph Cut for the npend pending ring slots (phases
 // ph[iJ][2 nE][kb] of those slots already computed), A read only.
 template <typename real>

@@ -233,7 +233,7 @@ def test_checkpoint_roundtrip():
 @pytest.mark.parametrize("pending", [1, 5, 8, 13])
 def test_pending_ring_read_equals_flushed(prec, pending):
     """A propagation that stops inside an energy ring leaves the slots pending: a probability
-    read adds up to eight of them on the fly (reading the accumulators only) and flushes more.
+    read adds up to eight (FP64) or sixteen (mixed) of them on the fly and flushes more.
     Either way the probabilities (total, reactant channels, product channels) equal those
     read after an explicit flush (a checkpoint save flushes); continuing afterwards gives the
     same state as one uninterrupted call.
