@@ -330,6 +330,7 @@ def run_ours(args, rank, world, local):
         tparts[2] += t3 - t2
     barrier()
     te = mdist.max_over_ranks(time.perf_counter() - te0)   # wall clock: host copies included
+    prod_launches = 3 if pr.get_tuning("prod_gather") else 2
     pr.close()
     del pr
 
@@ -433,7 +434,9 @@ def run_ours(args, rank, world, local):
     # kernels per timed launch group on the tensor-core mixed path: the angular step is the
     # tcgen05 kernel and the norm reduction, products are the node and dot kernels, a flush is
     # the phase table and the ring GEMM; the others are one kernel each
-    per_group = {"angular_tc": 2, "products": 2, "sums_flush": 2}
+    # (three for the products in the plane-major form: the column gather, the node sums and
+    # the dots)
+    per_group = {"angular_tc": 2, "products": prod_launches, "sums_flush": 2}
     launches = sum(v[1] * per_group.get(k, 1) for k, v in per.items())
 
     cpu = None
@@ -456,6 +459,11 @@ def run_ours(args, rank, world, local):
         "config": {"workload": WORKLOADS[args.config], "grid": [g["NR"], g["nr"], g["ngamma"]],
                    "J": cfg["J"] if len(cfg["J"]) > 1 else cfg["J"][0], "electronic_states": nelec,
                    "blocks": nblk, "energies": nE, "kb": kb,
+                   # energy rings that fill inside the timed region are flushed there; slots
+                   # of a ring still open at its end stay pending (a probability read adds
+                   # them), so K not a multiple of kb leaves that share of a flush untimed
+                   "flushes_timed": (args.warmup + args.steps) // kb - args.warmup // kb,
+                   "ring_slots_pending_after": (args.warmup + args.steps) % kb,
                    "l2": f"state vectors {nblk * npts * 4 / 1e6:.0f} MB each (> 129 MB L2), "
                          "no flush needed",
                    "parallelism": f"replicas x{world}"},

@@ -393,6 +393,12 @@ int mw3_product_probabilities(mw3_ctx* ctx, double* P);
  *                "up_direct_last" (read only) is 1 when the last upload did
  *   "tc_tma"     0/1: tile copies of the tile-major angular step by the tensor memory
  *                accelerator (2-D tensor maps) instead of cp.async; default 0
+ *   "prod_gather" 0/1: product-channel node sums (Section 2.4) in the plane-major form: the
+ *                distinct grid columns of all interpolation stencils are first copied, per
+ *                block, into rows that hold all FBR rows of a column contiguously (1, the
+ *                default), or the stencils are read from the state directly (0); both sum
+ *                the stencil terms in the state's precision and the rest in FP64;
+ *                "prod_points" (read only) is the number of distinct stencil columns
  * Values outside a key's range return MW3_ERR_BAD_ARG. mw3_get_tuning reads a key. */
 int mw3_set_tuning(mw3_ctx* ctx, const char* key, long value);
 long mw3_get_tuning(const mw3_ctx* ctx, const char* key);

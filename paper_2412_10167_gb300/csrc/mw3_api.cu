@@ -90,7 +90,7 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1, 0, 0, 0};
+  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1, 0, 0, 0, 1};
   int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   int kh = 0;          // parity-split operand size, resident form (0: not applicable)
@@ -161,6 +161,12 @@ struct mw3_ctx {
   int prod_nn = 0, prod_ltop = 0;
   std::vector<int> prod_idx;               // [node][8]: R stencil, then r stencil
   std::vector<double> prod_w;              // [node][8] Lagrange weights (R ones / sqrt(dR dr))
+  // plane-major form: distinct stencil columns r * NR + R, sorted and padded to a multiple of
+  // 32 (prod_spad) with copies of the last one; per node and stencil point s = 4 c + a its
+  // row in that list and the weight wR_a wr_c; FBR rows padded to prod_ngp
+  std::vector<int> prod_pts, prod_pix;
+  std::vector<double> prod_wst;
+  int prod_npts = 0, prod_spad = 0, prod_ngp = 0;
   std::vector<double> prod_pl;             // [node][ltop][ng] P-bar_(Omega+i)^Omega(cos gamma)
   std::vector<double> prod_T;              // per J: [node][nom][nom] helicity transforms
   std::vector<double> prod_jac;            // [node] r'R'/(rR)
@@ -1308,6 +1314,31 @@ int mw3_set_products(mw3_ctx* ctx, const mw3_products_desc* d) {
               &ctx->prod_w[(size_t)v * 8 + 4], 1.0);
       ctx->prod_jac[v] = rp[a] * d->Rinf / (r * R);
     }
+  {   // plane-major form: the distinct stencil columns, sorted, and each node's rows in them
+    std::vector<int> cols((size_t)nn * 16);
+    for (int v = 0; v < nn; ++v)
+      for (int c = 0; c < 4; ++c)
+        for (int a = 0; a < 4; ++a)
+          cols[(size_t)v * 16 + 4 * c + a] =
+              ctx->prod_idx[(size_t)v * 8 + 4 + c] * ctx->NR + ctx->prod_idx[(size_t)v * 8 + a];
+    std::vector<int> u(cols);
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end()), u.end());
+    ctx->prod_npts = (int)u.size();
+    ctx->prod_spad = (ctx->prod_npts + 31) / 32 * 32;
+    ctx->prod_ngp = (ng + 31) / 32 * 32;
+    ctx->prod_pts = u;
+    ctx->prod_pts.resize(ctx->prod_spad, u.back());
+    ctx->prod_pix.resize((size_t)nn * 16);
+    ctx->prod_wst.resize((size_t)nn * 16);
+    for (int v = 0; v < nn; ++v)
+      for (int c = 0; c < 4; ++c)
+        for (int a = 0; a < 4; ++a) {
+          const size_t k = (size_t)v * 16 + 4 * c + a;
+          ctx->prod_pix[k] = (int)(std::lower_bound(u.begin(), u.end(), cols[k]) - u.begin());
+          ctx->prod_wst[k] = ctx->prod_w[(size_t)v * 8 + a] * ctx->prod_w[(size_t)v * 8 + 4 + c];
+        }
+  }
   // Legendre rows of every helicity at the nodes' reactant angles
   int ltop = 0;
   for (int iJ = 0; iJ < ctx->nJ; ++iJ) ltop = std::max(ltop, ctx->omtop[iJ] + 1);
@@ -1591,6 +1622,13 @@ int mw3_set_analysis(mw3_ctx* ctx, const mw3_analysis_desc* d) {
         (st = upload_real(ctx, "p_W", ctx->prod_W, true)) ||
         (st = upload_raw(ctx, "p_groups", ctx->prod_groups)) ||
         (st = dalloc(ctx, "p_v", ctx->prod_groups.size() * (size_t)ctx->prod_nn * 8)))
+      return st;
+    // plane-major form: the stencil weights wR_a wr_c in the state's precision (they multiply
+    // the state in the sixteen-term stencil sums), the gathered rows of every block
+    if ((st = upload_raw(ctx, "p_pts", ctx->prod_pts)) ||
+        (st = upload_raw(ctx, "p_pix", ctx->prod_pix)) ||
+        (st = upload_real(ctx, "p_wst", ctx->prod_wst)) ||
+        (st = dalloc(ctx, "p_G", (size_t)ctx->nblk * ctx->prod_spad * ctx->prod_ngp * ctx->rs())))
       return st;
   }
   if ((st = dalloc(ctx, "d_iter", 8))) return st;
@@ -1883,6 +1921,9 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
   }
   if (analysis && ctx->prod_on) {
     Timer tm(ctx, 8, timed);
+    ProdGather<real> pg{(const int*)dptr(ctx, "p_pts"), (const int*)dptr(ctx, "p_pix"),
+                        (const real*)dptr(ctx, "p_wst"), (real*)dptr(ctx, "p_G"), ctx->prod_spad,
+                        ctx->prod_ngp, B.blocks, ctx->nblk};
     LK(launch_products<real>(qk, ctx->ng, ctx->nr, ctx->NR, ctx->prod_nn,
                              (const int*)dptr(ctx, "p_idx"), (const double*)dptr(ctx, "p_w"),
                              (const real*)dptr(ctx, "p_pl"), ctx->prod_ltop,
@@ -1890,7 +1931,8 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
                              (const ProdGroup*)dptr(ctx, "p_groups"), (const int*)dptr(ctx, "p_jl"),
                              (int)ctx->prod_jl.size(), ctx->prod_max_nom, (double*)dptr(ctx, "p_v"),
                              (const double*)dptr(ctx, "p_W"), (const int2*)dptr(ctx, "p_chan"),
-                             (int)ctx->prod_first[ctx->nJ], cutc_slot, st));
+                             (int)ctx->prod_first[ctx->nJ], cutc_slot,
+                             ctx->tune.prod_gather ? &pg : nullptr, st));
     tm.stop();
   }
   if (!tc) {
@@ -2686,6 +2728,8 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
   } else if (k == "tc_tma") {
     ctx->tune.tc_tma = v != 0;
     drop_graphs();
+  } else if (k == "prod_gather") {
+    ctx->tune.prod_gather = v != 0;
   } else if (k == "tc_persist") {
     if (v < 0 || v > 4) return ctx->fail(MW3_ERR_BAD_ARG, "tc_persist must be in 0..4");
     ctx->tune.tc_persist = (int)v;
@@ -2711,6 +2755,8 @@ long mw3_get_tuning(const mw3_ctx* ctx, const char* key) {
   if (k == "kin_warp") return ctx->tune.kin_warp;
   if (k == "tc_persist") return ctx->tune.tc_persist;
   if (k == "tc_tma") return ctx->tune.tc_tma;
+  if (k == "prod_gather") return ctx->tune.prod_gather;
+  if (k == "prod_points") return ctx->prod_npts;
   if (k == "kin_fused") return ctx->tune.kin_fused;
   if (k == "up_direct") return ctx->tune.up_direct;
   if (k == "up_direct_last") return ctx->up_direct_last ? 1 : 0;

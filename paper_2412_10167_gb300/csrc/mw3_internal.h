@@ -81,6 +81,8 @@ struct Tuning {
                     // 4.49 against 5.05 ms for both state vectors of config 2)
   int tc_tma;       // tile-major angular step: tile copies by TMA (1) or cp.async (0, the
                     // default: 0.380 against 0.399 ms per step on config 2)
+  int prod_gather;  // product-channel node sums: stencil columns gathered plane-major first
+                    // (1) or read as 4 x 4 stencils straight from the state (0)
 };
 
 // --------------------------------------------------------------- launchers
@@ -252,12 +254,29 @@ struct ProdGroup {
 // accumulated in FP64 whatever the state's precision: the state (real) times the Legendre
 // rows (real) in partial sums of eight rows, FP64 across them and in every later stage
 // (stencil weights, helicity rotation, Jacobian, channel dots); cut is the FP64 channel ring.
+// Plane-major form of the node sums (tuning key "prod_gather"): the distinct (r, R) grid
+// columns of all stencils, sorted (pts, padded to spad, a multiple of 32, with copies of the
+// last column), are first gathered per block into G[b][s][i] (rows padded to ngp, a multiple
+// of 32); node v then takes stencil point s (= 4 c + a) from row pix[v][s] of G with the
+// weight wst[v][s] = wR_a wr_c. Unset (gather == nullptr): the stencils are read from q.
+template <typename real>
+struct ProdGather {
+  const int* pts;
+  const int* pix;
+  const real* wst;
+  real* G;
+  int spad, ngp;
+  const DevBlock* blocks;
+  int nblk;
+};
+
 template <typename real>
 cudaError_t launch_products(const real* q, int ng, int nr, int NR, int nn, const int* idx,
                             const double* w, const real* pl, int ltop, const double* T,
                             const double* jac, const ProdGroup* groups, const int* jl_group,
                             int njl, int max_nom, double* vbuf, const double* W, const int2* chan,
-                            int nchan, double* cut_slot, cudaStream_t st);
+                            int nchan, double* cut_slot, const ProdGather<real>* gather,
+                            cudaStream_t st);
 
 // Fused tensor-core angular step (mw3_tc.cu), FP32 state, ngamma padded to kp <= 112.
 struct TcArgs {

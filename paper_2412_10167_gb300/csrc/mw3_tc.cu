@@ -1504,10 +1504,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
   // once the copy groups it needs have landed (all, or all but the newest: visible to the tensor
   // core) and the operand stores to tensor memory are complete; the wait comes later, so that
   // CUDA-core work overlaps the MMAs
-  auto issue_mma2 = [&](uint32_t de, uint32_t dodd, bool one_pending) {
+  auto issue_mma2 = [&](uint32_t de, uint32_t dodd, bool gemm1) {
     tmem_st_wait();
-    // TMA form: the only cp.async group in flight is the half matrices this GEMM needs
-    if (one_pending && !TMA) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    // GEMM 1 of unit u: the groups [t(u)] and [c_(k-1)(u)] may still be in flight (the
+    // remainder reads them after GEMM 2 is issued). TMA form: the only cp.async groups are
+    // half matrices, all of which this GEMM needs.
+    if (gemm1 && !TMA) asm volatile("cp.async.wait_group 2;" ::: "memory");
     else asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1529,17 +1531,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
     asm volatile("tcgen05.fence::after_thread_sync;");
   };
 
-  // Copy groups, in commit order: [c(u)] during GEMM 1 of unit u-1, [t(u), G1e G1o(u)] after
-  // GEMM 2 of unit u-1, [c_(k-1)(u)] after the result of unit u-1 is written, [G2e G2o(u)]
-  // after GEMM 1 of unit u; the first unit's three come from here.
+  // Copy groups, in commit order: [c(u)] during GEMM 1 of unit u-1, [G1e G1o(u)] and then
+  // [t(u)] after GEMM 2 of unit u-1, [c_(k-1)(u)] after the result of unit u-1 is written,
+  // [G2e G2o(u)] after GEMM 1 of unit u; the first unit's four come from here. GEMM 1 of unit
+  // u waits for [G1e G1o(u)] only, so the t tile's DRAM latency overlaps GEMM 1 and the
+  // potential; GEMM 2's wait (all groups) covers everything the remainder reads.
   // (TMA form: the tile copies complete on their own barriers; only the half-matrix groups
   // remain cp.async groups.)
   const int b00 = u0 < u1 ? unit_block(u0) : 0;
   const long c00 = u0 < u1 ? (long)unit_tile(u0) * TC_M : 0;
   if (u0 < u1) stage(0, cs, a.ck + (long)b00 * a.npts, b00, a.blocks[b00].nrow, c00);
   asm volatile("cp.async.commit_group;" ::: "memory");
-  if (u0 < u1) stage(1, ts, a.t + (long)b00 * a.npts, b00, a.blocks[b00].nrow, c00);
   issue_b2(u0, 0);
+  if (u0 < u1) stage(1, ts, a.t + (long)b00 * a.npts, b00, a.blocks[b00].nrow, c00);
+  asm volatile("cp.async.commit_group;" ::: "memory");
   if (u0 < u1 && a.mode == 0)
     stage(2, ps, a.ckm1 + (long)b00 * a.npts, b00, a.blocks[b00].nrow, c00);
   asm volatile("cp.async.commit_group;" ::: "memory");
@@ -1569,9 +1574,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
       // tensor memory are done: one barrier
       ok = __syncthreads_and(wait_tiles_local(1) ? 1 : 0) != 0;
       if (!ok) break;
-    } else {
-      __syncthreads();   // previous unit's readers of ts, ps, cs and tensor memory are done
-      asm volatile("cp.async.wait_group 2;" ::: "memory");   // this unit's c tile
+    } else if (u == u0) {
+      // the first unit's c tile: groups [c], [G1e G1o], [t], [c_(k-1)] are in flight. Later
+      // units need no wait here: their c tile was part of the previous unit's GEMM 2 wait,
+      // whose CTA barrier made it visible, and the previous unit's closing barrier orders
+      // every reader of ts, ps, cs and tensor memory before this unit's writes.
+      asm volatile("cp.async.wait_group 3;" ::: "memory");
       __syncthreads();
     }
     // ---- GEMM 1 operands (both parities) and the raw c tile, from shared memory
@@ -1601,7 +1609,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
     }
     // ---- GEMM 1: E = c_even G1e, O = c_odd G1o. While it runs: stage the next unit's c tile
     // (this unit's upper neighbour), and on a new tile load the potential
-    issue_mma2(tE, tO, true);                     // [t G1e G1o](u) landed; [c_(k-1)](u) may not
+    issue_mma2(tE, tO, true);                     // [G1e G1o](u) landed; [t], [c_(k-1)](u) may not
     if (u + 1 < u1) {
       const int bn = unit_block(u + 1);
       stage(0, cs, a.ck + (long)bn * a.npts, bn, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
@@ -1743,12 +1751,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
     }
     wait_mma(tiles_ok);
     if (!ok) break;
-    // t is free: the next unit's t with its G1e G1o, one group
+    // t is free: the next unit's G1e G1o, then its t, one group each
+    issue_b2(u + 1, 0);
     if (u + 1 < u1) {
       const int bn = unit_block(u + 1);
       stage(1, ts, a.t + (long)bn * a.npts, bn, a.blocks[bn].nrow, (long)unit_tile(u + 1) * TC_M);
     }
-    issue_b2(u + 1, 0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
 
     // ---- result = k1 w + r2, eight rows per tensor-memory wait (w even: rows i0, i0 + 2, ...;
     // w odd: rows i0 + 1, i0 + 3, ...); rows nrow..ng-1 of the block are zero

@@ -16,6 +16,8 @@ library's own per-kernel CUDA-event timers (mw3_kernel_times) over a sweep of
   tc_tma      tile copies of the tile-major angular step by the tensor memory
               accelerator (1) or cp.async (0),
   flush_tc    energy-sum flush on the tensor cores (1) or the CUDA cores (0),
+  prod_gather product-channel node sums from stencil columns gathered plane-major
+              first (1) or from 4 x 4 stencils read straight from the state (0),
   kb          iterations per energy-sum flush (ring depth),
 and keeps, for each knob, the value with the lowest time of the kernels it
 controls. Results are cached in a JSON file keyed by the shape, so a later
@@ -33,12 +35,13 @@ DEFAULT_CACHE = os.environ.get("MW3_TUNE_CACHE",
                                os.path.join(os.path.expanduser("~"), ".cache", "mw3_tuning.json"))
 
 SWEEP = dict(kin_warp=[2, 3, 1, 0], kin_fused=[0, 1, 2, 4, 8], rows_pairs=[2, 4, 8, 16], cols_tile=[8, 16, 32, 64],
-             tc_persist=[4, 2, 1, 0], tc_tma=[0, 1], flush_tc=[1, 0], kb=[32, 64, 128])
+             tc_persist=[4, 2, 1, 0], tc_tma=[0, 1], flush_tc=[1, 0], prod_gather=[1, 0],
+             kb=[32, 64, 128])
 RADIAL = ["kinetic_rows", "kinetic_cols", "kinetic_radial"]
 CONTROLS = dict(kin_warp=RADIAL, kin_fused=RADIAL, rows_pairs=["kinetic_rows"],
                 cols_tile=["kinetic_cols"],
                 tc_persist=["angular_tc", "gamma_to_dvr", "gamma_update"], tc_tma=["angular_tc"],
-                flush_tc=["sums_flush"], kb=["sums_flush"])
+                flush_tc=["sums_flush"], prod_gather=["products"], kb=["sums_flush"])
 
 
 def shape_key(cfg: dict, precision: str) -> str:

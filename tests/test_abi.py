@@ -47,6 +47,24 @@ def test_host_setup_matches_oracle(name):
     assert pr.shape == H.shape
 
 
+@pytest.mark.parametrize("name", ["c2s", "c3s", "c4s"])
+def test_product_stencil_columns_host(name):
+    """Plane-major product-channel sums (tuning key prod_gather, the default): the set-up
+    gathers each distinct grid column of the 4 x 4 interpolation stencils once; their
+    number equals the count from the oracle's own product quadrature stencils (Section
+    2.4; points beyond the grid are column 0 with weight 0 on both sides)."""
+    from paper_2412_10167_gb300 import mw3
+    from oracle import products as PR
+    cfg = W.SMALL[name]
+    pr = mw3.Propagator(cfg, device=-1)
+    H = GridHamiltonian(cfg)
+    pa = PR.ProductAnalysis(H, cfg["analysis"]["products"])
+    cols = {int(k) * H.NR + int(m) for n in range(len(pa.R)) for k in pa.kidx[n] for m in pa.midx[n]}
+    assert pr.get_tuning("prod_gather") == 1
+    assert pr.get_tuning("prod_points") == len(cols)
+    assert pr.set_tuning("prod_gather", 0) is None and pr.get_tuning("prod_gather") == 0
+
+
 def test_error_paths_host_only():
     from paper_2412_10167_gb300 import mw3
     lib = mw3.lib

@@ -123,17 +123,20 @@ def test_propagation_fp64_parity(name):
 
 @pytest.mark.parametrize("name", ["c2s", "c3s", "c4s"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_product_channels_match_oracle(name, prec):
+@pytest.mark.parametrize("gather", [1, 0])
+def test_product_channels_match_oracle(name, prec, gather):
     """Product-channel probabilities (Eq. S-matrix-from-chebyshev) from a random first
     iterate that already overlaps the product surface: FP64 to 1e-9 of the largest
     value (summation order only), the mixed path to 1e-3 of it (FP32 state and sums
-    within a flush block)."""
+    within a flush block). Both forms of the node sums: stencil columns gathered
+    plane-major first (gather 1) and stencils read from the state (gather 0)."""
     cfg = W.SMALL[name]
     H = GridHamiltonian(cfg)
     q0 = H.project(W.random_unit_state(H.shape, 31))
     N = 12
     ref = P.propagate(cfg, nsteps=N, H=H, q0=q0)
-    pr = mw3().Propagator(cfg, precision=prec)
+    pr = mw3().Propagator(cfg, precision=prec, tuning={"prod_gather": gather})
+    assert pr.get_tuning("prod_gather") == gather
     pr.set_state(q0)
     pr.propagate(N)
     got = pr.product_probabilities()
