@@ -131,6 +131,19 @@ def peaks():
         return {}
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_oracle_rate(nsteps):
     """Times the FP64 oracle (as it stands) for nsteps Chebyshev iterations of the
     workload in a child process on all host cores; returns (steps/s, cores, seconds)."""
@@ -184,6 +197,7 @@ def run_reference(args, rank, world):
         "config": {"workload": WORKLOAD, "grid_pts_omega": npts, "energies": 500},
         "grid_pts_omega_per_s": rate * npts,
         "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(),
                          "sample": f"{n_timed} oracle iterations of the full workload "
                                    f"({secs:.1f} s; --steps {args.steps} capped at {REF_MAX_STEPS})"},
         "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -444,6 +458,7 @@ def run_ours(args, rank, world, local):
         try:
             rate, cores, secs = cpu_oracle_rate(args.cpu_sample_steps)
             cpu = {"value": rate, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                   "cpu_model": cpu_model(),
                    "sample": f"{args.cpu_sample_steps} FP64 oracle iterations of the full workload "
                              f"({secs:.1f} s)"}
         except Exception as e:  # report, do not hide

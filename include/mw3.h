@@ -399,6 +399,12 @@ int mw3_product_probabilities(mw3_ctx* ctx, double* P);
  *                default), or the stencils are read from the state directly (0); both sum
  *                the stencil terms in the state's precision and the rest in FP64;
  *                "prod_points" (read only) is the number of distinct stencil columns
+ *   "tc_wait_limit" 0..2^22: polls of each bounded mbarrier wait of the tile-major angular
+ *                step (default 2^22). A wait that runs out makes its CTA stop, wait (with the
+ *                full 2^22 bound) for the tensor-core work already committed, free its tensor
+ *                memory and set the error word that mw3_propagate returns as
+ *                MW3_ERR_TIMEOUT; 0 makes every wait run out (the failure-detection test).
+ *                The context is not usable for propagation after a timeout; the device is.
  * Values outside a key's range return MW3_ERR_BAD_ARG. mw3_get_tuning reads a key. */
 int mw3_set_tuning(mw3_ctx* ctx, const char* key, long value);
 long mw3_get_tuning(const mw3_ctx* ctx, const char* key);

@@ -90,7 +90,7 @@ struct mw3_ctx {
   void* alloc_user = nullptr;
   std::string err;
   int stage = 0;  // 1 grid, 2 potential, 3 packet, 4 absorber, 5 analysis
-  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1, 0, 0, 0, 1};
+  Tuning tune{4, 32, 32, 1, 0, 2, 4, 1, 0, 0, 0, 1, 1L << 22};
   int nsm = 152;       // streaming multiprocessors of the device
   int kp = 0;          // ngamma padded to a multiple of 16 (tensor-core path)
   int kh = 0;          // parity-split operand size, resident form (0: not applicable)
@@ -1864,6 +1864,7 @@ int step(mw3_ctx* ctx, int slot, bool first, bool timed, int mode = 0, real* hs_
     a.out = (float*)hs_out;
     a.npart = mode == 0 ? (double*)dptr(ctx, "npart") : nullptr;
     a.err = (int*)dptr(ctx, "tc_err");
+    a.wait_limit = ctx->tune.tc_wait_limit;
     a.erot = (float)ctx->erot;
     a.alpha = first ? 1.0f : 2.0f;
     a.beta = first ? 0.0f : 1.0f;
@@ -2730,6 +2731,9 @@ int mw3_set_tuning(mw3_ctx* ctx, const char* key, long v) {
     drop_graphs();
   } else if (k == "prod_gather") {
     ctx->tune.prod_gather = v != 0;
+  } else if (k == "tc_wait_limit") {
+    if (v < 0 || v > (1L << 22)) return ctx->fail(MW3_ERR_BAD_ARG, "tc_wait_limit must be in 0..2^22");
+    ctx->tune.tc_wait_limit = v;
   } else if (k == "tc_persist") {
     if (v < 0 || v > 4) return ctx->fail(MW3_ERR_BAD_ARG, "tc_persist must be in 0..4");
     ctx->tune.tc_persist = (int)v;
@@ -2756,6 +2760,7 @@ long mw3_get_tuning(const mw3_ctx* ctx, const char* key) {
   if (k == "tc_persist") return ctx->tune.tc_persist;
   if (k == "tc_tma") return ctx->tune.tc_tma;
   if (k == "prod_gather") return ctx->tune.prod_gather;
+  if (k == "tc_wait_limit") return ctx->tune.tc_wait_limit;
   if (k == "prod_points") return ctx->prod_npts;
   if (k == "kin_fused") return ctx->tune.kin_fused;
   if (k == "up_direct") return ctx->tune.up_direct;

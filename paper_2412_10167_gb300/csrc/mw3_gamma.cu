@@ -663,12 +663,16 @@ __global__ void __launch_bounds__(256) k_flux_partial(
 // (A = psi column p, B = dpsi column np + p). The pending terms and their products with A
 // are FP32 values like the flush's own products; each thread sums its points in FP32 and the
 // CTA in FP64, so the FP64 accumulators are not read at all.
+// A thread takes two neighbouring points at a time (8-byte loads: cut columns start at
+// multiples of 4, the accumulator rows and np are even because NR is) and keeps their pending
+// ring values in registers for all of the CTA's energies; each phase value read from shared
+// memory then serves four products.
 __global__ void __launch_bounds__(256) k_flux_cross(
     const float* __restrict__ acc32, int nJ, int nE, const long* __restrict__ accoff,
     const long* __restrict__ ncols, const long* __restrict__ ncut, const float* __restrict__ ph,
     int kb, int npend, const float* __restrict__ cut, long ncut_total,
     const long* __restrict__ colbase, double* __restrict__ part) {
-  __shared__ float sph[kFluxE][2][kPeekMaxX];
+  __shared__ __align__(16) float sph[kFluxE][2][kPeekMaxX];
   __shared__ double red[kFluxE][256];
   const int e0 = blockIdx.x * kFluxE;
   const int iJ = blockIdx.y;
@@ -682,36 +686,48 @@ __global__ void __launch_bounds__(256) k_flux_cross(
     const int row = (prt ? nE : 0) + e0 + q;
     sph[q][prt][sl] = (q < ne && sl < npend) ? ph[((long)iJ * 2 * nE + row) * kb + sl] : 0.0f;
   }
-  // a thread's FP32 sums in shared memory (it owns its column): four energies at a time keep the
-  // register count, and the occupancy, up
+  // a thread's FP32 sums in shared memory (it owns its column): the energy loop stays rolled,
+  // so that the phases are read per energy instead of being held in registers across points
   __shared__ float accs[kFluxE][256];
 #pragma unroll
   for (int q = 0; q < kFluxE; ++q) accs[q][threadIdx.x] = 0.0f;
   __syncthreads();
-  for (long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    float cp[kPeekMaxX], cq[kPeekMaxX];
+  for (long p = p0 + 2 * threadIdx.x; p < p1; p += 2 * blockDim.x) {
+    float2 cp[kPeekMaxX], cq[kPeekMaxX];
 #pragma unroll
     for (int sl = 0; sl < kPeekMaxX; ++sl) {
-      cp[sl] = sl < npend ? cj[(long)sl * ncut_total + p] : 0.0f;
-      cq[sl] = sl < npend ? cj[(long)sl * ncut_total + np + p] : 0.0f;
+      const float* c = cj + (long)sl * ncut_total + p;
+      cp[sl] = sl < npend ? *reinterpret_cast<const float2*>(c) : make_float2(0.0f, 0.0f);
+      cq[sl] = sl < npend ? *reinterpret_cast<const float2*>(c + np) : make_float2(0.0f, 0.0f);
     }
-#pragma unroll 4
-    for (int q = 0; q < kFluxE; ++q) {
-      if (q < ne) {
-        const float* re = A + (long)(e0 + q) * nc;
-        const float* im = A + (long)(nE + e0 + q) * nc;
-        float dra = 0, dia = 0, drb = 0, dib = 0;
+#pragma unroll 1
+    for (int q = 0; q < ne; ++q) {
+      {
+        const float* re = A + (long)(e0 + q) * nc + p;
+        const float* im = A + (long)(nE + e0 + q) * nc + p;
+        const float2 ra = *reinterpret_cast<const float2*>(re);
+        const float2 ia = *reinterpret_cast<const float2*>(im);
+        const float2 rb = *reinterpret_cast<const float2*>(re + np);
+        const float2 ib = *reinterpret_cast<const float2*>(im + np);
+        float2 dra = make_float2(0.0f, 0.0f), dia = dra, drb = dra, dib = dra;
 #pragma unroll
         for (int sl = 0; sl < kPeekMaxX; ++sl) {
           if (sl < npend) {
-            dra += sph[q][0][sl] * cp[sl];
-            dia += sph[q][1][sl] * cp[sl];
-            drb += sph[q][0][sl] * cq[sl];
-            dib += sph[q][1][sl] * cq[sl];
+            const float pr = sph[q][0][sl], pi = sph[q][1][sl];
+            dra.x += pr * cp[sl].x;
+            dra.y += pr * cp[sl].y;
+            dia.x += pi * cp[sl].x;
+            dia.y += pi * cp[sl].y;
+            drb.x += pr * cq[sl].x;
+            drb.y += pr * cq[sl].y;
+            dib.x += pi * cq[sl].x;
+            dib.y += pi * cq[sl].y;
           }
         }
-        const float ra = re[p], ia = im[p], rb = re[np + p], ib = im[np + p];
-        accs[q][threadIdx.x] += ra * dib + dra * ib - ia * drb - dia * rb + dra * dib - dia * drb;
+        accs[q][threadIdx.x] += (ra.x * dib.x + dra.x * ib.x - ia.x * drb.x - dia.x * rb.x +
+                                 dra.x * dib.x - dia.x * drb.x) +
+                                (ra.y * dib.y + dra.y * ib.y - ia.y * drb.y - dia.y * rb.y +
+                                 dra.y * dib.y - dia.y * drb.y);
       }
     }
   }

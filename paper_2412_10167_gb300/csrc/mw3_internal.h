@@ -83,6 +83,8 @@ struct Tuning {
                     // default: 0.380 against 0.399 ms per step on config 2)
   int prod_gather;  // product-channel node sums: stencil columns gathered plane-major first
                     // (1) or read as 4 x 4 stencils straight from the state (0)
+  long tc_wait_limit;   // polls of the tile-major angular step's bounded waits (2^22; smaller
+                        // values serve the failure-detection test)
 };
 
 // --------------------------------------------------------------- launchers
@@ -298,6 +300,8 @@ struct TcArgs {
   float* out;           // mode 1: H_s c
   double* npart;        // [group][tile] sums of squares of c_(k+1)
   int* err;             // set on a wait that timed out
+  long wait_limit;      // polls of a bounded wait in the tile-major form (the wait for the MMAs
+                        // of an expired phase before tensor memory is freed keeps 2^22)
   float erot, alpha, beta;
   long ncol, npts;
   int ng, kp, NR, nelec, mode, ntiles, tmem_cols;

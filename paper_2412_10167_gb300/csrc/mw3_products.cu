@@ -150,8 +150,9 @@ __global__ void __launch_bounds__(256) k_prod_gather(const real* __restrict__ q,
 // Node sums from the gathered rows: CTA (node v, (J, Lambda')), warp Omega; lane l takes the
 // rows i = l, l + 32, ...: per row the stencil combination sum_s wst_s G[b][pix_s][i] in the
 // state's precision (sixteen terms), times P-bar_(Omega+i)^Omega(cos gamma_v), the product
-// and the sums over rows and lanes in FP64. Then the same helicity rotation.
-template <typename real>
+// and the sums over rows and lanes in FP64. Then the same helicity rotation. NCH = ngp / 32
+// row chunks at compile time (all of them in flight per stencil point); NCH = 0: any ngp.
+template <typename real, int NCH>
 __global__ void __launch_bounds__(1024) k_prod_nodes_g(const real* __restrict__ Gs, int ng, int ngp,
                                                        int spad, int nn,
                                                        const int* __restrict__ pix,
@@ -172,21 +173,33 @@ __global__ void __launch_bounds__(1024) k_prod_nodes_g(const real* __restrict__ 
     const int b = G.b0 + warp * G.bstride;
     const real* gb = Gs + (long)b * spad * ngp + lane;
     const real* P = pl + ((long)v * ltop + warp) * ng;
-    int off[16];
-    real wv[16];
-#pragma unroll
-    for (int s = 0; s < 16; ++s) {
-      off[s] = pix[v * 16 + s] * ngp;
-      wv[s] = wst[v * 16 + s];
-    }
     double acc = 0.0;
-    for (int i0 = 0; i0 < ngp; i0 += 32) {
-      real ts = 0;
+    if constexpr (NCH > 0) {
+      real ts[NCH];
 #pragma unroll
-      for (int s = 0; s < 16; ++s) ts += wv[s] * gb[off[s] + i0];
-      const int i = i0 + lane;
-      const real p = i < ng ? P[i] : (real)0;
-      acc = fma((double)p, (double)ts, acc);
+      for (int k = 0; k < NCH; ++k) ts[k] = 0;
+#pragma unroll
+      for (int s = 0; s < 16; ++s) {
+        const real* src = gb + pix[v * 16 + s] * ngp;
+        const real w = wst[v * 16 + s];
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) ts[k] += w * src[32 * k];
+      }
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) {
+        const int i = 32 * k + lane;
+        const real p = i < ng ? P[i] : (real)0;
+        acc = fma((double)p, (double)ts[k], acc);
+      }
+    } else {
+      for (int i0 = 0; i0 < ngp; i0 += 32) {
+        real ts = 0;
+#pragma unroll
+        for (int s = 0; s < 16; ++s) ts += wst[v * 16 + s] * gb[pix[v * 16 + s] * ngp + i0];
+        const int i = i0 + lane;
+        const real p = i < ng ? P[i] : (real)0;
+        acc = fma((double)p, (double)ts, acc);
+      }
     }
     const double s = warp_sum(acc);
     if (lane == 0) us[warp] = s;
@@ -251,9 +264,20 @@ cudaError_t launch_products(const real* q, int ng, int nr, int NR, int nn, const
                                             pg.blocks, pg.G);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_prod_nodes_g<real><<<g1, 32 * max_nom, 0, st>>>(pg.G, ng, pg.ngp, pg.spad, nn, pg.pix,
-                                                      pg.wst, pl, ltop, T, jac, groups,
-                                                      jl_group, vbuf);
+#define NODES_G(nch)                                                                         \
+  k_prod_nodes_g<real, nch><<<g1, 32 * max_nom, 0, st>>>(pg.G, ng, pg.ngp, pg.spad, nn, pg.pix, \
+                                                         pg.wst, pl, ltop, T, jac, groups,     \
+                                                         jl_group, vbuf)
+    switch (pg.ngp / 32) {
+      case 1: NODES_G(1); break;
+      case 2: NODES_G(2); break;
+      case 3: NODES_G(3); break;
+      case 4: NODES_G(4); break;
+      case 5: NODES_G(5); break;
+      case 6: NODES_G(6); break;
+      default: NODES_G(0); break;
+    }
+#undef NODES_G
   } else {
     k_prod_nodes<real><<<g1, 32 * max_nom, 0, st>>>(q, ng, nr, NR, nn, idx, w, pl, ltop, T, jac,
                                                     groups, jl_group, vbuf);

@@ -78,8 +78,8 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
       : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long limit = kWaitLimit) {
+  for (long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -1461,11 +1461,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
     } else {
       (void)which;
       (void)b;
-      const int nch = nrow * (TC_M / 4);
-      for (int e = tid; e < nch; e += TC_THREADS) {
-        const int i = e / (TC_M / 4);
-        const int c4 = (e - i * (TC_M / 4)) * 4;
-        if (col0 + c4 < a.ncol) cp_async16(dst + i * TC_M + c4, src + (long)i * a.ncol + col0 + c4);
+      // 16-byte chunk (i, c4) of the tile goes to thread i * (TC_M / 4) + c4 / 4 modulo
+      // TC_THREADS: a thread keeps its column c4 and walks rows i, i + TC_THREADS / 32, ...
+      static_assert(TC_M / 4 == 32 && TC_THREADS % 32 == 0, "one warp per tile row");
+      constexpr int kRowStep = TC_THREADS / 32;
+      const int c4 = lane * 4;
+      if (col0 + c4 < a.ncol) {
+        const long gstep = (long)kRowStep * a.ncol;
+        const float* s = src + (long)warp * a.ncol + col0 + c4;
+        float* d = dst + warp * TC_M + c4;
+        for (int i = warp; i < nrow; i += kRowStep, s += gstep, d += kRowStep * TC_M)
+          cp_async16(d, s);
       }
     }
   };
@@ -1478,7 +1484,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
     if constexpr (TMA) {
       for (int w = 0; w < 3; ++w)
         if ((mask >> w & 1) && tpend[w]) {
-          if (mbar_wait(smem_u32(tbar + w), tph[w])) {
+          if (mbar_wait(smem_u32(tbar + w), tph[w], a.wait_limit)) {
             tph[w] ^= 1u;
             tpend[w] = false;
           } else {
@@ -1526,7 +1532,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_angular_tc5(const __grid_cons
     }
   };
   auto wait_mma = [&](bool also = true) {
-    ok = __syncthreads_and((mbar_wait(mb, phase) && also) ? 1 : 0) != 0;
+    ok = __syncthreads_and((mbar_wait(mb, phase, a.wait_limit) && also) ? 1 : 0) != 0;
     phase ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;");
   };
