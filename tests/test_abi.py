@@ -86,6 +86,11 @@ def test_error_paths_host_only():
     assert lib.mw3_set_tuning(h, b"nonsense", 1) == -1
     assert lib.mw3_set_tuning(h, b"use_tc", 1) == -1              # needs MW3_MIXED
     assert lib.mw3_set_tuning(h, b"kb", 48) == 0 and lib.mw3_get_tuning(h, b"kb") == 48
+    # bounded-wait poll limit of the tile-major angular step: 0..2^22, default 2^22
+    assert lib.mw3_get_tuning(h, b"tc_wait_limit") == 1 << 22
+    assert lib.mw3_set_tuning(h, b"tc_wait_limit", -1) == -1
+    assert lib.mw3_set_tuning(h, b"tc_wait_limit", (1 << 22) + 1) == -1
+    assert lib.mw3_set_tuning(h, b"tc_wait_limit", 0) == 0 and lib.mw3_get_tuning(h, b"tc_wait_limit") == 0
     lib.mw3_destroy(h)
     assert lib.mw3_status_string(-4) == b"propagation diverged"
 
