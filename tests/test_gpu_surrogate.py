@@ -90,3 +90,10 @@ def test_surrogate_pipeline_against_propagation():
     # the J values the spread let through and the fallback result are scored as they are
     assert rep["max_abs_dP"]["with_fallback"] <= rep["max_abs_dP"]["surrogate"] + 1e-12
     assert rep["seconds"]["surrogate_path"] >= rep["seconds"]["fit"]
+    # What the trained networks gain over interpolating without them: on this workload their
+    # cumulative sum_J (2J+1) P_J error is below that of linear interpolation in J between the
+    # training J (0.34 against 0.46 on GB300; seeded data and training, fixed-order sums).
+    # J-shifting, the paper's own interpolation, does better here (0.24); on the full J range
+    # of the two-state grid (J = 0..48) the networks beat both.
+    cre = rep["cumulative_rel_err"]
+    assert cre["surrogate"] < cre["linear"], cre
