@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(1024) k_prod_nodes(const real* __restrict__ q,
 // block's (i, r, R) planes at the 32 columns (sorted, so neighbouring lanes mostly read
 // neighbouring addresses), and the CTA writes them transposed through shared memory:
 // G[b][s][i] for 32 rows i at a time, rows nrow.. of the block as zeros. The loads of the next
-// 32 rows are issued before the transpose of the current ones.
+// 32 rows are issued before the transpose of the current ones. 256 threads: 8 warps x 4 rows
+// (or 4 columns) per 32 x 32 chunk.
 template <typename real>
 __global__ void __launch_bounds__(256) k_prod_gather(const real* __restrict__ q, int ng, long plane,
                                                      const int* __restrict__ pts, int spad, int ngp,
